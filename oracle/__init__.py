@@ -1,0 +1,145 @@
+"""Oracle for segmented Quickhull: TEST INFRASTRUCTURE ONLY.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its Python binding) never imports, links or runs anything here, and nothing
+here uses the product path.
+
+``qh_oracle.c`` is a plain sequential Quickhull in FP64 with exact predicates
+(see its header); this module compiles it with gcc and wraps it with ctypes.
+``segmented.py`` restates the paper's ``flagPermute`` (Algorithm 2) and
+``compact`` (Algorithm 3) in numpy.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "qh_oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_INVALID, ERR_NONFINITE, ERR_DEGENERATE, ERR_NOMEM = 0, 1, 2, 3, 4
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"oracle {what} failed with code {code}")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle (gcc, -ffp-contract=off so the FP64 error bounds hold)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            fp = ctypes.c_void_p
+            lib.oracle_hull2d.argtypes = [fp, fp, ctypes.c_int64, fp, i64p, i64p]
+            lib.oracle_hull2d.restype = ctypes.c_int
+            lib.oracle_hull3d.argtypes = [fp, fp, fp, ctypes.c_int64, fp, i64p, fp, fp, i64p, i64p]
+            lib.oracle_hull3d.restype = ctypes.c_int
+            for name, k in (("oracle_orient2d", 3), ("oracle_cmp_dist2", 4),
+                            ("oracle_orient3d", 4), ("oracle_cmp_dist3", 5)):
+                f = getattr(lib, name)
+                f.argtypes = [fp] * k
+                f.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def hull2d(x, y, return_iterations: bool = False):
+    """Hull vertex indices (int32), counter-clockwise from the lexicographically
+    smallest (x, y) vertex.  Raises OracleError on invalid/non-finite input."""
+    lib = _load()
+    x, y = _f32(x), _f32(y)
+    n = x.shape[0]
+    out = np.empty(max(n, 1), dtype=np.int32)
+    h = ctypes.c_int64(0)
+    it = ctypes.c_int64(0)
+    rc = lib.oracle_hull2d(_ptr(x), _ptr(y), n, _ptr(out), ctypes.byref(h), ctypes.byref(it))
+    if rc != OK:
+        raise OracleError(rc, "hull2d")
+    res = out[: h.value].copy()
+    return (res, it.value) if return_iterations else res
+
+
+def hull3d(x, y, z, return_iterations: bool = False):
+    """Canonical 3D hull: (vertices, faces) where vertices is a sorted int32
+    array and faces a list of int32 arrays (CCW from outside, each starting at
+    its smallest index, sorted lexicographically).  Raises OracleError with
+    code ERR_DEGENERATE when the points do not span 3D."""
+    lib = _load()
+    x, y, z = _f32(x), _f32(y), _f32(z)
+    n = x.shape[0]
+    verts = np.empty(max(n, 1), dtype=np.int32)
+    foff = np.empty(2 * n + 16, dtype=np.int32)
+    fidx = np.empty(6 * n + 16, dtype=np.int32)
+    nv, nf, it = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = lib.oracle_hull3d(_ptr(x), _ptr(y), _ptr(z), n, _ptr(verts), ctypes.byref(nv),
+                           _ptr(foff), _ptr(fidx), ctypes.byref(nf), ctypes.byref(it))
+    if rc != OK:
+        raise OracleError(rc, "hull3d")
+    faces = [fidx[foff[i]:foff[i + 1]].copy() for i in range(nf.value)]
+    res = (verts[: nv.value].copy(), faces)
+    return (res, it.value) if return_iterations else res
+
+
+def hull3d_csr(x, y, z):
+    """Same as hull3d, as (vertices, face_offsets, face_indices) arrays."""
+    verts, faces = hull3d(x, y, z)
+    off = np.zeros(len(faces) + 1, dtype=np.int32)
+    off[1:] = np.cumsum([len(f) for f in faces]) if faces else []
+    idx = np.concatenate(faces).astype(np.int32) if faces else np.zeros(0, np.int32)
+    return verts, off, idx
+
+
+def _pt(p) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(p, dtype=np.float64))
+
+
+def orient2d(a, b, c) -> int:
+    """Exact sign of orient2d: +1 when a, b, c turn counter-clockwise."""
+    return _load().oracle_orient2d(*(_ptr(_pt(v)) for v in (a, b, c)))
+
+
+def cmp_dist2(a, b, p1, p2) -> int:
+    """Exact sign of orient2d(a,b,p1) - orient2d(a,b,p2)."""
+    return _load().oracle_cmp_dist2(*(_ptr(_pt(v)) for v in (a, b, p1, p2)))
+
+
+def orient3d(a, b, c, p) -> int:
+    """Exact sign of det[b-a; c-a; p-a]."""
+    return _load().oracle_orient3d(*(_ptr(_pt(v)) for v in (a, b, c, p)))
+
+
+def cmp_dist3(a, b, c, p1, p2) -> int:
+    """Exact sign of det[b-a; c-a; p1-p2]."""
+    return _load().oracle_cmp_dist3(*(_ptr(_pt(v)) for v in (a, b, c, p1, p2)))
