@@ -1,0 +1,357 @@
+"""Throughput of the segmented-Quickhull hot path on GB300.
+
+Workload (one step): the convex hulls of three seeded 16M-point float32
+clouds in the plane (uniform in the unit square, uniform in the unit disk,
+on the unit circle with N(0, 1e-4) radial jitter), FP32-filtered exact
+predicates, one persistent kernel per hull.  value = points hulled per
+second over the whole job (Mpoints/s), inputs resident in HBM.
+
+Also reported: the plain GPU path (FP64 predicates, host-driven loop with a
+live-count readback per iteration), the end-to-end number through the C ABI
+with host buffers, the HBM roofline of the persistent kernel, and the CPU
+oracle on the host cores.  `--impl reference` times the oracle alone.
+
+Multi-GPU (torchrun, one rank per GPU): every rank hulls its own clouds
+(independent problems, no collective on the data path): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "hull Mpoints/s (2D, 3D, batched) vs plain GPU path; % HBM roofline; bwd/fwd"
+UNIT = "Mpoints/s"
+N_PER_CLOUD = 16 * 1024 * 1024
+WORKLOAD = ("2D at scale: 3 x 16M float32 points (uniform unit square, uniform unit disk, "
+            "unit circle with N(0,1e-4) radial jitter), FP32-filtered exact predicates")
+# dram bytes (read + write) per launch of the persistent kernel from one ncu
+# capture, keyed by the sha256 of the kernel sources they were taken on
+NCU_TRAFFIC = {}
+
+
+def kernel_sources_sha() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1201_2936_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        with open(os.path.join(d, fn), "rb") as f:
+            h.update(fn.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def clouds(rank: int, n: int):
+    from paper_1201_2936_gb300 import workloads as w
+    s = w.SEED_BASE + 1 + 1000 * rank
+    return [("square", w.uniform_square(n, s)),
+            ("disk", w.uniform_disk(n, s + 10)),
+            ("circle1e-4", w.circle_jitter(n, s + 20, 1e-4))]
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def oracle_step(data, limit=None):
+    import oracle
+    t0 = time.perf_counter()
+    pts = 0
+    for _, (x, y) in data:
+        if limit:
+            x, y = x[:limit], y[:limit]
+        oracle.hull2d(x, y)
+        pts += len(x)
+    return pts, time.perf_counter() - t0
+
+
+def run_reference(args, ws, rank):
+    # the oracle on the host cores, rank 0 only
+    if rank != 0:
+        return 0
+    sample = int(os.environ.get("QH_REF_SAMPLE", 2 * 1024 * 1024))
+    data = clouds(0, N_PER_CLOUD)
+    for _ in range(args.warmup):
+        oracle_step(data, sample)
+    tot_pts, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        p, t = oracle_step(data, sample)
+        tot_pts += p
+        tot_t += t
+    value = tot_pts / tot_t / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_points_per_cloud": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {sample} points of each of the 3 clouds per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=N_PER_CLOUD,
+                    help="points per cloud (profiling of smaller cases)")
+    ap.add_argument("--only", default="", help="comma-separated cloud names to keep")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    ws, rank = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1201_2936_gb300 as qh
+    from paper_1201_2936_gb300 import build as qbuild
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    qbuild.build()
+
+    ncl = args.n
+    data = clouds(rank, ncl)
+    if args.only:
+        keep = set(args.only.split(","))
+        data = [d for d in data if d[0] in keep]
+    stream = torch.cuda.current_stream()
+    dev_pts = [torch.from_numpy(np.stack([x, y])).to(dev) for _, (x, y) in data]
+    outs = [torch.empty(ncl, dtype=torch.int32, device=dev) for _ in data]
+    results = [torch.zeros(qh.RESULT_BYTES, dtype=torch.uint8, device=dev) for _ in data]
+    wss = [qh.Workspace(dev) for _ in data]
+    opts = qh.make_opts("f32", "persistent")
+
+    def step():
+        for i, P in enumerate(dev_pts):
+            qh.hull2d_async(P, None, outs[i], results[i], wss[i], opts)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    res = [qh.result_from_tensor(r) for r in results]
+    for r in res:
+        if r.status != 0:
+            raise SystemExit(f"hull failed: {qh.status_str(r.status)}")
+
+    # ---- timed region: K steps, per-launch events for the roofline
+    nl = len(dev_pts)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps * nl + 1)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    k = 1
+    for _ in range(args.steps):
+        for i, P in enumerate(dev_pts):
+            qh.hull2d_async(P, None, outs[i], results[i], wss[i], opts)
+            ev[k].record(stream)
+            k += 1
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = ev[0].elapsed_time(ev[-1])
+    launch_ms = [[] for _ in range(nl)]
+    for s in range(args.steps):
+        for i in range(nl):
+            j = 1 + s * nl + i
+            launch_ms[i].append(ev[j - 1].elapsed_time(ev[j]))
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    res = [qh.result_from_tensor(r) for r in results]
+    pts_per_step = nl * ncl
+    value = ws * pts_per_step * args.steps / (total_ms / 1e3) / 1e6
+
+    # ---- roofline of the persistent kernel (algorithmic bytes per launch)
+    peak, peak_kind = measured_peak()
+    per_cloud = []
+    ach = []
+    for i, (name, _) in enumerate(data):
+        r = res[i]
+        algo = 16 * ncl + 24 * r.survivor_total
+        ms = statistics.mean(launch_ms[i])
+        ach.append((algo, ms))
+        per_cloud.append({"cloud": name, "hull": r.count, "iterations": r.iterations,
+                          "ms": round(ms, 4), "algo_bytes": algo,
+                          "GBps": round(algo / (ms / 1e3) / 1e9, 1),
+                          "fallback_frac": r.filter_fallbacks / max(1, r.live_total),
+                          "exact_argmax_segments": r.exact_argmax,
+                          "phase_us": {"pass": r.extra[0] / 1e3, "update": r.extra[1] / 1e3,
+                                       "exact": r.extra[2] / 1e3, "other": r.extra[3] / 1e3}})
+    algo_tot = sum(a for a, _ in ach)
+    ms_tot = sum(m for _, m in ach)
+    achieved = algo_tot / (ms_tot / 1e3) / 1e9
+    sha = kernel_sources_sha()
+    traffic = NCU_TRAFFIC.get(sha)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                "traffic": traffic, "kernel": "qh2d_persistent<PredF32>",
+                "algo_bytes_per_launch": round(algo_tot / nl)}
+
+    line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD if ncl == N_PER_CLOUD and not args.only else
+                       f"reduced: {nl} cloud(s) x {ncl} points", "points_per_step_per_gpu": pts_per_step,
+                       "l2": "inputs larger than L2 (3 x 128 MB of coordinates per step)",
+                       "pred": "f32-filter+exact", "loop": "persistent"},
+            "per_cloud": per_cloud, "roofline": roofline, "clocks": clocks,
+            "gpu_launches": args.steps * nl}
+
+    # ---- plain GPU path: FP64 predicates, host loop with per-iteration readback
+    if not args.no_plain:
+        popts = qh.make_opts("f64", "host")
+        ksteps = max(1, args.steps // 10)
+        for i, P in enumerate(dev_pts):
+            qh.hull2d_async(P, None, outs[i], results[i], wss[i], popts)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ksteps):
+            for i, P in enumerate(dev_pts):
+                qh.hull2d_async(P, None, outs[i], results[i], wss[i], popts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / ksteps
+        pres = [qh.result_from_tensor(r) for r in results]
+        same = all(pres[i].count == res[i].count for i in range(nl))
+        line["plain_gpu"] = {"value": round(pts_per_step / (pms / 1e3) / 1e6, 2), "unit": UNIT,
+                             "ms_per_step": round(pms, 3), "pred": "f64-filter+exact",
+                             "loop": "host (live count read back every iteration)",
+                             "same_hull_sizes": same,
+                             "speedup_of_fast_path": round(pms / (total_ms / args.steps), 2)}
+
+    # ---- end to end through the C ABI with host buffers
+    if args.no_e2e:
+        host_pts = []
+    else:
+        host_pts = [torch.from_numpy(np.stack([x, y])).pin_memory() for _, (x, y) in data]
+    host_out = [torch.empty(ncl, dtype=torch.int32).pin_memory() for _ in host_pts]
+    esteps = max(3, args.steps // 10) if host_pts else 0
+    h2d = sum(t.numel() * 4 for t in host_pts)
+    d2h = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(esteps):
+        d2h = 0
+        for i, hp in enumerate(host_pts):
+            P = hp.to(dev, non_blocking=True)
+            idx = qh.hull2d(P, workspace=wss[i], out=outs[i])   # synchronous C-ABI call
+            host_out[i][: idx.numel()].copy_(idx, non_blocking=True)
+            d2h += idx.numel() * 4 + qh.RESULT_BYTES
+        torch.cuda.synchronize()
+    if esteps:
+        et = (time.perf_counter() - t0) / esteps
+        line["e2e"] = {"value": round(pts_per_step / et / 1e6, 2), "unit": UNIT,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # ---- CPU oracle on the host cores (rank 0, bounded sample)
+    if rank == 0 and not args.no_cpu_baseline:
+        sample = int(os.environ.get("QH_CPU_SAMPLE", 4 * 1024 * 1024))
+        p, t = oracle_step(data, sample)
+        line["cpu_baseline"] = {"value": round(p / t / 1e6, 3), "unit": UNIT, "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"first {sample} points of each of the 3 clouds"}
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

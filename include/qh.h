@@ -1,0 +1,151 @@
+/*
+ * qh.h: C ABI of the GB300 segmented-Quickhull library (libqh.so).
+ *
+ * The library computes convex hulls of float32 point sets on one CUDA
+ * device with the segmented Quickhull of Tzeng & Owens, "Finding Convex
+ * Hulls Using Quickhull on the GPU": the recursion of Quickhull (Section
+ * 3.2, Algorithm 1) is replaced by a permutation of one flat point array
+ * into segments (Section 3.1), and each iteration of the hot loop
+ * (Algorithm 4, "Recursive Step") computes every live point's distance to
+ * its segment's edge, reduces each segment to its farthest point, discards
+ * the points inside the triangle it forms and permutes the survivors into
+ * child segments (flagPermute, Section 4.1, and compact, Section 4.2, fused
+ * into one pass).
+ *
+ * Conventions shared by every call
+ *  - Points are structure-of-arrays float32: coordinate c of point i is at
+ *    d_c[i * stride].  stride = 1 for separate arrays, stride = 2 (or 3)
+ *    for interleaved xy (xyz) with d_y = d_x + 1 (d_z = d_x + 2).
+ *  - n is limited to 0 <= n <= QH_MAX_POINTS (int32 indices).
+ *  - Device pointers are named d_*, host pointers h_*.  The caller owns
+ *    every buffer, including the workspace d_ws of qh_workspace_bytes_*()
+ *    bytes (device memory, 256-byte aligned).  The library allocates no
+ *    device memory and keeps no state between calls except a per-device
+ *    cache of the occupancy query.
+ *  - Work is issued on `stream` (0 = legacy default stream).  The *_async
+ *    calls do not synchronise; results land in d_result when the stream
+ *    reaches that point.  The other calls synchronise the stream before
+ *    returning.
+ *  - Nothing throws across the ABI.  A non-QH_OK status leaves every output
+ *    unspecified (no partial output is valid).
+ *  - Predicates are exact: every orientation sign and every distance
+ *    comparison that decides the result is exact for the float32 inputs
+ *    read as real numbers (FP32 or FP64 filter with a forward error bound,
+ *    exact expansion arithmetic when the filter cannot decide).
+ *  - Calls that overlap on the same workspace race; distinct workspaces
+ *    may run concurrently on different streams.
+ */
+#ifndef QH_H
+#define QH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QH_MAX_POINTS ((int64_t)2147483000)
+
+typedef enum qh_status {
+    QH_OK = 0,
+    QH_ERR_INVALID_ARG = 1,   /* null pointer, negative n, bad stride, n too large */
+    QH_ERR_NONFINITE = 2,     /* an input coordinate is NaN or +-Inf */
+    QH_ERR_DEGENERATE = 3,    /* 3D input that does not span 3D */
+    QH_ERR_NOMEM = 4,         /* workspace smaller than qh_workspace_bytes_*() */
+    QH_ERR_CAPACITY = 5,      /* an internal table overflowed (should not happen) */
+    QH_ERR_TIMEOUT = 6,       /* a bounded device wait gave up (grid barrier) */
+    QH_ERR_NO_CONVERGENCE = 7,/* iteration cap reached */
+    QH_ERR_CUDA = 8,          /* a CUDA runtime call failed */
+    QH_ERR_NOT_SUPPORTED = 9  /* option combination not available */
+} qh_status;
+
+/* Predicate arithmetic of the fast filter stage. */
+#define QH_PRED_F32 0 /* FP32 values, FP32 static error bound (default) */
+#define QH_PRED_F64 1 /* FP64 values, FP64 error bound: the plain path */
+
+/* How the iterations are driven. */
+#define QH_LOOP_PERSISTENT 0 /* one cooperative persistent kernel, grid barriers (default) */
+#define QH_LOOP_HOST 1       /* one launch per phase, live count read back each iteration */
+
+typedef struct qh_opts {
+    int32_t pred_mode;    /* QH_PRED_* */
+    int32_t loop_mode;    /* QH_LOOP_* */
+    int32_t blocks_per_sm;/* persistent grid: CTAs per SM (0 = as many as fit) */
+    int32_t reserved0;
+    int64_t max_iters;    /* iteration cap (0 = n + 8) */
+    int64_t wait_ns;      /* bound of every device-side wait (0 = 2 s) */
+} qh_opts;
+
+/* Result record written by the device (async calls) and copied back by the
+ * synchronous calls.  All counts are totals over the call. */
+typedef struct qh_result {
+    int64_t count;            /* 2D: hull vertices written to d_out_idx */
+    int32_t status;           /* qh_status */
+    int32_t reserved0;
+    int64_t iterations;       /* Quickhull iterations (passes after the first split) */
+    int64_t live_total;       /* sum over passes of live points read (incl. first split) */
+    int64_t survivor_total;   /* sum over passes of points written */
+    int64_t segments_total;   /* sum over iterations of segments */
+    int64_t filter_fallbacks; /* predicate evaluations the fast filter could not decide */
+    int64_t exact_argmax;     /* segments whose farthest point needed exact resolution */
+    int64_t extra[4];         /* 2D persistent loop: nanoseconds spent in the pass,
+                                 update, exact-argmax and other phases (device
+                                 clock between grid barriers); 3D: [0] vertices,
+                                 [1] faces, [2] face index total */
+} qh_result;
+
+/* Human-readable name of a status code (static storage). */
+const char *qh_status_str(qh_status s);
+
+/* Library version string, e.g. "qh 0.1 sm_103a". */
+const char *qh_version(void);
+
+/* Default options (persistent loop, FP32 filter). */
+void qh_default_opts(qh_opts *opts);
+
+/* ---------------------------------------------------------------------- */
+/* 2D                                                                      */
+/* ---------------------------------------------------------------------- */
+
+/* Bytes of device workspace qh_hull2d* needs for n points. */
+size_t qh_workspace_bytes_2d(int64_t n, const qh_opts *opts);
+
+/*
+ * qh_hull2d_async: convex hull of n float32 points in the plane (Algorithm
+ * 4, 2DCUDAQuickhull: first split by the extrema along x, then repeated
+ * farthest-point / triangle-discard / flagPermute iterations until no
+ * segment has points; Section 4.3 states the problem as p_in -> ch_out).
+ *
+ *  d_x, d_y   device, n points, coordinate i at d_x[i*stride] (read only)
+ *  d_out_idx  device int32[max(n,1)]: hull vertex indices in counter-
+ *             clockwise order starting at the lexicographically smallest
+ *             (x, y) vertex; a location present several times is reported
+ *             as its lowest index; vertices in the middle of a straight
+ *             boundary run are not vertices.  n = 1 or all points equal ->
+ *             one index; all points collinear -> the two extreme points.
+ *  d_result   device qh_result (count, status, statistics)
+ *  d_ws       device workspace of qh_workspace_bytes_2d(n, opts) bytes
+ *  opts       may be NULL (defaults)
+ * Host-side argument errors are returned directly; data-dependent errors
+ * (QH_ERR_NONFINITE, QH_ERR_TIMEOUT, ...) appear in d_result->status.
+ * QH_LOOP_HOST synchronises the stream once per iteration.
+ */
+qh_status qh_hull2d_async(const float *d_x, const float *d_y, int64_t n, int64_t stride,
+                          int32_t *d_out_idx, qh_result *d_result, void *d_ws, size_t ws_bytes,
+                          const qh_opts *opts, cudaStream_t stream);
+
+/* Synchronous form of qh_hull2d_async: returns the device status, the hull
+ * size in *h_count and, when h_result is not NULL, the full result record.
+ * d_result is taken from the workspace. */
+qh_status qh_hull2d(const float *d_x, const float *d_y, int64_t n, int64_t stride,
+                    int32_t *d_out_idx, int64_t *h_count, qh_result *h_result, void *d_ws,
+                    size_t ws_bytes, const qh_opts *opts, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QH_H */

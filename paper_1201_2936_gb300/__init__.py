@@ -1,0 +1,142 @@
+"""GB300-native segmented Quickhull (Tzeng & Owens, "Finding Convex Hulls
+Using Quickhull on the GPU"): Python binding of libqh.
+
+Every step of the hull runs in the CUDA library (include/qh.h); this module
+only marshals PyTorch tensors (device memory, streams) into the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Tuple, Union
+
+import torch
+
+from . import _native
+from ._native import QhOpts, QhResult, RESULT_BYTES
+
+__all__ = ["QHError", "hull2d", "hull2d_async", "workspace_bytes_2d", "Workspace",
+           "make_opts", "status_str", "version", "RESULT_BYTES", "result_from_tensor"]
+
+PRED = {"f32": 0, "f64": 1}
+LOOP = {"persistent": 0, "host": 1}
+
+
+class QHError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        super().__init__(f"{what}: {status_str(status)}" if what else status_str(status))
+        self.status = status
+
+
+def status_str(s: int) -> str:
+    return _native.lib().qh_status_str(int(s)).decode()
+
+
+def version() -> str:
+    return _native.lib().qh_version().decode()
+
+
+def make_opts(pred: str = "f32", loop: str = "persistent", blocks_per_sm: int = 0,
+              max_iters: int = 0, wait_ns: int = 0) -> QhOpts:
+    o = QhOpts()
+    _native.lib().qh_default_opts(ctypes.byref(o))
+    o.pred_mode = PRED[pred]
+    o.loop_mode = LOOP[loop]
+    o.blocks_per_sm = blocks_per_sm
+    o.max_iters = max_iters
+    o.wait_ns = wait_ns
+    return o
+
+
+def workspace_bytes_2d(n: int, opts: Optional[QhOpts] = None) -> int:
+    return int(_native.lib().qh_workspace_bytes_2d(int(n), ctypes.byref(opts) if opts else None))
+
+
+class Workspace:
+    """Device workspace owned by PyTorch's allocator, grown on demand."""
+
+    def __init__(self, device=None):
+        self.device = torch.device(device if device is not None else "cuda")
+        self.buf: Optional[torch.Tensor] = None
+
+    def get(self, nbytes: int) -> torch.Tensor:
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        return self.buf
+
+
+def _stream_handle(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _points_2d(x: torch.Tensor, y: Optional[torch.Tensor]) -> Tuple[int, int, int, int, torch.device]:
+    """Return (x_ptr, y_ptr, n, stride, device) for [n,2], [2,n] or separate x, y."""
+    if y is None:
+        t = x
+        if t.dtype != torch.float32 or not t.is_cuda or t.dim() != 2:
+            raise ValueError("points must be a CUDA float32 tensor of shape [n, 2] or [2, n]")
+        if t.shape[1] == 2 and t.stride(1) == 1 and (t.shape[0] <= 1 or t.stride(0) == 2):
+            return t.data_ptr(), t.data_ptr() + 4, t.shape[0], 2, t.device
+        if t.shape[0] == 2 and t.stride(1) == 1:
+            return t[0].data_ptr(), t[1].data_ptr(), t.shape[1], 1, t.device
+        raise ValueError("points must be contiguous [n, 2] or row-contiguous [2, n]")
+    for t in (x, y):
+        if t.dtype != torch.float32 or not t.is_cuda or t.dim() != 1 or \
+                (t.numel() > 1 and t.stride(0) != 1):
+            raise ValueError("x and y must be contiguous 1-D CUDA float32 tensors")
+    if x.shape != y.shape or x.device != y.device:
+        raise ValueError("x and y must have the same length and device")
+    return x.data_ptr(), y.data_ptr(), x.shape[0], 1, x.device
+
+
+def hull2d_async(x: torch.Tensor, y: Optional[torch.Tensor], out: torch.Tensor,
+                 result: torch.Tensor, workspace: Workspace, opts: Optional[QhOpts] = None,
+                 stream=None) -> None:
+    """Launch the hull without synchronising.  `out` is an int32 CUDA tensor
+    of at least max(n, 1) entries, `result` a uint8 CUDA tensor of
+    RESULT_BYTES bytes that receives the qh_result record."""
+    xp, yp, n, stride, dev = _points_2d(x, y)
+    o = opts if opts is not None else make_opts()
+    nb = workspace_bytes_2d(n, o)
+    ws = workspace.get(nb)
+    st = _native.lib().qh_hull2d_async(xp, yp, n, stride, out.data_ptr(), result.data_ptr(),
+                                       ws.data_ptr(), ws.numel(), ctypes.byref(o),
+                                       _stream_handle(stream))
+    if st != 0:
+        raise QHError(st, "qh_hull2d_async")
+
+
+def result_from_tensor(result: torch.Tensor) -> QhResult:
+    raw = bytes(result.cpu().numpy().tobytes())
+    return QhResult.from_buffer_copy(raw[:RESULT_BYTES])
+
+
+_default_ws = {}
+
+
+def hull2d(x: torch.Tensor, y: Optional[torch.Tensor] = None, *, pred: str = "f32",
+           loop: str = "persistent", workspace: Optional[Workspace] = None,
+           out: Optional[torch.Tensor] = None, stream=None,
+           return_result: bool = False) -> Union[torch.Tensor, Tuple[torch.Tensor, dict]]:
+    """Convex hull of 2D float32 points on the GPU.
+
+    Returns an int32 CUDA tensor with the hull vertex indices in counter-
+    clockwise order from the lexicographically smallest (x, y) vertex.
+    Points are a [n, 2] tensor, a [2, n] tensor, or separate x and y.
+    """
+    xp, yp, n, stride, dev = _points_2d(x, y)
+    o = make_opts(pred, loop)
+    if workspace is None:
+        workspace = _default_ws.setdefault(str(dev), Workspace(dev))
+    ws = workspace.get(workspace_bytes_2d(n, o))
+    if out is None:
+        out = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    cnt = ctypes.c_int64(0)
+    res = QhResult()
+    st = _native.lib().qh_hull2d(xp, yp, n, stride, out.data_ptr(), ctypes.byref(cnt),
+                                 ctypes.byref(res), ws.data_ptr(), ws.numel(), ctypes.byref(o),
+                                 _stream_handle(stream))
+    if st != 0:
+        raise QHError(st, "qh_hull2d")
+    idx = out[: cnt.value]
+    return (idx, res.as_dict()) if return_result else idx

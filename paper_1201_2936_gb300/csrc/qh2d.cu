@@ -1,0 +1,1126 @@
+// 2D segmented Quickhull on one GPU (Tzeng & Owens, Algorithm 4).
+//
+// Layout in device memory (one workspace, see layout2d):
+//   * two point buffers (SoA x, y, idx) used ping-pong.  A segment owns a
+//     fixed physical range [pstart, pstart + len) of the buffers; its
+//     children are written into the same range of the other buffer, child 0
+//     growing from the left end and child 1 from the right end, so no global
+//     compaction of the array is ever needed and discarded points simply
+//     leave a hole.  The "virtual" order of live points (segment by segment,
+//     vstart = exclusive scan of live lengths) is what the pass tiles over.
+//   * two segment tables (Seg2) and two child accumulators (Acc2: count,
+//     top-2 farthest-point keys, max key error) by iteration parity.
+//   * the hull as slots (0 = lexicographic min a, 1 = lexicographic max b,
+//     then one slot per apex) with a successor link per slot; the links
+//     always form the current hull polygon, clockwise from a.
+//
+// One iteration (the hot loop of Algorithm 4):
+//   P  (pass2d)   every live point: classify against its segment's apex
+//                 (outside edge e0-q -> child 0, outside q-e1 -> child 1,
+//                 else discarded: inside the triangle, Algorithm 4 step 12),
+//                 block-local ranks by warp ballots, one atomic per
+//                 (tile, segment, child) for the global base, scatter of the
+//                 survivors, and the child's farthest-point reduction
+//                 (distance to the child edge is the classification value).
+//                 This fuses compact (Algorithm 3) and the 2-state
+//                 flagPermute (Algorithm 2) with the next iteration's
+//                 distance + segmented argmax (Algorithm 4 steps 9-14).
+//   U  (update2d) new segment table from the non-empty children, apex of
+//                 each (certified exact when the FP32 top-2 gap exceeds the
+//                 error bound), hull slots and links, tile -> segment map.
+//   X  (exact2d)  only for uncertified segments: exact farthest point.
+// The persistent kernel runs all iterations with grid barriers; the host
+// loop variant launches each phase and reads the live counts back every
+// iteration, as the paper's implementation does (Section 5 cost analysis).
+
+#include <climits>
+#include <cstdio>
+#include <cstring>
+
+#include "pred2.cuh"
+#include "qh_common.cuh"
+#include "qh_internal.h"
+
+namespace qh {
+
+constexpr int kBlock = 256;
+constexpr int kItems = 8;
+constexpr int kTile = kBlock * kItems;   // points per tile
+constexpr int kKeySeg = 64;              // segments per tile with shared-memory key slots
+constexpr int kGeoCache = 64;            // segments per tile with geometry in shared memory
+constexpr int kOutCap = 4096;            // hull slots ranked in one block's shared memory
+constexpr int kMaxGrid = 4096;
+constexpr int kMinBlocks = 4;            // resident CTAs per SM the register budget targets
+
+struct Seg2 {
+    float e0x, e0y, qx, qy, e1x, e1y;
+    int q_idx, e0_slot, q_slot, e1_slot;
+    int pstart, len, vstart;
+    float thr;          // exact-argmax candidate threshold (uncertified segments)
+    int pad[2];
+};
+static_assert(sizeof(Seg2) == 64, "Seg2 layout");
+
+struct Acc2 {
+    unsigned long long key1, key2;
+    unsigned int cnt, emax;
+    unsigned int pad[2];
+};
+static_assert(sizeof(Acc2) == 32, "Acc2 layout");
+
+struct Hdr2 {
+    GridBarrier bar;
+    int status;
+    int nonfinite;
+    unsigned long long lexmin, lexmax;
+    int a_idx, b_idx;
+    int S[2];
+    int L[2];
+    int hull_count;
+    int n_uncert;
+    int iter;
+    int pad0;
+    long long seg_total, surv_total;
+    unsigned long long fallbacks, exact_argmax;
+    unsigned long long phase_ns[4];  // pass, update, exact, other (persistent kernel)
+};
+
+struct Params2 {
+    const float *x, *y;
+    long long stride;
+    int n;
+    int *out_idx;
+    qh_result *res;
+    Hdr2 *hdr;
+    float *bx[2], *by[2];
+    int *bi[2];
+    Seg2 *seg[2];
+    Acc2 *acc[2];
+    int *tile_seg;
+    int *uncert;
+    int *hull_idx;
+    float *hull_x, *hull_y;
+    int *next;
+    long long max_iters;
+    long long wait_ns;
+    int cap_seg;
+};
+
+// ---------------------------------------------------------------- smem
+// Geometry of a segment as the pass needs it.
+struct Geo2 {
+    float e0x, e0y, qx, qy, e1x, e1y;
+    int q_idx, pstart, len, vstart;
+};
+
+struct SmemPass {
+    int vstart_l[kTile];
+    unsigned short sb0[kTile], sb1[kTile];
+    int gb0[kTile], gb1[kTile];
+    unsigned long long sk1[kKeySeg][2], sk2[kKeySeg][2];
+    unsigned int sem[kKeySeg][2];
+    unsigned long long ck1[2], ck2[2];
+    unsigned int cem[2];
+    unsigned int bal0[kBlock / 32][kItems], bal1[kBlock / 32][kItems];
+    int wt0[kBlock / 32], wt1[kBlock / 32];
+    int sfirst, carry_seg;
+    Geo2 geo[kGeoCache];
+};
+struct SmemU {
+    long long wsum[33];
+    int vs[kTile];
+    int small;
+};
+struct SmemX {
+    int bidx[kBlock];
+    float bx[kBlock], by[kBlock];
+};
+struct SmemOut {
+    int succ[kOutCap];
+    int dist[kOutCap];
+    long long wsum[33];
+};
+union SmemAll {
+    SmemPass pass;
+    SmemU u;
+    SmemX x;
+    SmemOut out;
+};
+
+__device__ __forceinline__ int vload_i(const volatile int *p) { return *p; }
+
+__device__ __forceinline__ void set_status(Hdr2 *H, int st) { atomicCAS(&H->status, 0, st); }
+
+// ---------------------------------------------------------------- phase 0
+__device__ void init2d(const Params2 &A)
+{
+    if (blockIdx.x != 0) return;
+    Hdr2 *H = A.hdr;
+    if (threadIdx.x == 0) {
+        H->lexmin = ~0ull;
+        H->lexmax = 0ull;
+        H->a_idx = INT_MAX;
+        H->b_idx = INT_MAX;
+        H->S[0] = 1;
+        H->L[0] = A.n;
+        H->hull_count = 2;
+    }
+    if (threadIdx.x < 2) {
+        Acc2 z = {};
+        A.acc[0][threadIdx.x] = z;
+    }
+}
+
+// ---------------------------------------------------------------- extrema
+// Lexicographic min and max of (x, y) over all points (Algorithm 4 step 3,
+// "min and max ... along the x axis", ties broken by y; the index tie-break
+// happens in the first split).  Also flags non-finite input.
+__device__ void extrema2d(const Params2 &A, SmemAll &sm)
+{
+    unsigned long long mn = ~0ull, mx = 0ull;
+    int bad = 0;
+    const long long s = A.stride;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float x = canon0(__ldg(A.x + i * s)), y = canon0(__ldg(A.y + i * s));
+        bad |= !(isfinite(x) && isfinite(y));
+        unsigned long long k = ((unsigned long long)ord_f32(x) << 32) | ord_f32(y);
+        mn = k < mn ? k : mn;
+        mx = k > mx ? k : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long a = __shfl_xor_sync(0xffffffffu, mn, o);
+        unsigned long long b = __shfl_xor_sync(0xffffffffu, mx, o);
+        mn = a < mn ? a : mn;
+        mx = b > mx ? b : mx;
+    }
+    bad = __syncthreads_or(bad);
+    unsigned long long *red = (unsigned long long *)sm.u.wsum;
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[w] = mn;
+        red[16 + w] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x >> 5); i++) {
+            mn = red[i] < mn ? red[i] : mn;
+            mx = red[16 + i] > mx ? red[16 + i] : mx;
+        }
+        if (A.n > 0) {
+            atomicMin(&A.hdr->lexmin, mn);
+            atomicMax(&A.hdr->lexmax, mx);
+        }
+        if (bad) atomicExch(&A.hdr->nonfinite, 1);
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- the pass
+__device__ __forceinline__ Geo2 geo_of(const Seg2 &g)
+{
+    Geo2 r;
+    r.e0x = g.e0x; r.e0y = g.e0y; r.qx = g.qx; r.qy = g.qy; r.e1x = g.e1x; r.e1y = g.e1y;
+    r.q_idx = g.q_idx; r.pstart = g.pstart; r.len = g.len; r.vstart = g.vstart;
+    return r;
+}
+
+template <bool FIRST>
+__device__ __forceinline__ Geo2 tile_geo(const SmemPass &sm, const Seg2 *seg, int sf, int ls)
+{
+    if (FIRST || ls < kGeoCache) return sm.geo[ls];
+    return geo_of(seg[sf + ls]);
+}
+
+// Merge a (top1, top2, emax) triple of one child into the global accumulator.
+__device__ __forceinline__ void acc_merge(Acc2 &ac, unsigned long long k1, unsigned long long k2,
+                                          unsigned em)
+{
+    if (!k1) return;
+    top2_insert(&ac.key1, &ac.key2, k1);
+    top2_insert(&ac.key1, &ac.key2, k2);
+    atomicMax(&ac.emax, em);
+}
+
+template <class P, bool FIRST>
+__device__ void pass2d(const Params2 &A, int par, SmemPass &sm)
+{
+    Hdr2 *H = A.hdr;
+    const int L = FIRST ? A.n : vload_i(&H->L[par]);
+    const int S = FIRST ? 1 : vload_i(&H->S[par]);
+    const Seg2 *seg = A.seg[par];
+    Acc2 *acc = A.acc[par];
+    float *ox = A.bx[par], *oy = A.by[par];
+    int *oi = A.bi[par];
+    const float *ix = A.bx[par ^ 1], *iy = A.by[par ^ 1];
+    const int *ii = A.bi[par ^ 1];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    unsigned fallbacks = 0;
+    const int ntiles = (L + kTile - 1) / kTile;
+    // a contiguous run of tiles per block keeps consecutive tiles in the same
+    // segment, so farthest-point keys are carried across tiles in shared memory
+    const int per = ntiles / gridDim.x, rem = ntiles % gridDim.x;
+    const int t_begin = blockIdx.x * per + min((int)blockIdx.x, rem);
+    const int t_end = t_begin + per + ((int)blockIdx.x < rem ? 1 : 0);
+    if (threadIdx.x == 0) sm.carry_seg = -1;
+
+    for (int tile = t_begin; tile < t_end; tile++) {
+        const int v0 = tile * kTile;
+        const int v1 = min(v0 + kTile, L);
+        __syncthreads();  // shared memory of the previous tile is free
+        if (threadIdx.x == 0) {
+            int sf = FIRST ? 0 : A.tile_seg[tile];
+            int cs = sm.carry_seg;
+            if (cs >= 0 && cs != sf) {
+                // the carried segment ended in the previous tile
+                acc_merge(acc[2 * cs], sm.ck1[0], sm.ck2[0], sm.cem[0]);
+                acc_merge(acc[2 * cs + 1], sm.ck1[1], sm.ck2[1], sm.cem[1]);
+                sm.carry_seg = -1;
+            }
+            sm.sfirst = sf;
+        }
+        __syncthreads();
+        const int sf = sm.sfirst;
+        for (int i = threadIdx.x; i < kKeySeg * 2; i += blockDim.x) {
+            int ls = i >> 1, c = i & 1;
+            bool carry = (ls == 0 && sm.carry_seg == sf);
+            sm.sk1[ls][c] = carry ? sm.ck1[c] : 0ull;
+            sm.sk2[ls][c] = carry ? sm.ck2[c] : 0ull;
+            sm.sem[ls][c] = carry ? sm.cem[c] : 0u;
+        }
+        // ---- segments overlapping the tile and their geometry
+        int m = 0;
+        for (int base = 0; base < kTile; base += kBlock) {
+            int s = sf + base + threadIdx.x;
+            int vs = INT_MAX;
+            if (FIRST) vs = (s == 0) ? 0 : INT_MAX;
+            else if (s < S) vs = seg[s].vstart;
+            bool in = vs < v1;
+            if (in) sm.vstart_l[base + threadIdx.x] = vs;
+            int c = __syncthreads_count(in);
+            m += c;
+            if (c < kBlock) break;
+        }
+        if (threadIdx.x < min(m, kGeoCache)) {
+            Geo2 g;
+            if (FIRST) {
+                unsigned long long kmn = *(volatile unsigned long long *)&H->lexmin;
+                unsigned long long kmx = *(volatile unsigned long long *)&H->lexmax;
+                g.e0x = g.e1x = unord_f32((uint32_t)(kmn >> 32));
+                g.e0y = g.e1y = unord_f32((uint32_t)kmn);
+                g.qx = unord_f32((uint32_t)(kmx >> 32));
+                g.qy = unord_f32((uint32_t)kmx);
+                g.q_idx = -1;
+                g.pstart = 0;
+                g.len = A.n;
+                g.vstart = 0;
+            } else {
+                g = geo_of(seg[sf + threadIdx.x]);
+            }
+            sm.geo[threadIdx.x] = g;
+        }
+        __syncthreads();
+
+        // ---- load and classify (state per item: x, y, idx, ls<<2 | class)
+        float px[kItems], py[kItems];
+        int pidx[kItems], pk[kItems];
+        const int wbase = v0 + warp * 32 * kItems;
+#pragma unroll
+        for (int k = 0; k < kItems; k++) {
+            int v = wbase + k * 32 + lane;
+            pk[k] = 3;  // class 3 = no element
+            if (v < v1) {
+                int ls = 0;
+                if (m > 1) {
+                    int lo = 0, hi = m - 1;
+                    while (lo < hi) {
+                        int mid = (lo + hi + 1) >> 1;
+                        if (sm.vstart_l[mid] <= v) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    ls = lo;
+                }
+                pk[k] = (ls << 2) | 2;
+                if (FIRST) {
+                    px[k] = __ldg(A.x + (long long)v * A.stride);
+                    py[k] = __ldg(A.y + (long long)v * A.stride);
+                    pidx[k] = v;
+                } else {
+                    int ps, vs;
+                    if (ls < kGeoCache) {
+                        ps = sm.geo[ls].pstart;
+                        vs = sm.geo[ls].vstart;
+                    } else {
+                        ps = seg[sf + ls].pstart;
+                        vs = seg[sf + ls].vstart;
+                    }
+                    int pos = ps + (v - vs);
+                    px[k] = ix[pos];
+                    py[k] = iy[pos];
+                    pidx[k] = ii[pos];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kItems; k++) {
+            if ((pk[k] & 3) != 2) continue;
+            int ls = pk[k] >> 2;
+            const Geo2 g = tile_geo<FIRST>(sm, seg, sf, ls);
+            float x = px[k], y = py[k];
+            if (FIRST) {
+                if (x == g.e0x && y == g.e0y) atomicMin(&H->a_idx, pidx[k]);
+                if (x == g.qx && y == g.qy) atomicMin(&H->b_idx, pidx[k]);
+            }
+            if (pidx[k] == g.q_idx) continue;  // the apex joins the hull
+            float d, e;
+            orient_value<P>(g.e0x, g.e0y, g.qx, g.qy, x, y, d, e);
+            if (orient_sign<P>(d, e, g.e0x, g.e0y, g.qx, g.qy, x, y, fallbacks) > 0) {
+                pk[k] = (ls << 2) | 0;
+                continue;
+            }
+            orient_value<P>(g.qx, g.qy, g.e1x, g.e1y, x, y, d, e);
+            if (orient_sign<P>(d, e, g.qx, g.qy, g.e1x, g.e1y, x, y, fallbacks) > 0)
+                pk[k] = (ls << 2) | 1;
+        }
+
+        // ---- tile-local ranks from warp ballots (kept in shared memory)
+        {
+            int w0 = 0, w1 = 0;
+#pragma unroll
+            for (int k = 0; k < kItems; k++) {
+                unsigned b0 = __ballot_sync(0xffffffffu, (pk[k] & 3) == 0);
+                unsigned b1 = __ballot_sync(0xffffffffu, (pk[k] & 3) == 1);
+                if (lane == 0) {
+                    sm.bal0[warp][k] = b0;
+                    sm.bal1[warp][k] = b1;
+                }
+                w0 += __popc(b0);
+                w1 += __popc(b1);
+            }
+            if (lane == 0) {
+                sm.wt0[warp] = w0;
+                sm.wt1[warp] = w1;
+            }
+        }
+        __syncthreads();
+        int base0 = 0, base1 = 0, tot0 = 0, tot1 = 0;
+#pragma unroll
+        for (int w = 0; w < kBlock / 32; w++) {
+            int a = sm.wt0[w], b = sm.wt1[w];
+            base0 += (w < warp) ? a : 0;
+            base1 += (w < warp) ? b : 0;
+            tot0 += a;
+            tot1 += b;
+        }
+        {
+            int r0 = base0, r1 = base1;
+#pragma unroll
+            for (int k = 0; k < kItems; k++) {
+                unsigned b0 = sm.bal0[warp][k], b1 = sm.bal1[warp][k];
+                int ls = pk[k] >> 2;
+                int v = wbase + k * 32 + lane;
+                if ((pk[k] & 3) != 3 && ls > 0 && sm.vstart_l[ls] == v) {
+                    sm.sb0[ls] = (unsigned short)(r0 + __popc(b0 & lt));
+                    sm.sb1[ls] = (unsigned short)(r1 + __popc(b1 & lt));
+                }
+                r0 += __popc(b0);
+                r1 += __popc(b1);
+            }
+        }
+        if (threadIdx.x == 0) {
+            sm.sb0[0] = 0;
+            sm.sb1[0] = 0;
+        }
+        __syncthreads();
+        // ---- global bases: one atomic per (tile, segment, child)
+        for (int ls = threadIdx.x; ls < m; ls += blockDim.x) {
+            int e0 = (ls + 1 < m) ? sm.sb0[ls + 1] : tot0;
+            int e1 = (ls + 1 < m) ? sm.sb1[ls + 1] : tot1;
+            int c0 = e0 - sm.sb0[ls], c1 = e1 - sm.sb1[ls];
+            int s = sf + ls;
+            sm.gb0[ls] = c0 ? (int)atomicAdd(&acc[2 * s].cnt, (unsigned)c0) : 0;
+            sm.gb1[ls] = c1 ? (int)atomicAdd(&acc[2 * s + 1].cnt, (unsigned)c1) : 0;
+        }
+        __syncthreads();
+        // ---- scatter survivors and reduce farthest-point keys
+        int cur = -1;
+        unsigned long long k1a = 0, k2a = 0, k1b = 0, k2b = 0;
+        unsigned ema = 0, emb = 0;
+        auto flush = [&](int ls) {
+            if (ls < 0) return;
+            if (ls < kKeySeg) {
+                if (k1a) {
+                    top2_insert(&sm.sk1[ls][0], &sm.sk2[ls][0], k1a);
+                    top2_insert(&sm.sk1[ls][0], &sm.sk2[ls][0], k2a);
+                    atomicMax(&sm.sem[ls][0], ema);
+                }
+                if (k1b) {
+                    top2_insert(&sm.sk1[ls][1], &sm.sk2[ls][1], k1b);
+                    top2_insert(&sm.sk1[ls][1], &sm.sk2[ls][1], k2b);
+                    atomicMax(&sm.sem[ls][1], emb);
+                }
+            } else {
+                int s = sf + ls;
+                acc_merge(acc[2 * s], k1a, k2a, ema);
+                acc_merge(acc[2 * s + 1], k1b, k2b, emb);
+            }
+        };
+        {
+            int r0 = base0, r1 = base1;
+#pragma unroll
+            for (int k = 0; k < kItems; k++) {
+                unsigned b0 = sm.bal0[warp][k], b1 = sm.bal1[warp][k];
+                int c = pk[k] & 3;
+                int pre0 = r0 + __popc(b0 & lt), pre1 = r1 + __popc(b1 & lt);
+                r0 += __popc(b0);
+                r1 += __popc(b1);
+                if (c > 1) continue;
+                int ls = pk[k] >> 2;
+                const Geo2 g = tile_geo<FIRST>(sm, seg, sf, ls);
+                int dst;
+                if (c == 0) dst = g.pstart + sm.gb0[ls] + (pre0 - sm.sb0[ls]);
+                else dst = g.pstart + g.len - 1 - (sm.gb1[ls] + (pre1 - sm.sb1[ls]));
+                ox[dst] = px[k];
+                oy[dst] = py[k];
+                oi[dst] = pidx[k];
+                if (ls != cur) {
+                    flush(cur);
+                    cur = ls;
+                    k1a = k2a = k1b = k2b = 0;
+                    ema = emb = 0;
+                }
+                // the distance to the child edge is the classification value
+                float d, e;
+                if (c == 0) orient_value<P>(g.e0x, g.e0y, g.qx, g.qy, px[k], py[k], d, e);
+                else orient_value<P>(g.qx, g.qy, g.e1x, g.e1y, px[k], py[k], d, e);
+                unsigned long long key = dist_key(d, pidx[k]);
+                unsigned eb = __float_as_uint(e);
+                if (c == 0) {
+                    top2_merge(k1a, k2a, key, 0ull);
+                    ema = eb > ema ? eb : ema;
+                } else {
+                    top2_merge(k1b, k2b, key, 0ull);
+                    emb = eb > emb ? eb : emb;
+                }
+            }
+        }
+        // warp-aggregated flush when the warp ends in one segment
+        {
+            int lmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)(cur + 1)) - 1;
+            bool same = __all_sync(0xffffffffu, cur == lmax || cur == -1);
+            if (same && lmax >= 0) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    unsigned long long a1 = __shfl_xor_sync(0xffffffffu, k1a, o);
+                    unsigned long long a2 = __shfl_xor_sync(0xffffffffu, k2a, o);
+                    unsigned long long c1 = __shfl_xor_sync(0xffffffffu, k1b, o);
+                    unsigned long long c2 = __shfl_xor_sync(0xffffffffu, k2b, o);
+                    top2_merge(k1a, k2a, a1, a2);
+                    top2_merge(k1b, k2b, c1, c2);
+                }
+                ema = __reduce_max_sync(0xffffffffu, ema);
+                emb = __reduce_max_sync(0xffffffffu, emb);
+                if (lane == 0) flush(lmax);
+            } else {
+                flush(cur);
+            }
+        }
+        __syncthreads();
+        // ---- merge the key slots of segments that end in this tile; the
+        // last segment is carried to the next tile of this block
+        const int mk = min(m, kKeySeg);
+        for (int i = threadIdx.x; i < 2 * mk; i += blockDim.x) {
+            int ls = i >> 1, c = i & 1;
+            if (ls == m - 1) {
+                sm.ck1[c] = sm.sk1[ls][c];
+                sm.ck2[c] = sm.sk2[ls][c];
+                sm.cem[c] = sm.sem[ls][c];
+                continue;
+            }
+            acc_merge(acc[2 * (sf + ls) + c], sm.sk1[ls][c], sm.sk2[ls][c], sm.sem[ls][c]);
+        }
+        if (threadIdx.x == 0) sm.carry_seg = (m - 1 < kKeySeg) ? sf + m - 1 : -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && sm.carry_seg >= 0) {
+        int cs = sm.carry_seg;
+        acc_merge(acc[2 * cs], sm.ck1[0], sm.ck2[0], sm.cem[0]);
+        acc_merge(acc[2 * cs + 1], sm.ck1[1], sm.ck2[1], sm.cem[1]);
+    }
+    // predicate fallback statistics
+    unsigned f = __reduce_add_sync(0xffffffffu, fallbacks);
+    if (lane == 0 && f) atomicAdd(&H->fallbacks, (unsigned long long)f);
+}
+
+// ---------------------------------------------------------------- update
+// Build the next segment table from the non-empty children (block 0 only).
+__device__ void update2d(const Params2 &A, int par, bool first, SmemU &sm)
+{
+    Hdr2 *H = A.hdr;
+    Seg2 *so = A.seg[par];
+    Acc2 *ac = A.acc[par];
+    Seg2 *sn = A.seg[par ^ 1];
+    Acc2 *an = A.acc[par ^ 1];
+    if (first) {
+        // the first split's pseudo segment: edge a -> a with apex b
+        if (threadIdx.x == 0) {
+            unsigned long long kmn = *(volatile unsigned long long *)&H->lexmin;
+            unsigned long long kmx = *(volatile unsigned long long *)&H->lexmax;
+            Seg2 g = {};
+            g.e0x = g.e1x = unord_f32((uint32_t)(kmn >> 32));
+            g.e0y = g.e1y = unord_f32((uint32_t)kmn);
+            g.qx = unord_f32((uint32_t)(kmx >> 32));
+            g.qy = unord_f32((uint32_t)kmx);
+            g.q_idx = -1;
+            g.e0_slot = 0;
+            g.q_slot = 1;
+            g.e1_slot = 0;
+            g.pstart = 0;
+            g.len = A.n;
+            so[0] = g;
+            int ai = *(volatile int *)&H->a_idx, bi = *(volatile int *)&H->b_idx;
+            A.hull_idx[0] = ai;
+            A.hull_x[0] = g.e0x;
+            A.hull_y[0] = g.e0y;
+            A.hull_idx[1] = bi;
+            A.hull_x[1] = g.qx;
+            A.hull_y[1] = g.qy;
+            A.next[0] = 1;
+            A.next[1] = 0;
+        }
+        __syncthreads();
+    }
+    const int S_old = *(volatile int *)&H->S[par];
+    const int hull_base = *(volatile int *)&H->hull_count;
+    if (threadIdx.x == 0) H->n_uncert = 0;
+    __syncthreads();
+    const int nslots = 2 * S_old;
+    long long carry_k = 0, carry_v = 0;
+    for (int base = 0; base < nslots; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        unsigned cnt = (i < nslots) ? ac[i].cnt : 0u;
+        long long packed = ((long long)(cnt > 0) << 32) | (long long)cnt;
+        long long tot;
+        long long ex = block_excl_scan64(packed, sm.wsum, &tot);
+        if (cnt > 0 && carry_k + (ex >> 32) >= A.cap_seg) {
+            set_status(H, kStCapacity);
+        } else if (cnt > 0) {
+            int k = (int)(carry_k + (ex >> 32));
+            int vs = (int)(carry_v + (ex & 0xffffffffll));
+            int j = i >> 1, c = i & 1;
+            Seg2 o = so[j];
+            Acc2 a = ac[i];
+            Seg2 g = {};
+            if (c == 0) {
+                g.e0x = o.e0x; g.e0y = o.e0y; g.e0_slot = o.e0_slot;
+                g.e1x = o.qx;  g.e1y = o.qy;  g.e1_slot = o.q_slot;
+                g.pstart = o.pstart;
+            } else {
+                g.e0x = o.qx;  g.e0y = o.qy;  g.e0_slot = o.q_slot;
+                g.e1x = o.e1x; g.e1y = o.e1y; g.e1_slot = o.e1_slot;
+                g.pstart = o.pstart + o.len - (int)cnt;
+            }
+            g.len = (int)cnt;
+            g.vstart = vs;
+            int qi = key_idx(a.key1);
+            g.q_idx = qi;
+            g.qx = __ldg(A.x + (long long)qi * A.stride);
+            g.qy = __ldg(A.y + (long long)qi * A.stride);
+            int slot = hull_base + k;
+            g.q_slot = slot;
+            // certified when the FP32 gap between the two best keys exceeds
+            // twice the largest error bound of the segment's keys
+            bool cert = true;
+            float em = __uint_as_float(a.emax);
+            float d1 = key_dist(a.key1);
+            if (cnt > 1) {
+                float d2 = key_dist(a.key2);
+                double gap = ((double)d1 - (double)d2) * (1.0 - 0x1p-50);
+                cert = gap > 2.0 * (double)em;
+            }
+            if (!cert) {
+                double thr = (double)d1 - (double)em - 2.0 * (double)em - fabs((double)d1) * 0x1p-20;
+                g.thr = isfinite(thr) ? __double2float_rd(thr) : -INFINITY;
+                int u = atomicAdd(&H->n_uncert, 1);
+                A.uncert[u] = k;
+            }
+            A.hull_idx[slot] = qi;
+            A.hull_x[slot] = g.qx;
+            A.hull_y[slot] = g.qy;
+            A.next[g.e0_slot] = slot;
+            A.next[slot] = g.e1_slot;
+            Acc2 z = {};
+            an[2 * k] = z;
+            an[2 * k + 1] = z;
+            sn[k] = g;
+            if (k < kTile) sm.vs[k] = vs;
+        }
+        carry_k += tot >> 32;
+        carry_v += tot & 0xffffffffll;
+    }
+    const int S_new = (int)carry_k, L_new = (int)carry_v;
+    __syncthreads();
+    // tile -> first segment map for the next pass
+    const int ntiles = (L_new + kTile - 1) / kTile;
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        int v = t * kTile;
+        int lo = 0, hi = S_new - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            int vs = (S_new <= kTile) ? sm.vs[mid] : sn[mid].vstart;
+            if (vs <= v) lo = mid;
+            else hi = mid - 1;
+        }
+        A.tile_seg[t] = lo;
+    }
+    if (threadIdx.x == 0) {
+        H->S[par ^ 1] = S_new;
+        H->L[par ^ 1] = L_new;
+        H->hull_count = hull_base + S_new;
+        H->seg_total += S_new;
+        H->surv_total += L_new;
+        H->exact_argmax += H->n_uncert;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- exact argmax
+// Farthest point of each uncertified segment with exact comparisons
+// (largest distance, then lowest index), one block per segment.
+template <class P>
+__device__ void exact2d(const Params2 &A, int par, SmemX &sm)
+{
+    Hdr2 *H = A.hdr;
+    const int nu = *(volatile int *)&H->n_uncert;
+    Seg2 *sn = A.seg[par ^ 1];
+    const float *bx = A.bx[par], *by = A.by[par];
+    const int *bi = A.bi[par];
+    for (int u = blockIdx.x; u < nu; u += gridDim.x) {
+        const int k = A.uncert[u];
+        const Seg2 g = sn[k];
+        int best = -1;
+        float bxv = 0.f, byv = 0.f;
+        for (int i = threadIdx.x; i < g.len; i += blockDim.x) {
+            int pos = g.pstart + i;
+            float x = bx[pos], y = by[pos];
+            int idx = bi[pos];
+            float d, e;
+            orient_value<P>(g.e0x, g.e0y, g.e1x, g.e1y, x, y, d, e);
+            if ((double)d + (double)e < (double)g.thr) continue;
+            if (best < 0) {
+                best = idx; bxv = x; byv = y;
+                continue;
+            }
+            int c = cmp_dist_exact(g.e0x, g.e0y, g.e1x, g.e1y, x, y, bxv, byv);
+            if (c > 0 || (c == 0 && idx < best)) {
+                best = idx; bxv = x; byv = y;
+            }
+        }
+        sm.bidx[threadIdx.x] = best;
+        sm.bx[threadIdx.x] = bxv;
+        sm.by[threadIdx.x] = byv;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) {
+                int o = threadIdx.x + s;
+                int oi = sm.bidx[o];
+                if (oi >= 0) {
+                    int mi = sm.bidx[threadIdx.x];
+                    bool take = mi < 0;
+                    if (!take) {
+                        int c = cmp_dist_exact(g.e0x, g.e0y, g.e1x, g.e1y, sm.bx[o], sm.by[o],
+                                               sm.bx[threadIdx.x], sm.by[threadIdx.x]);
+                        take = c > 0 || (c == 0 && oi < mi);
+                    }
+                    if (take) {
+                        sm.bidx[threadIdx.x] = oi;
+                        sm.bx[threadIdx.x] = sm.bx[o];
+                        sm.by[threadIdx.x] = sm.by[o];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0 && sm.bidx[0] >= 0) {
+            sn[k].q_idx = sm.bidx[0];
+            sn[k].qx = sm.bx[0];
+            sn[k].qy = sm.by[0];
+            A.hull_idx[g.q_slot] = sm.bidx[0];
+            A.hull_x[g.q_slot] = sm.bx[0];
+            A.hull_y[g.q_slot] = sm.by[0];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- output
+// Rank the hull links (clockwise from slot 0 = a) by pointer jumping,
+// reverse to counter-clockwise, drop vertices collinear with their
+// neighbours, write the indices (block 0 only).
+__device__ void output2d(const Params2 &A, SmemOut &sm)
+{
+    Hdr2 *H = A.hdr;
+    qh_result *R = A.res;
+    int st = *(volatile int *)&H->status;
+    long long count = 0;
+    if (st == 0) {
+        unsigned long long kmn = *(volatile unsigned long long *)&H->lexmin;
+        unsigned long long kmx = *(volatile unsigned long long *)&H->lexmax;
+        const int h = *(volatile int *)&H->hull_count;
+        if (A.n == 0) {
+            count = 0;
+        } else if (kmn == kmx) {
+            if (threadIdx.x == 0) A.out_idx[0] = *(volatile int *)&H->a_idx;
+            count = 1;
+        } else if (h > kOutCap) {
+            st = QH_ERR_CAPACITY;
+        } else {
+            for (int i = threadIdx.x; i < h; i += blockDim.x) {
+                int s = A.next[i];
+                sm.succ[i] = (s == 0) ? -1 : s;
+                sm.dist[i] = (s == 0) ? 0 : 1;
+            }
+            __syncthreads();
+            constexpr int kPer = kOutCap / kBlock;
+            for (int span = 1; span < h; span <<= 1) {
+                int ns[kPer], nd[kPer];
+#pragma unroll
+                for (int r = 0; r < kPer; r++) {
+                    int i = threadIdx.x + r * kBlock;
+                    ns[r] = -1;
+                    nd[r] = 0;
+                    if (i < h) {
+                        int s = sm.succ[i];
+                        nd[r] = sm.dist[i];
+                        ns[r] = s;
+                        if (s >= 0) {
+                            nd[r] += sm.dist[s];
+                            ns[r] = sm.succ[s];
+                        }
+                    }
+                }
+                __syncthreads();
+#pragma unroll
+                for (int r = 0; r < kPer; r++) {
+                    int i = threadIdx.x + r * kBlock;
+                    if (i < h) {
+                        sm.succ[i] = ns[r];
+                        sm.dist[i] = nd[r];
+                    }
+                }
+                __syncthreads();
+            }
+            // position counter-clockwise from a: pos = (h - rank) mod h with
+            // rank = h - 1 - dist (clockwise position)
+            for (int i = threadIdx.x; i < h; i += blockDim.x) {
+                int rank = h - 1 - sm.dist[i];
+                int pos = (h - rank) % h;
+                sm.succ[pos] = i;  // succ reused as order[]
+            }
+            __syncthreads();
+            int keep[kPer];
+            long long my = 0;
+#pragma unroll
+            for (int r = 0; r < kPer; r++) {
+                int p = threadIdx.x * kPer + r;
+                keep[r] = 0;
+                if (p < h) {
+                    if (h <= 2) {
+                        keep[r] = 1;
+                    } else {
+                        int sp = sm.succ[(p + h - 1) % h], sv = sm.succ[p], sx = sm.succ[(p + 1) % h];
+                        keep[r] = orient_exact_sign(A.hull_x[sp], A.hull_y[sp], A.hull_x[sv],
+                                                    A.hull_y[sv], A.hull_x[sx], A.hull_y[sx]) != 0;
+                    }
+                    my += keep[r];
+                }
+            }
+            long long tot;
+            long long off = block_excl_scan64(my, sm.wsum, &tot);
+#pragma unroll
+            for (int r = 0; r < kPer; r++) {
+                int p = threadIdx.x * kPer + r;
+                if (p < h && keep[r]) A.out_idx[off++] = A.hull_idx[sm.succ[p]];
+            }
+            count = tot;
+        }
+    }
+    if (threadIdx.x == 0) {
+        R->count = (st == 0) ? count : 0;
+        R->status = st;
+        R->iterations = *(volatile int *)&H->iter;
+        R->survivor_total = *(volatile long long *)&H->surv_total;
+        R->live_total = (long long)A.n + R->survivor_total;
+        R->segments_total = *(volatile long long *)&H->seg_total;
+        R->filter_fallbacks = *(volatile unsigned long long *)&H->fallbacks;
+        R->exact_argmax = *(volatile unsigned long long *)&H->exact_argmax;
+        for (int i = 0; i < 4; i++) R->extra[i] = (long long)*(volatile unsigned long long *)&H->phase_ns[i];
+    }
+}
+
+// ---------------------------------------------------------------- persistent kernel
+template <class P>
+__global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_persistent(Params2 A)
+{
+    __shared__ SmemAll sm;
+    Hdr2 *H = A.hdr;
+    int *fail = &H->status;
+    // phase clock (block 0, thread 0): time from one barrier exit to the next
+    const bool clk = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long tprev = clk ? globaltimer_ns() : 0;
+    auto sync_as = [&](int cat) {
+        grid_sync(&H->bar, fail, A.wait_ns);
+        if (clk) {
+            unsigned long long t = globaltimer_ns();
+            H->phase_ns[cat] += t - tprev;
+            tprev = t;
+        }
+    };
+    init2d(A);
+    sync_as(3);
+    extrema2d(A, sm);
+    sync_as(3);
+    if (*(volatile int *)&H->nonfinite) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(H, kStNonfinite);
+    } else if (*(volatile int *)&H->status == 0) {
+        pass2d<P, true>(A, 0, sm.pass);
+        sync_as(0);
+        int t = 0;
+        while (*(volatile int *)&H->status == 0) {
+            if (blockIdx.x == 0) update2d(A, t & 1, t == 0, sm.u);
+            sync_as(1);
+            if (*(volatile int *)&H->status) break;
+            if (*(volatile int *)&H->n_uncert > 0) {
+                exact2d<P>(A, t & 1, sm.x);
+                sync_as(2);
+            }
+            if (*(volatile int *)&H->S[(t + 1) & 1] == 0) break;
+            t++;
+            if (t > A.max_iters) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) set_status(H, kStNoConv);
+                break;
+            }
+            if (blockIdx.x == 0 && threadIdx.x == 0) H->iter = t;
+            pass2d<P, false>(A, t & 1, sm.pass);
+            sync_as(0);
+        }
+    }
+    sync_as(3);
+    if (blockIdx.x == 0) output2d(A, sm.out);
+}
+
+// ---------------------------------------------------------------- host-loop kernels
+__global__ void __launch_bounds__(kBlock) k_init2d(Params2 A) { init2d(A); }
+__global__ void __launch_bounds__(kBlock) k_extrema2d(Params2 A)
+{
+    __shared__ SmemAll sm;
+    extrema2d(A, sm);
+}
+template <class P, bool FIRST>
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_pass2d(Params2 A, int par)
+{
+    __shared__ SmemAll sm;
+    pass2d<P, FIRST>(A, par, sm.pass);
+}
+__global__ void __launch_bounds__(kBlock) k_update2d(Params2 A, int par, int first, int iter)
+{
+    __shared__ SmemAll sm;
+    if (threadIdx.x == 0) A.hdr->iter = iter;
+    update2d(A, par, first != 0, sm.u);
+}
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_exact2d(Params2 A, int par)
+{
+    __shared__ SmemAll sm;
+    exact2d<P>(A, par, sm.x);
+}
+__global__ void __launch_bounds__(kBlock) k_output2d(Params2 A, int nonfinite_check)
+{
+    __shared__ SmemAll sm;
+    if (nonfinite_check && A.hdr->nonfinite && threadIdx.x == 0) set_status(A.hdr, kStNonfinite);
+    __syncthreads();
+    output2d(A, sm.out);
+}
+
+// ---------------------------------------------------------------- host side
+struct Layout2 {
+    size_t hdr, bx[2], by[2], bi[2], seg[2], acc[2], tile_seg, uncert, hull_idx, hull_x, hull_y,
+        next, res, total;
+    int cap_seg;
+};
+
+static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+static Layout2 layout2d(int64_t n)
+{
+    Layout2 L = {};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o = align_up(o + bytes);
+        return r;
+    };
+    size_t np = (size_t)(n > 0 ? n : 1);
+    // live segments never exceed 2(n-2)/3: a new segment needs a live point,
+    // live points and earlier apexes are disjoint, and each old segment has at
+    // most two children (S_new <= min(n - 2 - A, 2A) for A earlier apexes)
+    L.cap_seg = (int)(2 * np / 3 + 8);
+    L.hdr = take(sizeof(Hdr2));
+    L.res = take(sizeof(qh_result));
+    for (int b = 0; b < 2; b++) {
+        L.bx[b] = take(np * 4);
+        L.by[b] = take(np * 4);
+        L.bi[b] = take(np * 4);
+    }
+    for (int b = 0; b < 2; b++) L.seg[b] = take((size_t)L.cap_seg * sizeof(Seg2));
+    for (int b = 0; b < 2; b++) L.acc[b] = take((size_t)2 * L.cap_seg * sizeof(Acc2));
+    L.tile_seg = take((np / kTile + 2) * 4);
+    L.uncert = take((size_t)L.cap_seg * 4);
+    L.hull_idx = take((np + 2) * 4);
+    L.hull_x = take((np + 2) * 4);
+    L.hull_y = take((np + 2) * 4);
+    L.next = take((np + 2) * 4);
+    L.total = o;
+    return L;
+}
+
+static Params2 make_params(const float *x, const float *y, int64_t n, int64_t stride,
+                           int32_t *out, qh_result *res, char *ws, const Layout2 &L,
+                           const qh_opts &o)
+{
+    Params2 A = {};
+    A.x = x;
+    A.y = y;
+    A.stride = stride;
+    A.n = (int)n;
+    A.out_idx = out;
+    A.res = res;
+    A.hdr = (Hdr2 *)(ws + L.hdr);
+    for (int b = 0; b < 2; b++) {
+        A.bx[b] = (float *)(ws + L.bx[b]);
+        A.by[b] = (float *)(ws + L.by[b]);
+        A.bi[b] = (int *)(ws + L.bi[b]);
+        A.seg[b] = (Seg2 *)(ws + L.seg[b]);
+        A.acc[b] = (Acc2 *)(ws + L.acc[b]);
+    }
+    A.tile_seg = (int *)(ws + L.tile_seg);
+    A.uncert = (int *)(ws + L.uncert);
+    A.hull_idx = (int *)(ws + L.hull_idx);
+    A.hull_x = (float *)(ws + L.hull_x);
+    A.hull_y = (float *)(ws + L.hull_y);
+    A.next = (int *)(ws + L.next);
+    A.max_iters = o.max_iters > 0 ? o.max_iters : n + 8;
+    A.cap_seg = L.cap_seg;
+    A.wait_ns = o.wait_ns > 0 ? o.wait_ns : 2000000000ll;
+    return A;
+}
+
+template <class P>
+static qh_status run2d(const Params2 &A, const qh_opts &o, cudaStream_t st)
+{
+    if (cudaMemsetAsync(A.hdr, 0, sizeof(Hdr2), st) != cudaSuccess) return QH_ERR_CUDA;
+    int grid = 0;
+    if (o.loop_mode == QH_LOOP_PERSISTENT) {
+        grid = persistent_grid((const void *)qh2d_persistent<P>, kBlock, o.blocks_per_sm);
+        if (grid <= 0) return QH_ERR_CUDA;
+        grid = grid > kMaxGrid ? kMaxGrid : grid;
+        Params2 a = A;
+        void *args[] = {&a};
+        cudaError_t e = cudaLaunchCooperativeKernel((const void *)qh2d_persistent<P>, dim3(grid),
+                                                    dim3(kBlock), args, 0, st);
+        return e == cudaSuccess ? QH_OK : QH_ERR_CUDA;
+    }
+    // host-driven loop: one launch per phase, live counts read back each iteration
+    grid = persistent_grid((const void *)k_pass2d<P, false>, kBlock, o.blocks_per_sm);
+    if (grid <= 0) return QH_ERR_CUDA;
+    grid = grid > kMaxGrid ? kMaxGrid : grid;
+    Hdr2 hh;
+    k_init2d<<<1, kBlock, 0, st>>>(A);
+    k_extrema2d<<<grid, kBlock, 0, st>>>(A);
+    if (cudaMemcpyAsync(&hh, A.hdr, sizeof(Hdr2), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return QH_ERR_CUDA;
+    if (hh.nonfinite) {
+        k_output2d<<<1, kBlock, 0, st>>>(A, 1);
+        return cudaGetLastError() == cudaSuccess ? QH_OK : QH_ERR_CUDA;
+    }
+    k_pass2d<P, true><<<grid, kBlock, 0, st>>>(A, 0);
+    int t = 0;
+    for (;;) {
+        k_update2d<<<1, kBlock, 0, st>>>(A, t & 1, t == 0, t);
+        if (cudaMemcpyAsync(&hh, A.hdr, sizeof(Hdr2), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return QH_ERR_CUDA;
+        if (hh.status) break;
+        if (hh.n_uncert > 0) k_exact2d<P><<<grid, kBlock, 0, st>>>(A, t & 1);
+        if (hh.S[(t + 1) & 1] == 0) break;
+        t++;
+        if (t > A.max_iters) {
+            int s = QH_ERR_NO_CONVERGENCE;
+            cudaMemcpyAsync(&A.hdr->status, &s, sizeof(int), cudaMemcpyHostToDevice, st);
+            cudaStreamSynchronize(st);
+            break;
+        }
+        int ntiles = (hh.S[(t) & 1] > 0) ? (hh.L[t & 1] + kTile - 1) / kTile : 0;
+        int g = ntiles < grid ? (ntiles > 0 ? ntiles : 1) : grid;
+        k_pass2d<P, false><<<g, kBlock, 0, st>>>(A, t & 1);
+    }
+    k_output2d<<<1, kBlock, 0, st>>>(A, 0);
+    return cudaGetLastError() == cudaSuccess ? QH_OK : QH_ERR_CUDA;
+}
+
+}  // namespace qh
+
+using namespace qh;
+
+extern "C" size_t qh_workspace_bytes_2d(int64_t n, const qh_opts *opts)
+{
+    (void)opts;
+    if (n < 0 || n > QH_MAX_POINTS) return 0;
+    return layout2d(n).total;
+}
+
+extern "C" qh_status qh_hull2d_async(const float *d_x, const float *d_y, int64_t n, int64_t stride,
+                                     int32_t *d_out_idx, qh_result *d_result, void *d_ws,
+                                     size_t ws_bytes, const qh_opts *opts, cudaStream_t stream)
+{
+    qh_opts o;
+    qh_default_opts(&o);
+    if (opts) o = *opts;
+    if (n < 0 || n > QH_MAX_POINTS || stride < 1 || !d_result || !d_ws) return QH_ERR_INVALID_ARG;
+    if (n > 0 && (!d_x || !d_y || !d_out_idx)) return QH_ERR_INVALID_ARG;
+    if (o.pred_mode != QH_PRED_F32 && o.pred_mode != QH_PRED_F64) return QH_ERR_INVALID_ARG;
+    if (o.loop_mode != QH_LOOP_PERSISTENT && o.loop_mode != QH_LOOP_HOST) return QH_ERR_INVALID_ARG;
+    if ((n - 1) * stride > (int64_t)1 << 40) return QH_ERR_INVALID_ARG;
+    Layout2 L = layout2d(n);
+    if (ws_bytes < L.total || ((uintptr_t)d_ws & 255)) return QH_ERR_NOMEM;
+    if (n == 0)
+        return cudaMemsetAsync(d_result, 0, sizeof(qh_result), stream) == cudaSuccess ? QH_OK
+                                                                                     : QH_ERR_CUDA;
+    Params2 A = make_params(d_x, d_y, n, stride, d_out_idx, d_result, (char *)d_ws, L, o);
+    if (o.pred_mode == QH_PRED_F32) return run2d<PredF32>(A, o, stream);
+    return run2d<PredF64>(A, o, stream);
+}
+
+extern "C" qh_status qh_hull2d(const float *d_x, const float *d_y, int64_t n, int64_t stride,
+                               int32_t *d_out_idx, int64_t *h_count, qh_result *h_result,
+                               void *d_ws, size_t ws_bytes, const qh_opts *opts,
+                               cudaStream_t stream)
+{
+    if (n < 0 || n > QH_MAX_POINTS || !d_ws) return QH_ERR_INVALID_ARG;
+    Layout2 L = layout2d(n);
+    if (ws_bytes < L.total || ((uintptr_t)d_ws & 255)) return QH_ERR_NOMEM;
+    qh_result *d_res = (qh_result *)((char *)d_ws + L.res);
+    qh_status s = qh_hull2d_async(d_x, d_y, n, stride, d_out_idx, d_res, d_ws, ws_bytes, opts, stream);
+    if (s != QH_OK) return s;
+    qh_result r;
+    if (cudaMemcpyAsync(&r, d_res, sizeof(r), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return QH_ERR_CUDA;
+    if (h_count) *h_count = r.count;
+    if (h_result) *h_result = r;
+    return (qh_status)r.status;
+}

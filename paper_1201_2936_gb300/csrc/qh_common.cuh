@@ -1,0 +1,157 @@
+// Device utilities shared by the hull kernels: status codes, orderable
+// float keys, grid-wide barrier with a bounded wait, small warp helpers.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qh.h"
+
+namespace qh {
+
+constexpr int kStOk = QH_OK;
+constexpr int kStNonfinite = QH_ERR_NONFINITE;
+constexpr int kStDegenerate = QH_ERR_DEGENERATE;
+constexpr int kStCapacity = QH_ERR_CAPACITY;
+constexpr int kStTimeout = QH_ERR_TIMEOUT;
+constexpr int kStNoConv = QH_ERR_NO_CONVERGENCE;
+
+// Total order on float bits that matches the numeric order (-0 < +0 apart).
+__device__ __forceinline__ uint32_t ord_f32(float f)
+{
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float unord_f32(uint32_t o)
+{
+    uint32_t u = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+    return __uint_as_float(u);
+}
+// Coordinates enter keys and comparisons with -0.0 mapped to +0.0 (same point).
+__device__ __forceinline__ float canon0(float f) { return f == 0.0f ? 0.0f : f; }
+
+// Argmax key of a point: larger distance first, then lower index.
+__device__ __forceinline__ unsigned long long dist_key(float d, int idx)
+{
+    return ((unsigned long long)ord_f32(d) << 32) | (unsigned long long)(0xffffffffu - (uint32_t)idx);
+}
+__device__ __forceinline__ int key_idx(unsigned long long k) { return (int)(0xffffffffu - (uint32_t)(k & 0xffffffffu)); }
+__device__ __forceinline__ float key_dist(unsigned long long k) { return unord_f32((uint32_t)(k >> 32)); }
+
+// Insert key k into a (top1, top2) pair held in memory with atomics: after any
+// set of insertions *t1 is the largest key and *t2 the largest of the others.
+// Every key displaced from, or refused by, *t1 is offered to *t2.
+template <class T>
+__device__ __forceinline__ void top2_insert(T *t1, T *t2, T k)
+{
+    if (k == 0) return;
+    T old = atomicMax(t1, k);
+    atomicMax(t2, old < k ? old : k);
+}
+
+__device__ __forceinline__ void top2_merge(unsigned long long &a1, unsigned long long &a2,
+                                           unsigned long long b1, unsigned long long b2)
+{
+    unsigned long long hi = a1 > b1 ? a1 : b1;
+    unsigned long long lo = a1 > b1 ? b1 : a1;
+    unsigned long long o2 = a2 > b2 ? a2 : b2;
+    a1 = hi;
+    a2 = lo > o2 ? lo : o2;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+};
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The
+// wait is bounded by wait_ns; on expiry the barrier raises *fail (status
+// QH_ERR_TIMEOUT) and returns so that the kernel can leave cleanly.
+__device__ __forceinline__ void grid_sync(GridBarrier *b, int *fail, long long wait_ns)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *vgen = &b->gen;
+        unsigned int g = *vgen;
+        __threadfence();
+        unsigned int arrived = atomicAdd(&b->count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            unsigned long long t0 = globaltimer_ns();
+            unsigned int spins = 0;
+            while (*vgen == g) {
+                __nanosleep(64);
+                if (((++spins) & 255u) == 0u &&
+                    (long long)(globaltimer_ns() - t0) > wait_ns) {
+                    atomicCAS(fail, 0, kStTimeout);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Inclusive warp scan of an int.
+__device__ __forceinline__ int warp_incl_scan(int v)
+{
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ long long warp_incl_scan64(long long v)
+{
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Block-wide exclusive scan of a 64-bit value (blockDim.x <= 1024).  wsum
+// must hold 33 entries.  Returns the exclusive prefix; *total gets the sum.
+__device__ __forceinline__ long long block_excl_scan64(long long v, long long *wsum, long long *total)
+{
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    long long inc = warp_incl_scan64(v);
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        long long s = lane < nw ? wsum[lane] : 0;
+        long long si = warp_incl_scan64(s);
+        if (lane < nw) wsum[lane] = si - s;
+        if (lane == nw - 1) wsum[32] = si;
+    }
+    __syncthreads();
+    long long r = wsum[w] + inc - v;
+    *total = wsum[32];
+    __syncthreads();
+    return r;
+}
+
+}  // namespace qh

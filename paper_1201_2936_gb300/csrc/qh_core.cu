@@ -1,0 +1,66 @@
+// Status strings, defaults and the occupancy cache of libqh.
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+
+#include "qh_internal.h"
+
+namespace qh {
+
+int persistent_grid(const void *func, int block, int blocks_per_sm)
+{
+    static std::mutex mu;
+    static std::unordered_map<unsigned long long, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    unsigned long long key = ((unsigned long long)(uintptr_t)func << 8) ^ (unsigned long long)dev;
+    int per_sm = 0, sms = 0;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            per_sm = it->second & 0xffff;
+            sms = it->second >> 16;
+        }
+    }
+    if (sms == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, block, 0) != cudaSuccess)
+            return 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 0;
+        std::lock_guard<std::mutex> g(mu);
+        cache[key] = (sms << 16) | per_sm;
+    }
+    if (per_sm <= 0) return 0;
+    if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
+    return per_sm * sms;
+}
+
+}  // namespace qh
+
+extern "C" const char *qh_status_str(qh_status s)
+{
+    switch (s) {
+    case QH_OK: return "QH_OK";
+    case QH_ERR_INVALID_ARG: return "QH_ERR_INVALID_ARG: invalid argument";
+    case QH_ERR_NONFINITE: return "QH_ERR_NONFINITE: input contains NaN or Inf";
+    case QH_ERR_DEGENERATE: return "QH_ERR_DEGENERATE: points do not span the space";
+    case QH_ERR_NOMEM: return "QH_ERR_NOMEM: workspace too small or misaligned";
+    case QH_ERR_CAPACITY: return "QH_ERR_CAPACITY: internal table overflow";
+    case QH_ERR_TIMEOUT: return "QH_ERR_TIMEOUT: a bounded device wait expired";
+    case QH_ERR_NO_CONVERGENCE: return "QH_ERR_NO_CONVERGENCE: iteration cap reached";
+    case QH_ERR_CUDA: return "QH_ERR_CUDA: CUDA runtime error";
+    case QH_ERR_NOT_SUPPORTED: return "QH_ERR_NOT_SUPPORTED: option combination not available";
+    }
+    return "unknown qh_status";
+}
+
+extern "C" const char *qh_version(void) { return "qh 0.1 sm_103a"; }
+
+extern "C" void qh_default_opts(qh_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->pred_mode = QH_PRED_F32;
+    o->loop_mode = QH_LOOP_PERSISTENT;
+}

@@ -1,0 +1,15 @@
+// Host-side helpers shared by the translation units of libqh.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "qh.h"
+
+namespace qh {
+
+// Grid size of a persistent (cooperative) launch of `func` with `block`
+// threads: SMs x resident CTAs per SM (capped by blocks_per_sm when > 0).
+// Returns 0 on a CUDA error.
+int persistent_grid(const void *func, int block, int blocks_per_sm);
+
+}  // namespace qh

@@ -1,0 +1,65 @@
+"""The C ABI library loads without a GPU and exports every function that
+include/qh.h declares; the ctypes binding names the same set."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(qh_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1201_2936_gb300 import build
+    build.build()
+    return ctypes.CDLL(build.LIB)
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert "qh_hull2d" in declared and "qh_status_str" in declared
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_header():
+    from paper_1201_2936_gb300 import _native
+    assert set(_native.exported_names()) == _declared()
+
+
+def test_status_strings_and_sizes(lib):
+    from paper_1201_2936_gb300 import _native
+    L = _native.lib()
+    assert L.qh_status_str(0) == b"QH_OK"
+    assert b"NONFINITE" in L.qh_status_str(2)
+    assert L.qh_workspace_bytes_2d(-1, None) == 0
+    w1 = L.qh_workspace_bytes_2d(1000, None)
+    w2 = L.qh_workspace_bytes_2d(2000, None)
+    assert 0 < w1 < w2
+    assert ctypes.sizeof(_native.QhResult) == 96
+
+
+def test_host_side_argument_errors(lib):
+    from paper_1201_2936_gb300 import _native
+    L = _native.lib()
+    res = ctypes.c_void_p(16)
+    # negative n, bad stride, null workspace: rejected before any device work
+    assert L.qh_hull2d_async(None, None, -1, 1, None, res, ctypes.c_void_p(256), 1 << 20, None, None) == 1
+    assert L.qh_hull2d_async(ctypes.c_void_p(256), ctypes.c_void_p(256), 10, 0, ctypes.c_void_p(256),
+                             res, ctypes.c_void_p(256), 1 << 20, None, None) == 1
+    assert L.qh_hull2d_async(ctypes.c_void_p(256), ctypes.c_void_p(256), 10, 1, ctypes.c_void_p(256),
+                             res, None, 1 << 20, None, None) == 1
+    # workspace too small
+    assert L.qh_hull2d_async(ctypes.c_void_p(256), ctypes.c_void_p(256), 10, 1, ctypes.c_void_p(256),
+                             res, ctypes.c_void_p(256), 16, None, None) == 4

@@ -1,0 +1,147 @@
+"""GPU parity for the 2D hull: the CUDA path (through the C ABI) against the
+oracle, index for index, on seeded inputs: several tiles with ragged tails,
+the paper's distributions, degenerate inputs, both predicate modes and both
+loop drivers."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1201_2936_gb300 import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qh():
+    from paper_1201_2936_gb300 import build
+    build.build()
+    oracle.build()
+    import paper_1201_2936_gb300 as q
+    return q
+
+
+def _gpu(qh, x, y, **kw):
+    X = torch.from_numpy(np.asarray(x, np.float32)).cuda()
+    Y = torch.from_numpy(np.asarray(y, np.float32)).cuda()
+    idx, res = qh.hull2d(X, Y, return_result=True, **kw)
+    return idx.cpu().numpy(), res
+
+
+MODES = [dict(pred="f32", loop="persistent"), dict(pred="f64", loop="host"),
+         dict(pred="f32", loop="host"), dict(pred="f64", loop="persistent")]
+
+
+@pytest.mark.parametrize("mode", MODES, ids=lambda m: f"{m['pred']}-{m['loop']}")
+def test_square_100k_matches_oracle(qh, mode):
+    x, y = w.uniform_square(w.N_SMALL_2D, w.SEED_BASE + 0)
+    got, res = _gpu(qh, x, y, **mode)
+    want = oracle.hull2d(x, y)
+    assert got.tolist() == want.tolist()
+    assert res["status"] == 0 and res["count"] == len(want)
+
+
+@pytest.mark.parametrize("gen,n", [("disk", 300_001), ("circle", 250_037), ("square", 4097),
+                                   ("gauss", 1_000_003), ("circle", 2049), ("disk", 2047)])
+def test_distributions_match_oracle(qh, gen, n):
+    seed = 77 + n
+    if gen == "disk":
+        x, y = w.uniform_disk(n, seed)
+    elif gen == "circle":
+        x, y = w.circle_jitter(n, seed, 1e-4)
+    elif gen == "square":
+        x, y = w.uniform_square(n, seed)
+    else:
+        r = np.random.default_rng(seed)
+        x, y = r.normal(size=(2, n)).astype(np.float32)
+    want = oracle.hull2d(x, y)
+    for mode in MODES[:2]:
+        got, res = _gpu(qh, x, y, **mode)
+        assert got.tolist() == want.tolist(), mode
+
+
+def test_tiny_and_degenerate(qh):
+    cases = [
+        ([], []),
+        ([1.5], [2.5]),
+        ([1, 1, 1, 1], [2, 2, 2, 2]),
+        ([0, 1], [0, 1]),
+        ([1, 0], [1, 0]),
+        ([2, 0, 1, 3], [2, 0, 1, 3]),               # collinear
+        ([0, 1, 0, 1, 1, 0], [0, 0, 1, 1, 0, 0]),   # duplicates of vertices
+        ([0.0, -0.0, 1.0, 0.0], [0.0, 0.0, 0.0, 1.0]),
+        ([0, 2, 1, 1, 1], [0, 0, 1, 1, -1]),
+    ]
+    rng = np.random.default_rng(3)
+    for _ in range(40):
+        n = int(rng.integers(1, 60))
+        cases.append((rng.integers(0, 4, n).tolist(), rng.integers(0, 4, n).tolist()))
+    for x, y in cases:
+        x = np.asarray(x, np.float32)
+        y = np.asarray(y, np.float32)
+        want = oracle.hull2d(x, y)
+        for mode in MODES:
+            got, res = _gpu(qh, x, y, **mode)
+            assert got.tolist() == want.tolist(), (x, y, mode)
+
+
+def test_integer_grid_many_ties(qh):
+    # lattice points: many exact distance ties, collinear runs on every side
+    rng = np.random.default_rng(5)
+    x = rng.integers(-300, 301, 400_000).astype(np.float32)
+    y = rng.integers(-200, 201, 400_000).astype(np.float32)
+    want = oracle.hull2d(x, y)
+    for mode in MODES[:2]:
+        got, res = _gpu(qh, x, y, **mode)
+        assert got.tolist() == want.tolist()
+        assert res["exact_argmax"] > 0
+
+
+def test_integer_circle_all_vertices(qh):
+    r = 5 ** 4  # x^2 + y^2 = 625^2: every lattice point is a hull vertex
+    pts = set()
+    for i in range(-r, r + 1):
+        j2 = r * r - i * i
+        j = int(np.sqrt(j2))
+        while j * j > j2:
+            j -= 1
+        while (j + 1) ** 2 <= j2:
+            j += 1
+        if j * j == j2:
+            pts.add((i, j))
+            pts.add((i, -j))
+    pts = np.array(sorted(pts), np.float32)
+    rng = np.random.default_rng(2)
+    inner = rng.uniform(-400, 400, (100_000, 2)).astype(np.float32)
+    P = np.concatenate([inner, pts])[rng.permutation(len(inner) + len(pts))]
+    want = oracle.hull2d(P[:, 0], P[:, 1])
+    assert len(want) == len(pts)
+    got, _ = _gpu(qh, P[:, 0], P[:, 1])
+    assert got.tolist() == want.tolist()
+
+
+def test_interleaved_and_soa_layouts(qh):
+    x, y = w.uniform_disk(100_003, 12)
+    want = oracle.hull2d(x, y)
+    P = torch.from_numpy(np.stack([x, y], 1)).cuda()       # [n, 2], stride 2
+    assert qh.hull2d(P).cpu().numpy().tolist() == want.tolist()
+    Q = torch.from_numpy(np.stack([x, y], 0)).cuda()       # [2, n]
+    assert qh.hull2d(Q).cpu().numpy().tolist() == want.tolist()
+
+
+def test_nonfinite_is_reported(qh):
+    x = np.array([0, 1, np.nan, 3], np.float32)
+    y = np.array([0, 1, 2, 3], np.float32)
+    for mode in MODES[:2]:
+        with pytest.raises(qh.QHError) as ei:
+            _gpu(qh, x, y, **mode)
+        assert ei.value.status == 2
+
+
+def test_repeat_calls_reuse_workspace(qh):
+    x, y = w.circle_jitter(500_000, 3, 1e-4)
+    want = oracle.hull2d(x, y)
+    ws = qh.Workspace()
+    for _ in range(3):
+        X, Y = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+        assert qh.hull2d(X, Y, workspace=ws).cpu().numpy().tolist() == want.tolist()
