@@ -174,6 +174,8 @@ def main():
     ap.add_argument("--n", type=int, default=N_PER_CLOUD,
                     help="points per cloud (profiling of smaller cases)")
     ap.add_argument("--only", default="", help="comma-separated cloud names to keep")
+    ap.add_argument("--timeline", action="store_true",
+                    help="print the per-iteration device timeline of each cloud to stderr")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -249,6 +251,13 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     res = [qh.result_from_tensor(r) for r in results]
+    if args.timeline:
+        for i, (name, _) in enumerate(data):
+            rows = qh.debug_timeline_2d(wss[i], ncl)
+            print(f"# timeline {name}: iter L S pass_us update_us", file=sys.stderr)
+            for r in rows:
+                print(f"#   {r[0]:3d} {r[1]:10d} {r[2]:7d} {r[3] / 1e3:9.2f} "
+                      f"{r[4] / 1e3:8.2f}", file=sys.stderr)
     pts_per_step = nl * ncl
     value = ws * pts_per_step * args.steps / (total_ms / 1e3) / 1e6
 

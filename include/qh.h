@@ -144,6 +144,22 @@ qh_status qh_hull2d(const float *d_x, const float *d_y, int64_t n, int64_t strid
                     int32_t *d_out_idx, int64_t *h_count, qh_result *h_result, void *d_ws,
                     size_t ws_bytes, const qh_opts *opts, cudaStream_t stream);
 
+/* ---------------------------------------------------------------------- */
+/* Diagnostics                                                             */
+/* ---------------------------------------------------------------------- */
+
+/* Per-iteration record of the last persistent-loop 2D call made on d_ws
+ * (which must be the workspace of a call with the same n, finished or not
+ * yet started on `stream`; the call synchronises the stream).  Row r holds
+ * {r, L_r, S_r, pass_ns, update_ns}: r = 0 is the first split, L_r the live
+ * points the pass of iteration r read, S_r its segments, then the device
+ * time of that pass and of the update that followed.  At most 64 rows and
+ * max_rows rows are written (h_rows: host int64[5 * max_rows]); *h_nrows
+ * receives the count.  Timing comes from %globaltimer between grid
+ * barriers. */
+qh_status qh_debug_timeline_2d(const void *d_ws, int64_t n, int64_t *h_rows, int32_t max_rows,
+                               int32_t *h_nrows, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

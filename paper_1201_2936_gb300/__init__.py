@@ -106,6 +106,20 @@ def hull2d_async(x: torch.Tensor, y: Optional[torch.Tensor], out: torch.Tensor,
         raise QHError(st, "qh_hull2d_async")
 
 
+def debug_timeline_2d(workspace: Workspace, n: int, stream=None):
+    """Per-iteration rows (iteration, live points, segments, pass ns, update ns)
+    of the last persistent-loop 2D call on `workspace` with n points."""
+    import numpy as np
+    rows = np.zeros((64, 5), dtype=np.int64)
+    nr = ctypes.c_int32(0)
+    st = _native.lib().qh_debug_timeline_2d(workspace.buf.data_ptr(), int(n),
+                                            rows.ctypes.data_as(ctypes.c_void_p), 64,
+                                            ctypes.byref(nr), _stream_handle(stream))
+    if st != 0:
+        raise QHError(st, "qh_debug_timeline_2d")
+    return rows[: nr.value]
+
+
 def result_from_tensor(result: torch.Tensor) -> QhResult:
     raw = bytes(result.cpu().numpy().tobytes())
     return QhResult.from_buffer_copy(raw[:RESULT_BYTES])

@@ -43,14 +43,24 @@
 
 namespace qh {
 
-constexpr int kBlock = 256;
-constexpr int kItems = 8;
+#ifndef QH2D_BLOCK
+#define QH2D_BLOCK 256
+#endif
+#ifndef QH2D_ITEMS
+#define QH2D_ITEMS 8
+#endif
+#ifndef QH2D_MINBLOCKS
+#define QH2D_MINBLOCKS 2
+#endif
+constexpr int kBlock = QH2D_BLOCK;
+constexpr int kItems = QH2D_ITEMS;
 constexpr int kTile = kBlock * kItems;   // points per tile
 constexpr int kKeySeg = 64;              // segments per tile with shared-memory key slots
 constexpr int kGeoCache = 64;            // segments per tile with geometry in shared memory
 constexpr int kOutCap = 4096;            // hull slots ranked in one block's shared memory
 constexpr int kMaxGrid = 4096;
-constexpr int kMinBlocks = 4;            // resident CTAs per SM the register budget targets
+constexpr int kMinBlocks = QH2D_MINBLOCKS;  // resident CTAs per SM the register budget targets
+constexpr int kTimeline = 64;            // iterations recorded by the diagnostic timeline
 
 struct Seg2 {
     float e0x, e0y, qx, qy, e1x, e1y;
@@ -62,9 +72,11 @@ struct Seg2 {
 static_assert(sizeof(Seg2) == 64, "Seg2 layout");
 
 struct Acc2 {
-    unsigned long long key1, key2;
-    unsigned int cnt, emax;
-    unsigned int pad[2];
+    unsigned long long key1;  // best key of the child (distance order bits, ~index)
+    unsigned int o2;          // distance order bits of the best other point
+    unsigned int cnt;         // points in the child
+    unsigned int emax;        // largest error bound of the child's keys (float bits)
+    unsigned int pad[3];
 };
 static_assert(sizeof(Acc2) == 32, "Acc2 layout");
 
@@ -83,6 +95,9 @@ struct Hdr2 {
     long long seg_total, surv_total;
     unsigned long long fallbacks, exact_argmax;
     unsigned long long phase_ns[4];  // pass, update, exact, other (persistent kernel)
+    // per-iteration record of the persistent kernel (first kTimeline iterations):
+    // live points L, segments S, pass and update nanoseconds
+    long long tl[kTimeline][4];
 };
 
 struct Params2 {
@@ -92,11 +107,12 @@ struct Params2 {
     int *out_idx;
     qh_result *res;
     Hdr2 *hdr;
-    float *bx[2], *by[2];
+    float2 *bxy[2];
     int *bi[2];
     Seg2 *seg[2];
     Acc2 *acc[2];
     int *tile_seg;
+    int *tile_m;
     int *uncert;
     int *hull_idx;
     float *hull_x, *hull_y;
@@ -113,17 +129,23 @@ struct Geo2 {
     int q_idx, pstart, len, vstart;
 };
 
+// Farthest-point accumulator of one child: best key (distance order bits,
+// then lowest index), order bits of the best distance among the other
+// points, and the largest error bound of any key.
+struct Top2 {
+    unsigned long long k1;
+    unsigned o2, em;
+};
+
 struct SmemPass {
     int vstart_l[kTile];
     unsigned short sb0[kTile], sb1[kTile];
     int gb0[kTile], gb1[kTile];
-    unsigned long long sk1[kKeySeg][2], sk2[kKeySeg][2];
-    unsigned int sem[kKeySeg][2];
-    unsigned long long ck1[2], ck2[2];
-    unsigned int cem[2];
-    unsigned int bal0[kBlock / 32][kItems], bal1[kBlock / 32][kItems];
+    unsigned long long sk1[kKeySeg][2];
+    unsigned int so2[kKeySeg][2], sem[kKeySeg][2];
+    Top2 carry[2];
     int wt0[kBlock / 32], wt1[kBlock / 32];
-    int sfirst, carry_seg;
+    int sfirst, m, carry_seg, par;
     Geo2 geo[kGeoCache];
 };
 struct SmemU {
@@ -180,13 +202,25 @@ __device__ void extrema2d(const Params2 &A, SmemAll &sm)
     unsigned long long mn = ~0ull, mx = 0ull;
     int bad = 0;
     const long long s = A.stride;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.n;
-         i += (long long)gridDim.x * blockDim.x) {
-        float x = canon0(__ldg(A.x + i * s)), y = canon0(__ldg(A.y + i * s));
-        bad |= !(isfinite(x) && isfinite(y));
-        unsigned long long k = ((unsigned long long)ord_f32(x) << 32) | ord_f32(y);
-        mn = k < mn ? k : mn;
-        mx = k > mx ? k : mx;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    constexpr int U = 8;  // loads in flight per thread
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < A.n; i0 += U * nthr) {
+        float xs[U], ys[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            long long i = i0 + u * nthr;
+            xs[u] = i < A.n ? __ldg(A.x + i * s) : 0.0f;
+            ys[u] = i < A.n ? __ldg(A.y + i * s) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (i0 + u * nthr >= A.n) continue;
+            float x = canon0(xs[u]), y = canon0(ys[u]);
+            bad |= !(isfinite(x) && isfinite(y));
+            unsigned long long k = ((unsigned long long)ord_f32(x) << 32) | ord_f32(y);
+            mn = k < mn ? k : mn;
+            mx = k > mx ? k : mx;
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -226,84 +260,316 @@ __device__ __forceinline__ Geo2 geo_of(const Seg2 &g)
     return r;
 }
 
-template <bool FIRST>
-__device__ __forceinline__ Geo2 tile_geo(const SmemPass &sm, const Seg2 *seg, int sf, int ls)
+__device__ __forceinline__ void top2_add(Top2 &t, unsigned long long k, unsigned em)
 {
-    if (FIRST || ls < kGeoCache) return sm.geo[ls];
-    return geo_of(seg[sf + ls]);
+    unsigned long long lo = k < t.k1 ? k : t.k1;
+    t.k1 = k > t.k1 ? k : t.k1;
+    unsigned lo_o = (unsigned)(lo >> 32);
+    t.o2 = lo_o > t.o2 ? lo_o : t.o2;
+    t.em = em > t.em ? em : t.em;
 }
 
-// Merge a (top1, top2, emax) triple of one child into the global accumulator.
-__device__ __forceinline__ void acc_merge(Acc2 &ac, unsigned long long k1, unsigned long long k2,
-                                          unsigned em)
+__device__ __forceinline__ void top2_join(Top2 &t, const Top2 &u)
 {
-    if (!k1) return;
-    top2_insert(&ac.key1, &ac.key2, k1);
-    top2_insert(&ac.key1, &ac.key2, k2);
-    atomicMax(&ac.emax, em);
+    top2_add(t, u.k1, u.em);
+    t.o2 = u.o2 > t.o2 ? u.o2 : t.o2;
+}
+
+// Insert an accumulator into memory (shared or global) with atomics: the key
+// displaced from, or refused by, k1 offers its distance to o2.
+__device__ __forceinline__ void top2_store(unsigned long long *k1, unsigned *o2, unsigned *em,
+                                           const Top2 &t)
+{
+    if (!t.k1) return;
+    unsigned long long old = atomicMax(k1, t.k1);
+    unsigned long long lo = old < t.k1 ? old : t.k1;
+    unsigned o = (unsigned)(lo >> 32);
+    atomicMax(o2, o > t.o2 ? o : t.o2);
+    atomicMax(em, t.em);
+}
+
+__device__ __forceinline__ void top2_warp(Top2 &t)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Top2 u;
+        u.k1 = __shfl_xor_sync(0xffffffffu, t.k1, o);
+        u.o2 = __shfl_xor_sync(0xffffffffu, t.o2, o);
+        u.em = __shfl_xor_sync(0xffffffffu, t.em, o);
+        top2_join(t, u);
+    }
+}
+
+__device__ __forceinline__ void acc_merge(Acc2 &ac, const Top2 &t)
+{
+    top2_store(&ac.key1, &ac.o2, &ac.emax, t);
+}
+
+// One tile of the pass.  SINGLE: the tile lies inside one segment (geometry
+// in registers, no per-item segment search).
+template <class P, bool FIRST, bool SINGLE>
+__device__ __forceinline__ void pass_tile(const Params2 &A, SmemPass &sm, const Seg2 *seg,
+                                          Acc2 *acc, int sf, int m, int v0, int v1,
+                                          unsigned &fallbacks)
+{
+    Hdr2 *H = A.hdr;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const float2 *ixy = A.bxy[FIRST ? 0 : (sm.par ^ 1)];
+    const int *ii = A.bi[FIRST ? 0 : (sm.par ^ 1)];
+    float2 *oxy = A.bxy[sm.par];
+    int *oi = A.bi[sm.par];
+    Geo2 g0;
+    if (SINGLE) g0 = sm.geo[0];
+    auto geo = [&](int ls) -> Geo2 {
+        if (SINGLE) return g0;
+        if (ls < kGeoCache) return sm.geo[ls];
+        return geo_of(seg[sf + ls]);
+    };
+
+    // ---- load, classify, accumulate farthest-point keys
+    float2 pxy[kItems];
+    int pidx[kItems], pk[kItems];
+    const int wbase = v0 + warp * 32 * kItems;
+#pragma unroll
+    for (int k = 0; k < kItems; k++) {
+        int v = wbase + k * 32 + lane;
+        pk[k] = 3;
+        if (v < v1) {
+            int ls = 0;
+            if (!SINGLE) {
+                int lo = 0, hi = m - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (sm.vstart_l[mid] <= v) lo = mid;
+                    else hi = mid - 1;
+                }
+                ls = lo;
+            }
+            pk[k] = (ls << 2) | 2;
+            if (FIRST) {
+                if (A.stride == 1) {
+                    pxy[k].x = __ldg(A.x + v);
+                    pxy[k].y = __ldg(A.y + v);
+                } else {
+                    pxy[k].x = __ldg(A.x + (long long)v * A.stride);
+                    pxy[k].y = __ldg(A.y + (long long)v * A.stride);
+                }
+                pidx[k] = v;
+            } else {
+                int ps, vs;
+                if (SINGLE) {
+                    ps = g0.pstart;
+                    vs = g0.vstart;
+                } else if (ls < kGeoCache) {
+                    ps = sm.geo[ls].pstart;
+                    vs = sm.geo[ls].vstart;
+                } else {
+                    ps = seg[sf + ls].pstart;
+                    vs = seg[sf + ls].vstart;
+                }
+                int pos = ps + (v - vs);
+                pxy[k] = ixy[pos];
+                pidx[k] = ii[pos];
+            }
+        }
+    }
+    int cur = -1;
+    Top2 ta = {0ull, 0u, 0u}, tb = {0ull, 0u, 0u};
+    auto flush = [&](int ls) {
+        if (ls < 0) return;
+        if (ls < kKeySeg) {
+            top2_store(&sm.sk1[ls][0], &sm.so2[ls][0], &sm.sem[ls][0], ta);
+            top2_store(&sm.sk1[ls][1], &sm.so2[ls][1], &sm.sem[ls][1], tb);
+        } else {
+            acc_merge(acc[2 * (sf + ls)], ta);
+            acc_merge(acc[2 * (sf + ls) + 1], tb);
+        }
+    };
+    int w0 = 0, w1 = 0;
+#pragma unroll
+    for (int k = 0; k < kItems; k++) {
+        int c = 3;
+        if (pk[k] != 3) {
+            int ls = pk[k] >> 2;
+            const Geo2 g = geo(ls);
+            float x = pxy[k].x, y = pxy[k].y;
+            c = 2;
+            if (FIRST) {
+                if (x == g.e0x && y == g.e0y) atomicMin(&H->a_idx, pidx[k]);
+                if (x == g.qx && y == g.qy) atomicMin(&H->b_idx, pidx[k]);
+            }
+            if (pidx[k] != g.q_idx) {  // the apex itself joins the hull
+                float d, e;
+                orient_value<P>(g.e0x, g.e0y, g.qx, g.qy, x, y, d, e);
+                if (orient_sign<P>(d, e, g.e0x, g.e0y, g.qx, g.qy, x, y, fallbacks) > 0) {
+                    c = 0;
+                } else {
+                    orient_value<P>(g.qx, g.qy, g.e1x, g.e1y, x, y, d, e);
+                    if (orient_sign<P>(d, e, g.qx, g.qy, g.e1x, g.e1y, x, y, fallbacks) > 0) c = 1;
+                }
+                if (c < 2) {
+                    if (!SINGLE && ls != cur) {
+                        flush(cur);
+                        ta = {0ull, 0u, 0u};
+                        tb = {0ull, 0u, 0u};
+                    }
+                    cur = ls;
+                    // the distance to the child edge is the classification value
+                    unsigned long long key = dist_key(d, pidx[k]);
+                    if (c == 0) top2_add(ta, key, __float_as_uint(e));
+                    else top2_add(tb, key, __float_as_uint(e));
+                }
+            }
+            pk[k] = (ls << 2) | c;
+        }
+        w0 += __popc(__ballot_sync(0xffffffffu, c == 0));
+        w1 += __popc(__ballot_sync(0xffffffffu, c == 1));
+    }
+    if (lane == 0) {
+        sm.wt0[warp] = w0;
+        sm.wt1[warp] = w1;
+    }
+    // warp-aggregated key flush when the warp ends in one segment
+    {
+        int lmax = SINGLE ? 0 : (int)__reduce_max_sync(0xffffffffu, (unsigned)(cur + 1)) - 1;
+        bool same = SINGLE || __all_sync(0xffffffffu, cur == lmax || cur == -1);
+        if (same && lmax >= 0) {
+            top2_warp(ta);
+            top2_warp(tb);
+            if (lane == 0) flush(lmax);
+        } else {
+            flush(cur);
+        }
+    }
+    __syncthreads();
+    int base0 = 0, base1 = 0, tot0 = 0, tot1 = 0;
+#pragma unroll
+    for (int w = 0; w < kBlock / 32; w++) {
+        int a = sm.wt0[w], b = sm.wt1[w];
+        base0 += (w < warp) ? a : 0;
+        base1 += (w < warp) ? b : 0;
+        tot0 += a;
+        tot1 += b;
+    }
+    if (!SINGLE) {
+        // tile-local prefix at each segment start
+        int r0 = base0, r1 = base1;
+#pragma unroll
+        for (int k = 0; k < kItems; k++) {
+            int c = pk[k] & 3;
+            unsigned b0 = __ballot_sync(0xffffffffu, c == 0);
+            unsigned b1 = __ballot_sync(0xffffffffu, c == 1);
+            int ls = pk[k] >> 2;
+            int v = wbase + k * 32 + lane;
+            if (c != 3 && ls > 0 && sm.vstart_l[ls] == v) {
+                sm.sb0[ls] = (unsigned short)(r0 + __popc(b0 & lt));
+                sm.sb1[ls] = (unsigned short)(r1 + __popc(b1 & lt));
+            }
+            r0 += __popc(b0);
+            r1 += __popc(b1);
+        }
+        if (threadIdx.x == 0) {
+            sm.sb0[0] = 0;
+            sm.sb1[0] = 0;
+        }
+        __syncthreads();
+    }
+    // ---- global bases: one atomic per (tile, segment, child)
+    for (int i = threadIdx.x; i < 2 * m; i += blockDim.x) {
+        int ls = i >> 1, c = i & 1;
+        int cnt;
+        if (SINGLE) cnt = c ? tot1 : tot0;
+        else if (c == 0) cnt = ((ls + 1 < m) ? sm.sb0[ls + 1] : tot0) - sm.sb0[ls];
+        else cnt = ((ls + 1 < m) ? sm.sb1[ls + 1] : tot1) - sm.sb1[ls];
+        int g = cnt ? (int)atomicAdd(&acc[2 * (sf + ls) + c].cnt, (unsigned)cnt) : 0;
+        if (c == 0) sm.gb0[ls] = g;
+        else sm.gb1[ls] = g;
+    }
+    __syncthreads();
+    // ---- scatter survivors
+    {
+        int r0 = base0, r1 = base1;
+#pragma unroll
+        for (int k = 0; k < kItems; k++) {
+            int c = pk[k] & 3;
+            unsigned b0 = __ballot_sync(0xffffffffu, c == 0);
+            unsigned b1 = __ballot_sync(0xffffffffu, c == 1);
+            int pre0 = r0 + __popc(b0 & lt), pre1 = r1 + __popc(b1 & lt);
+            r0 += __popc(b0);
+            r1 += __popc(b1);
+            if (c > 1) continue;
+            int ls = pk[k] >> 2;
+            int dst;
+            if (SINGLE) {
+                if (c == 0) dst = g0.pstart + sm.gb0[0] + pre0;
+                else dst = g0.pstart + g0.len - 1 - (sm.gb1[0] + pre1);
+            } else {
+                int ps, ln;
+                if (ls < kGeoCache) {
+                    ps = sm.geo[ls].pstart;
+                    ln = sm.geo[ls].len;
+                } else {
+                    ps = seg[sf + ls].pstart;
+                    ln = seg[sf + ls].len;
+                }
+                if (c == 0) dst = ps + sm.gb0[ls] + (pre0 - sm.sb0[ls]);
+                else dst = ps + ln - 1 - (sm.gb1[ls] + (pre1 - sm.sb1[ls]));
+            }
+            oxy[dst] = pxy[k];
+            oi[dst] = pidx[k];
+        }
+    }
 }
 
 template <class P, bool FIRST>
-__device__ void pass2d(const Params2 &A, int par, SmemPass &sm)
+__device__ void pass2d(const Params2 &A, int par, SmemPass &sm, int bid, int nb)
 {
     Hdr2 *H = A.hdr;
     const int L = FIRST ? A.n : vload_i(&H->L[par]);
     const int S = FIRST ? 1 : vload_i(&H->S[par]);
     const Seg2 *seg = A.seg[par];
     Acc2 *acc = A.acc[par];
-    float *ox = A.bx[par], *oy = A.by[par];
-    int *oi = A.bi[par];
-    const float *ix = A.bx[par ^ 1], *iy = A.by[par ^ 1];
-    const int *ii = A.bi[par ^ 1];
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned lt = lanemask_lt();
     unsigned fallbacks = 0;
     const int ntiles = (L + kTile - 1) / kTile;
     // a contiguous run of tiles per block keeps consecutive tiles in the same
     // segment, so farthest-point keys are carried across tiles in shared memory
-    const int per = ntiles / gridDim.x, rem = ntiles % gridDim.x;
-    const int t_begin = blockIdx.x * per + min((int)blockIdx.x, rem);
-    const int t_end = t_begin + per + ((int)blockIdx.x < rem ? 1 : 0);
-    if (threadIdx.x == 0) sm.carry_seg = -1;
-
+    const int per = ntiles / nb, rem = ntiles % nb;
+    const int t_begin = bid * per + min(bid, rem);
+    const int t_end = t_begin + per + (bid < rem ? 1 : 0);
+    if (threadIdx.x == 0) {
+        sm.carry_seg = -1;
+        sm.par = par;
+    }
     for (int tile = t_begin; tile < t_end; tile++) {
         const int v0 = tile * kTile;
         const int v1 = min(v0 + kTile, L);
         __syncthreads();  // shared memory of the previous tile is free
         if (threadIdx.x == 0) {
             int sf = FIRST ? 0 : A.tile_seg[tile];
+            int mm = FIRST ? 1 : A.tile_m[tile];
             int cs = sm.carry_seg;
             if (cs >= 0 && cs != sf) {
                 // the carried segment ended in the previous tile
-                acc_merge(acc[2 * cs], sm.ck1[0], sm.ck2[0], sm.cem[0]);
-                acc_merge(acc[2 * cs + 1], sm.ck1[1], sm.ck2[1], sm.cem[1]);
+                acc_merge(acc[2 * cs], sm.carry[0]);
+                acc_merge(acc[2 * cs + 1], sm.carry[1]);
                 sm.carry_seg = -1;
             }
             sm.sfirst = sf;
+            sm.m = mm;
         }
         __syncthreads();
-        const int sf = sm.sfirst;
-        for (int i = threadIdx.x; i < kKeySeg * 2; i += blockDim.x) {
+        const int sf = sm.sfirst, m = sm.m;
+        const bool carry = sm.carry_seg == sf;
+        for (int i = threadIdx.x; i < 2 * min(m, kKeySeg); i += blockDim.x) {
             int ls = i >> 1, c = i & 1;
-            bool carry = (ls == 0 && sm.carry_seg == sf);
-            sm.sk1[ls][c] = carry ? sm.ck1[c] : 0ull;
-            sm.sk2[ls][c] = carry ? sm.ck2[c] : 0ull;
-            sm.sem[ls][c] = carry ? sm.cem[c] : 0u;
+            bool cin = carry && ls == 0;
+            sm.sk1[ls][c] = cin ? sm.carry[c].k1 : 0ull;
+            sm.so2[ls][c] = cin ? sm.carry[c].o2 : 0u;
+            sm.sem[ls][c] = cin ? sm.carry[c].em : 0u;
         }
-        // ---- segments overlapping the tile and their geometry
-        int m = 0;
-        for (int base = 0; base < kTile; base += kBlock) {
-            int s = sf + base + threadIdx.x;
-            int vs = INT_MAX;
-            if (FIRST) vs = (s == 0) ? 0 : INT_MAX;
-            else if (s < S) vs = seg[s].vstart;
-            bool in = vs < v1;
-            if (in) sm.vstart_l[base + threadIdx.x] = vs;
-            int c = __syncthreads_count(in);
-            m += c;
-            if (c < kBlock) break;
-        }
+        if (m > 1)
+            for (int i = threadIdx.x; i < m; i += blockDim.x) sm.vstart_l[i] = seg[sf + i].vstart;
         if (threadIdx.x < min(m, kGeoCache)) {
             Geo2 g;
             if (FIRST) {
@@ -323,236 +589,29 @@ __device__ void pass2d(const Params2 &A, int par, SmemPass &sm)
             sm.geo[threadIdx.x] = g;
         }
         __syncthreads();
-
-        // ---- load and classify (state per item: x, y, idx, ls<<2 | class)
-        float px[kItems], py[kItems];
-        int pidx[kItems], pk[kItems];
-        const int wbase = v0 + warp * 32 * kItems;
-#pragma unroll
-        for (int k = 0; k < kItems; k++) {
-            int v = wbase + k * 32 + lane;
-            pk[k] = 3;  // class 3 = no element
-            if (v < v1) {
-                int ls = 0;
-                if (m > 1) {
-                    int lo = 0, hi = m - 1;
-                    while (lo < hi) {
-                        int mid = (lo + hi + 1) >> 1;
-                        if (sm.vstart_l[mid] <= v) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    ls = lo;
-                }
-                pk[k] = (ls << 2) | 2;
-                if (FIRST) {
-                    px[k] = __ldg(A.x + (long long)v * A.stride);
-                    py[k] = __ldg(A.y + (long long)v * A.stride);
-                    pidx[k] = v;
-                } else {
-                    int ps, vs;
-                    if (ls < kGeoCache) {
-                        ps = sm.geo[ls].pstart;
-                        vs = sm.geo[ls].vstart;
-                    } else {
-                        ps = seg[sf + ls].pstart;
-                        vs = seg[sf + ls].vstart;
-                    }
-                    int pos = ps + (v - vs);
-                    px[k] = ix[pos];
-                    py[k] = iy[pos];
-                    pidx[k] = ii[pos];
-                }
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < kItems; k++) {
-            if ((pk[k] & 3) != 2) continue;
-            int ls = pk[k] >> 2;
-            const Geo2 g = tile_geo<FIRST>(sm, seg, sf, ls);
-            float x = px[k], y = py[k];
-            if (FIRST) {
-                if (x == g.e0x && y == g.e0y) atomicMin(&H->a_idx, pidx[k]);
-                if (x == g.qx && y == g.qy) atomicMin(&H->b_idx, pidx[k]);
-            }
-            if (pidx[k] == g.q_idx) continue;  // the apex joins the hull
-            float d, e;
-            orient_value<P>(g.e0x, g.e0y, g.qx, g.qy, x, y, d, e);
-            if (orient_sign<P>(d, e, g.e0x, g.e0y, g.qx, g.qy, x, y, fallbacks) > 0) {
-                pk[k] = (ls << 2) | 0;
-                continue;
-            }
-            orient_value<P>(g.qx, g.qy, g.e1x, g.e1y, x, y, d, e);
-            if (orient_sign<P>(d, e, g.qx, g.qy, g.e1x, g.e1y, x, y, fallbacks) > 0)
-                pk[k] = (ls << 2) | 1;
-        }
-
-        // ---- tile-local ranks from warp ballots (kept in shared memory)
-        {
-            int w0 = 0, w1 = 0;
-#pragma unroll
-            for (int k = 0; k < kItems; k++) {
-                unsigned b0 = __ballot_sync(0xffffffffu, (pk[k] & 3) == 0);
-                unsigned b1 = __ballot_sync(0xffffffffu, (pk[k] & 3) == 1);
-                if (lane == 0) {
-                    sm.bal0[warp][k] = b0;
-                    sm.bal1[warp][k] = b1;
-                }
-                w0 += __popc(b0);
-                w1 += __popc(b1);
-            }
-            if (lane == 0) {
-                sm.wt0[warp] = w0;
-                sm.wt1[warp] = w1;
-            }
-        }
+        if (m == 1) pass_tile<P, FIRST, true>(A, sm, seg, acc, sf, m, v0, v1, fallbacks);
+        else pass_tile<P, FIRST, false>(A, sm, seg, acc, sf, m, v0, v1, fallbacks);
         __syncthreads();
-        int base0 = 0, base1 = 0, tot0 = 0, tot1 = 0;
-#pragma unroll
-        for (int w = 0; w < kBlock / 32; w++) {
-            int a = sm.wt0[w], b = sm.wt1[w];
-            base0 += (w < warp) ? a : 0;
-            base1 += (w < warp) ? b : 0;
-            tot0 += a;
-            tot1 += b;
-        }
-        {
-            int r0 = base0, r1 = base1;
-#pragma unroll
-            for (int k = 0; k < kItems; k++) {
-                unsigned b0 = sm.bal0[warp][k], b1 = sm.bal1[warp][k];
-                int ls = pk[k] >> 2;
-                int v = wbase + k * 32 + lane;
-                if ((pk[k] & 3) != 3 && ls > 0 && sm.vstart_l[ls] == v) {
-                    sm.sb0[ls] = (unsigned short)(r0 + __popc(b0 & lt));
-                    sm.sb1[ls] = (unsigned short)(r1 + __popc(b1 & lt));
-                }
-                r0 += __popc(b0);
-                r1 += __popc(b1);
-            }
-        }
-        if (threadIdx.x == 0) {
-            sm.sb0[0] = 0;
-            sm.sb1[0] = 0;
-        }
-        __syncthreads();
-        // ---- global bases: one atomic per (tile, segment, child)
-        for (int ls = threadIdx.x; ls < m; ls += blockDim.x) {
-            int e0 = (ls + 1 < m) ? sm.sb0[ls + 1] : tot0;
-            int e1 = (ls + 1 < m) ? sm.sb1[ls + 1] : tot1;
-            int c0 = e0 - sm.sb0[ls], c1 = e1 - sm.sb1[ls];
-            int s = sf + ls;
-            sm.gb0[ls] = c0 ? (int)atomicAdd(&acc[2 * s].cnt, (unsigned)c0) : 0;
-            sm.gb1[ls] = c1 ? (int)atomicAdd(&acc[2 * s + 1].cnt, (unsigned)c1) : 0;
-        }
-        __syncthreads();
-        // ---- scatter survivors and reduce farthest-point keys
-        int cur = -1;
-        unsigned long long k1a = 0, k2a = 0, k1b = 0, k2b = 0;
-        unsigned ema = 0, emb = 0;
-        auto flush = [&](int ls) {
-            if (ls < 0) return;
-            if (ls < kKeySeg) {
-                if (k1a) {
-                    top2_insert(&sm.sk1[ls][0], &sm.sk2[ls][0], k1a);
-                    top2_insert(&sm.sk1[ls][0], &sm.sk2[ls][0], k2a);
-                    atomicMax(&sm.sem[ls][0], ema);
-                }
-                if (k1b) {
-                    top2_insert(&sm.sk1[ls][1], &sm.sk2[ls][1], k1b);
-                    top2_insert(&sm.sk1[ls][1], &sm.sk2[ls][1], k2b);
-                    atomicMax(&sm.sem[ls][1], emb);
-                }
-            } else {
-                int s = sf + ls;
-                acc_merge(acc[2 * s], k1a, k2a, ema);
-                acc_merge(acc[2 * s + 1], k1b, k2b, emb);
-            }
-        };
-        {
-            int r0 = base0, r1 = base1;
-#pragma unroll
-            for (int k = 0; k < kItems; k++) {
-                unsigned b0 = sm.bal0[warp][k], b1 = sm.bal1[warp][k];
-                int c = pk[k] & 3;
-                int pre0 = r0 + __popc(b0 & lt), pre1 = r1 + __popc(b1 & lt);
-                r0 += __popc(b0);
-                r1 += __popc(b1);
-                if (c > 1) continue;
-                int ls = pk[k] >> 2;
-                const Geo2 g = tile_geo<FIRST>(sm, seg, sf, ls);
-                int dst;
-                if (c == 0) dst = g.pstart + sm.gb0[ls] + (pre0 - sm.sb0[ls]);
-                else dst = g.pstart + g.len - 1 - (sm.gb1[ls] + (pre1 - sm.sb1[ls]));
-                ox[dst] = px[k];
-                oy[dst] = py[k];
-                oi[dst] = pidx[k];
-                if (ls != cur) {
-                    flush(cur);
-                    cur = ls;
-                    k1a = k2a = k1b = k2b = 0;
-                    ema = emb = 0;
-                }
-                // the distance to the child edge is the classification value
-                float d, e;
-                if (c == 0) orient_value<P>(g.e0x, g.e0y, g.qx, g.qy, px[k], py[k], d, e);
-                else orient_value<P>(g.qx, g.qy, g.e1x, g.e1y, px[k], py[k], d, e);
-                unsigned long long key = dist_key(d, pidx[k]);
-                unsigned eb = __float_as_uint(e);
-                if (c == 0) {
-                    top2_merge(k1a, k2a, key, 0ull);
-                    ema = eb > ema ? eb : ema;
-                } else {
-                    top2_merge(k1b, k2b, key, 0ull);
-                    emb = eb > emb ? eb : emb;
-                }
-            }
-        }
-        // warp-aggregated flush when the warp ends in one segment
-        {
-            int lmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)(cur + 1)) - 1;
-            bool same = __all_sync(0xffffffffu, cur == lmax || cur == -1);
-            if (same && lmax >= 0) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    unsigned long long a1 = __shfl_xor_sync(0xffffffffu, k1a, o);
-                    unsigned long long a2 = __shfl_xor_sync(0xffffffffu, k2a, o);
-                    unsigned long long c1 = __shfl_xor_sync(0xffffffffu, k1b, o);
-                    unsigned long long c2 = __shfl_xor_sync(0xffffffffu, k2b, o);
-                    top2_merge(k1a, k2a, a1, a2);
-                    top2_merge(k1b, k2b, c1, c2);
-                }
-                ema = __reduce_max_sync(0xffffffffu, ema);
-                emb = __reduce_max_sync(0xffffffffu, emb);
-                if (lane == 0) flush(lmax);
-            } else {
-                flush(cur);
-            }
-        }
-        __syncthreads();
-        // ---- merge the key slots of segments that end in this tile; the
-        // last segment is carried to the next tile of this block
+        // ---- merge the key slots of segments that end in this tile; the last
+        // segment is carried to the next tile of this block
         const int mk = min(m, kKeySeg);
         for (int i = threadIdx.x; i < 2 * mk; i += blockDim.x) {
             int ls = i >> 1, c = i & 1;
-            if (ls == m - 1) {
-                sm.ck1[c] = sm.sk1[ls][c];
-                sm.ck2[c] = sm.sk2[ls][c];
-                sm.cem[c] = sm.sem[ls][c];
-                continue;
-            }
-            acc_merge(acc[2 * (sf + ls) + c], sm.sk1[ls][c], sm.sk2[ls][c], sm.sem[ls][c]);
+            Top2 t = {sm.sk1[ls][c], sm.so2[ls][c], sm.sem[ls][c]};
+            if (ls == m - 1) sm.carry[c] = t;
+            else acc_merge(acc[2 * (sf + ls) + c], t);
         }
         if (threadIdx.x == 0) sm.carry_seg = (m - 1 < kKeySeg) ? sf + m - 1 : -1;
     }
     __syncthreads();
     if (threadIdx.x == 0 && sm.carry_seg >= 0) {
         int cs = sm.carry_seg;
-        acc_merge(acc[2 * cs], sm.ck1[0], sm.ck2[0], sm.cem[0]);
-        acc_merge(acc[2 * cs + 1], sm.ck1[1], sm.ck2[1], sm.cem[1]);
+        acc_merge(acc[2 * cs], sm.carry[0]);
+        acc_merge(acc[2 * cs + 1], sm.carry[1]);
     }
     // predicate fallback statistics
     unsigned f = __reduce_add_sync(0xffffffffu, fallbacks);
-    if (lane == 0 && f) atomicAdd(&H->fallbacks, (unsigned long long)f);
+    if ((threadIdx.x & 31) == 0 && f) atomicAdd(&H->fallbacks, (unsigned long long)f);
 }
 
 // ---------------------------------------------------------------- update
@@ -637,7 +696,7 @@ __device__ void update2d(const Params2 &A, int par, bool first, SmemU &sm)
             float em = __uint_as_float(a.emax);
             float d1 = key_dist(a.key1);
             if (cnt > 1) {
-                float d2 = key_dist(a.key2);
+                float d2 = unord_f32(a.o2);
                 double gap = ((double)d1 - (double)d2) * (1.0 - 0x1p-50);
                 cert = gap > 2.0 * (double)em;
             }
@@ -663,10 +722,9 @@ __device__ void update2d(const Params2 &A, int par, bool first, SmemU &sm)
     }
     const int S_new = (int)carry_k, L_new = (int)carry_v;
     __syncthreads();
-    // tile -> first segment map for the next pass
+    // tile -> (first segment, number of segments) map for the next pass
     const int ntiles = (L_new + kTile - 1) / kTile;
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-        int v = t * kTile;
+    auto seg_of = [&](int v) {
         int lo = 0, hi = S_new - 1;
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
@@ -674,7 +732,14 @@ __device__ void update2d(const Params2 &A, int par, bool first, SmemU &sm)
             if (vs <= v) lo = mid;
             else hi = mid - 1;
         }
-        A.tile_seg[t] = lo;
+        return lo;
+    };
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        int v = t * kTile;
+        int vl = min(v + kTile, L_new) - 1;
+        int s0 = seg_of(v);
+        A.tile_seg[t] = s0;
+        A.tile_m[t] = seg_of(vl) - s0 + 1;
     }
     if (threadIdx.x == 0) {
         H->S[par ^ 1] = S_new;
@@ -691,21 +756,22 @@ __device__ void update2d(const Params2 &A, int par, bool first, SmemU &sm)
 // Farthest point of each uncertified segment with exact comparisons
 // (largest distance, then lowest index), one block per segment.
 template <class P>
-__device__ void exact2d(const Params2 &A, int par, SmemX &sm)
+__device__ void exact2d(const Params2 &A, int par, SmemX &sm, int bid, int nb)
 {
     Hdr2 *H = A.hdr;
     const int nu = *(volatile int *)&H->n_uncert;
     Seg2 *sn = A.seg[par ^ 1];
-    const float *bx = A.bx[par], *by = A.by[par];
+    const float2 *bxy = A.bxy[par];
     const int *bi = A.bi[par];
-    for (int u = blockIdx.x; u < nu; u += gridDim.x) {
+    for (int u = bid; u < nu; u += nb) {
         const int k = A.uncert[u];
         const Seg2 g = sn[k];
         int best = -1;
         float bxv = 0.f, byv = 0.f;
         for (int i = threadIdx.x; i < g.len; i += blockDim.x) {
             int pos = g.pstart + i;
-            float x = bx[pos], y = by[pos];
+            float2 p = bxy[pos];
+            float x = p.x, y = p.y;
             int idx = bi[pos];
             float d, e;
             orient_value<P>(g.e0x, g.e0y, g.e1x, g.e1y, x, y, d, e);
@@ -871,11 +937,19 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_persistent(Params2 A)
     // phase clock (block 0, thread 0): time from one barrier exit to the next
     const bool clk = blockIdx.x == 0 && threadIdx.x == 0;
     unsigned long long tprev = clk ? globaltimer_ns() : 0;
+    int it = 0;  // iteration being recorded (0 = first split)
     auto sync_as = [&](int cat) {
         grid_sync(&H->bar, fail, A.wait_ns);
         if (clk) {
             unsigned long long t = globaltimer_ns();
             H->phase_ns[cat] += t - tprev;
+            if (it < kTimeline && cat < 2) {
+                H->tl[it][2 + cat] += (long long)(t - tprev);
+                if (cat == 0) {
+                    H->tl[it][0] = *(volatile int *)&H->L[it & 1];
+                    H->tl[it][1] = *(volatile int *)&H->S[it & 1];
+                }
+            }
             tprev = t;
         }
     };
@@ -886,7 +960,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_persistent(Params2 A)
     if (*(volatile int *)&H->nonfinite) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(H, kStNonfinite);
     } else if (*(volatile int *)&H->status == 0) {
-        pass2d<P, true>(A, 0, sm.pass);
+        pass2d<P, true>(A, 0, sm.pass, blockIdx.x, gridDim.x);
         sync_as(0);
         int t = 0;
         while (*(volatile int *)&H->status == 0) {
@@ -894,7 +968,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_persistent(Params2 A)
             sync_as(1);
             if (*(volatile int *)&H->status) break;
             if (*(volatile int *)&H->n_uncert > 0) {
-                exact2d<P>(A, t & 1, sm.x);
+                exact2d<P>(A, t & 1, sm.x, blockIdx.x, gridDim.x);
                 sync_as(2);
             }
             if (*(volatile int *)&H->S[(t + 1) & 1] == 0) break;
@@ -904,7 +978,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_persistent(Params2 A)
                 break;
             }
             if (blockIdx.x == 0 && threadIdx.x == 0) H->iter = t;
-            pass2d<P, false>(A, t & 1, sm.pass);
+            it = t;
+            pass2d<P, false>(A, t & 1, sm.pass, blockIdx.x, gridDim.x);
             sync_as(0);
         }
     }
@@ -923,7 +998,7 @@ template <class P, bool FIRST>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_pass2d(Params2 A, int par)
 {
     __shared__ SmemAll sm;
-    pass2d<P, FIRST>(A, par, sm.pass);
+    pass2d<P, FIRST>(A, par, sm.pass, blockIdx.x, gridDim.x);
 }
 __global__ void __launch_bounds__(kBlock) k_update2d(Params2 A, int par, int first, int iter)
 {
@@ -935,7 +1010,7 @@ template <class P>
 __global__ void __launch_bounds__(kBlock) k_exact2d(Params2 A, int par)
 {
     __shared__ SmemAll sm;
-    exact2d<P>(A, par, sm.x);
+    exact2d<P>(A, par, sm.x, blockIdx.x, gridDim.x);
 }
 __global__ void __launch_bounds__(kBlock) k_output2d(Params2 A, int nonfinite_check)
 {
@@ -947,7 +1022,7 @@ __global__ void __launch_bounds__(kBlock) k_output2d(Params2 A, int nonfinite_ch
 
 // ---------------------------------------------------------------- host side
 struct Layout2 {
-    size_t hdr, bx[2], by[2], bi[2], seg[2], acc[2], tile_seg, uncert, hull_idx, hull_x, hull_y,
+    size_t hdr, bxy[2], bi[2], seg[2], acc[2], tile_seg, tile_m, uncert, hull_idx, hull_x, hull_y,
         next, res, total;
     int cap_seg;
 };
@@ -971,13 +1046,13 @@ static Layout2 layout2d(int64_t n)
     L.hdr = take(sizeof(Hdr2));
     L.res = take(sizeof(qh_result));
     for (int b = 0; b < 2; b++) {
-        L.bx[b] = take(np * 4);
-        L.by[b] = take(np * 4);
+        L.bxy[b] = take(np * 8);
         L.bi[b] = take(np * 4);
     }
     for (int b = 0; b < 2; b++) L.seg[b] = take((size_t)L.cap_seg * sizeof(Seg2));
     for (int b = 0; b < 2; b++) L.acc[b] = take((size_t)2 * L.cap_seg * sizeof(Acc2));
     L.tile_seg = take((np / kTile + 2) * 4);
+    L.tile_m = take((np / kTile + 2) * 4);
     L.uncert = take((size_t)L.cap_seg * 4);
     L.hull_idx = take((np + 2) * 4);
     L.hull_x = take((np + 2) * 4);
@@ -1000,13 +1075,13 @@ static Params2 make_params(const float *x, const float *y, int64_t n, int64_t st
     A.res = res;
     A.hdr = (Hdr2 *)(ws + L.hdr);
     for (int b = 0; b < 2; b++) {
-        A.bx[b] = (float *)(ws + L.bx[b]);
-        A.by[b] = (float *)(ws + L.by[b]);
+        A.bxy[b] = (float2 *)(ws + L.bxy[b]);
         A.bi[b] = (int *)(ws + L.bi[b]);
         A.seg[b] = (Seg2 *)(ws + L.seg[b]);
         A.acc[b] = (Acc2 *)(ws + L.acc[b]);
     }
     A.tile_seg = (int *)(ws + L.tile_seg);
+    A.tile_m = (int *)(ws + L.tile_m);
     A.uncert = (int *)(ws + L.uncert);
     A.hull_idx = (int *)(ws + L.hull_idx);
     A.hull_x = (float *)(ws + L.hull_x);
@@ -1103,6 +1178,28 @@ extern "C" qh_status qh_hull2d_async(const float *d_x, const float *d_y, int64_t
     Params2 A = make_params(d_x, d_y, n, stride, d_out_idx, d_result, (char *)d_ws, L, o);
     if (o.pred_mode == QH_PRED_F32) return run2d<PredF32>(A, o, stream);
     return run2d<PredF64>(A, o, stream);
+}
+
+extern "C" qh_status qh_debug_timeline_2d(const void *d_ws, int64_t n, int64_t *h_rows,
+                                          int32_t max_rows, int32_t *h_nrows, cudaStream_t stream)
+{
+    if (!d_ws || !h_rows || !h_nrows || max_rows < 0 || n < 0 || n > QH_MAX_POINTS)
+        return QH_ERR_INVALID_ARG;
+    Layout2 L = layout2d(n);
+    Hdr2 hh;
+    if (cudaMemcpyAsync(&hh, (const char *)d_ws + L.hdr, sizeof(Hdr2), cudaMemcpyDeviceToHost,
+                        stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return QH_ERR_CUDA;
+    int rows = hh.iter + 1;
+    if (rows > kTimeline) rows = kTimeline;
+    if (rows > max_rows) rows = max_rows;
+    for (int r = 0; r < rows; r++) {
+        h_rows[5 * r + 0] = r;
+        for (int c = 0; c < 4; c++) h_rows[5 * r + 1 + c] = hh.tl[r][c];
+    }
+    *h_nrows = rows;
+    return QH_OK;
 }
 
 extern "C" qh_status qh_hull2d(const float *d_x, const float *d_y, int64_t n, int64_t stride,
