@@ -144,6 +144,29 @@ qh_status qh_hull2d(const float *d_x, const float *d_y, int64_t n, int64_t strid
                     int32_t *d_out_idx, int64_t *h_count, qh_result *h_result, void *d_ws,
                     size_t ws_bytes, const qh_opts *opts, cudaStream_t stream);
 
+/*
+ * qh_hull2d_noalloc: qh_hull2d for callers that cannot allocate device
+ * memory while they run: plugins whose host owns every device allocation,
+ * real-time loops that allocate only at start-up, and code that may not let
+ * cudaMalloc/cudaFree synchronise the device.  (The paper has no
+ * counterpart; this is an interface convenience.)
+ *
+ * Same inputs, output and result order as qh_hull2d, but no workspace
+ * argument: the scratch is one fixed array of 32 MiB in device memory that
+ * every device holds once the library is loaded on it, until the process
+ * exits.  n may not exceed QH_NOALLOC_MAX_POINTS; larger n returns
+ * QH_ERR_INVALID_ARG without touching the device.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Every call on a device shares the array: calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  Nothing here calls cudaMalloc, cudaFree or an allocating library
+ * routine.  Synchronises `stream`.
+ */
+#define QH_NOALLOC_MAX_POINTS ((int64_t)131072)
+qh_status qh_hull2d_noalloc(const float *d_x, const float *d_y, int64_t n, int64_t stride,
+                            int32_t *d_out_idx, int64_t *h_count, cudaStream_t stream);
+
 /* ---------------------------------------------------------------------- */
 /* Diagnostics                                                             */
 /* ---------------------------------------------------------------------- */

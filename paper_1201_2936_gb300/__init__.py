@@ -120,6 +120,26 @@ def debug_timeline_2d(workspace: Workspace, n: int, stream=None):
     return rows[: nr.value]
 
 
+NOALLOC_MAX_POINTS = 131072
+
+
+def hull2d_noalloc(x: torch.Tensor, y: Optional[torch.Tensor] = None, *,
+                   out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """qh_hull2d_noalloc: the 2D hull with the library's fixed device scratch
+    (no workspace; n <= NOALLOC_MAX_POINTS).  For callers that cannot
+    allocate device memory while they run; calls on one device must not
+    overlap."""
+    xp, yp, n, stride, dev = _points_2d(x, y)
+    if out is None:
+        out = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    cnt = ctypes.c_int64(0)
+    st = _native.lib().qh_hull2d_noalloc(xp, yp, n, stride, out.data_ptr(), ctypes.byref(cnt),
+                                         _stream_handle(stream))
+    if st != 0:
+        raise QHError(st, "qh_hull2d_noalloc")
+    return out[: cnt.value]
+
+
 def result_from_tensor(result: torch.Tensor) -> QhResult:
     raw = bytes(result.cpu().numpy().tobytes())
     return QhResult.from_buffer_copy(raw[:RESULT_BYTES])

@@ -36,6 +36,7 @@
 #include <climits>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "pred2.cuh"
 #include "qh_common.cuh"
@@ -1178,6 +1179,43 @@ extern "C" qh_status qh_hull2d_async(const float *d_x, const float *d_y, int64_t
     Params2 A = make_params(d_x, d_y, n, stride, d_out_idx, d_result, (char *)d_ws, L, o);
     if (o.pred_mode == QH_PRED_F32) return run2d<PredF32>(A, o, stream);
     return run2d<PredF64>(A, o, stream);
+}
+
+// ---------------------------------------------------------------- no-alloc variant
+// Scratch for qh_hull2d_noalloc: a fixed array in device memory, created when
+// the module is loaded on a device and kept until the process exits.  Host
+// code may not use the symbol as a pointer; its device address is looked up
+// once per device with cudaGetSymbolAddress.
+constexpr size_t kNoAllocBytes = (size_t)32 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64];
+}  // namespace
+
+extern "C" qh_status qh_hull2d_noalloc(const float *d_x, const float *d_y, int64_t n, int64_t stride,
+                                       int32_t *d_out_idx, int64_t *h_count, cudaStream_t stream)
+{
+    if (n < 0 || n > QH_NOALLOC_MAX_POINTS || stride < 1 || !h_count) return QH_ERR_INVALID_ARG;
+    if (n > 0 && (!d_x || !d_y || !d_out_idx)) return QH_ERR_INVALID_ARG;
+    Layout2 L = layout2d(n);
+    if (L.total > kNoAllocBytes) return QH_ERR_CAPACITY;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return QH_ERR_CUDA;
+    void *ws = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            // first call on this device: resolve the array's device address
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return QH_ERR_CUDA;
+            g_noalloc_ptr[dev] = p;
+        }
+        ws = g_noalloc_ptr[dev];
+    }
+    return qh_hull2d(d_x, d_y, n, stride, d_out_idx, h_count, nullptr, ws, kNoAllocBytes, nullptr,
+                     stream);
 }
 
 extern "C" qh_status qh_debug_timeline_2d(const void *d_ws, int64_t n, int64_t *h_rows,
