@@ -35,9 +35,11 @@ UNIT = "Mpoints/s"
 N_PER_CLOUD = 16 * 1024 * 1024
 WORKLOAD = ("2D at scale: 3 x 16M float32 points (uniform unit square, uniform unit disk, "
             "unit circle with N(0,1e-4) radial jitter), FP32-filtered exact predicates")
-# dram bytes (read + write) per launch of the persistent kernel from one ncu
-# capture, keyed by the sha256 of the kernel sources they were taken on
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per algorithmic byte of the persistent kernel from one
+# ncu capture of a smaller case (8M-point circle, profiles/qh2d_persistent_circle8M_full.md),
+# keyed by the sha256 of the kernel sources it was taken on; the bench scales it
+# by its own algorithmic bytes per launch.  Absent for any other source state.
+NCU_TRAFFIC = {"322f73970cb75161": 1082.6 / 1310.7}
 
 
 def kernel_sources_sha() -> str:
@@ -281,7 +283,8 @@ def main():
     ms_tot = sum(m for _, m in ach)
     achieved = algo_tot / (ms_tot / 1e3) / 1e9
     sha = kernel_sources_sha()
-    traffic = NCU_TRAFFIC.get(sha)
+    ratio = NCU_TRAFFIC.get(sha)
+    traffic = round(ratio * algo_tot / nl) if ratio else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                 "traffic": traffic, "kernel": "qh2d_persistent<PredF32>",
