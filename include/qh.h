@@ -144,6 +144,41 @@ qh_status qh_hull2d(const float *d_x, const float *d_y, int64_t n, int64_t strid
                     int32_t *d_out_idx, int64_t *h_count, qh_result *h_result, void *d_ws,
                     size_t ws_bytes, const qh_opts *opts, cudaStream_t stream);
 
+/* ---------------------------------------------------------------------- */
+/* 3D                                                                      */
+/* ---------------------------------------------------------------------- */
+
+/* Bytes of device workspace qh_hull3d needs for n points
+ * (n <= QH_MAX_POINTS / 8). */
+size_t qh_workspace_bytes_3d(int64_t n, const qh_opts *opts);
+
+/*
+ * qh_hull3d: convex hull of n float32 points in space (Section 4.3, "3D and
+ * Higher Dimensions": first split by a plane through the extrema, then
+ * farthest-point insertion; read as Barber et al.'s Quickhull with several
+ * non-conflicting apexes inserted per iteration).
+ *
+ *  d_x, d_y, d_z  device, coordinate i at d_c[i*stride] (read only)
+ *  d_verts        device int32[max(n,1)]: the hull vertices, increasing index
+ *  h_nv           host: number of vertices
+ *  d_face_off     device int32[2n+1]: CSR offsets of the faces
+ *  d_face_idx     device int32[6n]: face vertex indices; each face is a
+ *                 maximal coplanar polygon, counter-clockwise seen from
+ *                 outside, starting at its smallest index; faces are sorted
+ *                 lexicographically
+ *  h_nf           host: number of faces
+ *  h_result       optional host qh_result (extra[0..2] = vertices, faces,
+ *                 face index total)
+ * Points that do not span 3D (n < 4, collinear, coplanar) give
+ * QH_ERR_DEGENERATE; n = 0 gives QH_OK with no faces.  Only the persistent
+ * loop is available (QH_LOOP_HOST returns QH_ERR_NOT_SUPPORTED).
+ * Synchronises `stream`.
+ */
+qh_status qh_hull3d(const float *d_x, const float *d_y, const float *d_z, int64_t n,
+                    int64_t stride, int32_t *d_verts, int64_t *h_nv, int32_t *d_face_off,
+                    int32_t *d_face_idx, int64_t *h_nf, qh_result *h_result, void *d_ws,
+                    size_t ws_bytes, const qh_opts *opts, cudaStream_t stream);
+
 /*
  * qh_hull2d_noalloc: qh_hull2d for callers that cannot allocate device
  * memory while they run: plugins whose host owns every device allocation,

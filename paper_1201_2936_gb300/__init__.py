@@ -120,6 +120,60 @@ def debug_timeline_2d(workspace: Workspace, n: int, stream=None):
     return rows[: nr.value]
 
 
+def workspace_bytes_3d(n: int, opts: Optional[QhOpts] = None) -> int:
+    return int(_native.lib().qh_workspace_bytes_3d(int(n), ctypes.byref(opts) if opts else None))
+
+
+def _points_3d(x, y, z):
+    if y is None and z is None:
+        t = x
+        if t.dtype != torch.float32 or not t.is_cuda or t.dim() != 2:
+            raise ValueError("points must be a CUDA float32 tensor of shape [n, 3] or [3, n]")
+        if t.shape[1] == 3 and t.stride(1) == 1 and (t.shape[0] <= 1 or t.stride(0) == 3):
+            p = t.data_ptr()
+            return p, p + 4, p + 8, t.shape[0], 3, t.device
+        if t.shape[0] == 3 and t.stride(1) == 1:
+            return t[0].data_ptr(), t[1].data_ptr(), t[2].data_ptr(), t.shape[1], 1, t.device
+        raise ValueError("points must be contiguous [n, 3] or row-contiguous [3, n]")
+    for t in (x, y, z):
+        if t.dtype != torch.float32 or not t.is_cuda or t.dim() != 1 or \
+                (t.numel() > 1 and t.stride(0) != 1):
+            raise ValueError("x, y, z must be contiguous 1-D CUDA float32 tensors")
+    if not (x.shape == y.shape == z.shape):
+        raise ValueError("x, y, z must have the same length")
+    return x.data_ptr(), y.data_ptr(), z.data_ptr(), x.shape[0], 1, x.device
+
+
+def hull3d(x: torch.Tensor, y: Optional[torch.Tensor] = None, z: Optional[torch.Tensor] = None,
+           *, pred: str = "f32", workspace: Optional[Workspace] = None, stream=None,
+           return_result: bool = False):
+    """Convex hull of 3D float32 points on the GPU.
+
+    Returns (vertices, face_offsets, face_indices) as int32 CUDA tensors:
+    sorted vertex indices and the faces as CSR polygons (maximal coplanar
+    faces, counter-clockwise from outside, starting at their smallest index,
+    sorted lexicographically).  Points are [n, 3], [3, n] or x, y, z."""
+    xp, yp, zp, n, stride, dev = _points_3d(x, y, z)
+    o = make_opts(pred, "persistent")
+    if workspace is None:
+        workspace = _default_ws.setdefault(str(dev), Workspace(dev))
+    ws = workspace.get(workspace_bytes_3d(n, o))
+    verts = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    foff = torch.empty(2 * n + 2, dtype=torch.int32, device=dev)
+    fidx = torch.empty(max(6 * n, 1), dtype=torch.int32, device=dev)
+    nv, nf = ctypes.c_int64(0), ctypes.c_int64(0)
+    res = QhResult()
+    st = _native.lib().qh_hull3d(xp, yp, zp, n, stride, verts.data_ptr(), ctypes.byref(nv),
+                                 foff.data_ptr(), fidx.data_ptr(), ctypes.byref(nf),
+                                 ctypes.byref(res), ws.data_ptr(), ws.numel(), ctypes.byref(o),
+                                 _stream_handle(stream))
+    if st != 0:
+        raise QHError(st, "qh_hull3d")
+    off = foff[: nf.value + 1] if nf.value > 0 else foff[:1].zero_()
+    out = (verts[: nv.value], off, fidx[: int(res.extra[2])])
+    return (out, res.as_dict()) if return_result else out
+
+
 NOALLOC_MAX_POINTS = 131072
 
 

@@ -74,7 +74,7 @@ __device__ __forceinline__ int exact_sum_sign(const double (&t)[M])
 }
 
 // Exact sign of (p1 - p2) x (p3 - p4) for float coordinates.
-__device__ __noinline__ int cross_diff_exact(float p1x, float p1y, float p2x, float p2y,
+static __device__ __noinline__ int cross_diff_exact(float p1x, float p1y, float p2x, float p2y,
                                              float p3x, float p3y, float p4x, float p4y)
 {
     double u[2], v[2], w[2], z[2];
@@ -111,7 +111,7 @@ __device__ __forceinline__ void cross_diff_f64(float p1x, float p1y, float p2x, 
 }
 
 // FP64 filter, then exact.
-__device__ __noinline__ int cross_diff_sign_slow(float p1x, float p1y, float p2x, float p2y,
+static __device__ __noinline__ int cross_diff_sign_slow(float p1x, float p1y, float p2x, float p2y,
                                                  float p3x, float p3y, float p4x, float p4y)
 {
     double det, err;

@@ -1,0 +1,909 @@
+// 3D segmented Quickhull on one GPU.
+//
+// The paper extends its 2D algorithm to 3D by a first split with a triangle
+// plane and a 3-state flagPermute in the recursion (Section 4.3, "3D and
+// Higher Dimensions", Algorithm 1).  Splitting each face's points among the
+// three faces of a tetrahedron built on it does not keep the partial hull
+// convex, so this implementation follows the Quickhull of Barber et al. that
+// the paper builds on: the farthest point of a facet's outside set (its
+// "segment") becomes an apex, the facets it sees strictly form its visible
+// set, the horizon of that set is coned to the apex, and the points of the
+// visible facets are reassigned to the first cone facet they are strictly
+// above (else discarded as interior).  Several apexes are inserted per
+// iteration: each candidate claims its visible facets with a priority; a
+// candidate whose visible set is entirely its own and whose horizon
+// neighbours carry no higher-priority claim is inserted.  Two insertions
+// chosen this way touch disjoint, non-adjacent facet sets, so they commute.
+//
+// Per iteration (persistent kernel, grid barriers between phases):
+//   S  (select)   one thread per segment: visible-set BFS from the facet with
+//                 exact orientation tests, priority claims.
+//   C  (cone)     winners build their cone facets and relink neighbours.
+//   A  (assign)   every live point: kept (its facet survives) or tested
+//                 against its winner's cone facets; warp-aggregated counts,
+//                 ranks and farthest-point keys per target facet.
+//   T  (table)    scan of the new segment sizes (kept segments in order,
+//                 then the new cone facets).
+//   B  (scatter)  points to their new positions; certification of each new
+//                 facet's farthest point (FP32 top-2 gap against the error
+//                 bound), tile -> segment map.
+//   X  (exact)    exact farthest point of uncertified facets.
+// The output (maximal coplanar faces, canonical order) is produced by the
+// kernels in qh3d_out.cu.
+
+#include <climits>
+#include <cstdio>
+#include <cstring>
+
+#include "pred3.cuh"
+#include "qh3d_internal.cuh"
+#include "qh_common.cuh"
+#include "qh_internal.h"
+
+namespace qh {
+namespace d3 {
+
+// ---------------------------------------------------------------- small helpers
+__device__ __forceinline__ void set_status(Hdr3 *H, int st) { atomicCAS(&H->status, 0, st); }
+
+__device__ __forceinline__ float4 load_input(const Params3 &A, long long i)
+{
+    const long long o = i * A.stride;
+    return make_float4(__ldg(A.x + o), __ldg(A.y + o), __ldg(A.z + o), __int_as_float((int)i));
+}
+
+__device__ __forceinline__ void fac_pts(const Fac3 &f, const float *&a, const float *&b,
+                                        const float *&c)
+{
+    a = f.p;
+    b = f.p + 3;
+    c = f.p + 6;
+}
+
+// Lexicographic (x, y, z, index) comparison for extrema; -0.0 == +0.0.
+__device__ __forceinline__ bool lex_less(float4 p, float4 q)
+{
+    if (p.x != q.x) return p.x < q.x;
+    if (p.y != q.y) return p.y < q.y;
+    if (p.z != q.z) return p.z < q.z;
+    return __float_as_int(p.w) < __float_as_int(q.w);
+}
+__device__ __forceinline__ bool lex_greater_lowidx(float4 p, float4 q)
+{
+    if (p.x != q.x) return p.x > q.x;
+    if (p.y != q.y) return p.y > q.y;
+    if (p.z != q.z) return p.z > q.z;
+    return __float_as_int(p.w) < __float_as_int(q.w);
+}
+
+// ---------------------------------------------------------------- initial simplex
+// Block-level reductions write one candidate per block; block 0 reduces them
+// after a grid barrier.
+
+__device__ void extrema3d(const Params3 &A, SmemAll3 &sm, int bid, int nb)
+{
+    float4 mn = make_float4(INFINITY, INFINITY, INFINITY, __int_as_float(INT_MAX));
+    float4 mx = make_float4(-INFINITY, -INFINITY, -INFINITY, __int_as_float(INT_MAX));
+    int bad = 0;
+    for (long long i = (long long)bid * blockDim.x + threadIdx.x; i < A.n;
+         i += (long long)nb * blockDim.x) {
+        float4 p = load_input(A, i);
+        p.x = canon0(p.x);
+        p.y = canon0(p.y);
+        p.z = canon0(p.z);
+        bad |= !(isfinite(p.x) && isfinite(p.y) && isfinite(p.z));
+        if (lex_less(p, mn)) mn = p;
+        if (lex_greater_lowidx(p, mx)) mx = p;
+    }
+    bad = __syncthreads_or(bad);
+    sm.red.a[threadIdx.x] = mn;
+    sm.red.b[threadIdx.x] = mx;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            if (lex_less(sm.red.a[threadIdx.x + s], sm.red.a[threadIdx.x]))
+                sm.red.a[threadIdx.x] = sm.red.a[threadIdx.x + s];
+            if (lex_greater_lowidx(sm.red.b[threadIdx.x + s], sm.red.b[threadIdx.x]))
+                sm.red.b[threadIdx.x] = sm.red.b[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        A.blk_a[bid] = sm.red.a[0];
+        A.blk_b[bid] = sm.red.b[0];
+        if (bad) atomicExch(&A.hdr->nonfinite, 1);
+    }
+    __syncthreads();
+}
+
+// Farthest point from the line ab (kind 0) or from the plane abc (kind 1),
+// FP32 magnitude, lowest index on ties.
+__device__ void farthest3d(const Params3 &A, SmemAll3 &sm, int bid, int nb, int kind)
+{
+    const Hdr3 *H = A.hdr;
+    const float a[3] = {H->pa.x, H->pa.y, H->pa.z};
+    const float b[3] = {H->pb.x, H->pb.y, H->pb.z};
+    const float c[3] = {H->pc.x, H->pc.y, H->pc.z};
+    float best = -1.0f;
+    int bi = INT_MAX;
+    for (long long i = (long long)bid * blockDim.x + threadIdx.x; i < A.n;
+         i += (long long)nb * blockDim.x) {
+        float4 p = load_input(A, i);
+        float v;
+        if (kind == 0) {
+            float ux = b[0] - a[0], uy = b[1] - a[1], uz = b[2] - a[2];
+            float wx = p.x - a[0], wy = p.y - a[1], wz = p.z - a[2];
+            float cx = uy * wz - uz * wy, cy = uz * wx - ux * wz, cz = ux * wy - uy * wx;
+            v = cx * cx + cy * cy + cz * cz;
+        } else {
+            float q[3] = {p.x, p.y, p.z};
+            float d, e;
+            orient3d_value<QH_PRED_F32>(a, b, c, q, d, e);
+            v = fabsf(d);
+        }
+        if (!(v <= best)) {  // NaN-safe: NaN never wins
+            if (v > best || (v == best && (int)i < bi)) {
+                best = v;
+                bi = (int)i;
+            }
+        }
+    }
+    sm.red.v[threadIdx.x] = best;
+    sm.red.i[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            float ov = sm.red.v[threadIdx.x + s];
+            int oi = sm.red.i[threadIdx.x + s];
+            if (ov > sm.red.v[threadIdx.x] || (ov == sm.red.v[threadIdx.x] && oi < sm.red.i[threadIdx.x])) {
+                sm.red.v[threadIdx.x] = ov;
+                sm.red.i[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        A.blk_v[bid] = sm.red.v[0];
+        A.blk_i[bid] = sm.red.i[0];
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ bool collinear3_exact(const float *a, const float *b, const float *c)
+{
+    for (int k = 0; k < 3; k++) {
+        int i = k, j = (k + 1) % 3;
+        if (orient_exact_sign(a[i], a[j], b[i], b[j], c[i], c[j]) != 0) return false;
+    }
+    return true;
+}
+
+// Any point not collinear with ab (kind 0) / not coplanar with abc (kind 1),
+// lowest index: exact fallback when the FP32 choice turned out degenerate.
+__device__ void exact_search3d(const Params3 &A, int bid, int nb, int kind)
+{
+    Hdr3 *H = A.hdr;
+    const float a[3] = {H->pa.x, H->pa.y, H->pa.z};
+    const float b[3] = {H->pb.x, H->pb.y, H->pb.z};
+    const float c[3] = {H->pc.x, H->pc.y, H->pc.z};
+    for (long long i = (long long)bid * blockDim.x + threadIdx.x; i < A.n;
+         i += (long long)nb * blockDim.x) {
+        float4 p = load_input(A, i);
+        float q[3] = {p.x, p.y, p.z};
+        bool ok = kind == 0 ? !collinear3_exact(a, b, q) : orient3d_exact_sign(a, b, c, q) != 0;
+        if (ok) atomicMin(&H->search_idx, (int)i);
+    }
+}
+
+// Block 0: reduce the per-block candidates of the previous phase.
+__device__ void simplex_step(const Params3 &A, SmemAll3 &sm, int step, int nblk)
+{
+    Hdr3 *H = A.hdr;
+    if (threadIdx.x != 0) return;
+    if (step == 0) {
+        float4 mn = A.blk_a[0], mx = A.blk_b[0];
+        for (int b = 1; b < nblk; b++) {
+            if (lex_less(A.blk_a[b], mn)) mn = A.blk_a[b];
+            if (lex_greater_lowidx(A.blk_b[b], mx)) mx = A.blk_b[b];
+        }
+        H->pa = mn;
+        H->pb = mx;
+        if (mn.x == mx.x && mn.y == mx.y && mn.z == mx.z) set_status(H, QH_ERR_DEGENERATE);
+    } else {
+        float bv = A.blk_v[0];
+        int bi = A.blk_i[0];
+        for (int b = 1; b < nblk; b++) {
+            if (A.blk_v[b] > bv || (A.blk_v[b] == bv && A.blk_i[b] < bi)) {
+                bv = A.blk_v[b];
+                bi = A.blk_i[b];
+            }
+        }
+        H->search_idx = INT_MAX;
+        H->cand_idx = bi;
+        // exact check of the FP32 choice
+        bool ok = false;
+        if (bi >= 0 && bi < A.n) {
+            float4 p = load_input(A, bi);
+            const float a[3] = {H->pa.x, H->pa.y, H->pa.z};
+            const float b[3] = {H->pb.x, H->pb.y, H->pb.z};
+            const float c[3] = {H->pc.x, H->pc.y, H->pc.z};
+            float q[3] = {p.x, p.y, p.z};
+            ok = step == 1 ? !collinear3_exact(a, b, q) : orient3d_exact_sign(a, b, c, q) != 0;
+        }
+        H->cand_ok = ok;
+    }
+}
+
+__device__ void simplex_take(const Params3 &A, int step)
+{
+    Hdr3 *H = A.hdr;
+    if (threadIdx.x != 0) return;
+    int i = H->cand_ok ? H->cand_idx : H->search_idx;
+    if (i == INT_MAX || i < 0) {
+        set_status(H, QH_ERR_DEGENERATE);
+        return;
+    }
+    float4 p = load_input(A, i);
+    if (step == 1) H->pc = p;
+    else H->pd = p;
+}
+
+// Block 0 thread 0: the tetrahedron (a, b, c, d), facets 0..3 oriented with the
+// opposite vertex strictly inside, and their neighbours.
+__device__ void build_tetra(const Params3 &A)
+{
+    Hdr3 *H = A.hdr;
+    if (threadIdx.x != 0) return;
+    float4 t[4] = {H->pa, H->pb, H->pc, H->pd};
+    for (int o = 0; o < 4; o++) {
+        int k[3], m = 0;
+        for (int j = 0; j < 4; j++)
+            if (j != o) k[m++] = j;
+        float pa[3] = {t[k[0]].x, t[k[0]].y, t[k[0]].z};
+        float pb[3] = {t[k[1]].x, t[k[1]].y, t[k[1]].z};
+        float pc[3] = {t[k[2]].x, t[k[2]].y, t[k[2]].z};
+        float po[3] = {t[o].x, t[o].y, t[o].z};
+        if (orient3d_exact_sign(pa, pb, pc, po) > 0) {
+            int s = k[1];
+            k[1] = k[2];
+            k[2] = s;
+        }
+        Fac3 f;
+        for (int j = 0; j < 3; j++) {
+            f.p[3 * j + 0] = t[k[j]].x;
+            f.p[3 * j + 1] = t[k[j]].y;
+            f.p[3 * j + 2] = t[k[j]].z;
+            f.v[j] = __float_as_int(t[k[j]].w);
+        }
+        f.nb[0] = f.nb[1] = f.nb[2] = -1;
+        f.alive = 1;
+        A.fac[o] = f;
+        Acc3 z = {};
+        A.acc[o] = z;
+        A.claim[o] = 0ull;
+    }
+    for (int i = 0; i < 4; i++)
+        for (int e = 0; e < 3; e++) {
+            int u = A.fac[i].v[e], v = A.fac[i].v[(e + 1) % 3];
+            for (int j = 0; j < 4; j++) {
+                if (j == i) continue;
+                for (int g = 0; g < 3; g++)
+                    if (A.fac[j].v[g] == v && A.fac[j].v[(g + 1) % 3] == u) A.fac[i].nb[e] = j;
+            }
+        }
+    H->fcount = 4;
+    H->hull_vertices = 4;
+    // the pseudo segment of the first assignment: every input point, coned to
+    // the four tetrahedron facets
+    A.cone[kPseudo] = make_int4(0, 4, -1, 0);
+}
+
+// ---------------------------------------------------------------- S: select
+// One thread per segment (candidate): visible-set BFS from its facet with
+// exact tests, then priority claims on the visible facets.
+template <int MODE>
+__device__ void select3d(const Params3 &A, int par, int iter, int bid, int nb)
+{
+    Hdr3 *H = A.hdr;
+    const int ne = *(volatile int *)&H->nent[par];
+    const Ent3 *ent = A.ent[par];
+    unsigned fallbacks = 0;
+    for (int e = bid * blockDim.x + threadIdx.x; e < ne; e += nb * blockDim.x) {
+        const int f0 = ent[e].f;
+        const float4 q4 = A.apex[f0];
+        const float q[3] = {q4.x, q4.y, q4.z};
+        int *V = A.vpool + (size_t)e * kVCap;
+        int *N = A.npool + (size_t)e * kNCap;
+        int nv = 1, nn = 0;
+        bool over = false;
+        V[0] = f0;
+        for (int i = 0; i < nv && !over; i++) {
+            const Fac3 &F = A.fac[V[i]];
+            for (int k = 0; k < 3 && !over; k++) {
+                const int g = F.nb[k];
+                bool seen = false;
+                for (int j = 0; j < nv && !seen; j++) seen = V[j] == g;
+                for (int j = 0; j < nn && !seen; j++) seen = N[j] == g;
+                if (seen) continue;
+                const Fac3 &G = A.fac[g];
+                const float *a, *b, *c;
+                fac_pts(G, a, b, c);
+                float d, err;
+                orient3d_value<MODE>(a, b, c, q, d, err);
+                if (orient3d_sign<MODE>(d, err, a, b, c, q, fallbacks) > 0) {
+                    if (nv == kVCap) over = true;
+                    else V[nv++] = g;
+                } else {
+                    if (nn == kNCap) over = true;
+                    else N[nn++] = g;
+                }
+            }
+        }
+        A.vn[e] = over ? make_int2(-1, -1) : make_int2(nv, nn);
+        if (!over) {
+            const unsigned long long mine = claim_key(iter, f0);
+            for (int j = 0; j < nv; j++) atomicMax(&A.claim[V[j]], mine);
+        }
+    }
+    unsigned f = __reduce_add_sync(0xffffffffu, fallbacks);
+    if ((threadIdx.x & 31) == 0 && f) atomicAdd(&H->fallbacks, (unsigned long long)f);
+}
+
+// Cone of one winner: horizon edges of V (edges whose neighbour is not in V),
+// one facet (u, v, q) per horizon edge, neighbours relinked.  V and N are the
+// winner's visible facets and horizon neighbours; hz is scratch for the
+// horizon (capacity >= |V| + 2).
+__device__ bool build_cone(const Params3 &A, int f0, const int *V, int nv, int *hz, int hcap,
+                           int iter)
+{
+    Hdr3 *H = A.hdr;
+    const unsigned long long mine = claim_key(iter, f0);
+    const float4 q4 = A.apex[f0];
+    const int qi = __float_as_int(q4.w);
+    int nh = 0;
+    for (int i = 0; i < nv; i++) {
+        const Fac3 &F = A.fac[V[i]];
+        for (int k = 0; k < 3; k++) {
+            int g = F.nb[k];
+            if (A.claim[g] == mine) continue;  // g is in V
+            if (nh == hcap) {  // a visible region that is not a disk: cannot happen
+                set_status(H, QH_ERR_CAPACITY);
+                return false;
+            }
+            hz[nh++] = V[i] * 3 + k;
+        }
+    }
+    const int base = atomicAdd(&H->fcount, nh);
+    if (base + nh > A.fcap) {
+        set_status(H, QH_ERR_CAPACITY);
+        return false;
+    }
+    for (int j = 0; j < nh; j++) {
+        const int hf = hz[j] / 3;
+        const Fac3 &F = A.fac[hf];
+        const int k = hz[j] - 3 * hf;
+        const int k1 = (k + 1) % 3;
+        Fac3 C;
+        C.p[0] = F.p[3 * k + 0]; C.p[1] = F.p[3 * k + 1]; C.p[2] = F.p[3 * k + 2];
+        C.p[3] = F.p[3 * k1 + 0]; C.p[4] = F.p[3 * k1 + 1]; C.p[5] = F.p[3 * k1 + 2];
+        C.p[6] = q4.x; C.p[7] = q4.y; C.p[8] = q4.z;
+        C.v[0] = F.v[k];
+        C.v[1] = F.v[k1];
+        C.v[2] = qi;
+        C.nb[0] = F.nb[k];
+        C.nb[1] = -1;
+        C.nb[2] = -1;
+        C.alive = 1;
+        A.fac[base + j] = C;
+        Acc3 z = {};
+        A.acc[base + j] = z;
+        A.claim[base + j] = 0ull;
+        // the horizon neighbour now points at the cone facet
+        Fac3 &G = A.fac[F.nb[k]];
+        for (int g = 0; g < 3; g++)
+            if (G.nb[g] == hf) G.nb[g] = base + j;
+    }
+    // cone facets around q: edge (v, q) meets the facet whose horizon edge
+    // starts at v, edge (q, u) the facet whose horizon edge ends at u
+    for (int j = 0; j < nh; j++) {
+        Fac3 &C = A.fac[base + j];
+        for (int i = 0; i < nh; i++) {
+            const Fac3 &D = A.fac[base + i];
+            if (D.v[0] == C.v[1]) C.nb[1] = base + i;
+            if (D.v[1] == C.v[0]) C.nb[2] = base + i;
+        }
+    }
+    for (int i = 0; i < nv; i++) {
+        A.fac[V[i]].alive = 0;
+        A.cone[V[i]] = make_int4(base, nh, qi, iter);
+    }
+    atomicAdd(&H->hull_vertices, 1);
+    atomicAdd(&H->nwin, 1);
+    return true;
+}
+
+// ---------------------------------------------------------------- C: winners
+__device__ void cone3d(const Params3 &A, int par, int iter, int bid, int nb)
+{
+    Hdr3 *H = A.hdr;
+    const int ne = *(volatile int *)&H->nent[par];
+    const Ent3 *ent = A.ent[par];
+    for (int e = bid * blockDim.x + threadIdx.x; e < ne; e += nb * blockDim.x) {
+        const int2 c = A.vn[e];
+        if (c.x < 0) continue;
+        const int f0 = ent[e].f;
+        const unsigned long long mine = claim_key(iter, f0);
+        const int *V = A.vpool + (size_t)e * kVCap;
+        const int *N = A.npool + (size_t)e * kNCap;
+        bool win = true;
+        for (int j = 0; j < c.x && win; j++) win = A.claim[V[j]] == mine;
+        for (int j = 0; j < c.y && win; j++) win = A.claim[N[j]] < mine;
+        if (!win) continue;
+        // the horizon list reuses the candidate's neighbour slice (>= |V| + 2)
+        build_cone(A, f0, V, c.x, A.npool + (size_t)e * kNCap, kNCap, iter);
+    }
+}
+
+// No winner at all means the highest-priority candidate overflowed its
+// fixed-size lists: insert it alone with the large scratch (one thread).
+template <int MODE>
+__device__ void fallback3d(const Params3 &A, int par, int iter)
+{
+    Hdr3 *H = A.hdr;
+    if (threadIdx.x != 0) return;
+    const int ne = H->nent[par];
+    const Ent3 *ent = A.ent[par];
+    int f0 = INT_MAX;
+    for (int e = 0; e < ne; e++) f0 = min(f0, ent[e].f);
+    if (f0 == INT_MAX) return;
+    const float4 q4 = A.apex[f0];
+    const float q[3] = {q4.x, q4.y, q4.z};
+    int *V = A.big_v;
+    int nv = 1;
+    V[0] = f0;
+    const unsigned long long mine = claim_key(iter, f0);
+    A.claim[f0] = mine;
+    unsigned fb = 0;
+    for (int i = 0; i < nv; i++) {
+        const Fac3 &F = A.fac[V[i]];
+        for (int k = 0; k < 3; k++) {
+            const int g = F.nb[k];
+            if (A.claim[g] == mine || A.big_mark[g] == iter) continue;
+            const Fac3 &G = A.fac[g];
+            const float *a, *b, *c;
+            fac_pts(G, a, b, c);
+            float d, err;
+            orient3d_value<MODE>(a, b, c, q, d, err);
+            if (orient3d_sign<MODE>(d, err, a, b, c, q, fb) > 0) {
+                A.claim[g] = mine;
+                V[nv++] = g;
+            } else {
+                A.big_mark[g] = iter;
+            }
+        }
+    }
+    build_cone(A, f0, V, nv, A.big_h, A.fcap, iter);
+}
+
+// ---------------------------------------------------------------- A: assign
+// Target of every live point: its own facet if that facet survives (rank =
+// position in the segment), else the first cone facet of its winner that it
+// is strictly above (warp-aggregated count, rank and farthest-point key), else
+// discarded (-1).  FIRST: the input points against the tetrahedron.
+template <int MODE, bool FIRST>
+__device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int nb)
+{
+    Hdr3 *H = A.hdr;
+    const int L = FIRST ? A.n : *(volatile int *)&H->L[par];
+    const int ne = FIRST ? 1 : *(volatile int *)&H->nent[par];
+    const Ent3 *ent = A.ent[par];
+    const float4 *P = A.pts[par];
+    const int lane = threadIdx.x & 31;
+    unsigned fallbacks = 0;
+    const int ntiles = (L + kTile - 1) / kTile;
+    for (int tile = bid; tile < ntiles; tile += nb) {
+        const int v0 = tile * kTile, v1 = min(v0 + kTile, L);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            sm.a.e0 = FIRST ? 0 : A.tile_ent[tile];
+            sm.a.m = FIRST ? 1 : A.tile_m[tile];
+        }
+        __syncthreads();
+        const int e0 = sm.a.e0, m = sm.a.m;
+        for (int i = threadIdx.x; i < m && i < kTile; i += blockDim.x) {
+            if (FIRST) {
+                sm.a.start[i] = 0;
+                sm.a.f[i] = kPseudo;
+            } else {
+                sm.a.start[i] = ent[e0 + i].start;
+                sm.a.f[i] = ent[e0 + i].f;
+            }
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int k = 0; k < kItems; k++) {
+            const int v = v0 + k * blockDim.x + threadIdx.x;
+            const bool valid = v < v1;
+            int target = -1, rank = 0;
+            float d = 0.0f, err = 0.0f;
+            int idx = 0;
+            bool cone_t = false;
+            if (valid) {
+                int lo = 0, hi = m - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (sm.a.start[mid] <= v) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int f = sm.a.f[lo];
+                const float4 p4 = FIRST ? load_input(A, v) : P[v];
+                idx = __float_as_int(p4.w);
+                const float p[3] = {p4.x, p4.y, p4.z};
+                if (!FIRST && A.fac[f].alive) {
+                    target = f;
+                    rank = v - sm.a.start[lo];
+                } else {
+                    const int4 cn = A.cone[f];
+                    if (idx != cn.z) {
+                        for (int c = 0; c < cn.y; c++) {
+                            const Fac3 &C = A.fac[cn.x + c];
+                            const float *a, *b, *cc;
+                            fac_pts(C, a, b, cc);
+                            orient3d_value<MODE>(a, b, cc, p, d, err);
+                            if (orient3d_sign<MODE>(d, err, a, b, cc, p, fallbacks) > 0) {
+                                target = cn.x + c;
+                                cone_t = true;
+                                break;
+                            }
+                        }
+                    }
+                }
+            }
+            // warp-aggregated count, rank and key per cone target
+            const unsigned act = __ballot_sync(0xffffffffu, cone_t);
+            if (cone_t) {
+                const unsigned grp = __match_any_sync(act, target);
+                const int leader = __ffs(grp) - 1;
+                const unsigned o = ord_f32(d);
+                const unsigned top_o = __reduce_max_sync(grp, o);
+                const unsigned cand = (o == top_o) ? (unsigned)idx : 0xffffffffu;
+                const unsigned top_i = __reduce_min_sync(grp, cand);
+                const unsigned sec = (o == top_o && (unsigned)idx == top_i) ? 0u : o;
+                const unsigned sec_o = __reduce_max_sync(grp, sec);
+                const unsigned em = __reduce_max_sync(grp, __float_as_uint(err));
+                unsigned base = 0;
+                if (lane == leader) {
+                    Acc3 &ac = A.acc[target];
+                    base = atomicAdd(&ac.cnt, (unsigned)__popc(grp));
+                    const unsigned long long k1 =
+                        ((unsigned long long)top_o << 32) | (0xffffffffu - top_i);
+                    unsigned long long old = atomicMax(&ac.key1, k1);
+                    unsigned long long lo = old < k1 ? old : k1;
+                    unsigned lo_o = (unsigned)(lo >> 32);
+                    atomicMax(&ac.o2, lo_o > sec_o ? lo_o : sec_o);
+                    atomicMax(&ac.emax, em);
+                }
+                base = __shfl_sync(grp, base, leader);
+                rank = (int)base + __popc(grp & lanemask_lt());
+            }
+            if (valid) A.code[v] = make_int2(target, rank);
+        }
+    }
+    unsigned fsum = __reduce_add_sync(0xffffffffu, fallbacks);
+    if (lane == 0 && fsum) atomicAdd(&H->fallbacks, (unsigned long long)fsum);
+}
+
+// ---------------------------------------------------------------- T: table
+// New segment table: the old segments whose facet survives (in order), then
+// the cone facets created this iteration that received points.  Grid-wide
+// exclusive scan in two steps (block sums, then offsets).
+__device__ __forceinline__ int table_item_len(const Params3 &A, int par, int ne, int fc0, int j,
+                                              int &f)
+{
+    if (j < ne) {
+        const Ent3 en = A.ent[par][j];
+        f = en.f;
+        return A.fac[en.f].alive ? en.len : 0;
+    }
+    f = fc0 + (j - ne);
+    return (int)A.acc[f].cnt;
+}
+
+__device__ void table_sum(const Params3 &A, int par, bool first, SmemAll3 &sm, int bid, int nb)
+{
+    Hdr3 *H = A.hdr;
+    const int ne = first ? 0 : *(volatile int *)&H->nent[par];
+    const int fc0 = first ? 0 : *(volatile int *)&H->fc_iter[par];
+    const int fc1 = *(volatile int *)&H->fcount;
+    const int m = ne + (fc1 - fc0);
+    const int chunk = (m + nb - 1) / nb;
+    const int j0 = bid * chunk, j1 = min(j0 + chunk, m);
+    long long s = 0;
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        int f;
+        int len = table_item_len(A, par, ne, fc0, j, f);
+        s += ((long long)(len > 0) << 32) | (long long)len;
+    }
+    long long tot;
+    block_excl_scan64(s, sm.t.wsum, &tot);
+    if (threadIdx.x == 0) A.part[bid] = tot;
+}
+
+__device__ void table_write(const Params3 &A, int par, bool first, SmemAll3 &sm, int bid, int nb)
+{
+    Hdr3 *H = A.hdr;
+    const int ne = first ? 0 : *(volatile int *)&H->nent[par];
+    const int fc0 = first ? 0 : *(volatile int *)&H->fc_iter[par];
+    const int fc1 = *(volatile int *)&H->fcount;
+    const int m = ne + (fc1 - fc0);
+    const int chunk = (m + nb - 1) / nb;
+    const int j0 = bid * chunk, j1 = min(j0 + chunk, m);
+    // prefix of the earlier blocks
+    long long pre = 0;
+    for (int b = threadIdx.x; b < bid; b += blockDim.x) pre += A.part[b];
+    long long pre_tot;
+    block_excl_scan64(pre, sm.t.wsum, &pre_tot);
+    long long carry = pre_tot;
+    Ent3 *out = A.ent[par ^ 1];
+    for (int base = j0; base < j1; base += blockDim.x) {
+        const int j = base + threadIdx.x;
+        int f = -1, len = 0;
+        if (j < j1) len = table_item_len(A, par, ne, fc0, j, f);
+        long long s = ((long long)(len > 0) << 32) | (long long)len;
+        long long tot;
+        long long ex = block_excl_scan64(s, sm.t.wsum, &tot) + carry;
+        if (len > 0) {
+            const int k = (int)(ex >> 32), st = (int)(ex & 0xffffffffll);
+            Ent3 en;
+            en.f = f;
+            en.start = st;
+            en.len = len;
+            en.pad = 0;
+            out[k] = en;
+            A.nstart[f] = st;
+        }
+        carry += tot;
+    }
+    if (bid == nb - 1 && threadIdx.x == 0) {
+        H->nent[par ^ 1] = (int)(carry >> 32);
+        H->L[par ^ 1] = (int)(carry & 0xffffffffll);
+        H->fc_lo_last = fc0;
+        H->fc_iter[par ^ 1] = fc1;  // read by the next table phase (other parity)
+    }
+}
+
+// ---------------------------------------------------------------- B: scatter
+template <bool FIRST>
+__device__ void scatter3d(const Params3 &A, int par, int bid, int nb)
+{
+    Hdr3 *H = A.hdr;
+    const int L = FIRST ? A.n : *(volatile int *)&H->L[par];
+    const float4 *P = A.pts[par];
+    float4 *Q = A.pts[par ^ 1];
+    for (long long v = (long long)bid * blockDim.x + threadIdx.x; v < L;
+         v += (long long)nb * blockDim.x) {
+        const int2 cr = A.code[v];
+        if (cr.x < 0) continue;
+        const float4 p = FIRST ? load_input(A, v) : P[v];
+        Q[A.nstart[cr.x] + cr.y] = p;
+    }
+}
+
+// New facets: certify the FP32 farthest point (top-2 gap against twice the
+// largest error bound) or queue it for the exact phase; record the apex.
+// Also the tile -> entry map of the next assign phase.
+__device__ void certify3d(const Params3 &A, int par, int bid, int nb)
+{
+    Hdr3 *H = A.hdr;
+    const int ne = *(volatile int *)&H->nent[par ^ 1];
+    const int L = *(volatile int *)&H->L[par ^ 1];
+    const Ent3 *ent = A.ent[par ^ 1];
+    for (int e = bid * blockDim.x + threadIdx.x; e < ne; e += nb * blockDim.x) {
+        const int f = ent[e].f;
+        const Acc3 a = A.acc[f];
+        if (f >= *(volatile int *)&H->fc_lo_last) {
+            // a facet created this iteration: its apex is new
+            const int qi = key_idx(a.key1);
+            const float4 q = load_input(A, qi);
+            A.apex[f] = q;
+            bool cert = true;
+            const float em = __uint_as_float(a.emax);
+            const float d1 = key_dist(a.key1);
+            if (a.cnt > 1) {
+                const float d2 = unord_f32(a.o2);
+                const double gap = ((double)d1 - (double)d2) * (1.0 - 0x1p-50);
+                cert = gap > 2.0 * (double)em;
+            }
+            if (!cert) {
+                const double thr = (double)d1 - 3.0 * (double)em - fabs((double)d1) * 0x1p-20;
+                A.thr[f] = isfinite(thr) ? __double2float_rd(thr) : -INFINITY;
+                A.uncert[atomicAdd(&H->n_uncert, 1)] = e;
+            }
+        }
+    }
+    const int ntiles = (L + kTile - 1) / kTile;
+    for (int t = bid * blockDim.x + threadIdx.x; t < ntiles; t += nb * blockDim.x) {
+        const int v = t * kTile, vl = min(v + kTile, L) - 1;
+        auto ent_of = [&](int x) {
+            int lo = 0, hi = ne - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (ent[mid].start <= x) lo = mid;
+                else hi = mid - 1;
+            }
+            return lo;
+        };
+        const int s0 = ent_of(v);
+        A.tile_ent[t] = s0;
+        A.tile_m[t] = ent_of(vl) - s0 + 1;
+    }
+}
+
+// ---------------------------------------------------------------- X: exact apex
+template <int MODE>
+__device__ void exact3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int nb)
+{
+    Hdr3 *H = A.hdr;
+    const int nu = *(volatile int *)&H->n_uncert;
+    const Ent3 *ent = A.ent[par ^ 1];
+    const float4 *Q = A.pts[par ^ 1];
+    for (int u = bid; u < nu; u += nb) {
+        const Ent3 en = ent[A.uncert[u]];
+        const Fac3 F = A.fac[en.f];
+        const float *a, *b, *c;
+        fac_pts(F, a, b, c);
+        const float thr = A.thr[en.f];
+        int best = -1;
+        float4 bp = make_float4(0, 0, 0, 0);
+        for (int i = threadIdx.x; i < en.len; i += blockDim.x) {
+            const float4 p4 = Q[en.start + i];
+            const float p[3] = {p4.x, p4.y, p4.z};
+            float d, e;
+            orient3d_value<MODE>(a, b, c, p, d, e);
+            if ((double)d + (double)e < (double)thr) continue;
+            const int idx = __float_as_int(p4.w);
+            if (best >= 0) {
+                const float q[3] = {bp.x, bp.y, bp.z};
+                const int s = cmp_dist3_exact_sign(a, b, c, p, q);
+                if (!(s > 0 || (s == 0 && idx < best))) continue;
+            }
+            best = idx;
+            bp = p4;
+        }
+        sm.x.idx[threadIdx.x] = best;
+        sm.x.p[threadIdx.x] = bp;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) {
+                const int oi = sm.x.idx[threadIdx.x + s];
+                const int mi = sm.x.idx[threadIdx.x];
+                if (oi >= 0) {
+                    bool take = mi < 0;
+                    if (!take) {
+                        const float4 o = sm.x.p[threadIdx.x + s], me = sm.x.p[threadIdx.x];
+                        const float po[3] = {o.x, o.y, o.z}, pm[3] = {me.x, me.y, me.z};
+                        const int c2 = cmp_dist3_exact_sign(a, b, c, po, pm);
+                        take = c2 > 0 || (c2 == 0 && oi < mi);
+                    }
+                    if (take) {
+                        sm.x.idx[threadIdx.x] = oi;
+                        sm.x.p[threadIdx.x] = sm.x.p[threadIdx.x + s];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0 && sm.x.idx[0] >= 0) A.apex[en.f] = sm.x.p[0];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- persistent kernel
+template <int MODE>
+__global__ void __launch_bounds__(kBlock) qh3d_persistent(Params3 A)
+{
+    __shared__ SmemAll3 sm;
+    Hdr3 *H = A.hdr;
+    int *fail = &H->status;
+    const int bid = blockIdx.x, nb = gridDim.x;
+    auto sync = [&]() { grid_sync(&H->bar, fail, A.wait_ns); };
+    auto ok = [&]() { return *(volatile int *)&H->status == 0; };
+
+    // ---- initial simplex
+    extrema3d(A, sm, bid, nb);
+    sync();
+    if (bid == 0) simplex_step(A, sm, 0, nb);
+    sync();
+    if (*(volatile int *)&H->nonfinite) {
+        if (bid == 0 && threadIdx.x == 0) set_status(H, QH_ERR_NONFINITE);
+    }
+    for (int step = 1; step <= 2 && ok(); step++) {
+        if (step == 2) {
+            // c is known: plane abc
+        }
+        farthest3d(A, sm, bid, nb, step - 1);
+        sync();
+        if (bid == 0) simplex_step(A, sm, step, nb);
+        sync();
+        if (!*(volatile int *)&H->cand_ok) {
+            exact_search3d(A, bid, nb, step - 1);
+            sync();
+        }
+        if (bid == 0) simplex_take(A, step);
+        sync();
+    }
+    if (ok()) {
+        if (bid == 0) build_tetra(A);
+        sync();
+        // ---- first assignment: every input point against the tetrahedron;
+        // table 1 / buffer 1 receive the result
+        assign3d<MODE, true>(A, 0, sm, bid, nb);
+        sync();
+        table_sum(A, 0, true, sm, bid, nb);
+        sync();
+        table_write(A, 0, true, sm, bid, nb);
+        if (bid == 0 && threadIdx.x == 0) H->n_uncert = 0;
+        sync();
+        scatter3d<true>(A, 0, bid, nb);
+        sync();
+        certify3d(A, 0, bid, nb);
+        sync();
+        if (*(volatile int *)&H->n_uncert > 0) {
+            exact3d<MODE>(A, 0, sm, bid, nb);
+            sync();
+        }
+    }
+    // ---- iterations: table `cur` describes the live points in buffer `cur`
+    int cur = 1;
+    int iter = 0;
+    while (ok() && *(volatile int *)&H->nent[cur] > 0) {
+        iter++;
+        if (iter > A.max_iters) {
+            if (bid == 0 && threadIdx.x == 0) set_status(H, QH_ERR_NO_CONVERGENCE);
+            break;
+        }
+        if (bid == 0 && threadIdx.x == 0) {
+            H->iter = iter;
+            H->nwin = 0;
+            H->seg_total += H->nent[cur];
+        }
+        select3d<MODE>(A, cur, iter, bid, nb);
+        sync();
+        cone3d(A, cur, iter, bid, nb);
+        sync();
+        if (*(volatile int *)&H->nwin == 0) {
+            if (bid == 0) fallback3d<MODE>(A, cur, iter);
+            sync();
+        }
+        if (!ok()) break;
+        assign3d<MODE, false>(A, cur, sm, bid, nb);
+        sync();
+        table_sum(A, cur, false, sm, bid, nb);
+        sync();
+        table_write(A, cur, false, sm, bid, nb);
+        if (bid == 0 && threadIdx.x == 0) H->n_uncert = 0;
+        sync();
+        scatter3d<false>(A, cur, bid, nb);
+        sync();
+        certify3d(A, cur, bid, nb);
+        if (bid == 0 && threadIdx.x == 0) H->surv_total += H->L[cur ^ 1];
+        sync();
+        if (*(volatile int *)&H->n_uncert > 0) {
+            exact3d<MODE>(A, cur, sm, bid, nb);
+            if (bid == 0 && threadIdx.x == 0) H->exact_argmax += H->n_uncert;
+            sync();
+        }
+        cur ^= 1;
+    }
+}
+
+// Kernel entry of the persistent 3D loop for a predicate mode (the launch
+// happens in qh3d_out.cu).
+const void *persistent_kernel(int mode)
+{
+    return mode == QH_PRED_F32 ? (const void *)qh3d_persistent<QH_PRED_F32>
+                               : (const void *)qh3d_persistent<QH_PRED_F64>;
+}
+
+}  // namespace d3
+}  // namespace qh

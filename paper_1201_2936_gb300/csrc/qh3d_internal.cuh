@@ -1,0 +1,150 @@
+// Data structures shared by the 3D kernels (qh3d.cu) and the 3D output and
+// host code (qh3d_out.cu).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qh.h"
+#include "qh_common.cuh"
+
+namespace qh {
+namespace d3 {
+
+constexpr int kBlock = 256;
+constexpr int kItems = 4;                // points per thread in the assign pass
+constexpr int kTile = kBlock * kItems;   // points per assign tile
+constexpr int kVCap = 32;                // visible facets a candidate may list
+constexpr int kNCap = 64;                // horizon neighbours a candidate may list (>= kVCap + 2)
+constexpr int kMaxGrid = 4096;
+
+// A facet of the current triangulated hull.
+struct Fac3 {
+    float p[9];   // vertex coordinates a, b, c, counter-clockwise seen from outside
+    int v[3];     // vertex point indices
+    int nb[3];    // nb[i]: facet across edge (v[i], v[i+1])
+    int alive;
+};
+static_assert(sizeof(Fac3) == 64, "Fac3 layout");
+
+// Farthest-point accumulator of a facet's outside set (its segment).
+struct Acc3 {
+    unsigned long long key1;  // (distance order bits << 32) | ~index of the best point
+    unsigned o2;              // distance order bits of the best other point
+    unsigned cnt;             // points
+    unsigned emax;            // largest error bound of the keys (float bits)
+    unsigned pad[3];
+};
+static_assert(sizeof(Acc3) == 32, "Acc3 layout");
+
+// Segment table entry: facet and the range of its outside set in a buffer.
+struct Ent3 {
+    int f, start, len, pad;
+};
+
+struct Hdr3 {
+    GridBarrier bar;
+    int status, nonfinite;
+    float4 pa, pb, pc, pd;  // initial simplex (w: point index bits)
+    int search_idx, cand_idx, cand_ok;
+    int fcount;             // facets created so far
+    int fc_iter[2];         // facet count when the table of that parity was built
+    int fc_lo_last;         // first facet id created in the last iteration
+    int hull_vertices;
+    int nwin, iter;
+    int nent[2], L[2];
+    int n_uncert;
+    int pad0;
+    long long seg_total, surv_total;
+    unsigned long long fallbacks, exact_argmax;
+    // output stage
+    int nalive, ncop, nbedge, ngroup, nface, nvert, changed, pad1;
+    long long nfidx;
+};
+
+struct Params3 {
+    const float *x, *y, *z;
+    long long stride;
+    int n;
+    int fcap, ecap;
+    Hdr3 *hdr;
+    qh_result *res;
+    // facets
+    Fac3 *fac;
+    Acc3 *acc;
+    float4 *apex;                 // apex (farthest point) of each facet with a segment
+    unsigned long long *claim;    // (iteration << 32) | ~candidate facet
+    int4 *cone;                   // deleted facet: (first cone facet, count, apex index, iteration)
+    float *thr;                   // exact-apex candidate threshold
+    int *nstart;                  // new segment start of a facet
+    int *big_mark;
+    int *big_v, *big_h;
+    // segments
+    Ent3 *ent[2];
+    int *tile_ent, *tile_m;
+    int2 *vn;                     // (|V|, |N|) of a candidate, (-1,-1) on overflow
+    int *vpool, *npool;
+    int *uncert;
+    // points
+    float4 *pts[2];
+    int2 *code;                   // (target facet, rank) of each live point
+    // reductions
+    long long *part;
+    float4 *blk_a, *blk_b;
+    float *blk_v;
+    int *blk_i;
+    long long max_iters, wait_ns;
+};
+
+// The pseudo facet of the first assignment (every input point coned to the
+// tetrahedron): cone[kPseudoSlot(A)].
+#define kPseudo (A.fcap)
+
+__device__ __forceinline__ unsigned long long claim_key(int iter, int f)
+{
+    return ((unsigned long long)(unsigned)iter << 32) | (unsigned long long)(0xffffffffu - (unsigned)f);
+}
+
+struct SmemRed {
+    float4 a[kBlock], b[kBlock];
+    float v[kBlock];
+    int i[kBlock];
+};
+struct SmemAssign {
+    int e0, m;
+    int start[kTile];
+    int f[kTile];
+};
+struct SmemTable {
+    long long wsum[33];
+};
+struct SmemX3 {
+    int idx[kBlock];
+    float4 p[kBlock];
+};
+union SmemAll3 {
+    SmemRed red;
+    SmemAssign a;
+    SmemTable t;
+    SmemX3 x;
+};
+
+struct Layout3 {
+    size_t hdr, res, fac, acc, apex, claim, cone, thr, nstart, big_mark, big_v, big_h;
+    size_t ent[2], tile_ent, tile_m, vn, vpool, npool, uncert, pts[2], code, part, blk_a, blk_b,
+        blk_v, blk_i;
+    // output stage
+    size_t alive, label, cop, ekey[2], eval[2], hist, hist_off, gstart, poly, glen, fkey[2], fval[2],
+        vflag, scan_tmp;
+    size_t total;
+    int fcap, ecap, hist_blocks;
+};
+
+Layout3 layout3d(int64_t n);
+const void *persistent_kernel(int mode);
+Params3 make_params3(const float *x, const float *y, const float *z, int64_t n, int64_t stride,
+                     char *ws, const Layout3 &L, const qh_opts &o);
+
+}  // namespace d3
+}  // namespace qh

@@ -1,0 +1,625 @@
+// 3D hull: workspace layout, device scan and radix sort, the output stage
+// (canonical face lattice) and the C entry points.
+//
+// Output (reading of the paper's ch_out for 3D): the faces of the hull as
+// maximal coplanar polygons, counter-clockwise seen from outside, each
+// rotated to start at its smallest point index, sorted lexicographically;
+// vertices that lie inside a face or on an edge are not vertices.  From the
+// final triangulation:
+//   1. alive facets, and for each edge whether the neighbour across it is
+//      coplanar (exact orientation of the neighbour's opposite vertex);
+//   2. coplanar groups by minimum-label propagation;
+//   3. boundary edges of every group, sorted by (group, start vertex): each
+//      group's boundary is one cycle, walked by one thread;
+//   4. vertices collinear with their cycle neighbours dropped (exact), cycle
+//      rotated to its smallest index;
+//   5. faces sorted by (first, second) vertex — unique, since two faces that
+//      start at the same vertex leave it along different edges;
+//   6. vertex list = vertices of the faces, in index order.
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+
+#include "pred3.cuh"
+#include "qh3d_internal.cuh"
+#include "qh_internal.h"
+
+namespace qh {
+namespace d3 {
+
+// ---------------------------------------------------------------- layout
+static size_t au(size_t v) { return (v + 255) & ~(size_t)255; }
+
+constexpr int kScanTile = 2048;  // elements per block of the scan and sort kernels
+
+Layout3 layout3d(int64_t n)
+{
+    Layout3 L = {};
+    size_t o = 0;
+    auto take = [&](size_t b) {
+        size_t r = o;
+        o = au(o + b);
+        return r;
+    };
+    const size_t np = (size_t)(n > 0 ? n : 1);
+    L.fcap = (int)(6 * np + 64);
+    L.ecap = (int)(np + 64);
+    const size_t fc = (size_t)L.fcap + 1;
+    L.hdr = take(sizeof(Hdr3));
+    L.res = take(sizeof(qh_result));
+    L.fac = take(fc * sizeof(Fac3));
+    L.acc = take(fc * sizeof(Acc3));
+    L.apex = take(fc * sizeof(float4));
+    L.claim = take(fc * 8);
+    L.cone = take(fc * sizeof(int4));
+    L.thr = take(fc * 4);
+    L.nstart = take(fc * 4);
+    L.big_mark = take(fc * 4);
+    L.big_v = take(fc * 4);
+    L.big_h = take(fc * 4);
+    for (int b = 0; b < 2; b++) L.ent[b] = take((size_t)L.ecap * sizeof(Ent3));
+    L.tile_ent = take((np / kTile + 2) * 4);
+    L.tile_m = take((np / kTile + 2) * 4);
+    L.vn = take((size_t)L.ecap * sizeof(int2));
+    L.vpool = take((size_t)L.ecap * kVCap * 4);
+    L.npool = take((size_t)L.ecap * kNCap * 4);
+    L.uncert = take((size_t)L.ecap * 4);
+    for (int b = 0; b < 2; b++) L.pts[b] = take(np * sizeof(float4));
+    L.code = take(np * sizeof(int2));
+    L.part = take(kMaxGrid * 8);
+    L.blk_a = take(kMaxGrid * sizeof(float4));
+    L.blk_b = take(kMaxGrid * sizeof(float4));
+    L.blk_v = take(kMaxGrid * 4);
+    L.blk_i = take(kMaxGrid * 4);
+    // output stage: boundary edges <= 3 per alive facet, groups <= alive facets
+    const size_t ecount = 3 * fc;
+    L.alive = take(fc * 4);
+    L.label = take(fc * 4);
+    L.cop = take(fc * 4);
+    for (int b = 0; b < 2; b++) {
+        L.ekey[b] = take(ecount * 8);
+        L.eval[b] = take(ecount * 4);
+        L.fkey[b] = take(fc * 8);
+        L.fval[b] = take(fc * 4);
+    }
+    L.hist_blocks = (int)((ecount + kScanTile - 1) / kScanTile);
+    L.hist = take((size_t)256 * L.hist_blocks * 4 + 256);
+    L.hist_off = take((size_t)256 * L.hist_blocks * 8 + 256);
+    L.gstart = take((fc + 1) * 8);
+    L.poly = take(ecount * 4);
+    L.glen = take(fc * 4);
+    L.vflag = take((np + 1) * 8);
+    L.scan_tmp = take(((ecount + np) / kScanTile + 64) * 8);
+    L.total = o;
+    return L;
+}
+
+Params3 make_params3(const float *x, const float *y, const float *z, int64_t n, int64_t stride,
+                     char *ws, const Layout3 &L, const qh_opts &o)
+{
+    Params3 A = {};
+    A.x = x;
+    A.y = y;
+    A.z = z;
+    A.stride = stride;
+    A.n = (int)n;
+    A.fcap = L.fcap;
+    A.ecap = L.ecap;
+    A.hdr = (Hdr3 *)(ws + L.hdr);
+    A.res = (qh_result *)(ws + L.res);
+    A.fac = (Fac3 *)(ws + L.fac);
+    A.acc = (Acc3 *)(ws + L.acc);
+    A.apex = (float4 *)(ws + L.apex);
+    A.claim = (unsigned long long *)(ws + L.claim);
+    A.cone = (int4 *)(ws + L.cone);
+    A.thr = (float *)(ws + L.thr);
+    A.nstart = (int *)(ws + L.nstart);
+    A.big_mark = (int *)(ws + L.big_mark);
+    A.big_v = (int *)(ws + L.big_v);
+    A.big_h = (int *)(ws + L.big_h);
+    for (int b = 0; b < 2; b++) {
+        A.ent[b] = (Ent3 *)(ws + L.ent[b]);
+        A.pts[b] = (float4 *)(ws + L.pts[b]);
+    }
+    A.tile_ent = (int *)(ws + L.tile_ent);
+    A.tile_m = (int *)(ws + L.tile_m);
+    A.vn = (int2 *)(ws + L.vn);
+    A.vpool = (int *)(ws + L.vpool);
+    A.npool = (int *)(ws + L.npool);
+    A.uncert = (int *)(ws + L.uncert);
+    A.code = (int2 *)(ws + L.code);
+    A.part = (long long *)(ws + L.part);
+    A.blk_a = (float4 *)(ws + L.blk_a);
+    A.blk_b = (float4 *)(ws + L.blk_b);
+    A.blk_v = (float *)(ws + L.blk_v);
+    A.blk_i = (int *)(ws + L.blk_i);
+    A.max_iters = o.max_iters > 0 ? o.max_iters : 4 * n + 16;
+    A.wait_ns = o.wait_ns > 0 ? o.wait_ns : 2000000000ll;
+    return A;
+}
+
+// ---------------------------------------------------------------- device scan
+// Exclusive scan of m int counts into long long offsets (3 kernels).
+__global__ void __launch_bounds__(256) k_scan_sums(const int *in, int m, long long *bsum)
+{
+    __shared__ long long ws[33];
+    const int b0 = blockIdx.x * kScanTile;
+    long long s = 0;
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x)
+        if (b0 + i < m) s += in[b0 + i];
+    long long tot;
+    block_excl_scan64(s, ws, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(256) k_scan_top(long long *bsum, int nb, long long *total)
+{
+    __shared__ long long ws[33];
+    long long carry = 0;
+    for (int base = 0; base < nb; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        long long v = i < nb ? bsum[i] : 0;
+        long long tot;
+        long long ex = block_excl_scan64(v, ws, &tot);
+        if (i < nb) bsum[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void __launch_bounds__(256) k_scan_apply(const int *in, int m, const long long *bsum,
+                                                     long long *out)
+{
+    __shared__ long long ws[33];
+    const int b0 = blockIdx.x * kScanTile;
+    constexpr int kPer = kScanTile / 256;
+    long long v[kPer];
+    long long s = 0;
+#pragma unroll
+    for (int r = 0; r < kPer; r++) {
+        const int i = b0 + threadIdx.x * kPer + r;
+        v[r] = i < m ? in[i] : 0;
+        s += v[r];
+    }
+    long long tot;
+    long long ex = block_excl_scan64(s, ws, &tot) + bsum[blockIdx.x];
+#pragma unroll
+    for (int r = 0; r < kPer; r++) {
+        const int i = b0 + threadIdx.x * kPer + r;
+        if (i < m) out[i] = ex;
+        ex += v[r];
+    }
+}
+
+static void scan_counts(const int *in, int m, long long *out, long long *tmp, long long *d_total,
+                        cudaStream_t st)
+{
+    const int nb = std::max(1, (m + kScanTile - 1) / kScanTile);
+    k_scan_sums<<<nb, 256, 0, st>>>(in, m, tmp);
+    k_scan_top<<<1, 256, 0, st>>>(tmp, nb, d_total);
+    k_scan_apply<<<nb, 256, 0, st>>>(in, m, tmp, out);
+}
+
+// ---------------------------------------------------------------- radix sort
+// Stable LSD radix sort of (u64 key, int value) pairs, 8-bit digits.
+__global__ void __launch_bounds__(256) k_rs_hist(const unsigned long long *key, int m, int shift,
+                                                  int nblk, int *hist)
+{
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int b0 = blockIdx.x * kScanTile;
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x)
+        if (b0 + i < m) atomicAdd(&h[(key[b0 + i] >> shift) & 255], 1);
+    __syncthreads();
+    hist[threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(256) k_rs_scatter(const unsigned long long *key, const int *val,
+                                                     int m, int shift, int nblk,
+                                                     const long long *off,
+                                                     unsigned long long *okey, int *oval)
+{
+    __shared__ long long run[256];
+    __shared__ int cnt[8][256];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    run[threadIdx.x] = off[threadIdx.x * nblk + blockIdx.x];
+    const int b0 = blockIdx.x * kScanTile;
+    for (int sub = 0; sub < kScanTile; sub += 256) {
+        for (int w = 0; w < 8; w++) cnt[w][threadIdx.x] = 0;
+        __syncthreads();
+        const int i = b0 + sub + threadIdx.x;
+        const bool valid = i < m;
+        unsigned long long k = valid ? key[i] : 0ull;
+        const int d = valid ? (int)((k >> shift) & 255) : 256;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int wrank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && wrank == 0) cnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            long long pre = 0;
+            for (int w = 0; w < warp; w++) pre += cnt[w][d];
+            const long long dst = run[d] + pre + wrank;
+            okey[dst] = k;
+            oval[dst] = val[i];
+        }
+        __syncthreads();
+        long long add = 0;
+        for (int w = 0; w < 8; w++) add += cnt[w][threadIdx.x];
+        run[threadIdx.x] += add;
+        __syncthreads();
+    }
+}
+
+// Sorts keys/vals in place (ping-pong through tkey/tval); bits: key bits to sort.
+static void radix_sort(unsigned long long *key, int *val, unsigned long long *tkey, int *tval,
+                       int m, int bits, int *hist, long long *hist_off, long long *tmp,
+                       cudaStream_t st)
+{
+    if (m <= 1) return;
+    const int nblk = (m + kScanTile - 1) / kScanTile;
+    int passes = (bits + 7) / 8;
+    if (passes & 1) passes++;  // even: the result ends in key/val
+    for (int p = 0; p < passes; p++) {
+        const int shift = 8 * p;
+        unsigned long long *ik = (p & 1) ? tkey : key, *ok = (p & 1) ? key : tkey;
+        int *iv = (p & 1) ? tval : val, *ov = (p & 1) ? val : tval;
+        k_rs_hist<<<nblk, 256, 0, st>>>(ik, m, shift, nblk, hist);
+        scan_counts(hist, 256 * nblk, hist_off, tmp, nullptr, st);
+        k_rs_scatter<<<nblk, 256, 0, st>>>(ik, iv, m, shift, nblk, hist_off, ok, ov);
+    }
+}
+
+// ---------------------------------------------------------------- output kernels
+struct OutBufs {
+    int *alive, *label, *cop, *eval[2], *fval[2], *glen, *poly, *hist, *vflag;
+    unsigned long long *ekey[2], *fkey[2];
+    long long *gstart, *scan_tmp, *hist_off;
+};
+
+__device__ __forceinline__ void point_xyz(const Params3 &A, int i, float *p)
+{
+    const long long o = (long long)i * A.stride;
+    p[0] = __ldg(A.x + o);
+    p[1] = __ldg(A.y + o);
+    p[2] = __ldg(A.z + o);
+}
+
+__global__ void __launch_bounds__(256) k_alive(Params3 A, OutBufs O)
+{
+    Hdr3 *H = A.hdr;
+    const int fc = H->fcount;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < fc; f += gridDim.x * blockDim.x) {
+        const Fac3 F = A.fac[f];
+        if (!F.alive) continue;
+        O.alive[atomicAdd(&H->nalive, 1)] = f;
+        O.label[f] = f;
+        int bits = 0;
+        for (int k = 0; k < 3; k++) {
+            const Fac3 &G = A.fac[F.nb[k]];
+            int opp = 0;
+            for (int g = 0; g < 3; g++)
+                if (G.v[g] != F.v[k] && G.v[g] != F.v[(k + 1) % 3]) opp = g;
+            const float *q = G.p + 3 * opp;
+            if (orient3d_exact_sign(F.p, F.p + 3, F.p + 6, q) == 0) bits |= 1 << k;
+        }
+        O.cop[f] = bits;
+        if (bits) atomicAdd(&H->ncop, 1);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_label_round(Params3 A, OutBufs O)
+{
+    Hdr3 *H = A.hdr;
+    const int na = H->nalive;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < na; i += gridDim.x * blockDim.x) {
+        const int f = O.alive[i];
+        const int bits = O.cop[f];
+        if (!bits) continue;
+        int m = O.label[f];
+        for (int k = 0; k < 3; k++)
+            if (bits & (1 << k)) m = min(m, O.label[A.fac[f].nb[k]]);
+        m = min(m, O.label[m]);
+        if (m < O.label[f]) {
+            atomicMin(&O.label[f], m);
+            H->changed = 1;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_bedges(Params3 A, OutBufs O)
+{
+    Hdr3 *H = A.hdr;
+    const int na = H->nalive;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < na; i += gridDim.x * blockDim.x) {
+        const int f = O.alive[i];
+        const int bits = O.cop[f];
+        const Fac3 &F = A.fac[f];
+        for (int k = 0; k < 3; k++) {
+            if (bits & (1 << k)) continue;
+            const int slot = atomicAdd(&H->nbedge, 1);
+            O.ekey[0][slot] = ((unsigned long long)(unsigned)O.label[f] << 32) | (unsigned)F.v[k];
+            O.eval[0][slot] = F.v[(k + 1) % 3];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_gmark(Params3 A, OutBufs O)
+{
+    const int ne = A.hdr->nbedge;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += gridDim.x * blockDim.x) {
+        const bool st = i == 0 || (O.ekey[0][i] >> 32) != (O.ekey[0][i - 1] >> 32);
+        O.poly[i] = st ? 1 : 0;  // poly doubles as the start-flag array here
+    }
+}
+
+__global__ void __launch_bounds__(256) k_gwrite(Params3 A, OutBufs O, const long long *gidx)
+{
+    Hdr3 *H = A.hdr;
+    const int ne = H->nbedge;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += gridDim.x * blockDim.x) {
+        if (O.poly[i]) O.gstart[gidx[i]] = i;
+        if (i == ne - 1) {
+            const int ng = (int)gidx[i] + O.poly[i];
+            H->ngroup = ng;
+            O.gstart[ng] = ne;
+        }
+    }
+}
+
+__device__ __forceinline__ bool collinear3(const float *a, const float *b, const float *c)
+{
+    for (int k = 0; k < 3; k++) {
+        const int i = k, j = (k + 1) % 3;
+        if (orient_exact_sign(a[i], a[j], b[i], b[j], c[i], c[j]) != 0) return false;
+    }
+    return true;
+}
+
+// One thread per group: walk its boundary cycle from the smallest start
+// vertex, drop vertices collinear with their neighbours, rotate to the
+// smallest index.  The polygon is written into poly[gstart .. gstart+len).
+__global__ void __launch_bounds__(128) k_walk(Params3 A, OutBufs O)
+{
+    Hdr3 *H = A.hdr;
+    const int ng = H->ngroup;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        const int s = (int)O.gstart[g], e = (int)O.gstart[g + 1];
+        const int len = e - s;
+        int *cyc = O.poly + s;            // cycle, then the kept vertices
+        int *tmp = O.eval[1] + s;         // scratch of the same size
+        const unsigned long long *key = O.ekey[0] + s;
+        const int *nxt = O.eval[0] + s;
+        int cur = (int)(unsigned)(key[0] & 0xffffffffu);
+        const int first = cur;
+        int got = 0;
+        for (int step = 0; step < len; step++) {
+            tmp[step] = cur;
+            got++;
+            int lo = 0, hi = len - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if ((int)(unsigned)(key[mid] & 0xffffffffu) < cur) lo = mid + 1;
+                else hi = mid;
+            }
+            cur = nxt[lo];
+            if (cur == first) break;
+        }
+        int m = 0;
+        for (int j = 0; j < got; j++) {
+            float pp[3], pv[3], pn[3];
+            point_xyz(A, tmp[(j + got - 1) % got], pp);
+            point_xyz(A, tmp[j], pv);
+            point_xyz(A, tmp[(j + 1) % got], pn);
+            if (got < 3 || !collinear3(pp, pv, pn)) cyc[m++] = tmp[j];
+        }
+        int arg = 0;
+        for (int j = 1; j < m; j++)
+            if (cyc[j] < cyc[arg]) arg = j;
+        for (int j = 0; j < m; j++) tmp[j] = cyc[(arg + j) % m];
+        for (int j = 0; j < m; j++) cyc[j] = tmp[j];
+        O.glen[g] = m;
+        O.fkey[0][g] = ((unsigned long long)(unsigned)cyc[0] << 32) | (unsigned)(m > 1 ? cyc[1] : 0);
+        O.fval[0][g] = g;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_fsizes(Params3 A, OutBufs O)
+{
+    const int ng = A.hdr->ngroup;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x)
+        O.eval[1][i] = O.glen[O.fval[0][i]];  // sizes in sorted face order
+}
+
+__global__ void __launch_bounds__(256) k_fcopy(Params3 A, OutBufs O, const long long *foff,
+                                               int32_t *face_off, int32_t *face_idx)
+{
+    const int ng = A.hdr->ngroup;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
+        const int g = O.fval[0][i];
+        const int s = (int)O.gstart[g], m = O.glen[g];
+        const long long o = foff[i];
+        face_off[i] = (int32_t)o;
+        for (int j = 0; j < m; j++) {
+            const int v = O.poly[s + j];
+            face_idx[o + j] = v;
+            O.vflag[v] = 1;
+        }
+        if (i == ng - 1) face_off[ng] = (int32_t)(o + m);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_vclear(Params3 A, OutBufs O)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x)
+        O.vflag[i] = 0;
+}
+
+__global__ void __launch_bounds__(256) k_vpack(Params3 A, OutBufs O, const long long *voff,
+                                               int32_t *verts)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x)
+        if (O.vflag[i]) verts[voff[i]] = i;
+}
+
+static OutBufs out_bufs(char *ws, const Layout3 &L)
+{
+    OutBufs O;
+    O.alive = (int *)(ws + L.alive);
+    O.label = (int *)(ws + L.label);
+    O.cop = (int *)(ws + L.cop);
+    for (int b = 0; b < 2; b++) {
+        O.ekey[b] = (unsigned long long *)(ws + L.ekey[b]);
+        O.eval[b] = (int *)(ws + L.eval[b]);
+        O.fkey[b] = (unsigned long long *)(ws + L.fkey[b]);
+        O.fval[b] = (int *)(ws + L.fval[b]);
+    }
+    O.hist = (int *)(ws + L.hist);
+    O.hist_off = (long long *)(ws + L.hist_off);
+    O.gstart = (long long *)(ws + L.gstart);
+    O.poly = (int *)(ws + L.poly);
+    O.glen = (int *)(ws + L.glen);
+    O.vflag = (int *)(ws + L.vflag);
+    O.scan_tmp = (long long *)(ws + L.scan_tmp);
+    return O;
+}
+
+}  // namespace d3
+}  // namespace qh
+
+using namespace qh;
+using namespace qh::d3;
+
+extern "C" size_t qh_workspace_bytes_3d(int64_t n, const qh_opts *opts)
+{
+    (void)opts;
+    if (n < 0 || n > QH_MAX_POINTS / 8) return 0;
+    return layout3d(n).total;
+}
+
+static int grid_for(int items, int block)
+{
+    int g = (items + block - 1) / block;
+    return std::max(1, std::min(g, 152 * 16));
+}
+
+extern "C" qh_status qh_hull3d(const float *d_x, const float *d_y, const float *d_z, int64_t n,
+                               int64_t stride, int32_t *d_verts, int64_t *h_nv, int32_t *d_face_off,
+                               int32_t *d_face_idx, int64_t *h_nf, qh_result *h_result, void *d_ws,
+                               size_t ws_bytes, const qh_opts *opts, cudaStream_t st)
+{
+    qh_opts o;
+    qh_default_opts(&o);
+    if (opts) o = *opts;
+    if (h_nv) *h_nv = 0;
+    if (h_nf) *h_nf = 0;
+    if (n < 0 || n > QH_MAX_POINTS / 8 || stride < 1 || !d_ws || !h_nv || !h_nf)
+        return QH_ERR_INVALID_ARG;
+    if (n > 0 && (!d_x || !d_y || !d_z || !d_verts || !d_face_off || !d_face_idx))
+        return QH_ERR_INVALID_ARG;
+    if (o.pred_mode != QH_PRED_F32 && o.pred_mode != QH_PRED_F64) return QH_ERR_INVALID_ARG;
+    if (o.loop_mode != QH_LOOP_PERSISTENT) return QH_ERR_NOT_SUPPORTED;
+    const Layout3 L = layout3d(n);
+    if (ws_bytes < L.total || ((uintptr_t)d_ws & 255)) return QH_ERR_NOMEM;
+    qh_result r = {};
+    if (n == 0) {
+        if (cudaMemsetAsync(d_face_off, 0, 4, st) != cudaSuccess) return QH_ERR_CUDA;
+        if (h_result) *h_result = r;
+        return cudaStreamSynchronize(st) == cudaSuccess ? QH_OK : QH_ERR_CUDA;
+    }
+    char *ws = (char *)d_ws;
+    Params3 A = make_params3(d_x, d_y, d_z, n, stride, ws, L, o);
+    if (cudaMemsetAsync(A.hdr, 0, sizeof(Hdr3), st) != cudaSuccess ||
+        cudaMemsetAsync(A.big_mark, 0xff, ((size_t)L.fcap + 1) * 4, st) != cudaSuccess)
+        return QH_ERR_CUDA;
+    const void *fn = persistent_kernel(o.pred_mode);
+    int grid = persistent_grid(fn, kBlock, o.blocks_per_sm);
+    if (grid <= 0) return QH_ERR_CUDA;
+    grid = std::min(grid, kMaxGrid);
+    void *args[] = {&A};
+    if (cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, 0, st) != cudaSuccess)
+        return QH_ERR_CUDA;
+    Hdr3 hh;
+    auto read_hdr = [&]() {
+        return cudaMemcpyAsync(&hh, A.hdr, sizeof(Hdr3), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+               cudaStreamSynchronize(st) == cudaSuccess;
+    };
+    if (!read_hdr()) return QH_ERR_CUDA;
+    r.status = hh.status;
+    r.iterations = hh.iter;
+    r.survivor_total = hh.surv_total;
+    r.live_total = n + hh.surv_total;
+    r.segments_total = hh.seg_total;
+    r.filter_fallbacks = (int64_t)hh.fallbacks;
+    r.exact_argmax = (int64_t)hh.exact_argmax;
+    if (hh.status != 0) {
+        if (h_result) *h_result = r;
+        return (qh_status)hh.status;
+    }
+    // ---- output stage
+    OutBufs O = out_bufs(ws, L);
+    const int fc = hh.fcount;
+    k_alive<<<grid_for(fc, 256), 256, 0, st>>>(A, O);
+    if (!read_hdr()) return QH_ERR_CUDA;
+    const int na = hh.nalive;
+    if (hh.ncop > 0) {
+        for (int round = 0; round < 4 * na + 8; round++) {
+            int zero = 0;
+            cudaMemcpyAsync(&A.hdr->changed, &zero, 4, cudaMemcpyHostToDevice, st);
+            k_label_round<<<grid_for(na, 256), 256, 0, st>>>(A, O);
+            if (!read_hdr()) return QH_ERR_CUDA;
+            if (!hh.changed) break;
+        }
+    }
+    k_bedges<<<grid_for(na, 256), 256, 0, st>>>(A, O);
+    if (!read_hdr()) return QH_ERR_CUDA;
+    const int ne = hh.nbedge;
+    int lbits = 1;
+    while ((1ll << lbits) <= (long long)fc) lbits++;
+    radix_sort(O.ekey[0], O.eval[0], O.ekey[1], O.eval[1], ne, 32 + lbits, O.hist, O.hist_off,
+               O.scan_tmp, st);
+    k_gmark<<<grid_for(ne, 256), 256, 0, st>>>(A, O);
+    // start-flag scan -> group index (the edge-sort scratch keys are free now)
+    long long *gscan = (long long *)O.ekey[1];
+    scan_counts(O.poly, ne, gscan, O.scan_tmp, nullptr, st);
+    k_gwrite<<<grid_for(ne, 256), 256, 0, st>>>(A, O, gscan);
+    if (!read_hdr()) return QH_ERR_CUDA;
+    const int ng = hh.ngroup;
+    if ((long long)ng > 2 * n) return QH_ERR_CAPACITY;  // a polytope has at most 2n - 4 faces
+    k_walk<<<grid_for(ng, 128), 128, 0, st>>>(A, O);
+    int vbits = 1;
+    while ((1ll << vbits) <= (long long)n) vbits++;
+    radix_sort(O.fkey[0], O.fval[0], O.fkey[1], O.fval[1], ng, 32 + vbits, O.hist, O.hist_off,
+               O.scan_tmp, st);
+    k_fsizes<<<grid_for(ng, 256), 256, 0, st>>>(A, O);
+    long long *foff = (long long *)O.ekey[1];
+    long long *d_ftot = (long long *)O.fkey[1];
+    scan_counts(O.eval[1], ng, foff, O.scan_tmp, d_ftot, st);
+    long long ftot = 0;
+    if (cudaMemcpyAsync(&ftot, d_ftot, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return QH_ERR_CUDA;
+    if (ftot > 6 * n) return QH_ERR_CAPACITY;  // face indices: 2E <= 6n
+    k_vclear<<<grid_for((int)n, 256), 256, 0, st>>>(A, O);
+    k_fcopy<<<grid_for(ng, 256), 256, 0, st>>>(A, O, foff, d_face_off, d_face_idx);
+    long long *voff = (long long *)O.eval[1];  // n long longs fit: eval[1] holds 3 * fcap ints
+    long long *d_nv = (long long *)O.fkey[1];
+    scan_counts(O.vflag, (int)n, voff, O.scan_tmp, d_nv, st);
+    k_vpack<<<grid_for((int)n, 256), 256, 0, st>>>(A, O, voff, d_verts);
+    long long nv = 0;
+    int32_t fidx_total = 0;
+    if (cudaMemcpyAsync(&nv, d_nv, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&fidx_total, d_face_off + ng, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return QH_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return QH_ERR_CUDA;
+    *h_nv = nv;
+    *h_nf = ng;
+    r.count = nv;
+    r.extra[0] = nv;
+    r.extra[1] = ng;
+    r.extra[2] = fidx_total;
+    if (h_result) *h_result = r;
+    return QH_OK;
+}

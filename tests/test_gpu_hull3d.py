@@ -1,0 +1,94 @@
+"""GPU parity for the 3D hull: vertex list and canonical face list of the
+CUDA path (through the C ABI) equal the oracle's, on seeded inputs of the
+paper's distributions (in, on, near the sphere), Gaussian clouds, lattices
+with coplanar faces and collinear edges, and degenerate inputs."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1201_2936_gb300 import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qh():
+    from paper_1201_2936_gb300 import build
+    build.build()
+    oracle.build()
+    import paper_1201_2936_gb300 as q
+    return q
+
+
+def _gpu(qh, x, y, z, **kw):
+    X, Y, Z = (torch.from_numpy(np.ascontiguousarray(c, dtype=np.float32)).cuda() for c in (x, y, z))
+    (v, off, idx), res = qh.hull3d(X, Y, Z, return_result=True, **kw)
+    v, off, idx = v.cpu().numpy(), off.cpu().numpy(), idx.cpu().numpy()
+    faces = [idx[off[i]:off[i + 1]].tolist() for i in range(len(off) - 1)]
+    return v.tolist(), faces, res
+
+
+def _oracle(x, y, z):
+    v, f = oracle.hull3d(x, y, z)
+    return v.tolist(), [t.tolist() for t in f]
+
+
+@pytest.mark.parametrize("gen,n", [("ball", 1000), ("ball", 100_003), ("sphere", 20_000),
+                                   ("near", 50_000), ("gauss", 200_001), ("ball", 5)])
+def test_distributions_match_oracle(qh, gen, n):
+    seed = 300 + n
+    if gen == "ball":
+        x, y, z = w.uniform_ball(n, seed)
+    elif gen == "sphere":
+        x, y, z = w.on_sphere(n, seed)
+    elif gen == "near":
+        x, y, z = w.near_sphere(n, seed, 1e-3)
+    else:
+        r = np.random.default_rng(seed)
+        x, y, z = (r.normal(size=(3, n)) * np.array([[1.0], [0.3], [2.0]])).astype(np.float32)
+    want = _oracle(x, y, z)
+    for pred in ("f32", "f64"):
+        v, f, res = _gpu(qh, x, y, z, pred=pred)
+        assert v == want[0], (gen, n, pred)
+        assert f == want[1], (gen, n, pred)
+
+
+def test_cube_lattice_and_coplanar(qh):
+    rng = np.random.default_rng(7)
+    corners = np.array([[i, j, k] for i in (-1, 1) for j in (-1, 1) for k in (-1, 1)], np.float32)
+    inner = rng.uniform(-0.99, 0.99, (5000, 3)).astype(np.float32)
+    onface = rng.uniform(-1, 1, (500, 3)).astype(np.float32)
+    onface[np.arange(500), rng.integers(0, 3, 500)] = rng.choice([-1.0, 1.0], 500)
+    P = np.concatenate([inner, corners, onface])[rng.permutation(5508)]
+    want = _oracle(P[:, 0], P[:, 1], P[:, 2])
+    v, f, _ = _gpu(qh, P[:, 0], P[:, 1], P[:, 2])
+    assert (v, f) == (want[0], want[1])
+    assert len(f) == 6
+    for k in range(6):  # small lattices: many coplanar facets and ties
+        P = rng.integers(-3, 4, (400 + 50 * k, 3)).astype(np.float32)
+        want = _oracle(P[:, 0], P[:, 1], P[:, 2])
+        v, f, _ = _gpu(qh, P[:, 0], P[:, 1], P[:, 2])
+        assert (v, f) == (want[0], want[1]), k
+
+
+def test_degenerate_inputs(qh):
+    for pts in ([[0, 0, 0], [1, 1, 1], [2, 2, 2], [3, 3, 3]],
+                [[0, 0, 2], [1, 0, 2], [0, 1, 2], [1, 1, 2], [0.5, 0.5, 2]],
+                [[1, 2, 3]] * 10):
+        P = np.array(pts, np.float32)
+        with pytest.raises(qh.QHError) as ei:
+            _gpu(qh, P[:, 0], P[:, 1], P[:, 2])
+        assert ei.value.status == 3
+    P = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], np.float32)
+    v, f, _ = _gpu(qh, P[:, 0], P[:, 1], P[:, 2])
+    assert (v, f) == _oracle(P[:, 0], P[:, 1], P[:, 2])
+
+
+def test_interleaved_layout(qh):
+    x, y, z = w.uniform_ball(30_000, 11)
+    want = _oracle(x, y, z)
+    P = torch.from_numpy(np.stack([x, y, z], 1)).cuda()
+    v, off, idx = qh.hull3d(P)
+    faces = [idx[off[i]:off[i + 1]].tolist() for i in range(len(off) - 1)]
+    assert v.tolist() == want[0] and faces == want[1]
