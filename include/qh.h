@@ -149,7 +149,8 @@ qh_status qh_hull2d(const float *d_x, const float *d_y, int64_t n, int64_t strid
 /* ---------------------------------------------------------------------- */
 
 /* Bytes of device workspace qh_hull3d needs for n points
- * (n <= QH_MAX_POINTS / 8). */
+ * (n <= QH_MAX_POINTS_3D). */
+#define QH_MAX_POINTS_3D ((int64_t)44000000)
 size_t qh_workspace_bytes_3d(int64_t n, const qh_opts *opts);
 
 /*
@@ -216,6 +217,15 @@ qh_status qh_hull2d_noalloc(const float *d_x, const float *d_y, int64_t n, int64
  * receives the count.  Timing comes from %globaltimer between grid
  * barriers. */
 qh_status qh_debug_timeline_2d(const void *d_ws, int64_t n, int64_t *h_rows, int32_t max_rows,
+                               int32_t *h_nrows, cudaStream_t stream);
+
+/* Per-iteration record of the last qh_hull3d call made on d_ws (same n; the
+ * call synchronises the stream).  Row r (h_rows: int64[10 * max_rows]) holds
+ * {iteration, live points, segments, apexes inserted, then the device time in
+ * ns of: visible-set search, selection rounds and cones, point assignment,
+ * segment table, scatter and certification, exact farthest points}.  At most
+ * 64 rows. */
+qh_status qh_debug_timeline_3d(const void *d_ws, int64_t n, int64_t *h_rows, int32_t max_rows,
                                int32_t *h_nrows, cudaStream_t stream);
 
 #ifdef __cplusplus

@@ -194,6 +194,21 @@ def hull2d_noalloc(x: torch.Tensor, y: Optional[torch.Tensor] = None, *,
     return out[: cnt.value]
 
 
+def debug_timeline_3d(workspace: Workspace, n: int, stream=None):
+    """Per-iteration rows of the last 3D call on `workspace` with n points:
+    iteration, live points, segments, apexes, then ns of select, rounds,
+    assign, table, scatter, exact."""
+    import numpy as np
+    rows = np.zeros((64, 10), dtype=np.int64)
+    nr = ctypes.c_int32(0)
+    st = _native.lib().qh_debug_timeline_3d(workspace.buf.data_ptr(), int(n),
+                                            rows.ctypes.data_as(ctypes.c_void_p), 64,
+                                            ctypes.byref(nr), _stream_handle(stream))
+    if st != 0:
+        raise QHError(st, "qh_debug_timeline_3d")
+    return rows[: nr.value]
+
+
 def result_from_tensor(result: torch.Tensor) -> QhResult:
     raw = bytes(result.cpu().numpy().tobytes())
     return QhResult.from_buffer_copy(raw[:RESULT_BYTES])

@@ -49,6 +49,8 @@ SIGNATURES = [
     ("qh_workspace_bytes_3d", _sz, [_i64, _POpts]),
     ("qh_hull3d", ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, _vp, ctypes.POINTER(_i64), _vp, _vp,
                                  ctypes.POINTER(_i64), _PRes, _vp, _sz, _POpts, _vp]),
+    ("qh_debug_timeline_3d", ctypes.c_int, [_vp, _i64, _vp, ctypes.c_int32,
+                                            ctypes.POINTER(ctypes.c_int32), _vp]),
     ("qh_hull2d_noalloc", ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, ctypes.POINTER(_i64), _vp]),
     ("qh_debug_timeline_2d", ctypes.c_int, [_vp, _i64, _vp, ctypes.c_int32,
                                             ctypes.POINTER(ctypes.c_int32), _vp]),

@@ -300,9 +300,9 @@ __device__ void build_tetra(const Params3 &A)
 
 // ---------------------------------------------------------------- S: select
 // One thread per segment (candidate): visible-set BFS from its facet with
-// exact tests, then priority claims on the visible facets.
+// exact tests.  V: visible facets, N: their non-visible neighbours.
 template <int MODE>
-__device__ void select3d(const Params3 &A, int par, int iter, int bid, int nb)
+__device__ void select3d(const Params3 &A, int par, int bid, int nb)
 {
     Hdr3 *H = A.hdr;
     const int ne = *(volatile int *)&H->nent[par];
@@ -340,24 +340,50 @@ __device__ void select3d(const Params3 &A, int par, int iter, int bid, int nb)
             }
         }
         A.vn[e] = over ? make_int2(-1, -1) : make_int2(nv, nn);
-        if (!over) {
-            const unsigned long long mine = claim_key(iter, f0);
-            for (int j = 0; j < nv; j++) atomicMax(&A.claim[V[j]], mine);
-        }
+        A.cstate[e] = over ? 2 : 0;
     }
     unsigned f = __reduce_add_sync(0xffffffffu, fallbacks);
     if ((threadIdx.x & 31) == 0 && f) atomicAdd(&H->fallbacks, (unsigned long long)f);
+}
+
+// Round `round` of the selection: every still-active candidate drops out if
+// a winner of an earlier round deleted a facet of V or N (their regions would
+// touch), else claims its visible facets.
+__device__ void claim3d(const Params3 &A, int par, int iter, int round, int bid, int nb)
+{
+    Hdr3 *H = A.hdr;
+    if (bid == 0 && threadIdx.x == 0) H->nactive[(round + 1) & 1] = 0;  // next round's counter
+    const int ne = *(volatile int *)&H->nent[par];
+    const Ent3 *ent = A.ent[par];
+    for (int e = bid * blockDim.x + threadIdx.x; e < ne; e += nb * blockDim.x) {
+        if (A.cstate[e] != 0) continue;
+        const int2 c = A.vn[e];
+        const int *V = A.vpool + (size_t)e * kVCap;
+        const int *N = A.npool + (size_t)e * kNCap;
+        bool touched = false;
+        if (round > 0) {
+            for (int j = 0; j < c.x && !touched; j++) touched = A.taken[V[j]] == iter;
+            for (int j = 0; j < c.y && !touched; j++) touched = A.taken[N[j]] == iter;
+        }
+        if (touched) {
+            A.cstate[e] = 2;
+            continue;
+        }
+        const unsigned long long mine = claim_key(iter, round, ent[e].f, ent[e].len);
+        for (int j = 0; j < c.x; j++) atomicMax(&A.claim[V[j]], mine);
+        atomicAdd(&H->nactive[round & 1], 1);
+    }
 }
 
 // Cone of one winner: horizon edges of V (edges whose neighbour is not in V),
 // one facet (u, v, q) per horizon edge, neighbours relinked.  V and N are the
 // winner's visible facets and horizon neighbours; hz is scratch for the
 // horizon (capacity >= |V| + 2).
-__device__ bool build_cone(const Params3 &A, int f0, const int *V, int nv, int *hz, int hcap,
-                           int iter)
+__device__ bool build_cone(const Params3 &A, int f0, int len, const int *V, int nv, int *hz,
+                           int hcap, int iter, int round)
 {
     Hdr3 *H = A.hdr;
-    const unsigned long long mine = claim_key(iter, f0);
+    const unsigned long long mine = claim_key(iter, round, f0, len);
     const float4 q4 = A.apex[f0];
     const int qi = __float_as_int(q4.w);
     int nh = 0;
@@ -415,6 +441,7 @@ __device__ bool build_cone(const Params3 &A, int f0, const int *V, int nv, int *
     }
     for (int i = 0; i < nv; i++) {
         A.fac[V[i]].alive = 0;
+        A.taken[V[i]] = iter;
         A.cone[V[i]] = make_int4(base, nh, qi, iter);
     }
     atomicAdd(&H->hull_vertices, 1);
@@ -423,24 +450,133 @@ __device__ bool build_cone(const Params3 &A, int f0, const int *V, int nv, int *
 }
 
 // ---------------------------------------------------------------- C: winners
-__device__ void cone3d(const Params3 &A, int par, int iter, int bid, int nb)
+// One warp per candidate that claimed in this round.  A winner owns every
+// facet of V and no facet of N carries a higher claim; it builds its cone at
+// once: horizon edges found by the lanes (ballot-compacted), one cone facet
+// per horizon edge, the horizon neighbours relinked, and the cone facets
+// linked around the apex by matching edge ends across lanes (shuffles).
+__device__ void cone_warp(const Params3 &A, int e, int f0, int len, const int *V, int nv,
+                          int *hz, int iter, int round)
+{
+    Hdr3 *H = A.hdr;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const unsigned long long mine = claim_key(iter, round, f0, len);
+    const float4 q4 = A.apex[f0];
+    const int qi = __float_as_int(q4.w);
+    int nh = 0;
+    for (int p0 = 0; p0 < 3 * nv; p0 += 32) {
+        const int p = p0 + lane;
+        bool is_h = false;
+        if (p < 3 * nv) {
+            const int i = p / 3, k = p - 3 * (p / 3);
+            is_h = A.claim[A.fac[V[i]].nb[k]] != mine;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, is_h);
+        if (is_h) {
+            const int pos = nh + __popc(b & lt);
+            if (pos < kNCap) hz[pos] = V[p / 3] * 3 + (p - 3 * (p / 3));
+        }
+        nh += __popc(b);
+    }
+    if (nh > kNCap) {  // a visible region that is not a disk: cannot happen
+        if (lane == 0) set_status(H, QH_ERR_CAPACITY);
+        return;
+    }
+    __syncwarp();
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&H->fcount, nh);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base + nh > A.fcap) {
+        if (lane == 0) set_status(H, QH_ERR_CAPACITY);
+        return;
+    }
+    int u[2] = {-1, -1}, w[2] = {-1, -1};
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        const int j = lane + 32 * r;
+        if (j >= nh) continue;
+        const int hf = hz[j] / 3, k = hz[j] - 3 * (hz[j] / 3), k1 = (k + 1) % 3;
+        const Fac3 &F = A.fac[hf];
+        Fac3 C;
+        C.p[0] = F.p[3 * k + 0]; C.p[1] = F.p[3 * k + 1]; C.p[2] = F.p[3 * k + 2];
+        C.p[3] = F.p[3 * k1 + 0]; C.p[4] = F.p[3 * k1 + 1]; C.p[5] = F.p[3 * k1 + 2];
+        C.p[6] = q4.x; C.p[7] = q4.y; C.p[8] = q4.z;
+        C.v[0] = F.v[k];
+        C.v[1] = F.v[k1];
+        C.v[2] = qi;
+        const int g = F.nb[k];
+        C.nb[0] = g;
+        C.nb[1] = -1;
+        C.nb[2] = -1;
+        C.alive = 1;
+        u[r] = C.v[0];
+        w[r] = C.v[1];
+        A.fac[base + j] = C;
+        Acc3 z = {};
+        A.acc[base + j] = z;
+        A.claim[base + j] = 0ull;
+        Fac3 &G = A.fac[g];
+        for (int t = 0; t < 3; t++)
+            if (G.nb[t] == hf) G.nb[t] = base + j;
+    }
+    // edge (w, q) of a cone facet meets the cone facet whose horizon edge starts
+    // at w; edge (q, u) meets the one whose horizon edge ends at u
+    int n1[2] = {-1, -1}, n2[2] = {-1, -1};
+    for (int src = 0; src < 32; src++) {
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            const int su = __shfl_sync(0xffffffffu, u[r], src);
+            const int sw = __shfl_sync(0xffffffffu, w[r], src);
+            const int sj = src + 32 * r;
+            if (sj >= nh) continue;
+#pragma unroll
+            for (int mr = 0; mr < 2; mr++) {
+                if (u[mr] < 0) continue;
+                if (su == w[mr]) n1[mr] = base + sj;
+                if (sw == u[mr]) n2[mr] = base + sj;
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        const int j = lane + 32 * r;
+        if (j >= nh) continue;
+        A.fac[base + j].nb[1] = n1[r];
+        A.fac[base + j].nb[2] = n2[r];
+    }
+    for (int i = lane; i < nv; i += 32) {
+        A.fac[V[i]].alive = 0;
+        A.taken[V[i]] = iter;
+        A.cone[V[i]] = make_int4(base, nh, qi, iter);
+    }
+    if (lane == 0) {
+        atomicAdd(&H->hull_vertices, 1);
+        atomicAdd(&H->nwin, 1);
+        A.cstate[e] = 1;
+    }
+}
+
+__device__ void cone3d(const Params3 &A, int par, int iter, int round, int bid, int nb)
 {
     Hdr3 *H = A.hdr;
     const int ne = *(volatile int *)&H->nent[par];
     const Ent3 *ent = A.ent[par];
-    for (int e = bid * blockDim.x + threadIdx.x; e < ne; e += nb * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (bid * blockDim.x + threadIdx.x) >> 5, nw = (nb * blockDim.x) >> 5;
+    for (int e = gw; e < ne; e += nw) {
+        if (A.cstate[e] != 0) continue;
         const int2 c = A.vn[e];
-        if (c.x < 0) continue;
-        const int f0 = ent[e].f;
-        const unsigned long long mine = claim_key(iter, f0);
+        const int f0 = ent[e].f, len = ent[e].len;
+        const unsigned long long mine = claim_key(iter, round, f0, len);
         const int *V = A.vpool + (size_t)e * kVCap;
         const int *N = A.npool + (size_t)e * kNCap;
-        bool win = true;
-        for (int j = 0; j < c.x && win; j++) win = A.claim[V[j]] == mine;
-        for (int j = 0; j < c.y && win; j++) win = A.claim[N[j]] < mine;
-        if (!win) continue;
+        bool ok = true;
+        for (int j = lane; j < c.x; j += 32) ok &= A.claim[V[j]] == mine;
+        for (int j = lane; j < c.y; j += 32) ok &= A.claim[N[j]] < mine;
+        if (!__all_sync(0xffffffffu, ok)) continue;
         // the horizon list reuses the candidate's neighbour slice (>= |V| + 2)
-        build_cone(A, f0, V, c.x, A.npool + (size_t)e * kNCap, kNCap, iter);
+        cone_warp(A, e, f0, len, V, c.x, A.npool + (size_t)e * kNCap, iter, round);
     }
 }
 
@@ -453,15 +589,19 @@ __device__ void fallback3d(const Params3 &A, int par, int iter)
     if (threadIdx.x != 0) return;
     const int ne = H->nent[par];
     const Ent3 *ent = A.ent[par];
-    int f0 = INT_MAX;
-    for (int e = 0; e < ne; e++) f0 = min(f0, ent[e].f);
+    int f0 = INT_MAX, len = 0;
+    for (int e = 0; e < ne; e++)
+        if (ent[e].len > len || (ent[e].len == len && ent[e].f < f0)) {
+            f0 = ent[e].f;
+            len = ent[e].len;
+        }
     if (f0 == INT_MAX) return;
     const float4 q4 = A.apex[f0];
     const float q[3] = {q4.x, q4.y, q4.z};
     int *V = A.big_v;
     int nv = 1;
     V[0] = f0;
-    const unsigned long long mine = claim_key(iter, f0);
+    const unsigned long long mine = claim_key(iter, kRounds, f0, len);
     A.claim[f0] = mine;
     unsigned fb = 0;
     for (int i = 0; i < nv; i++) {
@@ -482,7 +622,7 @@ __device__ void fallback3d(const Params3 &A, int par, int iter)
             }
         }
     }
-    build_cone(A, f0, V, nv, A.big_h, A.fcap, iter);
+    build_cone(A, f0, len, V, nv, A.big_h, A.fcap, iter, kRounds);
 }
 
 // ---------------------------------------------------------------- A: assign
@@ -495,10 +635,10 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int n
 {
     Hdr3 *H = A.hdr;
     const int L = FIRST ? A.n : *(volatile int *)&H->L[par];
-    const int ne = FIRST ? 1 : *(volatile int *)&H->nent[par];
     const Ent3 *ent = A.ent[par];
     const float4 *P = A.pts[par];
     const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
     unsigned fallbacks = 0;
     const int ntiles = (L + kTile - 1) / kTile;
     for (int tile = bid; tile < ntiles; tile += nb) {
@@ -507,6 +647,13 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int n
         if (threadIdx.x == 0) {
             sm.a.e0 = FIRST ? 0 : A.tile_ent[tile];
             sm.a.m = FIRST ? 1 : A.tile_m[tile];
+        }
+        for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
+            sm.a.skey[i] = -1;
+            sm.a.scnt[i] = 0;
+            sm.a.sk1[i] = 0ull;
+            sm.a.so2[i] = 0u;
+            sm.a.sem[i] = 0u;
         }
         __syncthreads();
         const int e0 = sm.a.e0, m = sm.a.m;
@@ -520,11 +667,13 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int n
             }
         }
         __syncthreads();
-#pragma unroll 1
+        // ---- classify; cone targets get a tile-local slot (shared hash table)
+        int tgt[kItems], rk[kItems], slot[kItems];
+#pragma unroll
         for (int k = 0; k < kItems; k++) {
             const int v = v0 + k * blockDim.x + threadIdx.x;
             const bool valid = v < v1;
-            int target = -1, rank = 0;
+            int target = -1, rank = 0, s = -1;
             float d = 0.0f, err = 0.0f;
             int idx = 0;
             bool cone_t = false;
@@ -559,7 +708,6 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int n
                     }
                 }
             }
-            // warp-aggregated count, rank and key per cone target
             const unsigned act = __ballot_sync(0xffffffffu, cone_t);
             if (cone_t) {
                 const unsigned grp = __match_any_sync(act, target);
@@ -571,22 +719,68 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int n
                 const unsigned sec = (o == top_o && (unsigned)idx == top_i) ? 0u : o;
                 const unsigned sec_o = __reduce_max_sync(grp, sec);
                 const unsigned em = __reduce_max_sync(grp, __float_as_uint(err));
-                unsigned base = 0;
+                int base = 0;
                 if (lane == leader) {
-                    Acc3 &ac = A.acc[target];
-                    base = atomicAdd(&ac.cnt, (unsigned)__popc(grp));
+                    // find or insert the target's slot (linear probing)
+                    int h = (int)(((unsigned)target * 0x9E3779B1u) >> (32 - kSlotBits));
+                    for (int probe = 0; probe < kSlots; probe++) {
+                        const int prev = atomicCAS(&sm.a.skey[h], -1, target);
+                        if (prev == -1 || prev == target) {
+                            s = h;
+                            break;
+                        }
+                        h = (h + 1) & (kSlots - 1);
+                    }
                     const unsigned long long k1 =
                         ((unsigned long long)top_o << 32) | (0xffffffffu - top_i);
-                    unsigned long long old = atomicMax(&ac.key1, k1);
-                    unsigned long long lo = old < k1 ? old : k1;
-                    unsigned lo_o = (unsigned)(lo >> 32);
-                    atomicMax(&ac.o2, lo_o > sec_o ? lo_o : sec_o);
-                    atomicMax(&ac.emax, em);
+                    if (s >= 0) {
+                        base = atomicAdd(&sm.a.scnt[s], __popc(grp));
+                        const unsigned long long old = atomicMax(&sm.a.sk1[s], k1);
+                        const unsigned long long lo2 = old < k1 ? old : k1;
+                        const unsigned lo_o = (unsigned)(lo2 >> 32);
+                        atomicMax(&sm.a.so2[s], lo_o > sec_o ? lo_o : sec_o);
+                        atomicMax(&sm.a.sem[s], em);
+                    } else {
+                        // table full: straight to the global accumulator
+                        Acc3 &ac = A.acc[target];
+                        base = (int)atomicAdd(&ac.cnt, (unsigned)__popc(grp));
+                        const unsigned long long old = atomicMax(&ac.key1, k1);
+                        const unsigned long long lo2 = old < k1 ? old : k1;
+                        const unsigned lo_o = (unsigned)(lo2 >> 32);
+                        atomicMax(&ac.o2, lo_o > sec_o ? lo_o : sec_o);
+                        atomicMax(&ac.emax, em);
+                    }
                 }
                 base = __shfl_sync(grp, base, leader);
-                rank = (int)base + __popc(grp & lanemask_lt());
+                s = __shfl_sync(grp, s, leader);
+                rank = base + __popc(grp & lt);
             }
-            if (valid) A.code[v] = make_int2(target, rank);
+            tgt[k] = valid ? target : -2;
+            rk[k] = rank;
+            slot[k] = s;
+        }
+        __syncthreads();
+        // ---- one global reservation and key merge per (tile, target)
+        for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
+            const int t = sm.a.skey[i];
+            if (t < 0) continue;
+            Acc3 &ac = A.acc[t];
+            sm.a.sbase[i] = (int)atomicAdd(&ac.cnt, (unsigned)sm.a.scnt[i]);
+            const unsigned long long k1 = sm.a.sk1[i];
+            const unsigned long long old = atomicMax(&ac.key1, k1);
+            const unsigned long long lo2 = old < k1 ? old : k1;
+            const unsigned lo_o = (unsigned)(lo2 >> 32);
+            const unsigned o2 = sm.a.so2[i];
+            atomicMax(&ac.o2, lo_o > o2 ? lo_o : o2);
+            atomicMax(&ac.emax, sm.a.sem[i]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kItems; k++) {
+            const int v = v0 + k * blockDim.x + threadIdx.x;
+            if (tgt[k] == -2) continue;
+            const int r = (slot[k] >= 0) ? sm.a.sbase[slot[k]] + rk[k] : rk[k];
+            A.code[v] = make_int2(tgt[k], r);
         }
     }
     unsigned fsum = __reduce_add_sync(0xffffffffu, fallbacks);
@@ -808,6 +1002,15 @@ __global__ void __launch_bounds__(kBlock) qh3d_persistent(Params3 A)
     const int bid = blockIdx.x, nb = gridDim.x;
     auto sync = [&]() { grid_sync(&H->bar, fail, A.wait_ns); };
     auto ok = [&]() { return *(volatile int *)&H->status == 0; };
+    // phase clock of block 0, thread 0 (per-iteration record)
+    const bool clk = bid == 0 && threadIdx.x == 0;
+    unsigned long long tprev = clk ? globaltimer_ns() : 0;
+    auto mark = [&](int it, int col) {
+        if (!clk) return;
+        const unsigned long long t = globaltimer_ns();
+        if (it > 0 && it <= kTimeline3) H->tl[it - 1][col] += (long long)(t - tprev);
+        tprev = t;
+    };
 
     // ---- initial simplex
     extrema3d(A, sm, bid, nb);
@@ -866,33 +1069,51 @@ __global__ void __launch_bounds__(kBlock) qh3d_persistent(Params3 A)
             H->iter = iter;
             H->nwin = 0;
             H->seg_total += H->nent[cur];
+            if (iter <= kTimeline3) {
+                H->tl[iter - 1][0] = H->L[cur];
+                H->tl[iter - 1][1] = H->nent[cur];
+            }
         }
-        select3d<MODE>(A, cur, iter, bid, nb);
+        mark(0, 0);
+        select3d<MODE>(A, cur, bid, nb);
         sync();
-        cone3d(A, cur, iter, bid, nb);
+        mark(iter, 3);
+        if (bid == 0 && threadIdx.x == 0) H->nactive[0] = 0;
         sync();
+        for (int round = 0; round < kRounds; round++) {
+            claim3d(A, cur, iter, round, bid, nb);
+            sync();
+            if (*(volatile int *)&H->nactive[round & 1] == 0) break;
+            cone3d(A, cur, iter, round, bid, nb);
+            sync();
+        }
         if (*(volatile int *)&H->nwin == 0) {
             if (bid == 0) fallback3d<MODE>(A, cur, iter);
             sync();
         }
+        if (clk && iter <= kTimeline3) H->tl[iter - 1][2] = H->nwin;
+        mark(iter, 4);
         if (!ok()) break;
         assign3d<MODE, false>(A, cur, sm, bid, nb);
         sync();
+        mark(iter, 5);
         table_sum(A, cur, false, sm, bid, nb);
         sync();
         table_write(A, cur, false, sm, bid, nb);
         if (bid == 0 && threadIdx.x == 0) H->n_uncert = 0;
         sync();
+        mark(iter, 6);
         scatter3d<false>(A, cur, bid, nb);
-        sync();
-        certify3d(A, cur, bid, nb);
+        certify3d(A, cur, bid, nb);  // reads the table and accumulators only
         if (bid == 0 && threadIdx.x == 0) H->surv_total += H->L[cur ^ 1];
         sync();
+        mark(iter, 7);
         if (*(volatile int *)&H->n_uncert > 0) {
             exact3d<MODE>(A, cur, sm, bid, nb);
             if (bid == 0 && threadIdx.x == 0) H->exact_argmax += H->n_uncert;
             sync();
         }
+        mark(iter, 8);
         cur ^= 1;
     }
 }

@@ -52,7 +52,7 @@ struct Hdr3 {
     int fc_iter[2];         // facet count when the table of that parity was built
     int fc_lo_last;         // first facet id created in the last iteration
     int hull_vertices;
-    int nwin, iter;
+    int nwin, iter, nactive[2];
     int nent[2], L[2];
     int n_uncert;
     int pad0;
@@ -61,7 +61,12 @@ struct Hdr3 {
     // output stage
     int nalive, ncop, nbedge, ngroup, nface, nvert, changed, pad1;
     long long nfidx;
+    // per-iteration record (first kTimeline3 iterations): live points,
+    // segments, winners, then device time of select, rounds, assign, table,
+    // scatter + certify, exact (ns)
+    long long tl[64][9];
 };
+constexpr int kTimeline3 = 64;
 
 struct Params3 {
     const float *x, *y, *z;
@@ -84,6 +89,8 @@ struct Params3 {
     Ent3 *ent[2];
     int *tile_ent, *tile_m;
     int2 *vn;                     // (|V|, |N|) of a candidate, (-1,-1) on overflow
+    int *cstate;                  // candidate state in an iteration: 0 active, 1 won, 2 out
+    int *taken;                   // iteration whose winner deleted the facet
     int *vpool, *npool;
     int *uncert;
     // points
@@ -101,9 +108,20 @@ struct Params3 {
 // tetrahedron): cone[kPseudoSlot(A)].
 #define kPseudo (A.fcap)
 
-__device__ __forceinline__ unsigned long long claim_key(int iter, int f)
+// Claim of a candidate (the facet f whose segment of `len` points it heads)
+// in a selection round.  Later iterations and rounds win over earlier ones;
+// within a round larger segments go first (size class = log2(len) / 2, so a
+// segment with millions of points is not starved by small neighbours), then
+// a bijective pseudo-random permutation of the facet ids (28 bits), which
+// keeps keys unique and makes each round's winners a Luby-style independent
+// set.  Bits: iteration 28 | round 4 | size class 4 | permutation 28.
+constexpr int kRounds = 4;
+__device__ __forceinline__ unsigned long long claim_key(int iter, int round, int f, int len)
 {
-    return ((unsigned long long)(unsigned)iter << 32) | (unsigned long long)(0xffffffffu - (unsigned)f);
+    const unsigned perm = (((unsigned)f ^ ((unsigned)iter * 0x9E37u)) * 0x0B5AD4Bu) & 0x0FFFFFFFu;
+    const unsigned cls = min(15u, (31u - (unsigned)__clz(max(len, 1))) >> 1);
+    return ((unsigned long long)(unsigned)iter << 36) | ((unsigned long long)round << 32) |
+           ((unsigned long long)cls << 28) | perm;
 }
 
 struct SmemRed {
@@ -111,10 +129,15 @@ struct SmemRed {
     float v[kBlock];
     int i[kBlock];
 };
+constexpr int kSlotBits = 7;
+constexpr int kSlots = 1 << kSlotBits;   // distinct cone targets aggregated per assign tile
 struct SmemAssign {
     int e0, m;
     int start[kTile];
     int f[kTile];
+    int skey[kSlots], scnt[kSlots], sbase[kSlots];
+    unsigned long long sk1[kSlots];
+    unsigned so2[kSlots], sem[kSlots];
 };
 struct SmemTable {
     long long wsum[33];
@@ -132,8 +155,8 @@ union SmemAll3 {
 
 struct Layout3 {
     size_t hdr, res, fac, acc, apex, claim, cone, thr, nstart, big_mark, big_v, big_h;
-    size_t ent[2], tile_ent, tile_m, vn, vpool, npool, uncert, pts[2], code, part, blk_a, blk_b,
-        blk_v, blk_i;
+    size_t ent[2], tile_ent, tile_m, vn, cstate, taken, vpool, npool, uncert, pts[2], code, part,
+        blk_a, blk_b, blk_v, blk_i;
     // output stage
     size_t alive, label, cop, ekey[2], eval[2], hist, hist_off, gstart, poly, glen, fkey[2], fval[2],
         vflag, scan_tmp;

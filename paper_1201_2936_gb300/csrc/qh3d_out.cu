@@ -62,6 +62,8 @@ Layout3 layout3d(int64_t n)
     L.tile_ent = take((np / kTile + 2) * 4);
     L.tile_m = take((np / kTile + 2) * 4);
     L.vn = take((size_t)L.ecap * sizeof(int2));
+    L.cstate = take((size_t)L.ecap * 4);
+    L.taken = take(fc * 4);
     L.vpool = take((size_t)L.ecap * kVCap * 4);
     L.npool = take((size_t)L.ecap * kNCap * 4);
     L.uncert = take((size_t)L.ecap * 4);
@@ -125,6 +127,8 @@ Params3 make_params3(const float *x, const float *y, const float *z, int64_t n, 
     A.tile_ent = (int *)(ws + L.tile_ent);
     A.tile_m = (int *)(ws + L.tile_m);
     A.vn = (int2 *)(ws + L.vn);
+    A.cstate = (int *)(ws + L.cstate);
+    A.taken = (int *)(ws + L.taken);
     A.vpool = (int *)(ws + L.vpool);
     A.npool = (int *)(ws + L.npool);
     A.uncert = (int *)(ws + L.uncert);
@@ -491,10 +495,13 @@ static OutBufs out_bufs(char *ws, const Layout3 &L)
 using namespace qh;
 using namespace qh::d3;
 
+// facet ids must fit the 28-bit claim permutation: 6n + 64 < 2^28
+constexpr int64_t kMax3d = 44000000;
+
 extern "C" size_t qh_workspace_bytes_3d(int64_t n, const qh_opts *opts)
 {
     (void)opts;
-    if (n < 0 || n > QH_MAX_POINTS / 8) return 0;
+    if (n < 0 || n > kMax3d) return 0;
     return layout3d(n).total;
 }
 
@@ -502,6 +509,26 @@ static int grid_for(int items, int block)
 {
     int g = (items + block - 1) / block;
     return std::max(1, std::min(g, 152 * 16));
+}
+
+extern "C" qh_status qh_debug_timeline_3d(const void *d_ws, int64_t n, int64_t *h_rows,
+                                          int32_t max_rows, int32_t *h_nrows, cudaStream_t st)
+{
+    if (!d_ws || !h_rows || !h_nrows || max_rows < 0 || n < 0 || n > kMax3d)
+        return QH_ERR_INVALID_ARG;
+    const Layout3 L = layout3d(n);
+    Hdr3 hh;
+    if (cudaMemcpyAsync(&hh, (const char *)d_ws + L.hdr, sizeof(Hdr3), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return QH_ERR_CUDA;
+    int rows = std::min(std::min(hh.iter, kTimeline3), (int)max_rows);
+    for (int r = 0; r < rows; r++) {
+        h_rows[10 * r] = r + 1;
+        for (int c = 0; c < 9; c++) h_rows[10 * r + 1 + c] = hh.tl[r][c];
+    }
+    *h_nrows = rows;
+    return QH_OK;
 }
 
 extern "C" qh_status qh_hull3d(const float *d_x, const float *d_y, const float *d_z, int64_t n,
@@ -514,7 +541,7 @@ extern "C" qh_status qh_hull3d(const float *d_x, const float *d_y, const float *
     if (opts) o = *opts;
     if (h_nv) *h_nv = 0;
     if (h_nf) *h_nf = 0;
-    if (n < 0 || n > QH_MAX_POINTS / 8 || stride < 1 || !d_ws || !h_nv || !h_nf)
+    if (n < 0 || n > kMax3d || stride < 1 || !d_ws || !h_nv || !h_nf)
         return QH_ERR_INVALID_ARG;
     if (n > 0 && (!d_x || !d_y || !d_z || !d_verts || !d_face_off || !d_face_idx))
         return QH_ERR_INVALID_ARG;
@@ -531,7 +558,8 @@ extern "C" qh_status qh_hull3d(const float *d_x, const float *d_y, const float *
     char *ws = (char *)d_ws;
     Params3 A = make_params3(d_x, d_y, d_z, n, stride, ws, L, o);
     if (cudaMemsetAsync(A.hdr, 0, sizeof(Hdr3), st) != cudaSuccess ||
-        cudaMemsetAsync(A.big_mark, 0xff, ((size_t)L.fcap + 1) * 4, st) != cudaSuccess)
+        cudaMemsetAsync(A.big_mark, 0xff, ((size_t)L.fcap + 1) * 4, st) != cudaSuccess ||
+        cudaMemsetAsync(A.taken, 0, ((size_t)L.fcap + 1) * 4, st) != cudaSuccess)
         return QH_ERR_CUDA;
     const void *fn = persistent_kernel(o.pred_mode);
     int grid = persistent_grid(fn, kBlock, o.blocks_per_sm);
