@@ -6,10 +6,12 @@ on the unit circle with N(0, 1e-4) radial jitter), FP32-filtered exact
 predicates, one persistent kernel per hull.  value = points hulled per
 second over the whole job (Mpoints/s), inputs resident in HBM.
 
-Also reported: the plain GPU path (FP64 predicates, host-driven loop with a
-live-count readback per iteration), the end-to-end number through the C ABI
-with host buffers, the HBM roofline of the persistent kernel, and the CPU
-oracle on the host cores.  `--impl reference` times the oracle alone.
+Also reported: the 3D hull (8M points in the ball, 1M on the sphere) with the
+FP32 filter and with FP64 predicates; the plain GPU path (FP64 predicates,
+host-driven loop with a live-count readback per iteration); the end-to-end
+number through the C ABI with host buffers; the HBM roofline of the
+persistent kernel; and the CPU oracle on the host cores.  `--impl reference`
+times the oracle alone.
 
 Multi-GPU (torchrun, one rank per GPU): every rank hulls its own clouds
 (independent problems, no collective on the data path): weak scaling.
@@ -137,6 +139,59 @@ def oracle_step(data, limit=None):
     return pts, time.perf_counter() - t0
 
 
+def clouds_3d(rank: int, scale: int = 1):
+    from paper_1201_2936_gb300 import workloads as w
+    s = w.SEED_BASE + 2 + 1000 * rank
+    return [("ball8M", w.uniform_ball(w.N_BALL_3D // scale, s)),
+            ("sphere1M", w.on_sphere(w.N_SPHERE_3D // scale, s + 10))]
+
+
+def bench_3d(args, qh, dev, rank, peak, peak_kind):
+    """Per-cloud device time of qh_hull3d (extrema to canonical faces, host
+    readbacks of the output sizes included) with the FP32 filter and with
+    FP64 predicates.  Algorithmic bytes: 12 B per point for the extrema and
+    the first split's read, 16 B (x, y, z, idx) per live point read and per
+    survivor written afterwards."""
+    import torch
+    reps = max(3, args.steps // 10)
+    out = []
+    for name, (x, y, z) in clouds_3d(rank, args.scale_3d):
+        n = len(x)
+        P = torch.from_numpy(np.stack([x, y, z])).to(dev)
+        ws = qh.Workspace(dev)
+        row = {"cloud": name, "n": n}
+        verts = {}
+        for pred in ("f32", "f64"):
+            for _ in range(2):
+                (v, off, idx), r = qh.hull3d(P, pred=pred, workspace=ws, return_result=True)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+            torch.cuda.synchronize()
+            e[0].record()
+            for k in range(reps):
+                qh.hull3d(P, pred=pred, workspace=ws)
+                e[k + 1].record()
+            torch.cuda.synchronize()
+            ms = statistics.median(e[k].elapsed_time(e[k + 1]) for k in range(reps))
+            verts[pred] = (v.cpu(), off.cpu(), idx.cpu())
+            algo = 24 * n + 32 * r["survivor_total"]
+            row[pred] = {"ms": round(ms, 3), "Mpoints_s": round(n / ms / 1e3, 1),
+                         "iterations": r["iterations"], "algo_bytes": algo,
+                         "GBps": round(algo / (ms / 1e3) / 1e9, 1),
+                         "frac": round(algo / (ms / 1e3) / 1e9 / peak, 4),
+                         "fallback_frac": r["filter_fallbacks"] / max(1, r["live_total"]),
+                         "exact_argmax_segments": r["exact_argmax"]}
+        a, b = verts["f32"], verts["f64"]
+        row["hull_vertices"] = int(a[0].numel())
+        row["faces"] = int(a[1].numel() - 1)
+        row["same_hull_f32_f64"] = all(torch.equal(p, q) for p, q in zip(a, b))
+        row["speedup_f32_over_f64"] = round(row["f64"]["ms"] / row["f32"]["ms"], 2)
+        out.append(row)
+        del P, ws
+        torch.cuda.empty_cache()
+    return {"workload": "3D: 8M uniform in the unit ball, 1M on the unit sphere (float32)",
+            "peak": peak, "peak_kind": peak_kind, "reps": reps, "clouds": out}
+
+
 def run_reference(args, ws, rank):
     # the oracle on the host cores, rank 0 only
     if rank != 0:
@@ -176,6 +231,8 @@ def main():
     ap.add_argument("--n", type=int, default=N_PER_CLOUD,
                     help="points per cloud (profiling of smaller cases)")
     ap.add_argument("--only", default="", help="comma-separated cloud names to keep")
+    ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--scale-3d", type=int, default=1, help="divide the 3D cloud sizes")
     ap.add_argument("--timeline", action="store_true",
                     help="print the per-iteration device timeline of each cloud to stderr")
     args = ap.parse_args()
@@ -325,6 +382,11 @@ def main():
                              "loop": "host (live count read back every iteration)",
                              "same_hull_sizes": same,
                              "speedup_of_fast_path": round(pms / (total_ms / args.steps), 2)}
+
+    # ---- 3D (8M points uniform in the ball, 1M points on the sphere): FP32
+    # filter vs the FP64 plain path, same hulls required
+    if not args.no_3d:
+        line["hull3d"] = bench_3d(args, qh, dev, rank, peak, peak_kind)
 
     # ---- end to end through the C ABI with host buffers
     if args.no_e2e:

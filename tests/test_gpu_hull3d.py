@@ -92,3 +92,23 @@ def test_interleaved_layout(qh):
     v, off, idx = qh.hull3d(P)
     faces = [idx[off[i]:off[i + 1]].tolist() for i in range(len(off) - 1)]
     assert v.tolist() == want[0] and faces == want[1]
+
+
+@pytest.mark.parametrize("gen", ["ball8M", "sphere1M"])
+def test_full_size_matches_oracle(qh, gen):
+    # the 3D benchmark workloads at full size, in the launch configuration the
+    # benchmark times (persistent kernel, both predicate modes)
+    if gen == "ball8M":
+        x, y, z = w.uniform_ball(w.N_BALL_3D, w.SEED_BASE + 2)
+    else:
+        x, y, z = w.on_sphere(w.N_SPHERE_3D, w.SEED_BASE + 12)
+    ov, of = oracle.hull3d(x, y, z)
+    oo = np.zeros(len(of) + 1, np.int64)
+    oo[1:] = np.cumsum([len(f) for f in of])
+    oi = np.concatenate(of)
+    X, Y, Z = (torch.from_numpy(c).cuda() for c in (x, y, z))
+    for pred in ("f32", "f64"):
+        v, off, idx = qh.hull3d(X, Y, Z, pred=pred)
+        assert np.array_equal(v.cpu().numpy(), ov), pred
+        assert np.array_equal(off.cpu().numpy(), oo), pred
+        assert np.array_equal(idx.cpu().numpy(), oi), pred
