@@ -74,9 +74,11 @@ typedef struct qh_opts {
     int32_t pred_mode;    /* QH_PRED_* */
     int32_t loop_mode;    /* QH_LOOP_* */
     int32_t blocks_per_sm;/* persistent grid: CTAs per SM (0 = as many as fit) */
-    int32_t reserved0;
-    int64_t max_iters;    /* iteration cap (0 = n + 8) */
+    int32_t block;        /* 3D: threads per CTA, 128, 256 or 512 (0 = 256) */
+    int64_t max_iters;    /* iteration cap (0 = n + 8 in 2D, 4n + 16 in 3D) */
     int64_t wait_ns;      /* bound of every device-side wait (0 = 2 s) */
+    int32_t items;        /* 3D: points per thread of the assign pass, 2, 4 or 8 (0 = 4) */
+    int32_t reserved0;
 } qh_opts;
 
 /* Result record written by the device (async calls) and copied back by the
@@ -179,6 +181,72 @@ qh_status qh_hull3d(const float *d_x, const float *d_y, const float *d_z, int64_
                     int64_t stride, int32_t *d_verts, int64_t *h_nv, int32_t *d_face_off,
                     int32_t *d_face_idx, int64_t *h_nf, qh_result *h_result, void *d_ws,
                     size_t ws_bytes, const qh_opts *opts, cudaStream_t stream);
+
+/*
+ * Batched 3D hulls (no counterpart in the paper, whose input is one point
+ * set; its segments are what makes a batch cheap: every cloud's root
+ * segment simply joins the segment table of one persistent launch).
+ *
+ * The clouds are CSR: cloud c holds points [cloud_off[c], cloud_off[c+1])
+ * of the shared coordinate arrays, cloud_off[0] = 0, cloud_off[ncloud] = n,
+ * non-decreasing (empty clouds allowed).  1 <= ncloud and
+ * n + ncloud <= QH_MAX_POINTS_3D.
+ */
+size_t qh_workspace_bytes_3d_batched(int64_t n, int32_t ncloud, const qh_opts *opts);
+
+/*
+ * qh_hull3d_batched: the hull of every cloud, in one call that never
+ * synchronises the stream and allocates nothing, so it can be captured in a
+ * CUDA graph (run it once before the capture: the first call on a device
+ * queries the kernel occupancy).
+ *
+ *  d_cloud_off       device int64[ncloud+1] (checked on the device: bad
+ *                    offsets give QH_ERR_INVALID_ARG in d_result->status)
+ *  d_verts           device int32[n]: the vertices of all clouds, as global
+ *                    point indices in increasing order (so grouped by cloud)
+ *  d_cloud_vert_off  device int32[ncloud+1]: cloud c's vertices are
+ *                    d_verts[d_cloud_vert_off[c] .. d_cloud_vert_off[c+1])
+ *  d_face_off        device int32[2n+1], d_face_idx device int32[6n]: the
+ *                    faces of all clouds as in qh_hull3d (global indices,
+ *                    sorted, hence grouped by cloud)
+ *  d_cloud_face_off  device int32[ncloud+1]: cloud c's faces are faces
+ *                    d_cloud_face_off[c] .. d_cloud_face_off[c+1]
+ *  d_cloud_status    device int32[ncloud]: QH_OK, QH_ERR_DEGENERATE (fewer
+ *                    than 4 points or not spanning 3D: no faces) or
+ *                    QH_ERR_NONFINITE (no faces) per cloud; an empty cloud
+ *                    is QH_OK with no faces
+ *  d_result          device qh_result: status of the whole call, vertex and
+ *                    face totals (extra[0..2]) and statistics
+ * opts->block and opts->items choose the launch shape (see
+ * qh_autotune_3d_batched).  Returns QH_OK once the work is enqueued;
+ * argument errors are returned at once.
+ */
+qh_status qh_hull3d_batched(const float *d_x, const float *d_y, const float *d_z, int64_t stride,
+                            const int64_t *d_cloud_off, int32_t ncloud, int64_t n,
+                            int32_t *d_verts, int32_t *d_cloud_vert_off, int32_t *d_face_off,
+                            int32_t *d_face_idx, int32_t *d_cloud_face_off,
+                            int32_t *d_cloud_status, qh_result *d_result, void *d_ws,
+                            size_t ws_bytes, const qh_opts *opts, cudaStream_t stream);
+
+/*
+ * qh_autotune_3d_batched: times qh_hull3d_batched on the caller's batch for
+ * every launch shape (threads per CTA 128/256/512 x points per thread
+ * 2/4/8 x CTAs per SM 1/2/4, capped by occupancy): one untimed run, then
+ * `reps` (1..64) runs timed with CUDA events on `stream`; the median decides.
+ *  h_best    in: base options (predicate mode); out: the fastest shape
+ *  h_ms      host float[max_cand]: median ms of each candidate that ran
+ *  h_shape   host int32[3*max_cand]: (block, items, CTAs per SM) of each
+ *  h_ncand   host: candidates reported
+ * Synchronises the stream; the outputs hold the hulls of the last run.
+ */
+qh_status qh_autotune_3d_batched(const float *d_x, const float *d_y, const float *d_z,
+                                 int64_t stride, const int64_t *d_cloud_off, int32_t ncloud,
+                                 int64_t n, int32_t *d_verts, int32_t *d_cloud_vert_off,
+                                 int32_t *d_face_off, int32_t *d_face_idx,
+                                 int32_t *d_cloud_face_off, int32_t *d_cloud_status,
+                                 qh_result *d_result, void *d_ws, size_t ws_bytes, int32_t reps,
+                                 qh_opts *h_best, float *h_ms, int32_t *h_shape, int32_t max_cand,
+                                 int32_t *h_ncand, cudaStream_t stream);
 
 /*
  * qh_hull2d_noalloc: qh_hull2d for callers that cannot allocate device

@@ -121,6 +121,28 @@ def hull3d_csr(x, y, z):
     return verts, off, idx
 
 
+def hull3d_batched(x, y, z, off):
+    """Hulls of a batch of clouds (cloud c = points off[c]..off[c+1]): a plain
+    loop of hull3d over the clouds.  Returns a list of (status, vertices,
+    faces) with global point indices; status is OK, ERR_DEGENERATE or
+    ERR_NONFINITE (then no vertices or faces); an empty cloud is OK with no
+    faces."""
+    x, y, z = _f32(x), _f32(y), _f32(z)
+    out = []
+    for c in range(len(off) - 1):
+        a, b = int(off[c]), int(off[c + 1])
+        if a == b:
+            out.append((OK, np.zeros(0, np.int32), []))
+            continue
+        try:
+            v, f = hull3d(x[a:b], y[a:b], z[a:b])
+        except OracleError as e:
+            out.append((e.code, np.zeros(0, np.int32), []))
+            continue
+        out.append((OK, (v + a).astype(np.int32), [(t + a).astype(np.int32) for t in f]))
+    return out
+
+
 def _pt(p) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(p, dtype=np.float64))
 

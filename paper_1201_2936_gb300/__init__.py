@@ -14,7 +14,8 @@ import torch
 from . import _native
 from ._native import QhOpts, QhResult, RESULT_BYTES
 
-__all__ = ["QHError", "hull2d", "hull2d_async", "workspace_bytes_2d", "Workspace",
+__all__ = ["QHError", "hull2d", "hull2d_async", "workspace_bytes_2d", "Workspace", "hull3d",
+           "hull3d_batched", "Hull3DBatch", "workspace_bytes_3d", "workspace_bytes_3d_batched",
            "make_opts", "status_str", "version", "RESULT_BYTES", "result_from_tensor"]
 
 PRED = {"f32": 0, "f64": 1}
@@ -36,7 +37,7 @@ def version() -> str:
 
 
 def make_opts(pred: str = "f32", loop: str = "persistent", blocks_per_sm: int = 0,
-              max_iters: int = 0, wait_ns: int = 0) -> QhOpts:
+              max_iters: int = 0, wait_ns: int = 0, block: int = 0, items: int = 0) -> QhOpts:
     o = QhOpts()
     _native.lib().qh_default_opts(ctypes.byref(o))
     o.pred_mode = PRED[pred]
@@ -44,6 +45,8 @@ def make_opts(pred: str = "f32", loop: str = "persistent", blocks_per_sm: int = 
     o.blocks_per_sm = blocks_per_sm
     o.max_iters = max_iters
     o.wait_ns = wait_ns
+    o.block = block
+    o.items = items
     return o
 
 
@@ -243,3 +246,114 @@ def hull2d(x: torch.Tensor, y: Optional[torch.Tensor] = None, *, pred: str = "f3
         raise QHError(st, "qh_hull2d")
     idx = out[: cnt.value]
     return (idx, res.as_dict()) if return_result else idx
+
+
+# ---------------------------------------------------------------------- batched 3D
+def workspace_bytes_3d_batched(n: int, ncloud: int, opts: Optional[QhOpts] = None) -> int:
+    return int(_native.lib().qh_workspace_bytes_3d_batched(int(n), int(ncloud),
+                                                           ctypes.byref(opts) if opts else None))
+
+
+class Hull3DBatch:
+    """Hulls of a batch of 3D clouds (qh_hull3d_batched) with every output
+    buffer allocated once, so that one call can be captured in a CUDA graph
+    and replayed.  Points: [n, 3], [3, n] or x, y, z CUDA float32; cloud_off:
+    int64 CUDA tensor [ncloud + 1] (CSR offsets).  Output indices are global
+    (into the concatenated points)."""
+
+    def __init__(self, x, y=None, z=None, cloud_off: torch.Tensor = None, *, pred: str = "f32",
+                 opts: Optional[QhOpts] = None):
+        if cloud_off is None or cloud_off.dtype != torch.int64 or not cloud_off.is_cuda or \
+                cloud_off.dim() != 1 or cloud_off.numel() < 2:
+            raise ValueError("cloud_off must be a CUDA int64 tensor of ncloud + 1 offsets")
+        self._inputs = (x, y, z, cloud_off.contiguous())
+        self.xp, self.yp, self.zp, self.n, self.stride, dev = _points_3d(x, y, z)
+        self.cloud_off = self._inputs[3]
+        self.ncloud = cloud_off.numel() - 1
+        self.opts = opts if opts is not None else make_opts(pred)
+        n, nc = self.n, self.ncloud
+        i32 = dict(dtype=torch.int32, device=dev)
+        self.verts = torch.empty(max(n, 1), **i32)
+        self.cloud_voff = torch.empty(nc + 1, **i32)
+        self.face_off = torch.empty(2 * n + 1, **i32)
+        self.face_idx = torch.empty(max(6 * n, 1), **i32)
+        self.cloud_foff = torch.empty(nc + 1, **i32)
+        self.cloud_status = torch.empty(nc, **i32)
+        self.result = torch.zeros(RESULT_BYTES, dtype=torch.uint8, device=dev)
+        nb = workspace_bytes_3d_batched(n, nc, self.opts)
+        if nb == 0:
+            raise QHError(1, "qh_workspace_bytes_3d_batched")
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+        self.graph = None
+
+    def _args(self):
+        return (self.xp, self.yp, self.zp, self.stride, self.cloud_off.data_ptr(), self.ncloud,
+                self.n, self.verts.data_ptr(), self.cloud_voff.data_ptr(),
+                self.face_off.data_ptr(), self.face_idx.data_ptr(), self.cloud_foff.data_ptr(),
+                self.cloud_status.data_ptr(), self.result.data_ptr(), self.ws.data_ptr(),
+                self.ws.numel())
+
+    def enqueue(self, stream=None) -> None:
+        """Issue the whole batch on the stream (no synchronisation)."""
+        st = _native.lib().qh_hull3d_batched(*self._args(), ctypes.byref(self.opts),
+                                             _stream_handle(stream))
+        if st != 0:
+            raise QHError(st, "qh_hull3d_batched")
+
+    def tune(self, reps: int = 3, stream=None):
+        """Autotune the launch shape on this batch (qh_autotune_3d_batched);
+        keeps the fastest in self.opts and returns [(block, items,
+        ctas_per_sm, ms), ...]."""
+        import numpy as np
+        best = QhOpts()
+        ctypes.memmove(ctypes.byref(best), ctypes.byref(self.opts), ctypes.sizeof(QhOpts))
+        ms = np.zeros(64, dtype=np.float32)
+        shape = np.zeros(3 * 64, dtype=np.int32)
+        nc = ctypes.c_int32(0)
+        st = _native.lib().qh_autotune_3d_batched(
+            *self._args(), int(reps), ctypes.byref(best), ms.ctypes.data_as(ctypes.c_void_p),
+            shape.ctypes.data_as(ctypes.c_void_p), 64, ctypes.byref(nc), _stream_handle(stream))
+        if st != 0:
+            raise QHError(st, "qh_autotune_3d_batched")
+        self.opts = best
+        return [(int(shape[3 * i]), int(shape[3 * i + 1]), int(shape[3 * i + 2]), float(ms[i]))
+                for i in range(nc.value)]
+
+    def capture(self) -> None:
+        """Capture one enqueue() in a CUDA graph (after a warm-up run)."""
+        s = torch.cuda.Stream(device=self.verts.device)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.enqueue()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.enqueue()
+        self.graph = g
+
+    def replay(self) -> None:
+        self.graph.replay()
+
+    def result_dict(self) -> dict:
+        r = result_from_tensor(self.result)
+        return r.as_dict()
+
+    def outputs(self):
+        """(verts, cloud_vert_off, face_off, face_idx, cloud_face_off,
+        cloud_status) after the last run, sliced to their lengths
+        (synchronises).  Raises QHError if the call failed."""
+        r = result_from_tensor(self.result)
+        if r.status != 0:
+            raise QHError(r.status, "qh_hull3d_batched")
+        nv, nf, ni = int(r.extra[0]), int(r.extra[1]), int(r.extra[2])
+        return (self.verts[:nv], self.cloud_voff, self.face_off[: nf + 1], self.face_idx[:ni],
+                self.cloud_foff, self.cloud_status)
+
+
+def hull3d_batched(x, y=None, z=None, cloud_off: torch.Tensor = None, *, pred: str = "f32",
+                   opts: Optional[QhOpts] = None):
+    """One batched call (see Hull3DBatch.outputs for the returned tuple)."""
+    b = Hull3DBatch(x, y, z, cloud_off, pred=pred, opts=opts)
+    b.enqueue()
+    return b.outputs()

@@ -15,8 +15,9 @@ _lib = None
 
 class QhOpts(ctypes.Structure):
     _fields_ = [("pred_mode", ctypes.c_int32), ("loop_mode", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("reserved0", ctypes.c_int32),
-                ("max_iters", ctypes.c_int64), ("wait_ns", ctypes.c_int64)]
+                ("blocks_per_sm", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("max_iters", ctypes.c_int64), ("wait_ns", ctypes.c_int64),
+                ("items", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
 class QhResult(ctypes.Structure):
@@ -54,6 +55,13 @@ SIGNATURES = [
     ("qh_hull2d_noalloc", ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, ctypes.POINTER(_i64), _vp]),
     ("qh_debug_timeline_2d", ctypes.c_int, [_vp, _i64, _vp, ctypes.c_int32,
                                             ctypes.POINTER(ctypes.c_int32), _vp]),
+    ("qh_workspace_bytes_3d_batched", _sz, [_i64, ctypes.c_int32, _POpts]),
+    ("qh_hull3d_batched", ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, ctypes.c_int32, _i64, _vp, _vp,
+                                         _vp, _vp, _vp, _vp, _vp, _vp, _sz, _POpts, _vp]),
+    ("qh_autotune_3d_batched", ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, ctypes.c_int32, _i64, _vp,
+                                              _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz,
+                                              ctypes.c_int32, _POpts, _vp, _vp, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_int32), _vp]),
 ]
 
 

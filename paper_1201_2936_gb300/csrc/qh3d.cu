@@ -248,13 +248,11 @@ __device__ void simplex_take(const Params3 &A, int step)
     else H->pd = p;
 }
 
-// Block 0 thread 0: the tetrahedron (a, b, c, d), facets 0..3 oriented with the
-// opposite vertex strictly inside, and their neighbours.
-__device__ void build_tetra(const Params3 &A)
+// One thread: the tetrahedron (a, b, c, d) as facets base..base+3, oriented
+// with the opposite vertex strictly inside, their neighbours, and the cone
+// record of the cloud's pseudo facet.
+__device__ void build_tetra_at(const Params3 &A, int base, const float4 *t, int pseudo)
 {
-    Hdr3 *H = A.hdr;
-    if (threadIdx.x != 0) return;
-    float4 t[4] = {H->pa, H->pb, H->pc, H->pd};
     for (int o = 0; o < 4; o++) {
         int k[3], m = 0;
         for (int j = 0; j < 4; j++)
@@ -277,25 +275,220 @@ __device__ void build_tetra(const Params3 &A)
         }
         f.nb[0] = f.nb[1] = f.nb[2] = -1;
         f.alive = 1;
-        A.fac[o] = f;
+        A.fac[base + o] = f;
         Acc3 z = {};
-        A.acc[o] = z;
-        A.claim[o] = 0ull;
+        A.acc[base + o] = z;
+        A.claim[base + o] = 0ull;
+        A.taken[base + o] = 0;
+        A.big_mark[base + o] = -1;
     }
     for (int i = 0; i < 4; i++)
         for (int e = 0; e < 3; e++) {
-            int u = A.fac[i].v[e], v = A.fac[i].v[(e + 1) % 3];
+            int u = A.fac[base + i].v[e], v = A.fac[base + i].v[(e + 1) % 3];
             for (int j = 0; j < 4; j++) {
                 if (j == i) continue;
                 for (int g = 0; g < 3; g++)
-                    if (A.fac[j].v[g] == v && A.fac[j].v[(g + 1) % 3] == u) A.fac[i].nb[e] = j;
+                    if (A.fac[base + j].v[g] == v && A.fac[base + j].v[(g + 1) % 3] == u)
+                        A.fac[base + i].nb[e] = base + j;
             }
         }
+    A.cone[pseudo] = make_int4(base, 4, -1, 0);
+}
+
+// Four dead facets (a cloud without a tetrahedron) and an empty cone.
+__device__ void dead_tetra_at(const Params3 &A, int base, int pseudo)
+{
+    for (int o = 0; o < 4; o++) {
+        Fac3 f = {};
+        f.nb[0] = f.nb[1] = f.nb[2] = base + o;
+        A.fac[base + o] = f;
+        Acc3 z = {};
+        A.acc[base + o] = z;
+        A.claim[base + o] = 0ull;
+        A.taken[base + o] = 0;
+        A.big_mark[base + o] = -1;
+    }
+    A.cone[pseudo] = make_int4(0, 0, -1, 0);
+}
+
+// Block 0 thread 0, single cloud: facets 0..3.
+__device__ void build_tetra(const Params3 &A)
+{
+    Hdr3 *H = A.hdr;
+    if (threadIdx.x != 0) return;
+    const float4 t[4] = {H->pa, H->pb, H->pc, H->pd};
+    build_tetra_at(A, 0, t, A.fcap);
     H->fcount = 4;
     H->hull_vertices = 4;
-    // the pseudo segment of the first assignment: every input point, coned to
-    // the four tetrahedron facets
-    A.cone[kPseudo] = make_int4(0, 4, -1, 0);
+}
+
+// ---------------------------------------------------------------- clouds
+__device__ __forceinline__ int cloud_start(const Params3 &A, int c)
+{
+    return A.cloud_off ? (int)A.cloud_off[c] : (c == 0 ? 0 : A.n);
+}
+
+// Cloud of point v: the last cloud starting at or before v.
+__device__ __forceinline__ int cloud_of(const Params3 &A, int v)
+{
+    if (!A.cloud_off) return 0;
+    int lo = 0, hi = A.ncloud - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (A.cloud_off[mid] <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Block-wide reductions over a cloud for its initial simplex.
+__device__ void block_lex_extrema(const Params3 &A, SmemAll3 &sm, int lo, int hi, float4 &mn,
+                                  float4 &mx, bool &bad)
+{
+    float4 a = make_float4(INFINITY, INFINITY, INFINITY, __int_as_float(INT_MAX));
+    float4 b = make_float4(-INFINITY, -INFINITY, -INFINITY, __int_as_float(INT_MAX));
+    int nf = 0;
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        float4 p = load_input(A, i);
+        p.x = canon0(p.x);
+        p.y = canon0(p.y);
+        p.z = canon0(p.z);
+        nf |= !(isfinite(p.x) && isfinite(p.y) && isfinite(p.z));
+        if (lex_less(p, a)) a = p;
+        if (lex_greater_lowidx(p, b)) b = p;
+    }
+    bad = __syncthreads_or(nf);
+    sm.red.a[threadIdx.x] = a;
+    sm.red.b[threadIdx.x] = b;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            if (lex_less(sm.red.a[threadIdx.x + s], sm.red.a[threadIdx.x]))
+                sm.red.a[threadIdx.x] = sm.red.a[threadIdx.x + s];
+            if (lex_greater_lowidx(sm.red.b[threadIdx.x + s], sm.red.b[threadIdx.x]))
+                sm.red.b[threadIdx.x] = sm.red.b[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    mn = sm.red.a[0];
+    mx = sm.red.b[0];
+    __syncthreads();
+}
+
+// Farthest point of [lo, hi) from the line ab (kind 0) or the plane abc
+// (kind 1), FP32 magnitude, lowest index on ties; then the exact check that
+// it is off the line / plane, and if not, the lowest-index point that is.
+// Returns the point index or -1 (all points on the line / plane).
+__device__ int block_next_vertex(const Params3 &A, SmemAll3 &sm, int lo, int hi, const float *a,
+                                 const float *b, const float *c, int kind)
+{
+    float best = -1.0f;
+    int bi = INT_MAX;
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const float4 p = load_input(A, i);
+        float v;
+        if (kind == 0) {
+            const float ux = b[0] - a[0], uy = b[1] - a[1], uz = b[2] - a[2];
+            const float wx = p.x - a[0], wy = p.y - a[1], wz = p.z - a[2];
+            const float cx = uy * wz - uz * wy, cy = uz * wx - ux * wz, cz = ux * wy - uy * wx;
+            v = cx * cx + cy * cy + cz * cz;
+        } else {
+            const float q[3] = {p.x, p.y, p.z};
+            float d, e;
+            orient3d_value<QH_PRED_F32>(a, b, c, q, d, e);
+            v = fabsf(d);
+        }
+        if (v > best || (v == best && i < bi)) {
+            best = v;
+            bi = i;
+        }
+    }
+    sm.red.v[threadIdx.x] = best;
+    sm.red.i[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            const float ov = sm.red.v[threadIdx.x + s];
+            const int oi = sm.red.i[threadIdx.x + s];
+            if (ov > sm.red.v[threadIdx.x] ||
+                (ov == sm.red.v[threadIdx.x] && oi < sm.red.i[threadIdx.x])) {
+                sm.red.v[threadIdx.x] = ov;
+                sm.red.i[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    const int cand = sm.red.i[0];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool ok = false;
+        if (cand >= lo && cand < hi) {
+            const float4 p = load_input(A, cand);
+            const float q[3] = {p.x, p.y, p.z};
+            ok = kind == 0 ? !collinear3_exact(a, b, q) : orient3d_exact_sign(a, b, c, q) != 0;
+        }
+        sm.red.flag = ok ? cand : INT_MAX;
+    }
+    __syncthreads();
+    int r = sm.red.flag;
+    if (r == INT_MAX) {
+        // exact search (rare: the FP32 choice was degenerate)
+        for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const float4 p = load_input(A, i);
+            const float q[3] = {p.x, p.y, p.z};
+            const bool ok =
+                kind == 0 ? !collinear3_exact(a, b, q) : orient3d_exact_sign(a, b, c, q) != 0;
+            if (ok) atomicMin(&sm.red.flag, i);
+        }
+        __syncthreads();
+        r = sm.red.flag;
+    }
+    __syncthreads();
+    return r == INT_MAX ? -1 : r;
+}
+
+// One block per cloud: its initial simplex as facets 4c..4c+3 (dead facets
+// and a per-cloud status when the cloud does not span 3D or holds a
+// non-finite coordinate).
+__device__ void init_clouds(const Params3 &A, SmemAll3 &sm, int bid, int nb)
+{
+    Hdr3 *H = A.hdr;
+    for (int c = bid; c < A.ncloud; c += nb) {
+        const int lo = cloud_start(A, c), hi = cloud_start(A, c + 1);
+        const int base = 4 * c, pseudo = A.fcap + c;
+        int st = QH_OK;
+        float4 t[4];
+        if (hi - lo == 0) {
+            st = -1;  // empty cloud: no faces, status OK
+        } else if (hi - lo < 4) {
+            st = QH_ERR_DEGENERATE;
+        } else {
+            bool bad;
+            block_lex_extrema(A, sm, lo, hi, t[0], t[1], bad);
+            if (bad) st = QH_ERR_NONFINITE;
+            else if (t[0].x == t[1].x && t[0].y == t[1].y && t[0].z == t[1].z)
+                st = QH_ERR_DEGENERATE;
+        }
+        for (int step = 0; step < 2 && st == QH_OK; step++) {
+            const float a[3] = {t[0].x, t[0].y, t[0].z};
+            const float b[3] = {t[1].x, t[1].y, t[1].z};
+            const float cc[3] = {t[2].x, t[2].y, t[2].z};
+            const int i = block_next_vertex(A, sm, lo, hi, a, b, cc, step);
+            if (i < 0) st = QH_ERR_DEGENERATE;
+            else t[2 + step] = load_input(A, i);
+        }
+        if (threadIdx.x == 0) {
+            if (st == QH_OK) {
+                build_tetra_at(A, base, t, pseudo);
+                atomicAdd(&H->hull_vertices, 4);
+            } else {
+                dead_tetra_at(A, base, pseudo);
+            }
+            A.cloud_status[c] = st < 0 ? QH_OK : st;
+        }
+        __syncthreads();
+    }
+    if (bid == 0 && threadIdx.x == 0) H->fcount = 4 * A.ncloud;
 }
 
 // ---------------------------------------------------------------- S: select
@@ -424,6 +617,8 @@ __device__ bool build_cone(const Params3 &A, int f0, int len, const int *V, int 
         Acc3 z = {};
         A.acc[base + j] = z;
         A.claim[base + j] = 0ull;
+        A.taken[base + j] = 0;
+        A.big_mark[base + j] = -1;
         // the horizon neighbour now points at the cone facet
         Fac3 &G = A.fac[F.nb[k]];
         for (int g = 0; g < 3; g++)
@@ -516,6 +711,8 @@ __device__ void cone_warp(const Params3 &A, int e, int f0, int len, const int *V
         Acc3 z = {};
         A.acc[base + j] = z;
         A.claim[base + j] = 0ull;
+        A.taken[base + j] = 0;
+        A.big_mark[base + j] = -1;
         Fac3 &G = A.fac[g];
         for (int t = 0; t < 3; t++)
             if (G.nb[t] == hf) G.nb[t] = base + j;
@@ -630,7 +827,7 @@ __device__ void fallback3d(const Params3 &A, int par, int iter)
 // position in the segment), else the first cone facet of its winner that it
 // is strictly above (warp-aggregated count, rank and farthest-point key), else
 // discarded (-1).  FIRST: the input points against the tetrahedron.
-template <int MODE, bool FIRST>
+template <int MODE, int ITEMS, bool FIRST>
 __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int nb)
 {
     Hdr3 *H = A.hdr;
@@ -640,13 +837,20 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int n
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     unsigned fallbacks = 0;
-    const int ntiles = (L + kTile - 1) / kTile;
+    const int T = A.tile;  // blockDim.x * ITEMS
+    const int ntiles = (L + T - 1) / T;
     for (int tile = bid; tile < ntiles; tile += nb) {
-        const int v0 = tile * kTile, v1 = min(v0 + kTile, L);
+        const int v0 = tile * T, v1 = min(v0 + T, L);
         __syncthreads();
         if (threadIdx.x == 0) {
-            sm.a.e0 = FIRST ? 0 : A.tile_ent[tile];
-            sm.a.m = FIRST ? 1 : A.tile_m[tile];
+            if (FIRST) {  // entries = the clouds the tile meets
+                const int c0 = cloud_of(A, v0);
+                sm.a.e0 = c0;
+                sm.a.m = cloud_of(A, v1 - 1) - c0 + 1;
+            } else {
+                sm.a.e0 = A.tile_ent[tile];
+                sm.a.m = A.tile_m[tile];
+            }
         }
         for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
             sm.a.skey[i] = -1;
@@ -657,10 +861,13 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int n
         }
         __syncthreads();
         const int e0 = sm.a.e0, m = sm.a.m;
-        for (int i = threadIdx.x; i < m && i < kTile; i += blockDim.x) {
+        // FIRST: a tile that meets more clouds than the stage holds (runs of
+        // empty clouds) searches the cloud offsets in global memory instead
+        const bool staged = m <= kMaxTile;
+        for (int i = threadIdx.x; i < m && i < kMaxTile; i += blockDim.x) {
             if (FIRST) {
-                sm.a.start[i] = 0;
-                sm.a.f[i] = kPseudo;
+                sm.a.start[i] = cloud_start(A, e0 + i);
+                sm.a.f[i] = A.fcap + e0 + i;
             } else {
                 sm.a.start[i] = ent[e0 + i].start;
                 sm.a.f[i] = ent[e0 + i].f;
@@ -668,9 +875,9 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int n
         }
         __syncthreads();
         // ---- classify; cone targets get a tile-local slot (shared hash table)
-        int tgt[kItems], rk[kItems], slot[kItems];
+        int tgt[ITEMS], rk[ITEMS], slot[ITEMS];
 #pragma unroll
-        for (int k = 0; k < kItems; k++) {
+        for (int k = 0; k < ITEMS; k++) {
             const int v = v0 + k * blockDim.x + threadIdx.x;
             const bool valid = v < v1;
             int target = -1, rank = 0, s = -1;
@@ -678,13 +885,18 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int n
             int idx = 0;
             bool cone_t = false;
             if (valid) {
-                int lo = 0, hi = m - 1;
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if (sm.a.start[mid] <= v) lo = mid;
-                    else hi = mid - 1;
+                int lo = 0, hi = m - 1, f;
+                if (FIRST && !staged) {
+                    lo = cloud_of(A, v) - e0;
+                    f = A.fcap + e0 + lo;
+                } else {
+                    while (lo < hi) {
+                        int mid = (lo + hi + 1) >> 1;
+                        if (sm.a.start[mid] <= v) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    f = sm.a.f[lo];
                 }
-                const int f = sm.a.f[lo];
                 const float4 p4 = FIRST ? load_input(A, v) : P[v];
                 idx = __float_as_int(p4.w);
                 const float p[3] = {p4.x, p4.y, p4.z};
@@ -776,7 +988,7 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int n
         }
         __syncthreads();
 #pragma unroll
-        for (int k = 0; k < kItems; k++) {
+        for (int k = 0; k < ITEMS; k++) {
             const int v = v0 + k * blockDim.x + threadIdx.x;
             if (tgt[k] == -2) continue;
             const int r = (slot[k] >= 0) ? sm.a.sbase[slot[k]] + rk[k] : rk[k];
@@ -915,9 +1127,10 @@ __device__ void certify3d(const Params3 &A, int par, int bid, int nb)
             }
         }
     }
-    const int ntiles = (L + kTile - 1) / kTile;
+    const int T = A.tile;
+    const int ntiles = (L + T - 1) / T;
     for (int t = bid * blockDim.x + threadIdx.x; t < ntiles; t += nb * blockDim.x) {
-        const int v = t * kTile, vl = min(v + kTile, L) - 1;
+        const int v = t * T, vl = min(v + T, L) - 1;
         auto ent_of = [&](int x) {
             int lo = 0, hi = ne - 1;
             while (lo < hi) {
@@ -993,8 +1206,8 @@ __device__ void exact3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int nb
 }
 
 // ---------------------------------------------------------------- persistent kernel
-template <int MODE>
-__global__ void __launch_bounds__(kBlock) qh3d_persistent(Params3 A)
+template <int MODE, int ITEMS>
+__global__ void __launch_bounds__(kMaxBlock) qh3d_persistent(Params3 A)
 {
     __shared__ SmemAll3 sm;
     Hdr3 *H = A.hdr;
@@ -1012,35 +1225,40 @@ __global__ void __launch_bounds__(kBlock) qh3d_persistent(Params3 A)
         tprev = t;
     };
 
-    // ---- initial simplex
-    extrema3d(A, sm, bid, nb);
-    sync();
-    if (bid == 0) simplex_step(A, sm, 0, nb);
-    sync();
-    if (*(volatile int *)&H->nonfinite) {
-        if (bid == 0 && threadIdx.x == 0) set_status(H, QH_ERR_NONFINITE);
-    }
-    for (int step = 1; step <= 2 && ok(); step++) {
-        if (step == 2) {
-            // c is known: plane abc
+    // ---- initial simplex: grid-wide for one cloud, one block per cloud for
+    // a batch
+    if (A.cloud_off) {
+        if (ok()) init_clouds(A, sm, bid, nb);  // offsets checked before the launch
+        sync();
+    } else {
+        extrema3d(A, sm, bid, nb);
+        sync();
+        if (bid == 0) simplex_step(A, sm, 0, nb);
+        sync();
+        if (*(volatile int *)&H->nonfinite) {
+            if (bid == 0 && threadIdx.x == 0) set_status(H, QH_ERR_NONFINITE);
         }
-        farthest3d(A, sm, bid, nb, step - 1);
-        sync();
-        if (bid == 0) simplex_step(A, sm, step, nb);
-        sync();
-        if (!*(volatile int *)&H->cand_ok) {
-            exact_search3d(A, bid, nb, step - 1);
+        for (int step = 1; step <= 2 && ok(); step++) {
+            farthest3d(A, sm, bid, nb, step - 1);
+            sync();
+            if (bid == 0) simplex_step(A, sm, step, nb);
+            sync();
+            if (!*(volatile int *)&H->cand_ok) {
+                exact_search3d(A, bid, nb, step - 1);
+                sync();
+            }
+            if (bid == 0) simplex_take(A, step);
             sync();
         }
-        if (bid == 0) simplex_take(A, step);
-        sync();
+        if (ok()) {
+            if (bid == 0) build_tetra(A);
+            sync();
+        }
     }
     if (ok()) {
-        if (bid == 0) build_tetra(A);
-        sync();
         // ---- first assignment: every input point against the tetrahedron;
         // table 1 / buffer 1 receive the result
-        assign3d<MODE, true>(A, 0, sm, bid, nb);
+        assign3d<MODE, ITEMS, true>(A, 0, sm, bid, nb);
         sync();
         table_sum(A, 0, true, sm, bid, nb);
         sync();
@@ -1094,7 +1312,7 @@ __global__ void __launch_bounds__(kBlock) qh3d_persistent(Params3 A)
         if (clk && iter <= kTimeline3) H->tl[iter - 1][2] = H->nwin;
         mark(iter, 4);
         if (!ok()) break;
-        assign3d<MODE, false>(A, cur, sm, bid, nb);
+        assign3d<MODE, ITEMS, false>(A, cur, sm, bid, nb);
         sync();
         mark(iter, 5);
         table_sum(A, cur, false, sm, bid, nb);
@@ -1118,12 +1336,18 @@ __global__ void __launch_bounds__(kBlock) qh3d_persistent(Params3 A)
     }
 }
 
-// Kernel entry of the persistent 3D loop for a predicate mode (the launch
-// happens in qh3d_out.cu).
-const void *persistent_kernel(int mode)
+// Kernel entry of the persistent 3D loop for a predicate mode and points per
+// thread of the assign pass (2, 4 or 8; the launch happens in qh3d_out.cu).
+const void *persistent_kernel(int mode, int items)
 {
-    return mode == QH_PRED_F32 ? (const void *)qh3d_persistent<QH_PRED_F32>
-                               : (const void *)qh3d_persistent<QH_PRED_F64>;
+    if (mode == QH_PRED_F32) {
+        if (items == 2) return (const void *)qh3d_persistent<QH_PRED_F32, 2>;
+        if (items == 8) return (const void *)qh3d_persistent<QH_PRED_F32, 8>;
+        return (const void *)qh3d_persistent<QH_PRED_F32, 4>;
+    }
+    if (items == 2) return (const void *)qh3d_persistent<QH_PRED_F64, 2>;
+    if (items == 8) return (const void *)qh3d_persistent<QH_PRED_F64, 8>;
+    return (const void *)qh3d_persistent<QH_PRED_F64, 4>;
 }
 
 }  // namespace d3

@@ -12,9 +12,13 @@
 namespace qh {
 namespace d3 {
 
-constexpr int kBlock = 256;
-constexpr int kItems = 4;                // points per thread in the assign pass
-constexpr int kTile = kBlock * kItems;   // points per assign tile
+// Launch shape of the persistent kernel: threads per CTA (runtime, up to
+// kMaxBlock) and points per thread of the assign pass (template: 2, 4, 8).
+constexpr int kMaxBlock = 512;
+constexpr int kDefBlock = 256;
+constexpr int kDefItems = 4;
+constexpr int kMaxTile = 4096;           // points per assign tile (block x items), upper bound
+constexpr int kMinTile = 256;            // lower bound (sizes the tile maps)
 constexpr int kVCap = 32;                // visible facets a candidate may list
 constexpr int kNCap = 64;                // horizon neighbours a candidate may list (>= kVCap + 2)
 constexpr int kMaxGrid = 4096;
@@ -59,8 +63,10 @@ struct Hdr3 {
     long long seg_total, surv_total;
     unsigned long long fallbacks, exact_argmax;
     // output stage
-    int nalive, ncop, nbedge, ngroup, nface, nvert, changed, pad1;
-    long long nfidx;
+    int nalive, ncop, nbedge, ngroup;
+    int sort_m;             // entries of the radix-sort histogram being scanned
+    int uf_fail, pad1, pad2;
+    long long nfidx, nv_out;
     // per-iteration record (first kTimeline3 iterations): live points,
     // segments, winners, then device time of select, rounds, assign, table,
     // scatter + certify, exact (ns)
@@ -73,6 +79,12 @@ struct Params3 {
     long long stride;
     int n;
     int fcap, ecap;
+    int tile;                     // points per assign tile (block x items)
+    // clouds: cloud c holds points [cloud_off[c], cloud_off[c+1]); a single
+    // cloud when cloud_off is null
+    const long long *cloud_off;
+    int ncloud;
+    int *cloud_status;            // per-cloud qh_status (batched calls)
     Hdr3 *hdr;
     qh_result *res;
     // facets
@@ -104,9 +116,9 @@ struct Params3 {
     long long max_iters, wait_ns;
 };
 
-// The pseudo facet of the first assignment (every input point coned to the
-// tetrahedron): cone[kPseudoSlot(A)].
-#define kPseudo (A.fcap)
+// The pseudo facet of cloud c in the first assignment (every point of the
+// cloud coned to its tetrahedron) is fcap + c; its cone record lists the
+// tetrahedron's facets.
 
 // Claim of a candidate (the facet f whose segment of `len` points it heads)
 // in a selection round.  Later iterations and rounds win over earlier ones;
@@ -125,16 +137,17 @@ __device__ __forceinline__ unsigned long long claim_key(int iter, int round, int
 }
 
 struct SmemRed {
-    float4 a[kBlock], b[kBlock];
-    float v[kBlock];
-    int i[kBlock];
+    float4 a[kMaxBlock], b[kMaxBlock];
+    float v[kMaxBlock];
+    int i[kMaxBlock];
+    int flag;
 };
 constexpr int kSlotBits = 7;
 constexpr int kSlots = 1 << kSlotBits;   // distinct cone targets aggregated per assign tile
 struct SmemAssign {
     int e0, m;
-    int start[kTile];
-    int f[kTile];
+    int start[kMaxTile];
+    int f[kMaxTile];
     int skey[kSlots], scnt[kSlots], sbase[kSlots];
     unsigned long long sk1[kSlots];
     unsigned so2[kSlots], sem[kSlots];
@@ -143,8 +156,8 @@ struct SmemTable {
     long long wsum[33];
 };
 struct SmemX3 {
-    int idx[kBlock];
-    float4 p[kBlock];
+    int idx[kMaxBlock];
+    float4 p[kMaxBlock];
 };
 union SmemAll3 {
     SmemRed red;
@@ -161,11 +174,11 @@ struct Layout3 {
     size_t alive, label, cop, ekey[2], eval[2], hist, hist_off, gstart, poly, glen, fkey[2], fval[2],
         vflag, scan_tmp;
     size_t total;
-    int fcap, ecap, hist_blocks;
+    int fcap, ecap, hist_blocks, ncloud;
 };
 
-Layout3 layout3d(int64_t n);
-const void *persistent_kernel(int mode);
+Layout3 layout3d(int64_t n, int ncloud = 1);
+const void *persistent_kernel(int mode, int items);
 Params3 make_params3(const float *x, const float *y, const float *z, int64_t n, int64_t stride,
                      char *ws, const Layout3 &L, const qh_opts &o);
 

@@ -1,7 +1,8 @@
 // Status strings, defaults and the occupancy cache of libqh.
 #include <cstring>
 #include <mutex>
-#include <unordered_map>
+#include <map>
+#include <tuple>
 
 #include "qh_internal.h"
 
@@ -10,10 +11,10 @@ namespace qh {
 int persistent_grid(const void *func, int block, int blocks_per_sm)
 {
     static std::mutex mu;
-    static std::unordered_map<unsigned long long, int> cache;
+    static std::map<std::tuple<uintptr_t, int, int>, int> cache;  // (func, device, block)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    unsigned long long key = ((unsigned long long)(uintptr_t)func << 8) ^ (unsigned long long)dev;
+    const auto key = std::make_tuple((uintptr_t)func, dev, block);
     int per_sm = 0, sms = 0;
     {
         std::lock_guard<std::mutex> g(mu);

@@ -124,3 +124,39 @@ def test_degenerate_3d():
     v, f = oracle.hull3d([0, 1, 0, 0], [0, 0, 1, 0], [0, 0, 0, 1])
     assert v.tolist() == [0, 1, 2, 3]
     assert [t.tolist() for t in f] == [[0, 1, 3], [0, 2, 1], [0, 3, 2], [1, 2, 3]]
+
+
+def test_batched_oracle_against_brute_force_and_closed_cases():
+    # a batch mixing brute-forced tiny clouds, a cube with interior points
+    # (closed form: its 8 corners and 6 square faces), an empty cloud and
+    # degenerate clouds (3 points; a coplanar set); global indices
+    clouds = list(_tiny_sets3(5, 24))
+    rng = np.random.default_rng(9)
+    corners = np.array([[i, j, k] for i in (0, 2) for j in (0, 2) for k in (0, 2)], np.float32)
+    cube = np.concatenate([rng.uniform(0.1, 1.9, (40, 3)).astype(np.float32), corners])
+    clouds.append(tuple(cube.T.copy()))
+    clouds.append(tuple(np.zeros((3, 0), np.float32)))
+    clouds.append(tuple(np.array([[0, 1, 0], [0, 0, 1], [0, 0, 0]], np.float32)))
+    flat = rng.random((3, 12)).astype(np.float32)
+    flat[2] = 0.5
+    clouds.append(tuple(flat))
+    off = np.zeros(len(clouds) + 1, np.int64)
+    off[1:] = np.cumsum([len(c[0]) for c in clouds])
+    x, y, z = (np.concatenate([c[i] for c in clouds]) for i in range(3))
+    got = oracle.hull3d_batched(x, y, z, off)
+    assert len(got) == len(clouds)
+    for c, ((st, v, f), (cx, cy, cz)) in enumerate(zip(got, clouds)):
+        a = int(off[c])
+        if len(cx) == 0:
+            assert st == oracle.OK and len(v) == 0 and f == []
+            continue
+        want = ex.brute_hull3d(cx, cy, cz)
+        if want is None:
+            assert st == oracle.ERR_DEGENERATE and len(v) == 0 and f == []
+            continue
+        assert st == oracle.OK
+        assert (v - a).tolist() == want[0]
+        assert [tuple((t - a).tolist()) for t in f] == [tuple(t) for t in want[1]]
+    st, v, f = got[24]
+    assert st == oracle.OK and len(v) == 8 and len(f) == 6 and all(len(t) == 4 for t in f)
+    assert sorted(v.tolist()) == list(range(int(off[24]) + 40, int(off[24]) + 48))
