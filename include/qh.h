@@ -249,6 +249,70 @@ qh_status qh_autotune_3d_batched(const float *d_x, const float *d_y, const float
                                  int32_t *h_ncand, cudaStream_t stream);
 
 /*
+ * Batched 2D hulls (no counterpart in the paper): one CTA runs the whole
+ * segmented Quickhull of one cloud, clouds taken from a queue by a
+ * persistent grid.  Meant for many small or medium clouds (up to about 10^5
+ * points each); large single clouds belong to qh_hull2d.  Clouds are CSR as
+ * in qh_hull3d_batched (1 <= ncloud, n >= 1).
+ *
+ *  d_out_idx       device int32[n]: the hull of cloud c (counter-clockwise
+ *                  from its lexicographically smallest point, collinear
+ *                  points dropped, global indices) at
+ *                  d_out_idx[cloud_off[c] .. cloud_off[c] + d_cloud_count[c])
+ *  d_cloud_count   device int32[ncloud]: hull size per cloud (0 when empty
+ *                  or non-finite, 1 when all points coincide)
+ *  d_cloud_status  device int32[ncloud]: QH_OK or QH_ERR_NONFINITE
+ *  d_result        device qh_result: whole-call status (QH_ERR_INVALID_ARG
+ *                  for bad offsets), count = total hull vertices, iterations
+ *                  = the largest per-cloud iteration count
+ * Never synchronises; allocates nothing (capturable in a CUDA graph after
+ * one call on the device).
+ */
+size_t qh_workspace_bytes_2d_batched(int64_t n, int32_t ncloud, const qh_opts *opts);
+qh_status qh_hull2d_batched(const float *d_x, const float *d_y, int64_t stride,
+                            const int64_t *d_cloud_off, int32_t ncloud, int64_t n,
+                            int32_t *d_out_idx, int32_t *d_cloud_count, int32_t *d_cloud_status,
+                            qh_result *d_result, void *d_ws, size_t ws_bytes, const qh_opts *opts,
+                            cudaStream_t stream);
+
+/*
+ * Differentiable measures (no counterpart in the paper, which computes the
+ * hull only).  On general-position inputs the hull's vertex set and faces
+ * are locally constant, so each measure is a smooth function of the hull
+ * vertices and its gradient is zero on every other point.  Sums are FP64.
+ *
+ * qh_measures2d: d_meas[2c] = perimeter, d_meas[2c+1] = area of cloud c's
+ *   hull as written by qh_hull2d_batched (d_hull, d_cloud_count; a single
+ *   qh_hull2d result is one cloud with offsets {0, n}).
+ * qh_hull2d_backward: with d_grad[2c], d_grad[2c+1] = dL/dperimeter and
+ *   dL/darea of cloud c, writes dL/dx, dL/dy of every point (float32, zero
+ *   off the hull) to d_gx[i*gstride], d_gy[i*gstride].
+ * qh_measures3d: d_meas[2c] = surface area, d_meas[2c+1] = volume of cloud
+ *   c's hull (faces d_cloud_face_off[c] .. d_cloud_face_off[c+1] of the CSR
+ *   face list of qh_hull3d / qh_hull3d_batched; faces are triangulated as
+ *   fans from their first vertex).
+ * qh_hull3d_backward: same for dL/darea, dL/dvolume; d_scratch is device
+ *   FP64 scratch of 3n values (the per-point sums before rounding).
+ * All four are asynchronous on `stream`.
+ */
+qh_status qh_measures2d(const float *d_x, const float *d_y, int64_t stride,
+                        const int64_t *d_cloud_off, int32_t ncloud, const int32_t *d_hull,
+                        const int32_t *d_cloud_count, double *d_meas, cudaStream_t stream);
+qh_status qh_hull2d_backward(const float *d_x, const float *d_y, int64_t stride,
+                             const int64_t *d_cloud_off, int32_t ncloud, int64_t n,
+                             const int32_t *d_hull, const int32_t *d_cloud_count,
+                             const double *d_grad, float *d_gx, float *d_gy, int64_t gstride,
+                             cudaStream_t stream);
+qh_status qh_measures3d(const float *d_x, const float *d_y, const float *d_z, int64_t stride,
+                        int32_t ncloud, const int32_t *d_face_off, const int32_t *d_face_idx,
+                        const int32_t *d_cloud_face_off, double *d_meas, cudaStream_t stream);
+qh_status qh_hull3d_backward(const float *d_x, const float *d_y, const float *d_z, int64_t stride,
+                             int32_t ncloud, int64_t n, const int32_t *d_face_off,
+                             const int32_t *d_face_idx, const int32_t *d_cloud_face_off,
+                             const double *d_grad, float *d_gx, float *d_gy, float *d_gz,
+                             int64_t gstride, double *d_scratch, cudaStream_t stream);
+
+/*
  * qh_hull2d_noalloc: qh_hull2d for callers that cannot allocate device
  * memory while they run: plugins whose host owns every device allocation,
  * real-time loops that allocate only at start-up, and code that may not let

@@ -16,7 +16,9 @@ from ._native import QhOpts, QhResult, RESULT_BYTES
 
 __all__ = ["QHError", "hull2d", "hull2d_async", "workspace_bytes_2d", "Workspace", "hull3d",
            "hull3d_batched", "Hull3DBatch", "workspace_bytes_3d", "workspace_bytes_3d_batched",
-           "make_opts", "status_str", "version", "RESULT_BYTES", "result_from_tensor"]
+           "make_opts", "status_str", "version", "RESULT_BYTES", "result_from_tensor",
+           "Hull2DBatch", "hull2d_batched", "workspace_bytes_2d_batched", "hull_measures_2d",
+           "hull_measures_3d"]
 
 PRED = {"f32": 0, "f64": 1}
 LOOP = {"persistent": 0, "host": 1}
@@ -357,3 +359,180 @@ def hull3d_batched(x, y=None, z=None, cloud_off: torch.Tensor = None, *, pred: s
     b = Hull3DBatch(x, y, z, cloud_off, pred=pred, opts=opts)
     b.enqueue()
     return b.outputs()
+
+
+# ---------------------------------------------------------------------- batched 2D
+def workspace_bytes_2d_batched(n: int, ncloud: int, opts: Optional[QhOpts] = None) -> int:
+    return int(_native.lib().qh_workspace_bytes_2d_batched(int(n), int(ncloud),
+                                                           ctypes.byref(opts) if opts else None))
+
+
+def _check_off(cloud_off):
+    if cloud_off is None or cloud_off.dtype != torch.int64 or not cloud_off.is_cuda or \
+            cloud_off.dim() != 1 or cloud_off.numel() < 2 or \
+            (cloud_off.numel() > 1 and cloud_off.stride(0) != 1):
+        raise ValueError("cloud_off must be a contiguous CUDA int64 tensor of ncloud + 1 offsets")
+
+
+class Hull2DBatch:
+    """Hulls of a batch of 2D clouds (qh_hull2d_batched), output buffers
+    allocated once (graph-capturable).  Points [n, 2], [2, n] or x, y CUDA
+    float32; cloud_off int64 CUDA [ncloud + 1].  Cloud c's hull (global
+    indices) is out[cloud_off[c] : cloud_off[c] + count[c]]."""
+
+    def __init__(self, x, y=None, cloud_off: torch.Tensor = None, *, pred: str = "f32",
+                 opts: Optional[QhOpts] = None, workspace: Optional[Workspace] = None):
+        _check_off(cloud_off)
+        self._inputs = (x, y, cloud_off)
+        self.xp, self.yp, self.n, self.stride, dev = _points_2d(x, y)
+        self.cloud_off = cloud_off
+        self.ncloud = cloud_off.numel() - 1
+        self.opts = opts if opts is not None else make_opts(pred)
+        i32 = dict(dtype=torch.int32, device=dev)
+        self.out = torch.empty(max(self.n, 1), **i32)
+        self.count = torch.empty(self.ncloud, **i32)
+        self.status = torch.empty(self.ncloud, **i32)
+        self.result = torch.zeros(RESULT_BYTES, dtype=torch.uint8, device=dev)
+        nb = workspace_bytes_2d_batched(self.n, self.ncloud, self.opts)
+        if nb == 0:
+            raise QHError(1, "qh_workspace_bytes_2d_batched")
+        self.ws = (workspace or Workspace(dev)).get(nb)
+        self.graph = None
+
+    def enqueue(self, stream=None) -> None:
+        st = _native.lib().qh_hull2d_batched(
+            self.xp, self.yp, self.stride, self.cloud_off.data_ptr(), self.ncloud, self.n,
+            self.out.data_ptr(), self.count.data_ptr(), self.status.data_ptr(),
+            self.result.data_ptr(), self.ws.data_ptr(), self.ws.numel(), ctypes.byref(self.opts),
+            _stream_handle(stream))
+        if st != 0:
+            raise QHError(st, "qh_hull2d_batched")
+
+    def capture(self) -> None:
+        s = torch.cuda.Stream(device=self.out.device)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.enqueue()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.enqueue()
+        self.graph = g
+
+    def replay(self) -> None:
+        self.graph.replay()
+
+    def result_dict(self) -> dict:
+        return result_from_tensor(self.result).as_dict()
+
+    def outputs(self):
+        """(out, count, status) after the last run (synchronises); raises
+        QHError if the call failed."""
+        r = result_from_tensor(self.result)
+        if r.status != 0:
+            raise QHError(r.status, "qh_hull2d_batched")
+        return self.out, self.count, self.status
+
+
+def hull2d_batched(x, y=None, cloud_off: torch.Tensor = None, *, pred: str = "f32",
+                   opts: Optional[QhOpts] = None):
+    """One batched 2D call: (out, count, status), see Hull2DBatch."""
+    b = Hull2DBatch(x, y, cloud_off, pred=pred, opts=opts)
+    b.enqueue()
+    return b.outputs()
+
+
+# ---------------------------------------------------------------------- differentiable measures
+def _rows(pts: torch.Tensor, d: int):
+    """[d, n] row-contiguous or [n, d] contiguous float32 CUDA -> (row pointers, n, stride)."""
+    if pts.dtype != torch.float32 or not pts.is_cuda or pts.dim() != 2:
+        raise ValueError(f"points must be a CUDA float32 tensor [{d}, n] or [n, {d}]")
+    if pts.shape[0] == d and pts.stride(1) == 1:
+        return [pts[i].data_ptr() for i in range(d)], pts.shape[1], 1
+    if pts.shape[1] == d and pts.stride(1) == 1 and (pts.shape[0] <= 1 or pts.stride(0) == d):
+        return [pts.data_ptr() + 4 * i for i in range(d)], pts.shape[0], d
+    raise ValueError(f"points must be row-contiguous [{d}, n] or contiguous [n, {d}]")
+
+
+class _Measures2D(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, pts, cloud_off, pred):
+        (xp, yp), n, stride = _rows(pts, 2)
+        ws = _default_ws.setdefault(str(pts.device), Workspace(pts.device))
+        b = Hull2DBatch(pts.detach(), None, cloud_off, pred=pred, workspace=ws)
+        b.enqueue()
+        meas = torch.empty(b.ncloud, 2, dtype=torch.float64, device=pts.device)
+        st = _native.lib().qh_measures2d(xp, yp, stride, cloud_off.data_ptr(), b.ncloud,
+                                         b.out.data_ptr(), b.count.data_ptr(), meas.data_ptr(),
+                                         _stream_handle(None))
+        if st != 0:
+            raise QHError(st, "qh_measures2d")
+        b.outputs()  # raises on a failed hull
+        ctx.save_for_backward(pts, cloud_off, b.out, b.count)
+        return meas
+
+    @staticmethod
+    def backward(ctx, gm):
+        pts, cloud_off, out, count = ctx.saved_tensors
+        (xp, yp), n, stride = _rows(pts, 2)
+        g = gm.detach().to(torch.float64).contiguous()
+        grad = torch.empty_like(pts)
+        (gx, gy), _, gstride = _rows(grad, 2)
+        st = _native.lib().qh_hull2d_backward(xp, yp, stride, cloud_off.data_ptr(),
+                                              cloud_off.numel() - 1, n, out.data_ptr(),
+                                              count.data_ptr(), g.data_ptr(), gx, gy, gstride,
+                                              _stream_handle(None))
+        if st != 0:
+            raise QHError(st, "qh_hull2d_backward")
+        return grad, None, None
+
+
+def hull_measures_2d(pts: torch.Tensor, cloud_off: torch.Tensor, *, pred: str = "f32"):
+    """[ncloud, 2] float64: (perimeter, area) of each cloud's hull, differentiable
+    with respect to pts ([2, n] or [n, 2] CUDA float32; gradient on the hull
+    vertices only, computed by qh_hull2d_backward)."""
+    _check_off(cloud_off)
+    return _Measures2D.apply(pts, cloud_off, pred)
+
+
+class _Measures3D(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, pts, cloud_off, pred):
+        (xp, yp, zp), n, stride = _rows(pts, 3)
+        b = Hull3DBatch(pts.detach(), None, None, cloud_off, pred=pred)
+        b.enqueue()
+        meas = torch.empty(b.ncloud, 2, dtype=torch.float64, device=pts.device)
+        st = _native.lib().qh_measures3d(xp, yp, zp, stride, b.ncloud, b.face_off.data_ptr(),
+                                         b.face_idx.data_ptr(), b.cloud_foff.data_ptr(),
+                                         meas.data_ptr(), _stream_handle(None))
+        if st != 0:
+            raise QHError(st, "qh_measures3d")
+        b.outputs()  # raises on a failed hull
+        ctx.save_for_backward(pts, b.face_off, b.face_idx, b.cloud_foff)
+        ctx.ncloud = b.ncloud
+        return meas
+
+    @staticmethod
+    def backward(ctx, gm):
+        pts, foff, fidx, cfoff = ctx.saved_tensors
+        (xp, yp, zp), n, stride = _rows(pts, 3)
+        g = gm.detach().to(torch.float64).contiguous()
+        grad = torch.empty_like(pts)
+        (gx, gy, gz), _, gstride = _rows(grad, 3)
+        scratch = torch.empty(3 * max(n, 1), dtype=torch.float64, device=pts.device)
+        st = _native.lib().qh_hull3d_backward(xp, yp, zp, stride, ctx.ncloud, n,
+                                              foff.data_ptr(), fidx.data_ptr(), cfoff.data_ptr(),
+                                              g.data_ptr(), gx, gy, gz, gstride,
+                                              scratch.data_ptr(), _stream_handle(None))
+        if st != 0:
+            raise QHError(st, "qh_hull3d_backward")
+        return grad, None, None
+
+
+def hull_measures_3d(pts: torch.Tensor, cloud_off: torch.Tensor, *, pred: str = "f32"):
+    """[ncloud, 2] float64: (surface area, volume) of each cloud's hull,
+    differentiable with respect to pts ([3, n] or [n, 3] CUDA float32;
+    gradient on the hull vertices only, computed by qh_hull3d_backward)."""
+    _check_off(cloud_off)
+    return _Measures3D.apply(pts, cloud_off, pred)

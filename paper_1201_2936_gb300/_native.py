@@ -58,6 +58,16 @@ SIGNATURES = [
     ("qh_workspace_bytes_3d_batched", _sz, [_i64, ctypes.c_int32, _POpts]),
     ("qh_hull3d_batched", ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, ctypes.c_int32, _i64, _vp, _vp,
                                          _vp, _vp, _vp, _vp, _vp, _vp, _sz, _POpts, _vp]),
+    ("qh_workspace_bytes_2d_batched", _sz, [_i64, ctypes.c_int32, _POpts]),
+    ("qh_hull2d_batched", ctypes.c_int, [_vp, _vp, _i64, _vp, ctypes.c_int32, _i64, _vp, _vp, _vp,
+                                         _vp, _vp, _sz, _POpts, _vp]),
+    ("qh_measures2d", ctypes.c_int, [_vp, _vp, _i64, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp]),
+    ("qh_hull2d_backward", ctypes.c_int, [_vp, _vp, _i64, _vp, ctypes.c_int32, _i64, _vp, _vp, _vp,
+                                          _vp, _vp, _i64, _vp]),
+    ("qh_measures3d", ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.c_int32, _vp, _vp, _vp, _vp,
+                                     _vp]),
+    ("qh_hull3d_backward", ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.c_int32, _i64, _vp, _vp, _vp,
+                                          _vp, _vp, _vp, _vp, _i64, _vp, _vp]),
     ("qh_autotune_3d_batched", ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, ctypes.c_int32, _i64, _vp,
                                               _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz,
                                               ctypes.c_int32, _POpts, _vp, _vp, ctypes.c_int32,
