@@ -7,7 +7,9 @@ predicates, one persistent kernel per hull.  value = points hulled per
 second over the whole job (Mpoints/s), inputs resident in HBM.
 
 Also reported: the 3D hull (8M points in the ball, 1M on the sphere) with the
-FP32 filter and with FP64 predicates; the plain GPU path (FP64 predicates,
+FP32 filter and with FP64 predicates; the batched 3D hull (4096 clouds in one
+graph-replayed launch); the differentiable hulls (forward and hand-written
+backward, bwd/fwd); the plain GPU path (FP64 predicates,
 host-driven loop with a live-count readback per iteration); the end-to-end
 number through the C ABI with host buffers; the HBM roofline of the
 persistent kernel; and the CPU oracle on the host cores.  `--impl reference`
@@ -192,6 +194,147 @@ def bench_3d(args, qh, dev, rank, peak, peak_kind):
             "peak": peak, "peak_kind": peak_kind, "reps": reps, "clouds": out}
 
 
+def bench_batched(args, qh, dev, rank, peak, peak_kind):
+    """The batched 3D workload: 4096 anisotropic Gaussian clouds (sizes
+    log-uniform in [16, 65536]) in one persistent launch, launch shape from
+    the autotuner, replayed from a CUDA graph; against it the plain path (one
+    FP64 qh_hull3d call per cloud, host-synchronised) on the first clouds."""
+    import torch
+    from paper_1201_2936_gb300 import workloads as w
+    x, y, z, off = w.batched_clouds_3d(args.batch_clouds, w.SEED_BASE + 3 + 1000 * rank)
+    n = len(x)
+    P = torch.from_numpy(np.stack([x, y, z])).to(dev)
+    O = torch.from_numpy(off).to(dev)
+    b = qh.Hull3DBatch(P, cloud_off=O)
+    table = b.tune(reps=2)
+    b.capture()
+    reps = max(5, args.steps // 5)
+    for _ in range(3):
+        b.replay()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+    torch.cuda.synchronize()
+    e[0].record()
+    for k in range(reps):
+        b.replay()
+        e[k + 1].record()
+    torch.cuda.synchronize()
+    ms = statistics.median(e[k].elapsed_time(e[k + 1]) for k in range(reps))
+    r = b.result_dict()
+    st = b.cloud_status.cpu().numpy()
+    # the same batch enqueued directly (no graph)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        b.enqueue()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_direct = e0.elapsed_time(e1) / reps
+    algo = 24 * n + 32 * r["survivor_total"]
+    out = {"workload": f"{args.batch_clouds} clouds, sizes log-uniform in [16, 65536], "
+                       "anisotropic Gaussian, float32",
+           "points": n, "ms": round(ms, 3), "Mpoints_s": round(n / ms / 1e3, 1),
+           "ms_without_graph": round(ms_direct, 3), "iterations": r["iterations"],
+           "hull_vertices": r["extra"][0], "faces": r["extra"][1],
+           "clouds_ok": int((st == 0).sum()),
+           "algo_bytes": algo, "GBps": round(algo / (ms / 1e3) / 1e9, 1),
+           "frac": round(algo / (ms / 1e3) / 1e9 / peak, 4), "peak_kind": peak_kind,
+           "fallback_frac": r["filter_fallbacks"] / max(1, r["live_total"]),
+           "tuned": {"block": b.opts.block, "items": b.opts.items,
+                     "ctas_per_sm": b.opts.blocks_per_sm},
+           "tune_table_ms": [[bl, it, c, round(t, 3)] for bl, it, c, t in table]}
+    # plain path on a bounded sample of clouds
+    ns = min(args.batch_clouds, args.plain_clouds)
+    ws = qh.Workspace(dev)
+    pts = 0
+    torch.cuda.synchronize()
+    e0.record()
+    for c in range(ns):
+        a, bb = int(off[c]), int(off[c + 1])
+        if bb - a >= 4:
+            qh.hull3d(P[:, a:bb], pred="f64", workspace=ws)
+        pts += bb - a
+    e1.record()
+    torch.cuda.synchronize()
+    pms = e0.elapsed_time(e1)
+    out["plain_gpu"] = {"Mpoints_s": round(pts / pms / 1e3, 2), "clouds": ns, "points": pts,
+                        "ms": round(pms, 2),
+                        "pred": "f64-filter+exact", "calls": "one synchronous qh_hull3d per cloud",
+                        "speedup_of_batched": round((n / ms) / (pts / pms), 1)}
+    del b, P, O, ws
+    torch.cuda.empty_cache()
+    return out
+
+
+def _time(fn, reps):
+    import torch
+    for _ in range(2):
+        fn()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+    torch.cuda.synchronize()
+    e[0].record()
+    for k in range(reps):
+        fn()
+        e[k + 1].record()
+    torch.cuda.synchronize()
+    return statistics.median(e[k].elapsed_time(e[k + 1]) for k in range(reps))
+
+
+def bench_diff(args, qh, dev, rank):
+    """Differentiable hulls: forward = batched hull + FP64 measures, backward
+    = the hand-written gradient kernel, both timed on the device (CUDA
+    events), for 1024 clouds x 4096 points in the disk (perimeter + area)
+    and 256 clouds x 16384 points in the ball (area + volume)."""
+    import torch
+    from paper_1201_2936_gb300 import workloads as w
+    reps = max(5, args.steps // 5)
+    out = []
+    x, y, off = w.batched_disk_2d(1024, 4096, w.SEED_BASE + 4 + 1000 * rank)
+    x3, y3, z3, off3 = w.batched_ball_3d(256, 16384, w.SEED_BASE + 5 + 1000 * rank)
+    for dim, pts, o in ((2, np.stack([x, y]), off), (3, np.stack([x3, y3, z3]), off3)):
+        P = torch.from_numpy(pts).to(dev)
+        O = torch.from_numpy(o).to(dev)
+        nc = len(o) - 1
+        b = (qh.Hull2DBatch(P, None, O) if dim == 2 else qh.Hull3DBatch(P, None, None, O))
+        meas = torch.empty(nc, 2, dtype=torch.float64, device=dev)
+        gm = torch.ones(nc, 2, dtype=torch.float64, device=dev)
+        grad = torch.empty_like(P)
+
+        def fwd():
+            b.enqueue()
+            b.measures(meas)
+
+        fwd_ms = _time(fwd, reps)
+        bwd_ms = _time(lambda: b.backward(gm, grad), reps)
+        # the same through autograd (host round trip for the status check included)
+        Pg = P.clone().requires_grad_(True)
+        f = qh.hull_measures_2d if dim == 2 else qh.hull_measures_3d
+
+        def step():
+            m = f(Pg, O)
+            m.sum().backward()
+            Pg.grad = None
+
+        step()  # first use of the autograd engine
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        ag_ms = (time.perf_counter() - t0) / 3 * 1e3
+        n = pts.shape[1]
+        out.append({"workload": (f"2D: {nc} clouds x {n // nc} points in the disk, "
+                                 "loss = sum of perimeters + areas") if dim == 2 else
+                                (f"3D: {nc} clouds x {n // nc} points in the ball, "
+                                 "loss = sum of volumes + surface areas"),
+                    "fwd_ms": round(fwd_ms, 3), "bwd_ms": round(bwd_ms, 3),
+                    "bwd_over_fwd": round(bwd_ms / fwd_ms, 4),
+                    "fwd_Mpoints_s": round(n / fwd_ms / 1e3, 1),
+                    "autograd_step_ms": round(ag_ms, 3)})
+        del b, P, O
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args, ws, rank):
     # the oracle on the host cores, rank 0 only
     if rank != 0:
@@ -232,6 +375,11 @@ def main():
                     help="points per cloud (profiling of smaller cases)")
     ap.add_argument("--only", default="", help="comma-separated cloud names to keep")
     ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-diff", action="store_true")
+    ap.add_argument("--batch-clouds", type=int, default=4096)
+    ap.add_argument("--plain-clouds", type=int, default=256,
+                    help="clouds timed on the per-cloud plain path")
     ap.add_argument("--scale-3d", type=int, default=1, help="divide the 3D cloud sizes")
     ap.add_argument("--timeline", action="store_true",
                     help="print the per-iteration device timeline of each cloud to stderr")
@@ -387,6 +535,14 @@ def main():
     # filter vs the FP64 plain path, same hulls required
     if not args.no_3d:
         line["hull3d"] = bench_3d(args, qh, dev, rank, peak, peak_kind)
+
+    # ---- batched 3D: one persistent launch per batch, CUDA graph, autotuned shape
+    if not args.no_batched:
+        line["batched3d"] = bench_batched(args, qh, dev, rank, peak, peak_kind)
+
+    # ---- differentiable hulls: forward (hull + measures) and backward kernels
+    if not args.no_diff:
+        line["differentiable"] = bench_diff(args, qh, dev, rank)
 
     # ---- end to end through the C ABI with host buffers
     if args.no_e2e:

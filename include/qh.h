@@ -360,6 +360,13 @@ qh_status qh_debug_timeline_2d(const void *d_ws, int64_t n, int64_t *h_rows, int
 qh_status qh_debug_timeline_3d(const void *d_ws, int64_t n, int64_t *h_rows, int32_t max_rows,
                                int32_t *h_nrows, cudaStream_t stream);
 
+/* Device time of the last 3D call made on d_ws (qh_hull3d or
+ * qh_hull3d_batched): h_ns[0..3] = initial simplex, first assignment, its
+ * table, its scatter + certification + exact apexes; h_ns[4] = the whole
+ * persistent kernel (ns, device clock).  Synchronises `stream`.
+ * Diagnostics only. */
+qh_status qh_debug_phases_3d(const void *d_ws, int64_t *h_ns, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

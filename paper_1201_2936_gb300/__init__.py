@@ -125,6 +125,19 @@ def debug_timeline_2d(workspace: Workspace, n: int, stream=None):
     return rows[: nr.value]
 
 
+def debug_phases_3d(ws: torch.Tensor, stream=None):
+    """Device ns of the last 3D call on the workspace tensor `ws`: initial
+    simplex, first assignment, its table, its scatter + certify + exact, and
+    the whole persistent kernel."""
+    import numpy as np
+    out = np.zeros(5, dtype=np.int64)
+    st = _native.lib().qh_debug_phases_3d(ws.data_ptr(), out.ctypes.data_as(ctypes.c_void_p),
+                                          _stream_handle(stream))
+    if st != 0:
+        raise QHError(st, "qh_debug_phases_3d")
+    return out
+
+
 def workspace_bytes_3d(n: int, opts: Optional[QhOpts] = None) -> int:
     return int(_native.lib().qh_workspace_bytes_3d(int(n), ctypes.byref(opts) if opts else None))
 
@@ -341,6 +354,35 @@ class Hull3DBatch:
         r = result_from_tensor(self.result)
         return r.as_dict()
 
+    def measures(self, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """[ncloud, 2] float64 (surface area, volume) of the hulls of the last
+        run (qh_measures3d, asynchronous)."""
+        if out is None:
+            out = torch.empty(self.ncloud, 2, dtype=torch.float64, device=self.verts.device)
+        st = _native.lib().qh_measures3d(self.xp, self.yp, self.zp, self.stride, self.ncloud,
+                                         self.face_off.data_ptr(), self.face_idx.data_ptr(),
+                                         self.cloud_foff.data_ptr(), out.data_ptr(),
+                                         _stream_handle(stream))
+        if st != 0:
+            raise QHError(st, "qh_measures3d")
+        return out
+
+    def backward(self, grad_meas: torch.Tensor, grad: torch.Tensor, stream=None) -> torch.Tensor:
+        """dL/dpoints into `grad` (float32, same layout as the points) from
+        dL/d(area, volume) [ncloud, 2] float64 (qh_hull3d_backward)."""
+        (gx, gy, gz), _, gstride = _rows(grad, 3)
+        if getattr(self, "_scratch", None) is None:
+            self._scratch = torch.empty(3 * max(self.n, 1), dtype=torch.float64,
+                                        device=self.verts.device)
+        st = _native.lib().qh_hull3d_backward(self.xp, self.yp, self.zp, self.stride,
+                                              self.ncloud, self.n, self.face_off.data_ptr(),
+                                              self.face_idx.data_ptr(), self.cloud_foff.data_ptr(),
+                                              grad_meas.data_ptr(), gx, gy, gz, gstride,
+                                              self._scratch.data_ptr(), _stream_handle(stream))
+        if st != 0:
+            raise QHError(st, "qh_hull3d_backward")
+        return grad
+
     def outputs(self):
         """(verts, cloud_vert_off, face_off, face_idx, cloud_face_off,
         cloud_status) after the last run, sliced to their lengths
@@ -426,6 +468,31 @@ class Hull2DBatch:
     def result_dict(self) -> dict:
         return result_from_tensor(self.result).as_dict()
 
+    def measures(self, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """[ncloud, 2] float64 (perimeter, area) of the hulls of the last run
+        (qh_measures2d, asynchronous)."""
+        if out is None:
+            out = torch.empty(self.ncloud, 2, dtype=torch.float64, device=self.out.device)
+        st = _native.lib().qh_measures2d(self.xp, self.yp, self.stride, self.cloud_off.data_ptr(),
+                                         self.ncloud, self.out.data_ptr(), self.count.data_ptr(),
+                                         out.data_ptr(), _stream_handle(stream))
+        if st != 0:
+            raise QHError(st, "qh_measures2d")
+        return out
+
+    def backward(self, grad_meas: torch.Tensor, grad: torch.Tensor, stream=None) -> torch.Tensor:
+        """dL/dpoints into `grad` (float32, same layout as the points) from
+        dL/d(perimeter, area) [ncloud, 2] float64 (qh_hull2d_backward)."""
+        (gx, gy), _, gstride = _rows(grad, 2)
+        st = _native.lib().qh_hull2d_backward(self.xp, self.yp, self.stride,
+                                              self.cloud_off.data_ptr(), self.ncloud, self.n,
+                                              self.out.data_ptr(), self.count.data_ptr(),
+                                              grad_meas.data_ptr(), gx, gy, gstride,
+                                              _stream_handle(stream))
+        if st != 0:
+            raise QHError(st, "qh_hull2d_backward")
+        return grad
+
     def outputs(self):
         """(out, count, status) after the last run (synchronises); raises
         QHError if the call failed."""
@@ -458,33 +525,20 @@ def _rows(pts: torch.Tensor, d: int):
 class _Measures2D(torch.autograd.Function):
     @staticmethod
     def forward(ctx, pts, cloud_off, pred):
-        (xp, yp), n, stride = _rows(pts, 2)
         ws = _default_ws.setdefault(str(pts.device), Workspace(pts.device))
         b = Hull2DBatch(pts.detach(), None, cloud_off, pred=pred, workspace=ws)
         b.enqueue()
-        meas = torch.empty(b.ncloud, 2, dtype=torch.float64, device=pts.device)
-        st = _native.lib().qh_measures2d(xp, yp, stride, cloud_off.data_ptr(), b.ncloud,
-                                         b.out.data_ptr(), b.count.data_ptr(), meas.data_ptr(),
-                                         _stream_handle(None))
-        if st != 0:
-            raise QHError(st, "qh_measures2d")
+        meas = b.measures()
         b.outputs()  # raises on a failed hull
-        ctx.save_for_backward(pts, cloud_off, b.out, b.count)
+        ctx.batch = b
         return meas
 
     @staticmethod
     def backward(ctx, gm):
-        pts, cloud_off, out, count = ctx.saved_tensors
-        (xp, yp), n, stride = _rows(pts, 2)
+        b = ctx.batch
         g = gm.detach().to(torch.float64).contiguous()
-        grad = torch.empty_like(pts)
-        (gx, gy), _, gstride = _rows(grad, 2)
-        st = _native.lib().qh_hull2d_backward(xp, yp, stride, cloud_off.data_ptr(),
-                                              cloud_off.numel() - 1, n, out.data_ptr(),
-                                              count.data_ptr(), g.data_ptr(), gx, gy, gstride,
-                                              _stream_handle(None))
-        if st != 0:
-            raise QHError(st, "qh_hull2d_backward")
+        grad = b.backward(g, torch.empty_like(b._inputs[0]))
+        ctx.batch = None
         return grad, None, None
 
 
@@ -499,34 +553,19 @@ def hull_measures_2d(pts: torch.Tensor, cloud_off: torch.Tensor, *, pred: str = 
 class _Measures3D(torch.autograd.Function):
     @staticmethod
     def forward(ctx, pts, cloud_off, pred):
-        (xp, yp, zp), n, stride = _rows(pts, 3)
         b = Hull3DBatch(pts.detach(), None, None, cloud_off, pred=pred)
         b.enqueue()
-        meas = torch.empty(b.ncloud, 2, dtype=torch.float64, device=pts.device)
-        st = _native.lib().qh_measures3d(xp, yp, zp, stride, b.ncloud, b.face_off.data_ptr(),
-                                         b.face_idx.data_ptr(), b.cloud_foff.data_ptr(),
-                                         meas.data_ptr(), _stream_handle(None))
-        if st != 0:
-            raise QHError(st, "qh_measures3d")
+        meas = b.measures()
         b.outputs()  # raises on a failed hull
-        ctx.save_for_backward(pts, b.face_off, b.face_idx, b.cloud_foff)
-        ctx.ncloud = b.ncloud
+        ctx.batch = b
         return meas
 
     @staticmethod
     def backward(ctx, gm):
-        pts, foff, fidx, cfoff = ctx.saved_tensors
-        (xp, yp, zp), n, stride = _rows(pts, 3)
+        b = ctx.batch
         g = gm.detach().to(torch.float64).contiguous()
-        grad = torch.empty_like(pts)
-        (gx, gy, gz), _, gstride = _rows(grad, 3)
-        scratch = torch.empty(3 * max(n, 1), dtype=torch.float64, device=pts.device)
-        st = _native.lib().qh_hull3d_backward(xp, yp, zp, stride, ctx.ncloud, n,
-                                              foff.data_ptr(), fidx.data_ptr(), cfoff.data_ptr(),
-                                              g.data_ptr(), gx, gy, gz, gstride,
-                                              scratch.data_ptr(), _stream_handle(None))
-        if st != 0:
-            raise QHError(st, "qh_hull3d_backward")
+        grad = b.backward(g, torch.empty_like(b._inputs[0]))
+        ctx.batch = None
         return grad, None, None
 
 

@@ -58,6 +58,7 @@ SIGNATURES = [
     ("qh_workspace_bytes_3d_batched", _sz, [_i64, ctypes.c_int32, _POpts]),
     ("qh_hull3d_batched", ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, ctypes.c_int32, _i64, _vp, _vp,
                                          _vp, _vp, _vp, _vp, _vp, _vp, _sz, _POpts, _vp]),
+    ("qh_debug_phases_3d", ctypes.c_int, [_vp, _vp, _vp]),
     ("qh_workspace_bytes_2d_batched", _sz, [_i64, ctypes.c_int32, _POpts]),
     ("qh_hull2d_batched", ctypes.c_int, [_vp, _vp, _i64, _vp, ctypes.c_int32, _i64, _vp, _vp, _vp,
                                          _vp, _vp, _sz, _POpts, _vp]),

@@ -453,7 +453,16 @@ __device__ int block_next_vertex(const Params3 &A, SmemAll3 &sm, int lo, int hi,
 __device__ void init_clouds(const Params3 &A, SmemAll3 &sm, int bid, int nb)
 {
     Hdr3 *H = A.hdr;
-    for (int c = bid; c < A.ncloud; c += nb) {
+    (void)bid;
+    (void)nb;
+    for (;;) {
+        // clouds from a queue: a block that drew a large cloud does not hold
+        // back the small ones
+        __syncthreads();
+        if (threadIdx.x == 0) sm.red.flag = atomicAdd(&H->next_cloud, 1);
+        __syncthreads();
+        const int c = sm.red.flag;
+        if (c >= A.ncloud) break;
         const int lo = cloud_start(A, c), hi = cloud_start(A, c + 1);
         const int base = 4 * c, pseudo = A.fcap + c;
         int st = QH_OK;
@@ -905,7 +914,15 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int n
                     rank = v - sm.a.start[lo];
                 } else {
                     const int4 cn = A.cone[f];
-                    if (idx != cn.z) {
+                    bool skip = idx == cn.z;  // the apex itself
+                    if (FIRST && cn.y == 4) {
+                        // the simplex vertices: facets 0 and 1 of the
+                        // tetrahedron hold all four (exact zero tests else)
+                        const Fac3 &F0 = A.fac[cn.x], &F1 = A.fac[cn.x + 1];
+                        skip = idx == F0.v[0] || idx == F0.v[1] || idx == F0.v[2] ||
+                               idx == F1.v[0] || idx == F1.v[1] || idx == F1.v[2];
+                    }
+                    if (!skip) {
                         for (int c = 0; c < cn.y; c++) {
                             const Fac3 &C = A.fac[cn.x + c];
                             const float *a, *b, *cc;
@@ -1225,6 +1242,13 @@ __global__ void __launch_bounds__(kMaxBlock) qh3d_persistent(Params3 A)
         tprev = t;
     };
 
+    const unsigned long long t_start = tprev;
+    auto setup_mark = [&](int k) {
+        if (!clk) return;
+        const unsigned long long t = globaltimer_ns();
+        H->setup_ns[k] = (long long)(t - tprev);
+        tprev = t;
+    };
     // ---- initial simplex: grid-wide for one cloud, one block per cloud for
     // a batch
     if (A.cloud_off) {
@@ -1255,16 +1279,19 @@ __global__ void __launch_bounds__(kMaxBlock) qh3d_persistent(Params3 A)
             sync();
         }
     }
+    setup_mark(0);
     if (ok()) {
         // ---- first assignment: every input point against the tetrahedron;
         // table 1 / buffer 1 receive the result
         assign3d<MODE, ITEMS, true>(A, 0, sm, bid, nb);
         sync();
+        setup_mark(1);
         table_sum(A, 0, true, sm, bid, nb);
         sync();
         table_write(A, 0, true, sm, bid, nb);
         if (bid == 0 && threadIdx.x == 0) H->n_uncert = 0;
         sync();
+        setup_mark(2);
         scatter3d<true>(A, 0, bid, nb);
         sync();
         certify3d(A, 0, bid, nb);
@@ -1273,6 +1300,7 @@ __global__ void __launch_bounds__(kMaxBlock) qh3d_persistent(Params3 A)
             exact3d<MODE>(A, 0, sm, bid, nb);
             sync();
         }
+        setup_mark(3);
     }
     // ---- iterations: table `cur` describes the live points in buffer `cur`
     int cur = 1;
@@ -1334,6 +1362,7 @@ __global__ void __launch_bounds__(kMaxBlock) qh3d_persistent(Params3 A)
         mark(iter, 8);
         cur ^= 1;
     }
+    if (clk) H->kernel_ns = (long long)(globaltimer_ns() - t_start);
 }
 
 // Kernel entry of the persistent 3D loop for a predicate mode and points per

@@ -59,7 +59,7 @@ struct Hdr3 {
     int nwin, iter, nactive[2];
     int nent[2], L[2];
     int n_uncert;
-    int pad0;
+    int next_cloud;         // queue of the per-cloud setup
     long long seg_total, surv_total;
     unsigned long long fallbacks, exact_argmax;
     // output stage
@@ -71,6 +71,9 @@ struct Hdr3 {
     // segments, winners, then device time of select, rounds, assign, table,
     // scatter + certify, exact (ns)
     long long tl[64][9];
+    // device time of the setup (initial simplex, first assignment, its table,
+    // its scatter + certify + exact) and of the whole persistent kernel (ns)
+    long long setup_ns[4], kernel_ns;
 };
 constexpr int kTimeline3 = 64;
 

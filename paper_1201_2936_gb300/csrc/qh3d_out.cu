@@ -767,6 +767,19 @@ extern "C" qh_status qh_debug_timeline_3d(const void *d_ws, int64_t n, int64_t *
     return QH_OK;
 }
 
+extern "C" qh_status qh_debug_phases_3d(const void *d_ws, int64_t *h_ns, cudaStream_t st)
+{
+    if (!d_ws || !h_ns) return QH_ERR_INVALID_ARG;
+    Hdr3 hh;
+    if (cudaMemcpyAsync(&hh, (const char *)d_ws, sizeof(Hdr3), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return QH_ERR_CUDA;
+    for (int k = 0; k < 4; k++) h_ns[k] = hh.setup_ns[k];
+    h_ns[4] = hh.kernel_ns;
+    return QH_OK;
+}
+
 static bool opts_ok(const qh_opts &o)
 {
     return o.pred_mode == QH_PRED_F32 || o.pred_mode == QH_PRED_F64;
