@@ -1,0 +1,71 @@
+"""The multi-rank hull (paper_1201_2936_gb300.shard) on CPU ranks with gloo,
+world sizes 2 and 3: the hull of the gathered shard hulls equals the oracle's
+hull of the whole cloud (2D order and 3D vertex set), including duplicates
+across shards and a shard with no points."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+import oracle
+from paper_1201_2936_gb300 import shard
+from paper_1201_2936_gb300 import workloads as w
+
+
+def test_shard_ranges_cover_exactly():
+    for n in (0, 1, 5, 100, 101):
+        for world in (1, 2, 3, 7):
+            rs = [shard.shard_range(n, r, world) for r in range(world)]
+            assert rs[0][0] == 0 and rs[-1][1] == n
+            assert all(a[1] == b[0] for a, b in zip(rs, rs[1:]))
+            assert max(h - l for l, h in rs) - min(h - l for l, h in rs) <= 1
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, dim, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        oracle.build()
+        if dim == 2:
+            x, y = w.uniform_disk(20000, 77)
+            # duplicates of a hull vertex in a later shard, and a far point
+            x = np.concatenate([x, x[:50], np.float32([3.0])]).astype(np.float32)
+            y = np.concatenate([y, y[:50], np.float32([0.25])]).astype(np.float32)
+            final, _ = shard.sharded_hull_numpy([x, y], lambda c: oracle.hull2d(c[0], c[1]))
+            want = oracle.hull2d(x, y)
+        else:
+            x, y, z = w.uniform_ball(6000, 78)
+            final, _ = shard.sharded_hull_numpy([x, y, z],
+                                                lambda c: oracle.hull3d(c[0], c[1], c[2])[0])
+            want = oracle.hull3d(x, y, z)[0]
+        q.put((rank, final.tolist(), want.tolist()))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,dim", [(2, 2), (3, 2), (2, 3)])
+def test_sharded_hull_equals_whole_hull(world, dim):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, dim, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=300) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, final, want in res:
+        assert final == want, rank
