@@ -383,8 +383,19 @@ def main():
     ap.add_argument("--scale-3d", type=int, default=1, help="divide the 3D cloud sizes")
     ap.add_argument("--timeline", action="store_true",
                     help="print the per-iteration device timeline of each cloud to stderr")
+    ap.add_argument("--sections", default="",
+                    help="comma-separated subset of 3d,batched,diff,plain,e2e,cpu to run "
+                         "besides the 2D headline (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.sections:
+        keep = set(args.sections.split(","))
+        args.no_3d = "3d" not in keep
+        args.no_batched = "batched" not in keep
+        args.no_diff = "diff" not in keep
+        args.no_plain = "plain" not in keep
+        args.no_e2e = "e2e" not in keep
+        args.no_cpu_baseline = "cpu" not in keep
 
     ws, rank = dist_env()
     if args.impl == "reference":
