@@ -46,10 +46,14 @@ WORKLOAD = ("2D at scale: 3 x 16M float32 points (uniform unit square, uniform u
 NCU_TRAFFIC = {"322f73970cb75161": 1082.6 / 1310.7}
 
 
+KERNEL_2D_SOURCES = ("qh2d.cu", "pred2.cuh", "qh_common.cuh")
+
+
 def kernel_sources_sha() -> str:
+    """Hash of the sources the persistent 2D kernel is built from."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1201_2936_gb300", "csrc")
-    for fn in sorted(os.listdir(d)):
+    for fn in KERNEL_2D_SOURCES:
         with open(os.path.join(d, fn), "rb") as f:
             h.update(fn.encode())
             h.update(f.read())

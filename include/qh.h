@@ -78,7 +78,8 @@ typedef struct qh_opts {
     int64_t max_iters;    /* iteration cap (0 = n + 8 in 2D, 4n + 16 in 3D) */
     int64_t wait_ns;      /* bound of every device-side wait (0 = 2 s) */
     int32_t items;        /* 3D: points per thread of the assign pass, 2, 4 or 8 (0 = 4) */
-    int32_t reserved0;
+    int32_t max_ctas;     /* 2D persistent grid: at most this many CTAs (0 = no cap); lets
+                             several hulls share the GPU on different streams */
 } qh_opts;
 
 /* Result record written by the device (async calls) and copied back by the

@@ -39,7 +39,8 @@ def version() -> str:
 
 
 def make_opts(pred: str = "f32", loop: str = "persistent", blocks_per_sm: int = 0,
-              max_iters: int = 0, wait_ns: int = 0, block: int = 0, items: int = 0) -> QhOpts:
+              max_iters: int = 0, wait_ns: int = 0, block: int = 0, items: int = 0,
+              max_ctas: int = 0) -> QhOpts:
     o = QhOpts()
     _native.lib().qh_default_opts(ctypes.byref(o))
     o.pred_mode = PRED[pred]
@@ -49,6 +50,7 @@ def make_opts(pred: str = "f32", loop: str = "persistent", blocks_per_sm: int = 
     o.wait_ns = wait_ns
     o.block = block
     o.items = items
+    o.max_ctas = max_ctas
     return o
 
 
@@ -237,16 +239,17 @@ _default_ws = {}
 
 def hull2d(x: torch.Tensor, y: Optional[torch.Tensor] = None, *, pred: str = "f32",
            loop: str = "persistent", workspace: Optional[Workspace] = None,
-           out: Optional[torch.Tensor] = None, stream=None,
+           out: Optional[torch.Tensor] = None, stream=None, opts: Optional[QhOpts] = None,
            return_result: bool = False) -> Union[torch.Tensor, Tuple[torch.Tensor, dict]]:
     """Convex hull of 2D float32 points on the GPU.
 
     Returns an int32 CUDA tensor with the hull vertex indices in counter-
     clockwise order from the lexicographically smallest (x, y) vertex.
     Points are a [n, 2] tensor, a [2, n] tensor, or separate x and y.
+    `opts` (make_opts) overrides pred and loop.
     """
     xp, yp, n, stride, dev = _points_2d(x, y)
-    o = make_opts(pred, loop)
+    o = opts if opts is not None else make_opts(pred, loop)
     if workspace is None:
         workspace = _default_ws.setdefault(str(dev), Workspace(dev))
     ws = workspace.get(workspace_bytes_2d(n, o))

@@ -34,6 +34,7 @@
 // iteration, as the paper's implementation does (Section 5 cost analysis).
 
 #include <climits>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -121,6 +122,7 @@ struct Params2 {
     long long max_iters;
     long long wait_ns;
     int cap_seg;
+    int first_tma;  // first pass bulk copies: 0 none, 1 separate x, y arrays, 2 interleaved xy
 };
 
 // ---------------------------------------------------------------- smem
@@ -615,9 +617,504 @@ __device__ void pass2d(const Params2 &A, int par, SmemPass &sm, int bid, int nb)
     if ((threadIdx.x & 31) == 0 && f) atomicAdd(&H->fallbacks, (unsigned long long)f);
 }
 
+// ---------------------------------------------------------------- pipelined pass
+// The passes after the first split run pipelined: while a CTA works on tile
+// j of its run, the bulk-copy engine (TMA, non-tensor form) brings the points
+// of tile j+1 into the other shared-memory stage when that tile lies inside
+// one segment, and per-thread asynchronous copies bring tile j+1's segment
+// records and segment starts; the tile map of the whole run is read once.
+// The serial global round trips that used to open every tile are gone.
+constexpr int kRun = 256;           // tile-map entries of a CTA's run held in shared memory
+constexpr int kStage = kTile + 8;   // points per stage (a tile plus 16-byte alignment slack)
+
+struct SmemPipe {
+    float2 sxy[2][kStage];
+    int sidx[2][kStage];
+    Seg2 sgeo[2][kGeoCache];
+    int vstart_l[2][kTile];
+    unsigned short sb0[kTile], sb1[kTile];
+    int gb0[kTile], gb1[kTile];
+    unsigned long long sk1[kKeySeg][2];
+    unsigned int so2[kKeySeg][2], sem[kKeySeg][2];
+    Top2 carry[2][2];
+    int carry_seg[2];
+    int run_sf[kRun], run_m[kRun];
+    int wt0[kBlock / 32], wt1[kBlock / 32];
+    int shift[2];
+    int smode[2];   // 1 when stage b holds a bulk copy to wait for
+    int scnt[2];    // first pass: tile elements the bulk copy covers
+};
+static_assert(offsetof(SmemPipe, sidx) % 16 == 0 && offsetof(SmemPipe, sgeo) % 16 == 0 &&
+                  (sizeof(int) * kStage) % 16 == 0,
+              "stage and record buffers must be 16-byte aligned");
+
+// One tile of the pipelined pass (iterations after the first split).  The
+// tile's segment records (first kGeoCache) and segment starts are already in
+// shared memory buffer `b`; a single-segment tile's points are in the bulk-copy
+// stage `b` (element r of the tile at stage index r + shift).  Otherwise the
+// same steps as pass_tile.
+template <class P, bool SINGLE, bool FIRST>
+__device__ __forceinline__ void pass_tile_pipe(const Params2 &A, SmemPipe &sm, const Seg2 *seg,
+                                               Acc2 *acc, int sf, int m, int v0, int v1, int b,
+                                               const float2 *ixy, const int *ii, float2 *oxy,
+                                               int *oi, unsigned &fallbacks)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    Geo2 g0;
+    if (SINGLE) g0 = geo_of(sm.sgeo[b][0]);
+    const int shift = sm.shift[b];
+    auto geo = [&](int ls) -> Geo2 {
+        if (SINGLE) return g0;
+        if (ls < kGeoCache) return geo_of(sm.sgeo[b][ls]);
+        return geo_of(seg[sf + ls]);
+    };
+
+    // ---- load, classify, accumulate farthest-point keys
+    float2 pxy[kItems];
+    int pidx[kItems], pk[kItems];
+    const int wbase = v0 + warp * 32 * kItems;
+#pragma unroll
+    for (int k = 0; k < kItems; k++) {
+        int v = wbase + k * 32 + lane;
+        pk[k] = 3;
+        if (v < v1) {
+            int ls = 0;
+            if (!SINGLE) {
+                int lo = 0, hi = m - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (sm.vstart_l[b][mid] <= v) lo = mid;
+                    else hi = mid - 1;
+                }
+                ls = lo;
+            }
+            pk[k] = (ls << 2) | 2;
+            if (FIRST) {
+                // the caller's points: bulk-copied part from the stage, the
+                // rest (a ragged tail, or all when the layout does not allow
+                // bulk copies) from global memory
+                const int r = v - v0;
+                if (r < sm.scnt[b]) {
+                    if (A.first_tma == 1) {
+                        const float *xs = reinterpret_cast<const float *>(sm.sxy[b]);
+                        pxy[k] = make_float2(xs[r], xs[kStage + r]);
+                    } else {
+                        pxy[k] = sm.sxy[b][r];
+                    }
+                } else {
+                    pxy[k].x = __ldg(A.x + (long long)v * A.stride);
+                    pxy[k].y = __ldg(A.y + (long long)v * A.stride);
+                }
+                pidx[k] = v;
+            } else if (SINGLE) {
+                const int r = v - v0 + shift;
+                pxy[k] = sm.sxy[b][r];
+                pidx[k] = sm.sidx[b][r];
+            } else {
+                int ps, vs;
+                if (ls < kGeoCache) {
+                    ps = sm.sgeo[b][ls].pstart;
+                    vs = sm.sgeo[b][ls].vstart;
+                } else {
+                    ps = seg[sf + ls].pstart;
+                    vs = seg[sf + ls].vstart;
+                }
+                int pos = ps + (v - vs);
+                pxy[k] = ixy[pos];
+                pidx[k] = ii[pos];
+            }
+        }
+    }
+    int cur = -1;
+    Top2 ta = {0ull, 0u, 0u}, tb = {0ull, 0u, 0u};
+    auto flush = [&](int ls) {
+        if (ls < 0) return;
+        if (ls < kKeySeg) {
+            top2_store(&sm.sk1[ls][0], &sm.so2[ls][0], &sm.sem[ls][0], ta);
+            top2_store(&sm.sk1[ls][1], &sm.so2[ls][1], &sm.sem[ls][1], tb);
+        } else {
+            acc_merge(acc[2 * (sf + ls)], ta);
+            acc_merge(acc[2 * (sf + ls) + 1], tb);
+        }
+    };
+    int w0 = 0, w1 = 0;
+#pragma unroll
+    for (int k = 0; k < kItems; k++) {
+        int c = 3;
+        if (pk[k] != 3) {
+            int ls = pk[k] >> 2;
+            const Geo2 g = geo(ls);
+            float x = pxy[k].x, y = pxy[k].y;
+            c = 2;
+            if (FIRST) {
+                if (x == g.e0x && y == g.e0y) atomicMin(&A.hdr->a_idx, pidx[k]);
+                if (x == g.qx && y == g.qy) atomicMin(&A.hdr->b_idx, pidx[k]);
+            }
+            if (pidx[k] != g.q_idx) {  // the apex itself joins the hull
+                float d, e;
+                orient_value<P>(g.e0x, g.e0y, g.qx, g.qy, x, y, d, e);
+                if (orient_sign<P>(d, e, g.e0x, g.e0y, g.qx, g.qy, x, y, fallbacks) > 0) {
+                    c = 0;
+                } else {
+                    orient_value<P>(g.qx, g.qy, g.e1x, g.e1y, x, y, d, e);
+                    if (orient_sign<P>(d, e, g.qx, g.qy, g.e1x, g.e1y, x, y, fallbacks) > 0) c = 1;
+                }
+                if (c < 2) {
+                    if (!SINGLE && ls != cur) {
+                        flush(cur);
+                        ta = {0ull, 0u, 0u};
+                        tb = {0ull, 0u, 0u};
+                    }
+                    cur = ls;
+                    // the distance to the child edge is the classification value
+                    unsigned long long key = dist_key(d, pidx[k]);
+                    if (c == 0) top2_add(ta, key, __float_as_uint(e));
+                    else top2_add(tb, key, __float_as_uint(e));
+                }
+            }
+            pk[k] = (ls << 2) | c;
+        }
+        w0 += __popc(__ballot_sync(0xffffffffu, c == 0));
+        w1 += __popc(__ballot_sync(0xffffffffu, c == 1));
+    }
+    if (lane == 0) {
+        sm.wt0[warp] = w0;
+        sm.wt1[warp] = w1;
+    }
+    // warp-aggregated key flush when the warp ends in one segment
+    {
+        int lmax = SINGLE ? 0 : (int)__reduce_max_sync(0xffffffffu, (unsigned)(cur + 1)) - 1;
+        bool same = SINGLE || __all_sync(0xffffffffu, cur == lmax || cur == -1);
+        if (same && lmax >= 0) {
+            top2_warp(ta);
+            top2_warp(tb);
+            if (lane == 0) flush(lmax);
+        } else {
+            flush(cur);
+        }
+    }
+    __syncthreads();
+    int base0 = 0, base1 = 0, tot0 = 0, tot1 = 0;
+#pragma unroll
+    for (int w = 0; w < kBlock / 32; w++) {
+        int a = sm.wt0[w], b = sm.wt1[w];
+        base0 += (w < warp) ? a : 0;
+        base1 += (w < warp) ? b : 0;
+        tot0 += a;
+        tot1 += b;
+    }
+    if (!SINGLE) {
+        // tile-local prefix at each segment start
+        int r0 = base0, r1 = base1;
+#pragma unroll
+        for (int k = 0; k < kItems; k++) {
+            int c = pk[k] & 3;
+            unsigned b0 = __ballot_sync(0xffffffffu, c == 0);
+            unsigned b1 = __ballot_sync(0xffffffffu, c == 1);
+            int ls = pk[k] >> 2;
+            int v = wbase + k * 32 + lane;
+            if (c != 3 && ls > 0 && sm.vstart_l[b][ls] == v) {
+                sm.sb0[ls] = (unsigned short)(r0 + __popc(b0 & lt));
+                sm.sb1[ls] = (unsigned short)(r1 + __popc(b1 & lt));
+            }
+            r0 += __popc(b0);
+            r1 += __popc(b1);
+        }
+        if (threadIdx.x == 0) {
+            sm.sb0[0] = 0;
+            sm.sb1[0] = 0;
+        }
+        __syncthreads();
+    }
+    // ---- global bases: one atomic per (tile, segment, child)
+    for (int i = threadIdx.x; i < 2 * m; i += blockDim.x) {
+        int ls = i >> 1, c = i & 1;
+        int cnt;
+        if (SINGLE) cnt = c ? tot1 : tot0;
+        else if (c == 0) cnt = ((ls + 1 < m) ? sm.sb0[ls + 1] : tot0) - sm.sb0[ls];
+        else cnt = ((ls + 1 < m) ? sm.sb1[ls + 1] : tot1) - sm.sb1[ls];
+        int g = cnt ? (int)atomicAdd(&acc[2 * (sf + ls) + c].cnt, (unsigned)cnt) : 0;
+        if (c == 0) sm.gb0[ls] = g;
+        else sm.gb1[ls] = g;
+    }
+    __syncthreads();
+    // ---- scatter survivors
+    {
+        int r0 = base0, r1 = base1;
+#pragma unroll
+        for (int k = 0; k < kItems; k++) {
+            int c = pk[k] & 3;
+            unsigned b0 = __ballot_sync(0xffffffffu, c == 0);
+            unsigned b1 = __ballot_sync(0xffffffffu, c == 1);
+            int pre0 = r0 + __popc(b0 & lt), pre1 = r1 + __popc(b1 & lt);
+            r0 += __popc(b0);
+            r1 += __popc(b1);
+            if (c > 1) continue;
+            int ls = pk[k] >> 2;
+            int dst;
+            if (SINGLE) {
+                if (c == 0) dst = g0.pstart + sm.gb0[0] + pre0;
+                else dst = g0.pstart + g0.len - 1 - (sm.gb1[0] + pre1);
+            } else {
+                int ps, ln;
+                if (ls < kGeoCache) {
+                    ps = sm.sgeo[b][ls].pstart;
+                    ln = sm.sgeo[b][ls].len;
+                } else {
+                    ps = seg[sf + ls].pstart;
+                    ln = seg[sf + ls].len;
+                }
+                if (c == 0) dst = ps + sm.gb0[ls] + (pre0 - sm.sb0[ls]);
+                else dst = ps + ln - 1 - (sm.gb1[ls] + (pre1 - sm.sb1[ls]));
+            }
+            oxy[dst] = pxy[k];
+            oi[dst] = pidx[k];
+        }
+    }
+}
+
+
+// Farthest-point slots of tile j: segments that end in the tile go to the
+// global accumulators, the last one is carried (in shared memory) into the
+// next tile of the run; then the slots are zeroed for the next tile (each
+// thread touches only its own slots, so no barrier separates the two).
+__device__ __forceinline__ void merge_slots_pipe(SmemPipe &sm, Acc2 *acc, int j, int sf, int m,
+                                                 int mn)
+{
+    const int ob = j & 1;  // carry of the previous tile; the new one goes to ob ^ 1
+    const int mk = min(m, kKeySeg), mkn = min(mn, kKeySeg);
+    for (int i = threadIdx.x; i < 2 * max(mk, mkn); i += blockDim.x) {
+        const int ls = i >> 1, c = i & 1;
+        if (i < 2 * mk) {
+            Top2 t = {sm.sk1[ls][c], sm.so2[ls][c], sm.sem[ls][c]};
+            if (ls == 0) {
+                const int cs = sm.carry_seg[ob];
+                if (cs == sf) top2_join(t, sm.carry[ob][c]);
+                else if (cs >= 0) acc_merge(acc[2 * cs + c], sm.carry[ob][c]);
+            }
+            if (ls == m - 1) sm.carry[ob ^ 1][c] = t;
+            else acc_merge(acc[2 * (sf + ls) + c], t);
+        }
+        if (i < 2 * mkn) {
+            sm.sk1[ls][c] = 0ull;
+            sm.so2[ls][c] = 0u;
+            sm.sem[ls][c] = 0u;
+        }
+    }
+    if (threadIdx.x == 0) sm.carry_seg[ob ^ 1] = (m - 1 < kKeySeg) ? sf + m - 1 : -1;
+}
+
+template <class P, bool FIRST>
+__device__ void pass2d_pipe(const Params2 &A, int par, SmemPipe &sm, unsigned long long *mbar,
+                            unsigned &ph, int bid, int nb)
+{
+    Hdr2 *H = A.hdr;
+    const int L = FIRST ? A.n : vload_i(&H->L[par]);
+    const Seg2 *seg = A.seg[par];
+    Acc2 *acc = A.acc[par];
+    const float2 *ixy = A.bxy[par ^ 1];
+    const int *ii = A.bi[par ^ 1];
+    float2 *oxy = A.bxy[par];
+    int *oi = A.bi[par];
+    unsigned fallbacks = 0;
+    const int ntiles = (L + kTile - 1) / kTile;
+    const int per = ntiles / nb, rem = ntiles % nb;
+    const int t_begin = bid * per + min(bid, rem);
+    const int nt = per + (bid < rem ? 1 : 0);
+    if (FIRST) {
+        // one pseudo segment (edge a -> a, apex b) covers the whole input
+        if (threadIdx.x < 2) {
+            unsigned long long kmn = *(volatile unsigned long long *)&H->lexmin;
+            unsigned long long kmx = *(volatile unsigned long long *)&H->lexmax;
+            Seg2 g = {};
+            g.e0x = g.e1x = unord_f32((uint32_t)(kmn >> 32));
+            g.e0y = g.e1y = unord_f32((uint32_t)kmn);
+            g.qx = unord_f32((uint32_t)(kmx >> 32));
+            g.qy = unord_f32((uint32_t)kmx);
+            g.q_idx = -1;
+            g.pstart = 0;
+            g.len = A.n;
+            g.vstart = 0;
+            sm.sgeo[threadIdx.x][0] = g;
+        }
+    }
+    // tile -> (first segment, number of segments) of this CTA's run: binary
+    // search of the tiles' first and last virtual positions in the segment
+    // starts (staged in shared memory when they fit)
+    const int S = FIRST ? 1 : vload_i(&H->S[par]);
+    const bool vs_smem = S <= kTile;
+    if (!FIRST && vs_smem)
+        for (int i = threadIdx.x; i < S; i += blockDim.x) sm.vstart_l[1][i] = seg[i].vstart;
+    if (threadIdx.x == 0) sm.carry_seg[0] = sm.carry_seg[1] = -1;
+    __syncthreads();
+    auto seg_of = [&](int v, bool staged) {
+        int lo = 0, hi = S - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            const int vs = staged ? sm.vstart_l[1][mid] : seg[mid].vstart;
+            if (vs <= v) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    };
+    // staged: the starts are still in vstart_l[1] (only before the first tile)
+    auto tile_segs = [&](int j, int &sf, int &m, bool staged) {
+        const int v = (t_begin + j) * kTile, vl = min(v + kTile, L) - 1;
+        sf = seg_of(v, staged);
+        m = seg_of(vl, staged) - sf + 1;
+    };
+    if (!FIRST) {
+        for (int j = threadIdx.x; j < min(nt, kRun); j += blockDim.x)
+            tile_segs(j, sm.run_sf[j], sm.run_m[j], vs_smem);
+        __syncthreads();
+    }
+    auto tmap = [&](int j, int &sf, int &m) {
+        if (FIRST) {
+            sf = 0;
+            m = 1;
+        } else if (j < kRun) {
+            sf = sm.run_sf[j];
+            m = sm.run_m[j];
+        } else {
+            tile_segs(j, sf, m, false);  // runs longer than kRun tiles: searched again
+        }
+    };
+    // segment records and starts of tile j into buffer j & 1 (asynchronous)
+    auto meta_copy = [&](int j) {
+        if (FIRST) return;
+        int sf, m;
+        tmap(j, sf, m);
+        const int b = j & 1, mk = min(m, kGeoCache);
+        const int q = threadIdx.x == 0 ? -1 : (int)threadIdx.x + 3;  // 16-byte chunk
+        if (threadIdx.x == 0) {
+            for (int c = 0; c < 4; c++)
+                cp_async16((char *)&sm.sgeo[b][0] + 16 * c, (const char *)&seg[sf] + 16 * c);
+        } else if (q < 4 * mk) {
+            cp_async16((char *)&sm.sgeo[b][q >> 2] + 16 * (q & 3),
+                       (const char *)&seg[sf + (q >> 2)] + 16 * (q & 3));
+        }
+        if (m > 1)
+            for (int i = threadIdx.x; i < m; i += blockDim.x)
+                cp_async4(&sm.vstart_l[b][i], &seg[sf + i].vstart);
+        cp_async_commit();
+    };
+    // thread 0: bulk copy of tile j's points into stage j & 1.  Later passes:
+    // a single-segment tile's range of the point buffers (rounded out to
+    // 16-byte boundaries inside the buffers' slack).  First pass: the
+    // caller's x and y (or interleaved xy) for the whole 16-byte multiples
+    // of the tile; never past the caller's arrays.
+    auto issue_tma = [&](int j, int ps, int vs) {
+        const int v0 = (t_begin + j) * kTile, v1 = min(v0 + kTile, L);
+        const int cnt = v1 - v0, b = j & 1;
+        if (FIRST) {
+            int c = 0;
+            if (A.first_tma == 1) c = cnt & ~3;
+            else if (A.first_tma == 2) c = cnt & ~1;
+            sm.scnt[b] = c;
+            sm.smode[b] = c > 0;
+            if (c == 0) return;
+            fence_proxy_async();
+            if (A.first_tma == 1) {
+                float *xs = reinterpret_cast<float *>(sm.sxy[b]);
+                mbar_expect_tx(&mbar[b], (unsigned)c * 8u);
+                bulk_g2s(xs, A.x + v0, (unsigned)c * 4u, &mbar[b]);
+                bulk_g2s(xs + kStage, A.y + v0, (unsigned)c * 4u, &mbar[b]);
+            } else {
+                mbar_expect_tx(&mbar[b], (unsigned)c * 8u);
+                bulk_g2s(sm.sxy[b], A.x + 2ll * v0, (unsigned)c * 8u, &mbar[b]);
+            }
+            return;
+        }
+        const int pos0 = ps + (v0 - vs);
+        const int a0 = pos0 & ~3, a1 = (pos0 + cnt + 3) & ~3, nel = a1 - a0;
+        sm.shift[b] = pos0 - a0;
+        sm.smode[b] = 1;
+        fence_proxy_async();
+        mbar_expect_tx(&mbar[b], (unsigned)nel * 12u);
+        bulk_g2s(sm.sxy[b], ixy + a0, (unsigned)nel * 8u, &mbar[b]);
+        bulk_g2s(sm.sidx[b], ii + a0, (unsigned)nel * 4u, &mbar[b]);
+    };
+    // thread 0: the stage of tile j (bulk copy when the tile allows it)
+    auto stage_tile = [&](int j, int ps, int vs) {
+        int sf, m;
+        tmap(j, sf, m);
+        if (FIRST || m == 1) issue_tma(j, ps, vs);
+        else sm.smode[j & 1] = 0;
+    };
+    int nps = 0, nvs = 0;  // thread 0: pstart, vstart of the next tile's segment
+    if (nt > 0) {
+        meta_copy(0);
+        int sf0, m0;
+        tmap(0, sf0, m0);
+        if (threadIdx.x == 0) {
+            if (FIRST || m0 != 1) stage_tile(0, 0, 0);
+            else stage_tile(0, seg[sf0].pstart, seg[sf0].vstart);
+            if (!FIRST && nt > 1) {
+                int sf1, m1;
+                tmap(1, sf1, m1);
+                if (m1 == 1) {
+                    nps = seg[sf1].pstart;
+                    nvs = seg[sf1].vstart;
+                }
+            }
+        }
+        for (int i = threadIdx.x; i < 2 * min(m0, kKeySeg); i += blockDim.x) {
+            sm.sk1[i >> 1][i & 1] = 0ull;
+            sm.so2[i >> 1][i & 1] = 0u;
+            sm.sem[i >> 1][i & 1] = 0u;
+        }
+        cp_async_wait_all();
+        __syncthreads();
+    }
+    for (int j = 0; j < nt; j++) {
+        const int t = t_begin + j, b = j & 1;
+        const int v0 = t * kTile, v1 = min(v0 + kTile, L);
+        int sf, m;
+        tmap(j, sf, m);
+        // prefetch tile j+1 (its stage and buffers were released by tile j-1)
+        if (j + 1 < nt) {
+            meta_copy(j + 1);
+            if (threadIdx.x == 0) {
+                stage_tile(j + 1, nps, nvs);
+                if (!FIRST && j + 2 < nt) {
+                    int sf2, m2;
+                    tmap(j + 2, sf2, m2);
+                    if (m2 == 1) {
+                        nps = seg[sf2].pstart;
+                        nvs = seg[sf2].vstart;
+                    }
+                }
+            }
+        }
+        if (sm.smode[b]) {
+            if (!mbar_wait(&mbar[b], (ph >> b) & 1u, A.wait_ns) && threadIdx.x == 0)
+                set_status(H, kStTimeout);
+            ph ^= 1u << b;
+        }
+        if (m == 1)
+            pass_tile_pipe<P, true, FIRST>(A, sm, seg, acc, sf, m, v0, v1, b, ixy, ii, oxy, oi,
+                                           fallbacks);
+        else
+            pass_tile_pipe<P, false, false>(A, sm, seg, acc, sf, m, v0, v1, b, ixy, ii, oxy, oi,
+                                            fallbacks);
+        int sfn = -1, mn = 0;
+        if (j + 1 < nt) tmap(j + 1, sfn, mn);
+        merge_slots_pipe(sm, acc, j, sf, m, mn);
+        cp_async_wait_all();
+        __syncthreads();
+    }
+    if (threadIdx.x < 2 && nt > 0) {
+        const int cb = nt & 1, cs = sm.carry_seg[cb];
+        if (cs >= 0) acc_merge(acc[2 * cs + threadIdx.x], sm.carry[cb][threadIdx.x]);
+    }
+    unsigned f = __reduce_add_sync(0xffffffffu, fallbacks);
+    if ((threadIdx.x & 31) == 0 && f) atomicAdd(&H->fallbacks, (unsigned long long)f);
+}
+
 // ---------------------------------------------------------------- update
 // Build the next segment table from the non-empty children (block 0 only).
-__device__ void update2d(const Params2 &A, int par, bool first, SmemU &sm)
+__device__ void update2d(const Params2 &A, int par, bool first, SmemU &sm, bool tile_map = true)
 {
     Hdr2 *H = A.hdr;
     Seg2 *so = A.seg[par];
@@ -735,7 +1232,8 @@ __device__ void update2d(const Params2 &A, int par, bool first, SmemU &sm)
         }
         return lo;
     };
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+    // (the persistent kernel's passes find their own tiles' segments)
+    for (int t = threadIdx.x; tile_map && t < ntiles; t += blockDim.x) {
         int v = t * kTile;
         int vl = min(v + kTile, L_new) - 1;
         int s0 = seg_of(v);
@@ -929,10 +1427,24 @@ __device__ void output2d(const Params2 &A, SmemOut &sm)
 }
 
 // ---------------------------------------------------------------- persistent kernel
+// Shared memory of the persistent kernel (dynamic): the phases' union and the
+// pipelined pass's buffers alias; the bulk-copy barriers stay apart.
+extern __shared__ __align__(16) unsigned char qh2d_dsm[];
+constexpr size_t kPersistSmem = sizeof(SmemAll) > sizeof(SmemPipe) ? sizeof(SmemAll) : sizeof(SmemPipe);
+
 template <class P>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_persistent(Params2 A)
 {
-    __shared__ SmemAll sm;
+    SmemAll &sm = *reinterpret_cast<SmemAll *>(qh2d_dsm);
+    SmemPipe &sp = *reinterpret_cast<SmemPipe *>(qh2d_dsm);
+    __shared__ unsigned long long mbar[2];
+    unsigned ph = 0;  // completed phases of mbar[0], mbar[1] (bit 0, bit 1)
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
     Hdr2 *H = A.hdr;
     int *fail = &H->status;
     // phase clock (block 0, thread 0): time from one barrier exit to the next
@@ -961,11 +1473,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_persistent(Params2 A)
     if (*(volatile int *)&H->nonfinite) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(H, kStNonfinite);
     } else if (*(volatile int *)&H->status == 0) {
-        pass2d<P, true>(A, 0, sm.pass, blockIdx.x, gridDim.x);
+        pass2d_pipe<P, true>(A, 0, sp, mbar, ph, blockIdx.x, gridDim.x);
         sync_as(0);
         int t = 0;
         while (*(volatile int *)&H->status == 0) {
-            if (blockIdx.x == 0) update2d(A, t & 1, t == 0, sm.u);
+            if (blockIdx.x == 0) update2d(A, t & 1, t == 0, sm.u, false);
             sync_as(1);
             if (*(volatile int *)&H->status) break;
             if (*(volatile int *)&H->n_uncert > 0) {
@@ -980,7 +1492,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_persistent(Params2 A)
             }
             if (blockIdx.x == 0 && threadIdx.x == 0) H->iter = t;
             it = t;
-            pass2d<P, false>(A, t & 1, sm.pass, blockIdx.x, gridDim.x);
+            pass2d_pipe<P, false>(A, t & 1, sp, mbar, ph, blockIdx.x, gridDim.x);
             sync_as(0);
         }
     }
@@ -1046,9 +1558,11 @@ static Layout2 layout2d(int64_t n)
     L.cap_seg = (int)(2 * np / 3 + 8);
     L.hdr = take(sizeof(Hdr2));
     L.res = take(sizeof(qh_result));
+    // point buffers: 64 bytes of slack after each (the bulk copies of a tile
+    // round their range out to 16-byte boundaries)
     for (int b = 0; b < 2; b++) {
-        L.bxy[b] = take(np * 8);
-        L.bi[b] = take(np * 4);
+        L.bxy[b] = take(np * 8 + 64);
+        L.bi[b] = take(np * 4 + 64);
     }
     for (int b = 0; b < 2; b++) L.seg[b] = take((size_t)L.cap_seg * sizeof(Seg2));
     for (int b = 0; b < 2; b++) L.acc[b] = take((size_t)2 * L.cap_seg * sizeof(Acc2));
@@ -1090,6 +1604,10 @@ static Params2 make_params(const float *x, const float *y, int64_t n, int64_t st
     A.next = (int *)(ws + L.next);
     A.max_iters = o.max_iters > 0 ? o.max_iters : n + 8;
     A.cap_seg = L.cap_seg;
+    // the first pass may bulk-copy the caller's points when they are 16-byte
+    // aligned separate arrays or one interleaved xy array
+    if (stride == 1 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)y & 15) == 0) A.first_tma = 1;
+    else if (stride == 2 && y == x + 1 && ((uintptr_t)x & 15) == 0) A.first_tma = 2;
     A.wait_ns = o.wait_ns > 0 ? o.wait_ns : 2000000000ll;
     return A;
 }
@@ -1100,13 +1618,22 @@ static qh_status run2d(const Params2 &A, const qh_opts &o, cudaStream_t st)
     if (cudaMemsetAsync(A.hdr, 0, sizeof(Hdr2), st) != cudaSuccess) return QH_ERR_CUDA;
     int grid = 0;
     if (o.loop_mode == QH_LOOP_PERSISTENT) {
-        grid = persistent_grid((const void *)qh2d_persistent<P>, kBlock, o.blocks_per_sm);
+        const void *fn = (const void *)qh2d_persistent<P>;
+        static std::once_flag attr_once;
+        static cudaError_t attr_err = cudaSuccess;
+        std::call_once(attr_once, [&]() {
+            attr_err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kPersistSmem);
+        });
+        if (attr_err != cudaSuccess) return QH_ERR_CUDA;
+        grid = persistent_grid_smem(fn, kBlock, o.blocks_per_sm, kPersistSmem);
         if (grid <= 0) return QH_ERR_CUDA;
         grid = grid > kMaxGrid ? kMaxGrid : grid;
+        if (o.max_ctas > 0 && grid > o.max_ctas) grid = o.max_ctas;
         Params2 a = A;
         void *args[] = {&a};
-        cudaError_t e = cudaLaunchCooperativeKernel((const void *)qh2d_persistent<P>, dim3(grid),
-                                                    dim3(kBlock), args, 0, st);
+        cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args,
+                                                    kPersistSmem, st);
         return e == cudaSuccess ? QH_OK : QH_ERR_CUDA;
     }
     // host-driven loop: one launch per phase, live counts read back each iteration

@@ -10,11 +10,17 @@ namespace qh {
 
 int persistent_grid(const void *func, int block, int blocks_per_sm)
 {
+    return persistent_grid_smem(func, block, blocks_per_sm, 0);
+}
+
+int persistent_grid_smem(const void *func, int block, int blocks_per_sm, size_t dsmem)
+{
     static std::mutex mu;
-    static std::map<std::tuple<uintptr_t, int, int>, int> cache;  // (func, device, block)
+    // (func, device, block, dynamic shared memory)
+    static std::map<std::tuple<uintptr_t, int, int, size_t>, int> cache;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    const auto key = std::make_tuple((uintptr_t)func, dev, block);
+    const auto key = std::make_tuple((uintptr_t)func, dev, block, dsmem);
     int per_sm = 0, sms = 0;
     {
         std::lock_guard<std::mutex> g(mu);
@@ -25,7 +31,7 @@ int persistent_grid(const void *func, int block, int blocks_per_sm)
         }
     }
     if (sms == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, block, 0) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, block, dsmem) != cudaSuccess)
             return 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return 0;

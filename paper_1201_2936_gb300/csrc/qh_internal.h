@@ -11,5 +11,7 @@ namespace qh {
 // threads: SMs x resident CTAs per SM (capped by blocks_per_sm when > 0).
 // Returns 0 on a CUDA error.
 int persistent_grid(const void *func, int block, int blocks_per_sm);
+// The same for a kernel launched with `dsmem` bytes of dynamic shared memory.
+int persistent_grid_smem(const void *func, int block, int blocks_per_sm, size_t dsmem);
 
 }  // namespace qh

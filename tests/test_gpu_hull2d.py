@@ -145,3 +145,40 @@ def test_repeat_calls_reuse_workspace(qh):
     for _ in range(3):
         X, Y = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
         assert qh.hull2d(X, Y, workspace=ws).cpu().numpy().tolist() == want.tolist()
+
+
+@pytest.mark.parametrize("ctas", [1, 2, 3])
+def test_capped_grid_long_runs(qh, ctas):
+    # few CTAs: each one's run of tiles is longer than the tile map it stages
+    for x, y in (w.uniform_disk(1_000_003, 5), w.circle_jitter(700_001, 6, 1e-4)):
+        want = oracle.hull2d(x, y)
+        X, Y = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+        got = qh.hull2d(X, Y, opts=qh.make_opts("f32", max_ctas=ctas))
+        assert got.cpu().numpy().tolist() == want.tolist(), ctas
+
+
+def test_unaligned_inputs(qh):
+    # coordinates that start off a 16-byte boundary (no bulk copies of the
+    # caller's arrays in the first pass)
+    x, y = w.uniform_disk(200_001, 8)
+    want = oracle.hull2d(x[1:], y[1:])
+    X = torch.from_numpy(x).cuda()[1:]
+    Y = torch.from_numpy(y).cuda()[1:]
+    assert qh.hull2d(X, Y).cpu().numpy().tolist() == want.tolist()
+
+
+@pytest.mark.parametrize("cloud", ["square", "disk", "circle1e-4"])
+def test_full_size_bench_clouds(qh, cloud):
+    # the 2D benchmark workload at full size (16M points per cloud), in the
+    # launch configuration the benchmark times (persistent kernel, FP32 filter)
+    s = w.SEED_BASE + 1
+    if cloud == "square":
+        x, y = w.uniform_square(w.N_LARGE_2D, s)
+    elif cloud == "disk":
+        x, y = w.uniform_disk(w.N_LARGE_2D, s + 10)
+    else:
+        x, y = w.circle_jitter(w.N_LARGE_2D, s + 20, 1e-4)
+    want = oracle.hull2d(x, y)
+    P = torch.from_numpy(np.stack([x, y])).cuda()
+    got = qh.hull2d(P)
+    assert got.cpu().numpy().tolist() == want.tolist()
