@@ -39,11 +39,12 @@ UNIT = "Mpoints/s"
 N_PER_CLOUD = 16 * 1024 * 1024
 WORKLOAD = ("2D at scale: 3 x 16M float32 points (uniform unit square, uniform unit disk, "
             "unit circle with N(0,1e-4) radial jitter), FP32-filtered exact predicates")
-# DRAM bytes (read + write) per algorithmic byte of the persistent kernel from one
-# ncu capture of a smaller case (8M-point circle, profiles/qh2d_persistent_circle8M_full.md),
-# keyed by the sha256 of the kernel sources it was taken on; the bench scales it
-# by its own algorithmic bytes per launch.  Absent for any other source state.
-NCU_TRAFFIC = {"322f73970cb75161": 1082.6 / 1310.7}
+# DRAM bytes (read + write) per algorithmic byte of the persistent 2D kernel
+# from one ncu capture of a smaller case (3 clouds x 8M points,
+# profiles/qh2d_persistent_traffic_3x8M.md), keyed by the hash of the kernel's
+# sources it was taken on; the bench scales it by its own algorithmic bytes
+# per launch.  Absent (traffic null) for any other source state.
+NCU_TRAFFIC = {"f9a9f507f9371c4d": 1592.19 / 2164.09}
 
 
 KERNEL_2D_SOURCES = ("qh2d.cu", "pred2.cuh", "qh_common.cuh")

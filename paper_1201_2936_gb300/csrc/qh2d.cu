@@ -944,7 +944,7 @@ __device__ void pass2d_pipe(const Params2 &A, int par, SmemPipe &sm, unsigned lo
     // starts (staged in shared memory when they fit)
     const int S = FIRST ? 1 : vload_i(&H->S[par]);
     const bool vs_smem = S <= kTile;
-    if (!FIRST && vs_smem)
+    if (!FIRST && vs_smem && nt > 0)
         for (int i = threadIdx.x; i < S; i += blockDim.x) sm.vstart_l[1][i] = seg[i].vstart;
     if (threadIdx.x == 0) sm.carry_seg[0] = sm.carry_seg[1] = -1;
     __syncthreads();
