@@ -514,15 +514,16 @@ __device__ void select3d(const Params3 &A, int par, int bid, int nb)
         const int f0 = ent[e].f;
         const float4 q4 = A.apex[f0];
         const float q[3] = {q4.x, q4.y, q4.z};
-        int *V = A.vpool + (size_t)e * kVCap;
-        int *N = A.npool + (size_t)e * kNCap;
+        // the lists live in thread-local memory during the search (the
+        // membership scans stay in L1) and are stored once at the end
+        int V[kVCap], N[kNCap];
         int nv = 1, nn = 0;
         bool over = false;
         V[0] = f0;
         for (int i = 0; i < nv && !over; i++) {
-            const Fac3 &F = A.fac[V[i]];
+            const int3 nbr = make_int3(A.fac[V[i]].nb[0], A.fac[V[i]].nb[1], A.fac[V[i]].nb[2]);
             for (int k = 0; k < 3 && !over; k++) {
-                const int g = F.nb[k];
+                const int g = k == 0 ? nbr.x : (k == 1 ? nbr.y : nbr.z);
                 bool seen = false;
                 for (int j = 0; j < nv && !seen; j++) seen = V[j] == g;
                 for (int j = 0; j < nn && !seen; j++) seen = N[j] == g;
@@ -540,6 +541,12 @@ __device__ void select3d(const Params3 &A, int par, int bid, int nb)
                     else N[nn++] = g;
                 }
             }
+        }
+        if (!over) {
+            int *Vg = A.vpool + (size_t)e * kVCap;
+            int *Ng = A.npool + (size_t)e * kNCap;
+            for (int j = 0; j < nv; j++) Vg[j] = V[j];
+            for (int j = 0; j < nn; j++) Ng[j] = N[j];
         }
         A.vn[e] = over ? make_int2(-1, -1) : make_int2(nv, nn);
         A.cstate[e] = over ? 2 : 0;
@@ -770,19 +777,47 @@ __device__ void cone3d(const Params3 &A, int par, int iter, int round, int bid, 
     const Ent3 *ent = A.ent[par];
     const int lane = threadIdx.x & 31;
     const int gw = (bid * blockDim.x + threadIdx.x) >> 5, nw = (nb * blockDim.x) >> 5;
-    for (int e = gw; e < ne; e += nw) {
-        if (A.cstate[e] != 0) continue;
-        const int2 c = A.vn[e];
-        const int f0 = ent[e].f, len = ent[e].len;
-        const unsigned long long mine = claim_key(iter, round, f0, len);
-        const int *V = A.vpool + (size_t)e * kVCap;
-        const int *N = A.npool + (size_t)e * kNCap;
-        bool ok = true;
-        for (int j = lane; j < c.x; j += 32) ok &= A.claim[V[j]] == mine;
-        for (int j = lane; j < c.y; j += 32) ok &= A.claim[N[j]] < mine;
-        if (!__all_sync(0xffffffffu, ok)) continue;
-        // the horizon list reuses the candidate's neighbour slice (>= |V| + 2)
-        cone_warp(A, e, f0, len, V, c.x, A.npool + (size_t)e * kNCap, iter, round);
+    // Candidates in groups of G per warp, G ~ candidates / warps (1..32): with
+    // few candidates every candidate gets a warp (its lists checked by all
+    // lanes, its cone built at once); with many, each lane checks one
+    // candidate and the warp then builds the cones of the group's winners.
+    const int G = min(32, max(1, (ne + nw - 1) / nw));
+    for (int base = gw * G; base < ne; base += nw * G) {
+        unsigned wins;
+        if (G == 1) {
+            const int e = base;
+            bool ok = A.cstate[e] == 0;
+            if (ok) {
+                const int2 c = A.vn[e];
+                const unsigned long long mine = claim_key(iter, round, ent[e].f, ent[e].len);
+                const int *V = A.vpool + (size_t)e * kVCap;
+                const int *N = A.npool + (size_t)e * kNCap;
+                for (int j = lane; j < c.x; j += 32) ok &= A.claim[V[j]] == mine;
+                for (int j = lane; j < c.y; j += 32) ok &= A.claim[N[j]] < mine;
+            }
+            wins = __all_sync(0xffffffffu, ok) ? 1u : 0u;
+        } else {
+            const int e = base + lane;
+            bool win = false;
+            if (lane < G && e < ne && A.cstate[e] == 0) {
+                const int2 c = A.vn[e];
+                const unsigned long long mine = claim_key(iter, round, ent[e].f, ent[e].len);
+                const int *V = A.vpool + (size_t)e * kVCap;
+                const int *N = A.npool + (size_t)e * kNCap;
+                win = true;
+                for (int j = 0; j < c.x && win; j++) win = A.claim[V[j]] == mine;
+                for (int j = 0; j < c.y && win; j++) win = A.claim[N[j]] < mine;
+            }
+            wins = __ballot_sync(0xffffffffu, win);
+        }
+        while (wins) {
+            const int l = __ffs(wins) - 1;
+            wins &= wins - 1;
+            const int ew = base + l;
+            // the horizon list reuses the candidate's neighbour slice (>= |V| + 2)
+            cone_warp(A, ew, ent[ew].f, ent[ew].len, A.vpool + (size_t)ew * kVCap,
+                      A.vn[ew].x, A.npool + (size_t)ew * kNCap, iter, round);
+        }
     }
 }
 
