@@ -9,7 +9,7 @@ second over the whole job (Mpoints/s), inputs resident in HBM.
 Also reported: the 3D hull (8M points in the ball, 1M on the sphere) with the
 FP32 filter and with FP64 predicates; the batched 3D hull (4096 clouds in one
 graph-replayed launch); the differentiable hulls (forward and hand-written
-backward, bwd/fwd); the plain GPU path (FP64 predicates,
+backward, bwd/fwd); selection (medians) on the segmented primitives; the plain GPU path (FP64 predicates,
 host-driven loop with a live-count readback per iteration); the end-to-end
 number through the C ABI with host buffers; the HBM roofline of the
 persistent kernel; and the CPU oracle on the host cores.  `--impl reference`
@@ -340,6 +340,40 @@ def bench_diff(args, qh, dev, rank):
     return out
 
 
+def bench_select(args, qh, dev, rank):
+    """Selection on the segmented primitives (Section 6): the median of each
+    of 4096 segments of 4096 float32 values (16.7M values), 3-state
+    flagPermute + compact per round; against the plain definition (sort per
+    segment) on the host for the first 256 segments."""
+    import torch
+    import oracle
+    rng = np.random.default_rng(1207 + 1000 * rank)
+    nseg, L = 4096, 4096
+    v = rng.standard_normal(nseg * L).astype(np.float32)
+    off = np.arange(nseg + 1, dtype=np.int64) * L
+    k = np.full(nseg, L // 2 - 1, np.int64)
+    V, O, K = (torch.from_numpy(a).to(dev) for a in (v, off, k))
+    out, iters = qh.select(V, O, K, return_iters=True)
+    reps = max(3, args.steps // 20)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        qh.select(V, O, K)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) / reps * 1e3
+    ns = 256
+    t0 = time.perf_counter()
+    want = oracle.select(v[: ns * L], off[: ns + 1], k[:ns])
+    cpu_s = time.perf_counter() - t0
+    same = out[:ns].cpu().numpy().tolist() == want.tolist()
+    return {"workload": "median of each of 4096 segments x 4096 float32 values",
+            "ms": round(ms, 3), "Melements_s": round(nseg * L / ms / 1e3, 1), "rounds": iters,
+            "loop": "host (kept count read back each round)",
+            "matches_definition_first_256_segments": same,
+            "cpu_definition_Melements_s": round(ns * L / cpu_s / 1e6, 2),
+            "cpu_sample": "first 256 segments, numpy lexsort per segment, 1 thread"}
+
+
 def run_reference(args, ws, rank):
     # the oracle on the host cores, rank 0 only
     if rank != 0:
@@ -382,6 +416,7 @@ def main():
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
+    ap.add_argument("--no-select", action="store_true")
     ap.add_argument("--batch-clouds", type=int, default=4096)
     ap.add_argument("--plain-clouds", type=int, default=256,
                     help="clouds timed on the per-cloud plain path")
@@ -389,7 +424,7 @@ def main():
     ap.add_argument("--timeline", action="store_true",
                     help="print the per-iteration device timeline of each cloud to stderr")
     ap.add_argument("--sections", default="",
-                    help="comma-separated subset of 3d,batched,diff,plain,e2e,cpu to run "
+                    help="comma-separated subset of 3d,batched,diff,select,plain,e2e,cpu to run "
                          "besides the 2D headline (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -398,6 +433,7 @@ def main():
         args.no_3d = "3d" not in keep
         args.no_batched = "batched" not in keep
         args.no_diff = "diff" not in keep
+        args.no_select = "select" not in keep
         args.no_plain = "plain" not in keep
         args.no_e2e = "e2e" not in keep
         args.no_cpu_baseline = "cpu" not in keep
@@ -559,6 +595,10 @@ def main():
     # ---- differentiable hulls: forward (hull + measures) and backward kernels
     if not args.no_diff:
         line["differentiable"] = bench_diff(args, qh, dev, rank)
+
+    # ---- selection on the segmented primitives
+    if not args.no_select:
+        line["selection"] = bench_select(args, qh, dev, rank)
 
     # ---- end to end through the C ABI with host buffers
     if args.no_e2e:

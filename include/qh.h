@@ -361,6 +361,41 @@ qh_status qh_debug_timeline_2d(const void *d_ws, int64_t n, int64_t *h_rows, int
 qh_status qh_debug_timeline_3d(const void *d_ws, int64_t n, int64_t *h_rows, int32_t max_rows,
                                int32_t *h_nrows, cudaStream_t stream);
 
+/*
+ * The paper's segmented primitives and a second workload built on them.
+ * Arrays are int32 on the device; a segmented array of n elements carries
+ * head flags s[i] != 0 at the first element of every segment (element 0
+ * always starts a segment).  d_ws: qh_segmented_workspace_bytes(n, nseg)
+ * bytes (nseg only matters for qh_select).  All three calls synchronise.
+ *
+ * qh_flag_permute (Section 4.1, Algorithm 2): states d_f[i] in [0, k),
+ *   1 <= k <= 7.  d_p[i] = destination of element i when every segment is
+ *   regrouped by state (stably); d_s_new[0..n) = head flags of the result
+ *   (old heads plus one at every non-empty state group).  States outside
+ *   [0, k) give QH_ERR_INVALID_ARG.
+ * qh_compact (Section 4.2, Algorithm 3): flags d_b[i] in {0, 1}.  d_p[i] =
+ *   number of true flags before i (the destination of the kept elements);
+ *   *h_n_new = kept elements; d_s_new[0..n_new) = head flags of the kept
+ *   array (a segment with nothing kept disappears); d_s_new has n entries.
+ * qh_select (Section 6, k-th element selection: a 3-state flagPermute
+ *   around each segment's pivot, then a compact that keeps the part holding
+ *   the wanted rank): segments are CSR (d_seg_off[nseg+1], int64, every
+ *   segment non-empty), d_k[c] (int64) the wanted rank in segment c
+ *   (0 <= k < length).  d_out_idx[c] = index of the element of rank d_k[c]
+ *   in the order (value, index), values ordered by their bit patterns like
+ *   numbers (-0 before +0; NaNs at the ends).  *h_iters = rounds used.
+ */
+size_t qh_segmented_workspace_bytes(int64_t n, int32_t nseg);
+qh_status qh_flag_permute(const int32_t *d_f, const int32_t *d_s, int64_t n, int32_t k,
+                          int32_t *d_p, int32_t *d_s_new, void *d_ws, size_t ws_bytes,
+                          cudaStream_t stream);
+qh_status qh_compact(const int32_t *d_b, const int32_t *d_s, int64_t n, int32_t *d_p,
+                     int32_t *d_s_new, int64_t *h_n_new, void *d_ws, size_t ws_bytes,
+                     cudaStream_t stream);
+qh_status qh_select(const float *d_v, const int64_t *d_seg_off, int32_t nseg, int64_t n,
+                    const int64_t *d_k, int32_t *d_out_idx, int64_t *h_iters, void *d_ws,
+                    size_t ws_bytes, cudaStream_t stream);
+
 /* Device time of the last 3D call made on d_ws (qh_hull3d or
  * qh_hull3d_batched): h_ns[0..3] = initial simplex, first assignment, its
  * table, its scatter + certification + exact apexes; h_ns[4] = the whole

@@ -143,6 +143,23 @@ def hull3d_batched(x, y, z, off):
     return out
 
 
+def select(v, off, k):
+    """Index of the element of rank k[c] in every segment c: the plain
+    definition (sort each segment by (value, index), take position k[c]),
+    values ordered by their float32 bit patterns like numbers (-0 before +0,
+    NaNs at the ends)."""
+    v = np.ascontiguousarray(np.asarray(v, dtype=np.float32))
+    u = v.view(np.uint32).astype(np.uint64)
+    key = np.where(u & 0x80000000, (~u) & 0xFFFFFFFF, u | 0x80000000)
+    out = np.empty(len(off) - 1, dtype=np.int32)
+    for c in range(len(off) - 1):
+        a, b = int(off[c]), int(off[c + 1])
+        idx = np.arange(a, b)
+        order = np.lexsort((idx, key[a:b]))
+        out[c] = idx[order[int(k[c])]]
+    return out
+
+
 def _pt(p) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(p, dtype=np.float64))
 

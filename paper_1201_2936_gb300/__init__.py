@@ -18,7 +18,7 @@ __all__ = ["QHError", "hull2d", "hull2d_async", "workspace_bytes_2d", "Workspace
            "hull3d_batched", "Hull3DBatch", "workspace_bytes_3d", "workspace_bytes_3d_batched",
            "make_opts", "status_str", "version", "RESULT_BYTES", "result_from_tensor",
            "Hull2DBatch", "hull2d_batched", "workspace_bytes_2d_batched", "hull_measures_2d",
-           "hull_measures_3d"]
+           "hull_measures_3d", "flag_permute", "compact", "select"]
 
 PRED = {"f32": 0, "f64": 1}
 LOOP = {"persistent": 0, "host": 1}
@@ -578,3 +578,73 @@ def hull_measures_3d(pts: torch.Tensor, cloud_off: torch.Tensor, *, pred: str = 
     gradient on the hull vertices only, computed by qh_hull3d_backward)."""
     _check_off(cloud_off)
     return _Measures3D.apply(pts, cloud_off, pred)
+
+
+# ---------------------------------------------------------------------- segmented primitives
+def _i32_cuda(t, name):
+    if t.dtype != torch.int32 or not t.is_cuda or t.dim() != 1 or \
+            (t.numel() > 1 and t.stride(0) != 1):
+        raise ValueError(f"{name} must be a contiguous 1-D CUDA int32 tensor")
+
+
+def _seg_ws(n: int, nseg: int, dev) -> torch.Tensor:
+    nb = int(_native.lib().qh_segmented_workspace_bytes(int(n), int(nseg)))
+    if nb == 0:
+        raise QHError(1, "qh_segmented_workspace_bytes")
+    return _default_ws.setdefault("seg:" + str(dev), Workspace(dev)).get(nb)
+
+
+def flag_permute(f: torch.Tensor, s: torch.Tensor, k: int):
+    """k-state flagPermute (Algorithm 2) on the GPU: (p, s_new) as int32
+    CUDA tensors (qh_flag_permute)."""
+    _i32_cuda(f, "f")
+    _i32_cuda(s, "s")
+    n = f.numel()
+    p = torch.empty(max(n, 1), dtype=torch.int32, device=f.device)
+    s_new = torch.empty(max(n, 1), dtype=torch.int32, device=f.device)
+    ws = _seg_ws(n, 1, f.device)
+    st = _native.lib().qh_flag_permute(f.data_ptr(), s.data_ptr(), n, int(k), p.data_ptr(),
+                                       s_new.data_ptr(), ws.data_ptr(), ws.numel(),
+                                       _stream_handle(None))
+    if st != 0:
+        raise QHError(st, "qh_flag_permute")
+    return p[:n], s_new[:n]
+
+
+def compact(b: torch.Tensor, s: torch.Tensor):
+    """compact (Algorithm 3) on the GPU: (p, s_new, n_new) (qh_compact)."""
+    _i32_cuda(b, "b")
+    _i32_cuda(s, "s")
+    n = b.numel()
+    p = torch.empty(max(n, 1), dtype=torch.int32, device=b.device)
+    s_new = torch.empty(max(n, 1), dtype=torch.int32, device=b.device)
+    nn = ctypes.c_int64(0)
+    ws = _seg_ws(n, 1, b.device)
+    st = _native.lib().qh_compact(b.data_ptr(), s.data_ptr(), n, p.data_ptr(), s_new.data_ptr(),
+                                  ctypes.byref(nn), ws.data_ptr(), ws.numel(),
+                                  _stream_handle(None))
+    if st != 0:
+        raise QHError(st, "qh_compact")
+    return p[:n], s_new[: nn.value], nn.value
+
+
+def select(v: torch.Tensor, seg_off: torch.Tensor, k: torch.Tensor, return_iters: bool = False):
+    """Index of the element of rank k[c] in every segment c of v (qh_select):
+    v float32 CUDA [n], seg_off int64 CUDA [nseg + 1], k int64 CUDA [nseg]."""
+    if v.dtype != torch.float32 or not v.is_cuda or v.dim() != 1 or \
+            (v.numel() > 1 and v.stride(0) != 1):
+        raise ValueError("v must be a contiguous 1-D CUDA float32 tensor")
+    _check_off(seg_off)
+    if k.dtype != torch.int64 or not k.is_cuda or k.numel() != seg_off.numel() - 1:
+        raise ValueError("k must be a CUDA int64 tensor with one rank per segment")
+    k = k.contiguous()
+    nseg = seg_off.numel() - 1
+    out = torch.empty(nseg, dtype=torch.int32, device=v.device)
+    it = ctypes.c_int64(0)
+    ws = _seg_ws(v.numel(), nseg, v.device)
+    st = _native.lib().qh_select(v.data_ptr(), seg_off.data_ptr(), nseg, v.numel(), k.data_ptr(),
+                                 out.data_ptr(), ctypes.byref(it), ws.data_ptr(), ws.numel(),
+                                 _stream_handle(None))
+    if st != 0:
+        raise QHError(st, "qh_select")
+    return (out, it.value) if return_iters else out

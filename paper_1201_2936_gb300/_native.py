@@ -59,6 +59,11 @@ SIGNATURES = [
     ("qh_hull3d_batched", ctypes.c_int, [_vp, _vp, _vp, _i64, _vp, ctypes.c_int32, _i64, _vp, _vp,
                                          _vp, _vp, _vp, _vp, _vp, _vp, _sz, _POpts, _vp]),
     ("qh_debug_phases_3d", ctypes.c_int, [_vp, _vp, _vp]),
+    ("qh_segmented_workspace_bytes", _sz, [_i64, ctypes.c_int32]),
+    ("qh_flag_permute", ctypes.c_int, [_vp, _vp, _i64, ctypes.c_int32, _vp, _vp, _vp, _sz, _vp]),
+    ("qh_compact", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, ctypes.POINTER(_i64), _vp, _sz, _vp]),
+    ("qh_select", ctypes.c_int, [_vp, _vp, ctypes.c_int32, _i64, _vp, _vp, ctypes.POINTER(_i64),
+                                 _vp, _sz, _vp]),
     ("qh_workspace_bytes_2d_batched", _sz, [_i64, ctypes.c_int32, _POpts]),
     ("qh_hull2d_batched", ctypes.c_int, [_vp, _vp, _i64, _vp, ctypes.c_int32, _i64, _vp, _vp, _vp,
                                          _vp, _vp, _sz, _POpts, _vp]),

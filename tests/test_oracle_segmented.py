@@ -10,6 +10,7 @@ import os
 
 import numpy as np
 
+import oracle
 from oracle import segmented as sg
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -109,3 +110,23 @@ def test_compact_random_properties():
             if i == 0 or seg[keep[i - 1]] != seg[src]:
                 want[i] = 1
         assert s_new.tolist() == want.tolist()
+
+
+def test_select_oracle_against_sorting_and_ties():
+    # the selection oracle: for distinct values it is the k-th entry of the
+    # sorted segment; ties go to the lower index; -0.0 sorts before +0.0
+    rng = np.random.default_rng(4)
+    v = rng.permutation(200).astype(np.float32)
+    off = np.array([0, 50, 51, 200])
+    k = np.array([10, 0, 148])
+    got = oracle.select(v, off, k)
+    for c in range(3):
+        seg = v[off[c]:off[c + 1]]
+        assert v[got[c]] == np.sort(seg)[k[c]]
+    t = np.array([3, 1, 3, 1, 3], np.float32)
+    assert oracle.select(t, [0, 5], [0]).tolist() == [1]
+    assert oracle.select(t, [0, 5], [1]).tolist() == [3]
+    assert oracle.select(t, [0, 5], [2]).tolist() == [0]
+    assert oracle.select(t, [0, 5], [4]).tolist() == [4]
+    z = np.array([0.0, -0.0, -1.0], np.float32)
+    assert oracle.select(z, [0, 3], [1]).tolist() == [1]
