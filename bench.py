@@ -9,7 +9,8 @@ second over the whole job (Mpoints/s), inputs resident in HBM.
 Also reported: the 3D hull (8M points in the ball, 1M on the sphere) with the
 FP32 filter and with FP64 predicates; the batched 3D hull (4096 clouds in one
 graph-replayed launch); the differentiable hulls (forward and hand-written
-backward, bwd/fwd); selection (medians) on the segmented primitives; the plain GPU path (FP64 predicates,
+backward, bwd/fwd); selection (medians) on the segmented primitives; the
+CPU/GPU switchover of one 2D hull; the plain GPU path (FP64 predicates,
 host-driven loop with a live-count readback per iteration); the end-to-end
 number through the C ABI with host buffers; the HBM roofline of the
 persistent kernel; and the CPU oracle on the host cores.  `--impl reference`
@@ -44,7 +45,7 @@ WORKLOAD = ("2D at scale: 3 x 16M float32 points (uniform unit square, uniform u
 # profiles/qh2d_persistent_traffic_3x8M.md), keyed by the hash of the kernel's
 # sources it was taken on; the bench scales it by its own algorithmic bytes
 # per launch.  Absent (traffic null) for any other source state.
-NCU_TRAFFIC = {"f9a9f507f9371c4d": 1592.19 / 2164.09}
+NCU_TRAFFIC = {"16d42b7eb15ed134": 1591.59 / 2164.09}
 
 
 KERNEL_2D_SOURCES = ("qh2d.cu", "pred2.cuh", "qh_common.cuh")
@@ -374,6 +375,42 @@ def bench_select(args, qh, dev, rank):
             "cpu_sample": "first 256 segments, numpy lexsort per segment, 1 thread"}
 
 
+def bench_switchover(args, qh, dev):
+    """CPU/GPU switchover (Section 6's open question): wall time of one
+    synchronous 2D hull call through the C ABI (device-resident points)
+    against the oracle on the host, over n; the smallest n from which the GPU
+    call is faster."""
+    import torch
+    import oracle
+    from paper_1201_2936_gb300 import workloads as w
+    rows = []
+    ws = qh.Workspace(dev)
+    cross = None
+    for n in (64, 256, 1024, 4096, 16384, 65536, 262144, 1048576):
+        x, y = w.uniform_disk(n, 1208 + n)
+        P = torch.from_numpy(np.stack([x, y])).to(dev)
+        for _ in range(3):
+            qh.hull2d(P, workspace=ws)
+        reps = 20
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            qh.hull2d(P, workspace=ws)
+        g = (time.perf_counter() - t0) / reps * 1e6
+        reps_c = max(1, min(50, 2_000_000 // n))
+        t0 = time.perf_counter()
+        for _ in range(reps_c):
+            oracle.hull2d(x, y)
+        c = (time.perf_counter() - t0) / reps_c * 1e6
+        rows.append({"n": n, "gpu_us": round(g, 1), "cpu_oracle_us": round(c, 1)})
+        if cross is None and g < c:
+            cross = n
+    return {"workload": "2D uniform disk, one hull per call", "rows": rows,
+            "gpu_faster_from_n": cross,
+            "note": "GPU: synchronous qh_hull2d incl. launch and result readback; "
+                    "CPU: the exact FP64 oracle, one thread"}
+
+
 def run_reference(args, ws, rank):
     # the oracle on the host cores, rank 0 only
     if rank != 0:
@@ -417,6 +454,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--no-select", action="store_true")
+    ap.add_argument("--no-switchover", action="store_true")
     ap.add_argument("--batch-clouds", type=int, default=4096)
     ap.add_argument("--plain-clouds", type=int, default=256,
                     help="clouds timed on the per-cloud plain path")
@@ -424,7 +462,7 @@ def main():
     ap.add_argument("--timeline", action="store_true",
                     help="print the per-iteration device timeline of each cloud to stderr")
     ap.add_argument("--sections", default="",
-                    help="comma-separated subset of 3d,batched,diff,select,plain,e2e,cpu to run "
+                    help="comma-separated subset of 3d,batched,diff,select,switchover,plain,e2e,cpu to run "
                          "besides the 2D headline (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -434,6 +472,7 @@ def main():
         args.no_batched = "batched" not in keep
         args.no_diff = "diff" not in keep
         args.no_select = "select" not in keep
+        args.no_switchover = "switchover" not in keep
         args.no_plain = "plain" not in keep
         args.no_e2e = "e2e" not in keep
         args.no_cpu_baseline = "cpu" not in keep
@@ -599,6 +638,10 @@ def main():
     # ---- selection on the segmented primitives
     if not args.no_select:
         line["selection"] = bench_select(args, qh, dev, rank)
+
+    # ---- CPU/GPU switchover of the 2D hull
+    if rank == 0 and not args.no_switchover:
+        line["switchover"] = bench_switchover(args, qh, dev)
 
     # ---- end to end through the C ABI with host buffers
     if args.no_e2e:

@@ -1630,6 +1630,10 @@ static qh_status run2d(const Params2 &A, const qh_opts &o, cudaStream_t st)
         if (grid <= 0) return QH_ERR_CUDA;
         grid = grid > kMaxGrid ? kMaxGrid : grid;
         if (o.max_ctas > 0 && grid > o.max_ctas) grid = o.max_ctas;
+        // no more CTAs than the first pass has tiles: a small hull's grid
+        // barriers then involve few CTAs
+        const int first_tiles = (int)((A.n + kTile - 1) / kTile);
+        if (grid > first_tiles) grid = first_tiles > 0 ? first_tiles : 1;
         Params2 a = A;
         void *args[] = {&a};
         cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args,
