@@ -48,6 +48,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     flags = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
                     "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+    # tuning knobs (e.g. -DQH2D_SITEMS=4 -DQH2D_MINBLOCKS=3); a change needs force=True
+    flags += os.environ.get("QH_NVCC_EXTRA", "").split()
     if verbose:
         flags += ["-Xptxas", "-v"]
 

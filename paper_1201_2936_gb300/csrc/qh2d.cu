@@ -54,6 +54,9 @@ namespace qh {
 #ifndef QH2D_MINBLOCKS
 #define QH2D_MINBLOCKS 2
 #endif
+#ifndef QH2D_SITEMS
+#define QH2D_SITEMS 8
+#endif
 constexpr int kBlock = QH2D_BLOCK;
 constexpr int kItems = QH2D_ITEMS;
 constexpr int kTile = kBlock * kItems;   // points per tile
@@ -617,300 +620,190 @@ __device__ void pass2d(const Params2 &A, int par, SmemPass &sm, int bid, int nb)
     if ((threadIdx.x & 31) == 0 && f) atomicAdd(&H->fallbacks, (unsigned long long)f);
 }
 
-// ---------------------------------------------------------------- pipelined pass
-// The passes after the first split run pipelined: while a CTA works on tile
-// j of its run, the bulk-copy engine (TMA, non-tensor form) brings the points
-// of tile j+1 into the other shared-memory stage when that tile lies inside
-// one segment, and per-thread asynchronous copies bring tile j+1's segment
-// records and segment starts; the tile map of the whole run is read once.
-// The serial global round trips that used to open every tile are gone.
-constexpr int kRun = 256;           // tile-map entries of a CTA's run held in shared memory
-constexpr int kStage = kTile + 8;   // points per stage (a tile plus 16-byte alignment slack)
+// ---------------------------------------------------------------- streaming pass
+// The persistent kernel's passes run as a warp-specialised pipeline over each
+// CTA's run of tiles.  The CTA's last warp produces: it fills a ring of
+// kRing shared-memory stages with the bulk-copy engine (TMA, non-tensor
+// form), reserves each tile's output range in the segment's children with
+// one global atomic per child, and merges the farthest-point slots of tiles
+// that straddle segments.  The other kCW warps consume: they classify tile j
+// and then scatter tile j-1, whose reserved bases the producer has published
+// meanwhile, so the atomic's round trip overlaps a tile of work.  Producer and
+// consumers hand off through mbarriers only (per stage: full, empty; per tile
+// parity: counted, bases); there is no block-wide barrier inside the pass.
+//
+// A consumer keeps the farthest-point accumulators of its current segment in
+// registers for as long as its run stays in that segment.  A tile that
+// straddles segments is finished inside its classification step, warp by
+// warp: each row of 32 points groups its survivors by (segment, child) with a
+// match and reserves each group's range with one atomic.
+constexpr int kCW = kBlock / 32 - 1;        // consumer warps
+constexpr int kSItems = QH2D_SITEMS;        // points per consumer thread and tile
+constexpr int kSTile = kCW * 32 * kSItems;  // points per streaming tile
+constexpr int kRing = 4;                    // stages
+constexpr int kStage = kSTile + 8;          // points per stage (16-byte alignment slack)
+constexpr int kRun = 256;                   // tile-map entries of a CTA's run in shared memory
+constexpr int kMSlot = 32;                  // segments of a multi-segment tile with key slots
+static_assert(kSTile % 4 == 0, "tile starts must allow 16-byte bulk copies");
 
-struct SmemPipe {
-    float2 sxy[2][kStage];
-    int sidx[2][kStage];
-    Seg2 sgeo[2][kGeoCache];
-    int vstart_l[2][kTile];
-    unsigned short sb0[kTile], sb1[kTile];
-    int gb0[kTile], gb1[kTile];
-    unsigned long long sk1[kKeySeg][2];
-    unsigned int so2[kKeySeg][2], sem[kKeySeg][2];
-    Top2 carry[2][2];
-    int carry_seg[2];
-    int run_sf[kRun], run_m[kRun];
-    int wt0[kBlock / 32], wt1[kBlock / 32];
-    int shift[2];
-    int smode[2];   // 1 when stage b holds a bulk copy to wait for
-    int scnt[2];    // first pass: tile elements the bulk copy covers
+struct SmemStream {
+    float2 sxy[kRing][kStage];
+    int sidx[kRing][kStage];
+    Seg2 sseg[kRing];                      // segment record of a single-segment tile
+    unsigned long long sk1[2][kMSlot][2];  // key slots of a multi-segment tile, by tile parity
+    unsigned so2[2][kMSlot][2], sem[2][kMSlot][2];
+    int run_sf[kRun], run_m[kRun], run_ps[kRun], run_vs[kRun];
+    int tilecnt[2][2];                     // survivors per child of a tile (consumers add)
+    int gb[2][2];                          // the tile's reserved global base per child
+    int shift[kRing], scnt[kRing];
 };
-static_assert(offsetof(SmemPipe, sidx) % 16 == 0 && offsetof(SmemPipe, sgeo) % 16 == 0 &&
-                  (sizeof(int) * kStage) % 16 == 0,
-              "stage and record buffers must be 16-byte aligned");
+static_assert(offsetof(SmemStream, sidx) % 16 == 0 && offsetof(SmemStream, sseg) % 16 == 0 &&
+                  (sizeof(float2) * kStage) % 16 == 0 && (sizeof(int) * kStage) % 16 == 0,
+              "stages and segment records must be 16-byte aligned");
+// the run map's segment starts are staged in the (then idle) stage ring
+constexpr int kStageInts = (int)(sizeof(float2) * kRing * kStage / sizeof(int));
 
-// One tile of the pipelined pass (iterations after the first split).  The
-// tile's segment records (first kGeoCache) and segment starts are already in
-// shared memory buffer `b`; a single-segment tile's points are in the bulk-copy
-// stage `b` (element r of the tile at stage index r + shift).  Otherwise the
-// same steps as pass_tile.
-template <class P, bool SINGLE, bool FIRST>
-__device__ __forceinline__ void pass_tile_pipe(const Params2 &A, SmemPipe &sm, const Seg2 *seg,
-                                               Acc2 *acc, int sf, int m, int v0, int v1, int b,
-                                               const float2 *ixy, const int *ii, float2 *oxy,
-                                               int *oi, unsigned &fallbacks)
+// The pipeline's mbarriers (static shared memory of the persistent kernel,
+// initialised once per launch) and each thread's phase parities.
+struct PipeBars {
+    unsigned long long full[kRing];   // producer: expect_tx arrive (or plain arrive)
+    unsigned long long empty[kRing];  // one arrive per consumer warp after its scatter
+    unsigned long long counted[2];    // one arrive per consumer warp after classifying
+    unsigned long long bases[2];      // producer: bases published
+};
+// parity bits of the next phase to wait for, per thread
+constexpr int kPhFull = 0, kPhBases = 4, kPhCounted = 8, kPhEmpty = 12;
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Classification of one point against a segment (edge e0 -> e1, apex q):
+// 0 = strictly outside e0 -> q, 1 = strictly outside q -> e1, 2 = neither
+// (inside or on the triangle, or the apex itself).  d and e are the filter
+// value and bound of the deciding orientation (the distance key of the child).
+template <class P>
+__device__ __forceinline__ int classify2d(const Geo2 &g, float x, float y, int idx, float &d,
+                                          float &e, unsigned &fallbacks)
+{
+    if (idx == g.q_idx) return 2;
+    orient_value<P>(g.e0x, g.e0y, g.qx, g.qy, x, y, d, e);
+    if (orient_sign<P>(d, e, g.e0x, g.e0y, g.qx, g.qy, x, y, fallbacks) > 0) return 0;
+    orient_value<P>(g.qx, g.qy, g.e1x, g.e1y, x, y, d, e);
+    if (orient_sign<P>(d, e, g.qx, g.qy, g.e1x, g.e1y, x, y, fallbacks) > 0) return 1;
+    return 2;
+}
+
+// One multi-segment tile, by one consumer warp (later passes only): its
+// kSItems rows, classified, reserved per (segment, child) group and
+// scattered.  Keys of the tile's first kMSlot segments go to the slots of
+// parity p (merged by the producer), the others to the accumulators.
+template <class P>
+__device__ __forceinline__ void multi_tile(SmemStream &sm, const Seg2 *seg, Acc2 *acc, int sf,
+                                           int m, int v0, int v1, int p, const float2 *ixy,
+                                           const int *ii, float2 *oxy, int *oi,
+                                           unsigned &fallbacks)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
-    Geo2 g0;
-    if (SINGLE) g0 = geo_of(sm.sgeo[b][0]);
-    const int shift = sm.shift[b];
-    auto geo = [&](int ls) -> Geo2 {
-        if (SINGLE) return g0;
-        if (ls < kGeoCache) return geo_of(sm.sgeo[b][ls]);
-        return geo_of(seg[sf + ls]);
+    int mcur = -1;
+    Top2 ma = {0ull, 0u, 0u}, mb = {0ull, 0u, 0u};
+    auto mflush = [&]() {
+        if (mcur < 0) return;
+        if (mcur < kMSlot) {
+            top2_store(&sm.sk1[p][mcur][0], &sm.so2[p][mcur][0], &sm.sem[p][mcur][0], ma);
+            top2_store(&sm.sk1[p][mcur][1], &sm.so2[p][mcur][1], &sm.sem[p][mcur][1], mb);
+        } else {
+            acc_merge(acc[2 * (sf + mcur)], ma);
+            acc_merge(acc[2 * (sf + mcur) + 1], mb);
+        }
     };
-
-    // ---- load, classify, accumulate farthest-point keys
-    float2 pxy[kItems];
-    int pidx[kItems], pk[kItems];
-    const int wbase = v0 + warp * 32 * kItems;
+    // rows in batches of kMB: classify and reserve every row of the batch,
+    // then scatter (the reservations' round trips overlap)
+    constexpr int kMB = 4;
+    static_assert(kSItems % kMB == 0, "row batches");
+    const int wbase = v0 + warp * 32 * kSItems;
+#pragma unroll 1
+    for (int k0 = 0; k0 < kSItems; k0 += kMB) {
+        float2 pxy[kMB];
+        int pidx[kMB], pk[kMB], pbase[kMB];
+        unsigned pgrp[kMB];
 #pragma unroll
-    for (int k = 0; k < kItems; k++) {
-        int v = wbase + k * 32 + lane;
-        pk[k] = 3;
-        if (v < v1) {
-            int ls = 0;
-            if (!SINGLE) {
+        for (int k = 0; k < kMB; k++) {
+            const int v = wbase + (k0 + k) * 32 + lane;
+            int c = 3, ls = 0;
+            if (v < v1) {
+                // (the segment table is written inside this launch: plain loads)
                 int lo = 0, hi = m - 1;
                 while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if (sm.vstart_l[b][mid] <= v) lo = mid;
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (seg[sf + mid].vstart <= v) lo = mid;
                     else hi = mid - 1;
                 }
                 ls = lo;
-            }
-            pk[k] = (ls << 2) | 2;
-            if (FIRST) {
-                // the caller's points: bulk-copied part from the stage, the
-                // rest (a ragged tail, or all when the layout does not allow
-                // bulk copies) from global memory
-                const int r = v - v0;
-                if (r < sm.scnt[b]) {
-                    if (A.first_tma == 1) {
-                        const float *xs = reinterpret_cast<const float *>(sm.sxy[b]);
-                        pxy[k] = make_float2(xs[r], xs[kStage + r]);
-                    } else {
-                        pxy[k] = sm.sxy[b][r];
-                    }
-                } else {
-                    pxy[k].x = __ldg(A.x + (long long)v * A.stride);
-                    pxy[k].y = __ldg(A.y + (long long)v * A.stride);
-                }
-                pidx[k] = v;
-            } else if (SINGLE) {
-                const int r = v - v0 + shift;
-                pxy[k] = sm.sxy[b][r];
-                pidx[k] = sm.sidx[b][r];
-            } else {
-                int ps, vs;
-                if (ls < kGeoCache) {
-                    ps = sm.sgeo[b][ls].pstart;
-                    vs = sm.sgeo[b][ls].vstart;
-                } else {
-                    ps = seg[sf + ls].pstart;
-                    vs = seg[sf + ls].vstart;
-                }
-                int pos = ps + (v - vs);
+                const Seg2 &G = seg[sf + ls];
+                Geo2 g;
+                g.e0x = G.e0x; g.e0y = G.e0y;
+                g.qx = G.qx;   g.qy = G.qy;
+                g.e1x = G.e1x; g.e1y = G.e1y;
+                g.q_idx = G.q_idx;
+                const int pos = G.pstart + (v - G.vstart);
                 pxy[k] = ixy[pos];
                 pidx[k] = ii[pos];
-            }
-        }
-    }
-    int cur = -1;
-    Top2 ta = {0ull, 0u, 0u}, tb = {0ull, 0u, 0u};
-    auto flush = [&](int ls) {
-        if (ls < 0) return;
-        if (ls < kKeySeg) {
-            top2_store(&sm.sk1[ls][0], &sm.so2[ls][0], &sm.sem[ls][0], ta);
-            top2_store(&sm.sk1[ls][1], &sm.so2[ls][1], &sm.sem[ls][1], tb);
-        } else {
-            acc_merge(acc[2 * (sf + ls)], ta);
-            acc_merge(acc[2 * (sf + ls) + 1], tb);
-        }
-    };
-    int w0 = 0, w1 = 0;
-#pragma unroll
-    for (int k = 0; k < kItems; k++) {
-        int c = 3;
-        if (pk[k] != 3) {
-            int ls = pk[k] >> 2;
-            const Geo2 g = geo(ls);
-            float x = pxy[k].x, y = pxy[k].y;
-            c = 2;
-            if (FIRST) {
-                if (x == g.e0x && y == g.e0y) atomicMin(&A.hdr->a_idx, pidx[k]);
-                if (x == g.qx && y == g.qy) atomicMin(&A.hdr->b_idx, pidx[k]);
-            }
-            if (pidx[k] != g.q_idx) {  // the apex itself joins the hull
-                float d, e;
-                orient_value<P>(g.e0x, g.e0y, g.qx, g.qy, x, y, d, e);
-                if (orient_sign<P>(d, e, g.e0x, g.e0y, g.qx, g.qy, x, y, fallbacks) > 0) {
-                    c = 0;
-                } else {
-                    orient_value<P>(g.qx, g.qy, g.e1x, g.e1y, x, y, d, e);
-                    if (orient_sign<P>(d, e, g.qx, g.qy, g.e1x, g.e1y, x, y, fallbacks) > 0) c = 1;
-                }
+                float d = 0.f, e = 0.f;
+                c = classify2d<P>(g, pxy[k].x, pxy[k].y, pidx[k], d, e, fallbacks);
                 if (c < 2) {
-                    if (!SINGLE && ls != cur) {
-                        flush(cur);
-                        ta = {0ull, 0u, 0u};
-                        tb = {0ull, 0u, 0u};
+                    if (ls != mcur) {
+                        mflush();
+                        mcur = ls;
+                        ma = {0ull, 0u, 0u};
+                        mb = {0ull, 0u, 0u};
                     }
-                    cur = ls;
-                    // the distance to the child edge is the classification value
-                    unsigned long long key = dist_key(d, pidx[k]);
-                    if (c == 0) top2_add(ta, key, __float_as_uint(e));
-                    else top2_add(tb, key, __float_as_uint(e));
+                    const unsigned long long key = dist_key(d, pidx[k]);
+                    if (c == 0) top2_add(ma, key, __float_as_uint(e));
+                    else top2_add(mb, key, __float_as_uint(e));
                 }
             }
             pk[k] = (ls << 2) | c;
+            // survivors of this row grouped by (segment, child); one atomic per group
+            const unsigned gkey = c < 2 ? (unsigned)(ls * 2 + c) : 0x80000000u + (unsigned)lane;
+            const unsigned grp = __match_any_sync(0xffffffffu, gkey);
+            pgrp[k] = grp;
+            pbase[k] = 0;
+            if (c < 2 && lane == __ffs(grp) - 1)
+                pbase[k] = (int)atomicAdd(&acc[2 * (sf + ls) + c].cnt, (unsigned)__popc(grp));
         }
-        w0 += __popc(__ballot_sync(0xffffffffu, c == 0));
-        w1 += __popc(__ballot_sync(0xffffffffu, c == 1));
-    }
-    if (lane == 0) {
-        sm.wt0[warp] = w0;
-        sm.wt1[warp] = w1;
-    }
-    // warp-aggregated key flush when the warp ends in one segment
-    {
-        int lmax = SINGLE ? 0 : (int)__reduce_max_sync(0xffffffffu, (unsigned)(cur + 1)) - 1;
-        bool same = SINGLE || __all_sync(0xffffffffu, cur == lmax || cur == -1);
-        if (same && lmax >= 0) {
-            top2_warp(ta);
-            top2_warp(tb);
-            if (lane == 0) flush(lmax);
-        } else {
-            flush(cur);
-        }
-    }
-    __syncthreads();
-    int base0 = 0, base1 = 0, tot0 = 0, tot1 = 0;
 #pragma unroll
-    for (int w = 0; w < kBlock / 32; w++) {
-        int a = sm.wt0[w], b = sm.wt1[w];
-        base0 += (w < warp) ? a : 0;
-        base1 += (w < warp) ? b : 0;
-        tot0 += a;
-        tot1 += b;
-    }
-    if (!SINGLE) {
-        // tile-local prefix at each segment start
-        int r0 = base0, r1 = base1;
-#pragma unroll
-        for (int k = 0; k < kItems; k++) {
-            int c = pk[k] & 3;
-            unsigned b0 = __ballot_sync(0xffffffffu, c == 0);
-            unsigned b1 = __ballot_sync(0xffffffffu, c == 1);
-            int ls = pk[k] >> 2;
-            int v = wbase + k * 32 + lane;
-            if (c != 3 && ls > 0 && sm.vstart_l[b][ls] == v) {
-                sm.sb0[ls] = (unsigned short)(r0 + __popc(b0 & lt));
-                sm.sb1[ls] = (unsigned short)(r1 + __popc(b1 & lt));
+        for (int k = 0; k < kMB; k++) {
+            const unsigned grp = pgrp[k];
+            const int base = __shfl_sync(0xffffffffu, pbase[k], __ffs(grp) - 1);
+            const int c = pk[k] & 3;
+            if (c < 2) {
+                const Seg2 &G = seg[sf + (pk[k] >> 2)];
+                const int rank = base + __popc(grp & lt);
+                const int dst = c == 0 ? G.pstart + rank : G.pstart + G.len - 1 - rank;
+                oxy[dst] = pxy[k];
+                oi[dst] = pidx[k];
             }
-            r0 += __popc(b0);
-            r1 += __popc(b1);
-        }
-        if (threadIdx.x == 0) {
-            sm.sb0[0] = 0;
-            sm.sb1[0] = 0;
-        }
-        __syncthreads();
-    }
-    // ---- global bases: one atomic per (tile, segment, child)
-    for (int i = threadIdx.x; i < 2 * m; i += blockDim.x) {
-        int ls = i >> 1, c = i & 1;
-        int cnt;
-        if (SINGLE) cnt = c ? tot1 : tot0;
-        else if (c == 0) cnt = ((ls + 1 < m) ? sm.sb0[ls + 1] : tot0) - sm.sb0[ls];
-        else cnt = ((ls + 1 < m) ? sm.sb1[ls + 1] : tot1) - sm.sb1[ls];
-        int g = cnt ? (int)atomicAdd(&acc[2 * (sf + ls) + c].cnt, (unsigned)cnt) : 0;
-        if (c == 0) sm.gb0[ls] = g;
-        else sm.gb1[ls] = g;
-    }
-    __syncthreads();
-    // ---- scatter survivors
-    {
-        int r0 = base0, r1 = base1;
-#pragma unroll
-        for (int k = 0; k < kItems; k++) {
-            int c = pk[k] & 3;
-            unsigned b0 = __ballot_sync(0xffffffffu, c == 0);
-            unsigned b1 = __ballot_sync(0xffffffffu, c == 1);
-            int pre0 = r0 + __popc(b0 & lt), pre1 = r1 + __popc(b1 & lt);
-            r0 += __popc(b0);
-            r1 += __popc(b1);
-            if (c > 1) continue;
-            int ls = pk[k] >> 2;
-            int dst;
-            if (SINGLE) {
-                if (c == 0) dst = g0.pstart + sm.gb0[0] + pre0;
-                else dst = g0.pstart + g0.len - 1 - (sm.gb1[0] + pre1);
-            } else {
-                int ps, ln;
-                if (ls < kGeoCache) {
-                    ps = sm.sgeo[b][ls].pstart;
-                    ln = sm.sgeo[b][ls].len;
-                } else {
-                    ps = seg[sf + ls].pstart;
-                    ln = seg[sf + ls].len;
-                }
-                if (c == 0) dst = ps + sm.gb0[ls] + (pre0 - sm.sb0[ls]);
-                else dst = ps + ln - 1 - (sm.gb1[ls] + (pre1 - sm.sb1[ls]));
-            }
-            oxy[dst] = pxy[k];
-            oi[dst] = pidx[k];
         }
     }
-}
-
-
-// Farthest-point slots of tile j: segments that end in the tile go to the
-// global accumulators, the last one is carried (in shared memory) into the
-// next tile of the run; then the slots are zeroed for the next tile (each
-// thread touches only its own slots, so no barrier separates the two).
-__device__ __forceinline__ void merge_slots_pipe(SmemPipe &sm, Acc2 *acc, int j, int sf, int m,
-                                                 int mn)
-{
-    const int ob = j & 1;  // carry of the previous tile; the new one goes to ob ^ 1
-    const int mk = min(m, kKeySeg), mkn = min(mn, kKeySeg);
-    for (int i = threadIdx.x; i < 2 * max(mk, mkn); i += blockDim.x) {
-        const int ls = i >> 1, c = i & 1;
-        if (i < 2 * mk) {
-            Top2 t = {sm.sk1[ls][c], sm.so2[ls][c], sm.sem[ls][c]};
-            if (ls == 0) {
-                const int cs = sm.carry_seg[ob];
-                if (cs == sf) top2_join(t, sm.carry[ob][c]);
-                else if (cs >= 0) acc_merge(acc[2 * cs + c], sm.carry[ob][c]);
-            }
-            if (ls == m - 1) sm.carry[ob ^ 1][c] = t;
-            else acc_merge(acc[2 * (sf + ls) + c], t);
-        }
-        if (i < 2 * mkn) {
-            sm.sk1[ls][c] = 0ull;
-            sm.so2[ls][c] = 0u;
-            sm.sem[ls][c] = 0u;
-        }
-    }
-    if (threadIdx.x == 0) sm.carry_seg[ob ^ 1] = (m - 1 < kKeySeg) ? sf + m - 1 : -1;
+    mflush();
 }
 
 template <class P, bool FIRST>
-__device__ void pass2d_pipe(const Params2 &A, int par, SmemPipe &sm, unsigned long long *mbar,
-                            unsigned &ph, int bid, int nb)
+__device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBars &bars,
+                              unsigned &ph, int bid, int nb)
 {
     Hdr2 *H = A.hdr;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
     const int L = FIRST ? A.n : vload_i(&H->L[par]);
+    const int S = FIRST ? 1 : vload_i(&H->S[par]);
     const Seg2 *seg = A.seg[par];
     Acc2 *acc = A.acc[par];
     const float2 *ixy = A.bxy[par ^ 1];
@@ -918,57 +811,53 @@ __device__ void pass2d_pipe(const Params2 &A, int par, SmemPipe &sm, unsigned lo
     float2 *oxy = A.bxy[par];
     int *oi = A.bi[par];
     unsigned fallbacks = 0;
-    const int ntiles = (L + kTile - 1) / kTile;
+    const int ntiles = (L + kSTile - 1) / kSTile;
     const int per = ntiles / nb, rem = ntiles % nb;
     const int t_begin = bid * per + min(bid, rem);
     const int nt = per + (bid < rem ? 1 : 0);
-    if (FIRST) {
-        // one pseudo segment (edge a -> a, apex b) covers the whole input
-        if (threadIdx.x < 2) {
-            unsigned long long kmn = *(volatile unsigned long long *)&H->lexmin;
-            unsigned long long kmx = *(volatile unsigned long long *)&H->lexmax;
-            Seg2 g = {};
-            g.e0x = g.e1x = unord_f32((uint32_t)(kmn >> 32));
-            g.e0y = g.e1y = unord_f32((uint32_t)kmn);
-            g.qx = unord_f32((uint32_t)(kmx >> 32));
-            g.qy = unord_f32((uint32_t)kmx);
-            g.q_idx = -1;
-            g.pstart = 0;
-            g.len = A.n;
-            g.vstart = 0;
-            sm.sgeo[threadIdx.x][0] = g;
-        }
-    }
-    // tile -> (first segment, number of segments) of this CTA's run: binary
-    // search of the tiles' first and last virtual positions in the segment
-    // starts (staged in shared memory when they fit)
-    const int S = FIRST ? 1 : vload_i(&H->S[par]);
-    const bool vs_smem = S <= kTile;
-    if (!FIRST && vs_smem && nt > 0)
-        for (int i = threadIdx.x; i < S; i += blockDim.x) sm.vstart_l[1][i] = seg[i].vstart;
-    if (threadIdx.x == 0) sm.carry_seg[0] = sm.carry_seg[1] = -1;
-    __syncthreads();
+
+    // ---- run map: tile -> (first segment, number of segments, the first
+    // segment's physical and virtual start), by binary search of the tile's
+    // first and last virtual positions in the segment starts (staged in the
+    // idle stage ring when they fit)
+    int *svs = reinterpret_cast<int *>(&sm.sxy[0][0]);
+    const bool vs_smem = S <= kStageInts;
     auto seg_of = [&](int v, bool staged) {
         int lo = 0, hi = S - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            const int vs = staged ? sm.vstart_l[1][mid] : seg[mid].vstart;
+            const int vs = staged ? svs[mid] : seg[mid].vstart;
             if (vs <= v) lo = mid;
             else hi = mid - 1;
         }
         return lo;
     };
-    // staged: the starts are still in vstart_l[1] (only before the first tile)
     auto tile_segs = [&](int j, int &sf, int &m, bool staged) {
-        const int v = (t_begin + j) * kTile, vl = min(v + kTile, L) - 1;
+        const int v = (t_begin + j) * kSTile, vl = min(v + kSTile, L) - 1;
         sf = seg_of(v, staged);
         m = seg_of(vl, staged) - sf + 1;
     };
-    if (!FIRST) {
-        for (int j = threadIdx.x; j < min(nt, kRun); j += blockDim.x)
-            tile_segs(j, sm.run_sf[j], sm.run_m[j], vs_smem);
+    if (!FIRST && nt > 0) {
+        if (vs_smem)
+            for (int i = threadIdx.x; i < S; i += blockDim.x) svs[i] = seg[i].vstart;
         __syncthreads();
+        for (int j = threadIdx.x; j < min(nt, kRun); j += blockDim.x) {
+            int sf, m;
+            tile_segs(j, sf, m, vs_smem);
+            sm.run_sf[j] = sf;
+            sm.run_m[j] = m;
+            sm.run_ps[j] = seg[sf].pstart;
+            sm.run_vs[j] = vs_smem ? svs[sf] : seg[sf].vstart;
+        }
     }
+    for (int i = threadIdx.x; i < 2 * 2 * kMSlot; i += blockDim.x) {
+        const int q = i / (2 * kMSlot), s = (i >> 1) % kMSlot, c = i & 1;
+        sm.sk1[q][s][c] = 0ull;
+        sm.so2[q][s][c] = 0u;
+        sm.sem[q][s][c] = 0u;
+    }
+    if (threadIdx.x < 4) sm.tilecnt[threadIdx.x >> 1][threadIdx.x & 1] = 0;
+    __syncthreads();
     auto tmap = [&](int j, int &sf, int &m) {
         if (FIRST) {
             sf = 0;
@@ -980,136 +869,309 @@ __device__ void pass2d_pipe(const Params2 &A, int par, SmemPipe &sm, unsigned lo
             tile_segs(j, sf, m, false);  // runs longer than kRun tiles: searched again
         }
     };
-    // segment records and starts of tile j into buffer j & 1 (asynchronous)
-    auto meta_copy = [&](int j) {
-        if (FIRST) return;
-        int sf, m;
-        tmap(j, sf, m);
-        const int b = j & 1, mk = min(m, kGeoCache);
-        const int q = threadIdx.x == 0 ? -1 : (int)threadIdx.x + 3;  // 16-byte chunk
-        if (threadIdx.x == 0) {
-            for (int c = 0; c < 4; c++)
-                cp_async16((char *)&sm.sgeo[b][0] + 16 * c, (const char *)&seg[sf] + 16 * c);
-        } else if (q < 4 * mk) {
-            cp_async16((char *)&sm.sgeo[b][q >> 2] + 16 * (q & 3),
-                       (const char *)&seg[sf + (q >> 2)] + 16 * (q & 3));
+    // bounded waits: after one has expired the others return at once and no
+    // scatter uses a base that may not have been published
+    bool dead = vload_i(&H->status) != 0;
+    auto wait = [&](unsigned long long *bar, int bit) {
+        if (!dead && !mbar_wait(bar, (ph >> bit) & 1u, A.wait_ns)) {
+            dead = true;
+            set_status(H, kStTimeout);
         }
-        if (m > 1)
-            for (int i = threadIdx.x; i < m; i += blockDim.x)
-                cp_async4(&sm.vstart_l[b][i], &seg[sf + i].vstart);
-        cp_async_commit();
+        ph ^= 1u << bit;
     };
-    // thread 0: bulk copy of tile j's points into stage j & 1.  Later passes:
-    // a single-segment tile's range of the point buffers (rounded out to
-    // 16-byte boundaries inside the buffers' slack).  First pass: the
-    // caller's x and y (or interleaved xy) for the whole 16-byte multiples
-    // of the tile; never past the caller's arrays.
-    auto issue_tma = [&](int j, int ps, int vs) {
-        const int v0 = (t_begin + j) * kTile, v1 = min(v0 + kTile, L);
-        const int cnt = v1 - v0, b = j & 1;
-        if (FIRST) {
-            int c = 0;
-            if (A.first_tma == 1) c = cnt & ~3;
-            else if (A.first_tma == 2) c = cnt & ~1;
-            sm.scnt[b] = c;
-            sm.smode[b] = c > 0;
-            if (c == 0) return;
-            fence_proxy_async();
-            if (A.first_tma == 1) {
-                float *xs = reinterpret_cast<float *>(sm.sxy[b]);
-                mbar_expect_tx(&mbar[b], (unsigned)c * 8u);
-                bulk_g2s(xs, A.x + v0, (unsigned)c * 4u, &mbar[b]);
-                bulk_g2s(xs + kStage, A.y + v0, (unsigned)c * 4u, &mbar[b]);
-            } else {
-                mbar_expect_tx(&mbar[b], (unsigned)c * 8u);
-                bulk_g2s(sm.sxy[b], A.x + 2ll * v0, (unsigned)c * 8u, &mbar[b]);
+
+    if (warp == kCW) {
+        // ======== producer warp (warp-uniform control; lane 0 issues)
+        // the stage of tile j: later passes, single-segment tile: its range of
+        // the point buffers rounded out to 16-byte boundaries (inside the
+        // buffers' slack) and the segment record; first pass: the 16-byte
+        // multiples of the tile in the caller's x and y (or interleaved xy),
+        // never past the caller's arrays.  Other tiles: a plain arrive.
+        auto issue = [&](int j) {
+            const int s = j % kRing;
+            const int v0 = (t_begin + j) * kSTile, v1 = min(v0 + kSTile, L), cnt = v1 - v0;
+            if (FIRST) {
+                int c = 0;
+                if (A.first_tma == 1) c = cnt & ~3;
+                else if (A.first_tma == 2) c = cnt & ~1;
+                sm.scnt[s] = c;
+                if (c == 0) {
+                    mbar_arrive(&bars.full[s]);
+                    return;
+                }
+                fence_proxy_async();
+                mbar_expect_tx(&bars.full[s], (unsigned)c * 8u);
+                if (A.first_tma == 1) {
+                    float *xs = reinterpret_cast<float *>(sm.sxy[s]);
+                    bulk_g2s(xs, A.x + v0, (unsigned)c * 4u, &bars.full[s]);
+                    bulk_g2s(xs + kStage, A.y + v0, (unsigned)c * 4u, &bars.full[s]);
+                } else {
+                    bulk_g2s(sm.sxy[s], A.x + 2ll * v0, (unsigned)c * 8u, &bars.full[s]);
+                }
+                return;
             }
-            return;
+            int sf, m, ps, vs;
+            if (j < kRun) {
+                sf = sm.run_sf[j];
+                m = sm.run_m[j];
+                ps = sm.run_ps[j];
+                vs = sm.run_vs[j];
+            } else {
+                tile_segs(j, sf, m, false);
+                ps = seg[sf].pstart;
+                vs = seg[sf].vstart;
+            }
+            if (m != 1) {
+                mbar_arrive(&bars.full[s]);
+                return;
+            }
+            const int pos0 = ps + (v0 - vs);
+            const int a0 = pos0 & ~3, a1 = (pos0 + cnt + 3) & ~3, nel = a1 - a0;
+            sm.shift[s] = pos0 - a0;
+            fence_proxy_async();
+            mbar_expect_tx(&bars.full[s], (unsigned)nel * 12u + (unsigned)sizeof(Seg2));
+            bulk_g2s(sm.sxy[s], ixy + a0, (unsigned)nel * 8u, &bars.full[s]);
+            bulk_g2s(sm.sidx[s], ii + a0, (unsigned)nel * 4u, &bars.full[s]);
+            bulk_g2s(&sm.sseg[s], seg + sf, (unsigned)sizeof(Seg2), &bars.full[s]);
+        };
+        if (lane == 0) {
+            // the point buffers were written by other CTAs' generic stores
+            // before the grid barrier; order them before the bulk copies
+            fence_proxy_async_global();
+            for (int j = 0; j < min(nt, kRing); j++) issue(j);
         }
-        const int pos0 = ps + (v0 - vs);
-        const int a0 = pos0 & ~3, a1 = (pos0 + cnt + 3) & ~3, nel = a1 - a0;
-        sm.shift[b] = pos0 - a0;
-        sm.smode[b] = 1;
-        fence_proxy_async();
-        mbar_expect_tx(&mbar[b], (unsigned)nel * 12u);
-        bulk_g2s(sm.sxy[b], ixy + a0, (unsigned)nel * 8u, &mbar[b]);
-        bulk_g2s(sm.sidx[b], ii + a0, (unsigned)nel * 4u, &mbar[b]);
-    };
-    // thread 0: the stage of tile j (bulk copy when the tile allows it)
-    auto stage_tile = [&](int j, int ps, int vs) {
-        int sf, m;
-        tmap(j, sf, m);
-        if (FIRST || m == 1) issue_tma(j, ps, vs);
-        else sm.smode[j & 1] = 0;
-    };
-    int nps = 0, nvs = 0;  // thread 0: pstart, vstart of the next tile's segment
-    if (nt > 0) {
-        meta_copy(0);
-        int sf0, m0;
-        tmap(0, sf0, m0);
-        if (threadIdx.x == 0) {
-            if (FIRST || m0 != 1) stage_tile(0, 0, 0);
-            else stage_tile(0, seg[sf0].pstart, seg[sf0].vstart);
-            if (!FIRST && nt > 1) {
-                int sf1, m1;
-                tmap(1, sf1, m1);
-                if (m1 == 1) {
-                    nps = seg[sf1].pstart;
-                    nvs = seg[sf1].vstart;
+        __syncwarp();
+        for (int j = 0; j < nt; j++) {
+            const int p = j & 1;
+            wait(&bars.counted[p], kPhCounted + p);
+            int sf, m;
+            tmap(j, sf, m);
+            unsigned r0 = 0u, r1 = 0u;
+            if (m == 1 && lane == 0) {
+                const int t0 = sm.tilecnt[p][0], t1 = sm.tilecnt[p][1];
+                sm.tilecnt[p][0] = 0;
+                sm.tilecnt[p][1] = 0;
+                r0 = t0 ? atomicAdd(&acc[2 * sf].cnt, (unsigned)t0) : 0u;
+                r1 = t1 ? atomicAdd(&acc[2 * sf + 1].cnt, (unsigned)t1) : 0u;
+            }
+            if (m > 1) {
+                for (int i = lane; i < 2 * min(m, kMSlot); i += 32) {
+                    const int ls = i >> 1, c = i & 1;
+                    const Top2 t = {sm.sk1[p][ls][c], sm.so2[p][ls][c], sm.sem[p][ls][c]};
+                    if (t.k1) acc_merge(acc[2 * (sf + ls) + c], t);
+                    sm.sk1[p][ls][c] = 0ull;
+                    sm.so2[p][ls][c] = 0u;
+                    sm.sem[p][ls][c] = 0u;
                 }
             }
+            if (j >= 1) {
+                // tile j-1 scattered: its stage takes tile j-1+kRing
+                wait(&bars.empty[(j - 1) % kRing], kPhEmpty + (j - 1) % kRing);
+                if (lane == 0 && j - 1 + kRing < nt) issue(j - 1 + kRing);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                sm.gb[p][0] = (int)r0;
+                sm.gb[p][1] = (int)r1;
+                mbar_arrive(&bars.bases[p]);
+            }
+            __syncwarp();
         }
-        for (int i = threadIdx.x; i < 2 * min(m0, kKeySeg); i += blockDim.x) {
-            sm.sk1[i >> 1][i & 1] = 0ull;
-            sm.so2[i >> 1][i & 1] = 0u;
-            sm.sem[i >> 1][i & 1] = 0u;
+        if (nt > 0) wait(&bars.empty[(nt - 1) % kRing], kPhEmpty + (nt - 1) % kRing);
+    } else {
+        // ======== consumer warps
+        // the first split's pseudo segment (edge a -> a, apex b) covers the input
+        Geo2 gfirst = {};
+        if (FIRST) {
+            const unsigned long long kmn = *(volatile unsigned long long *)&H->lexmin;
+            const unsigned long long kmx = *(volatile unsigned long long *)&H->lexmax;
+            gfirst.e0x = gfirst.e1x = unord_f32((uint32_t)(kmn >> 32));
+            gfirst.e0y = gfirst.e1y = unord_f32((uint32_t)kmn);
+            gfirst.qx = unord_f32((uint32_t)(kmx >> 32));
+            gfirst.qy = unord_f32((uint32_t)kmx);
+            gfirst.q_idx = -1;
         }
-        cp_async_wait_all();
-        __syncthreads();
-    }
-    for (int j = 0; j < nt; j++) {
-        const int t = t_begin + j, b = j & 1;
-        const int v0 = t * kTile, v1 = min(v0 + kTile, L);
-        int sf, m;
-        tmap(j, sf, m);
-        // prefetch tile j+1 (its stage and buffers were released by tile j-1)
-        if (j + 1 < nt) {
-            meta_copy(j + 1);
-            if (threadIdx.x == 0) {
-                stage_tile(j + 1, nps, nvs);
-                if (!FIRST && j + 2 < nt) {
-                    int sf2, m2;
-                    tmap(j + 2, sf2, m2);
-                    if (m2 == 1) {
-                        nps = seg[sf2].pstart;
-                        nvs = seg[sf2].vstart;
+        // point r of stage s in the first pass: bulk-copied part, else the
+        // caller's arrays
+        auto first_point = [&](int s, int r, int v) {
+            if (r < sm.scnt[s]) {
+                if (A.first_tma == 1) {
+                    const float *xs = reinterpret_cast<const float *>(sm.sxy[s]);
+                    return make_float2(xs[r], xs[kStage + r]);
+                }
+                return sm.sxy[s][r];
+            }
+            return make_float2(__ldg(A.x + (long long)v * A.stride),
+                               __ldg(A.y + (long long)v * A.stride));
+        };
+        // farthest-point accumulators of segment `cur` (single-segment tiles)
+        int cur = FIRST ? 0 : -1;
+        Top2 ta = {0ull, 0u, 0u}, tb = {0ull, 0u, 0u};
+        auto flush = [&]() {
+            if (cur < 0) return;
+            top2_warp(ta);
+            top2_warp(tb);
+            if (lane == 0) {
+                acc_merge(acc[2 * cur], ta);
+                acc_merge(acc[2 * cur + 1], tb);
+            }
+        };
+        unsigned cls = 0, cls_prev = 0;  // 2-bit classes of this thread's items
+        int off0 = 0, off1 = 0, off0_prev = 0, off1_prev = 0;  // warp's offset in the tile
+        bool single = false, prev_single = false;
+        for (int j = 0; j <= nt; j++) {
+            if (j < nt) {
+                const int s = j % kRing, p = j & 1;
+                const int v0 = (t_begin + j) * kSTile, v1 = min(v0 + kSTile, L);
+                int sf, m;
+                tmap(j, sf, m);
+                single = m == 1;
+                wait(&bars.full[s], kPhFull + s);
+                if (single) {
+                    const Geo2 g = FIRST ? gfirst : geo_of(sm.sseg[s]);
+                    const int shift = FIRST ? 0 : sm.shift[s];
+                    if (!FIRST && sf != cur) {
+                        flush();
+                        cur = sf;
+                        ta = {0ull, 0u, 0u};
+                        tb = {0ull, 0u, 0u};
+                    }
+                    // phase 1, branch-free: filter values and classes of all
+                    // items (independent chains the compiler interleaves)
+                    const int wbase = v0 + warp * 32 * kSItems;
+                    float dsel[kSItems], esel[kSItems];
+                    int pidx[kSItems];
+                    unsigned unc = 0;
+                    cls = 0;
+#pragma unroll
+                    for (int k = 0; k < kSItems; k++) {
+                        const int v = wbase + k * 32 + lane;
+                        const bool ok = v < v1;
+                        const int r = ok ? v - v0 + shift : 0;
+                        float2 pt;
+                        if (FIRST) {
+                            pt = ok ? first_point(s, r, v) : make_float2(g.e0x, g.e0y);
+                            pidx[k] = v;
+                        } else {
+                            pt = sm.sxy[s][r];
+                            pidx[k] = sm.sidx[s][r];
+                        }
+                        float d0, e0, d1, e1;
+                        orient_value<P>(g.e0x, g.e0y, g.qx, g.qy, pt.x, pt.y, d0, e0);
+                        if (FIRST) {
+                            d1 = -d0;
+                            e1 = e0;
+                        } else {
+                            orient_value<P>(g.qx, g.qy, g.e1x, g.e1y, pt.x, pt.y, d1, e1);
+                        }
+                        const bool pos0 = d0 > e0, neg0 = -d0 > e0, pos1 = d1 > e1, neg1 = -d1 > e1;
+                        const bool apex = !FIRST && pidx[k] == g.q_idx;
+                        int c = pos0 ? 0 : (pos1 ? 1 : 2);
+                        c = apex ? 2 : c;
+                        c = ok ? c : 3;
+                        const bool u = ok && !apex && !pos0 && !(neg0 && (pos1 || neg1));
+                        unc |= (unsigned)u << k;
+                        dsel[k] = c == 0 ? d0 : d1;
+                        esel[k] = c == 0 ? e0 : e1;
+                        cls |= (unsigned)c << (2 * k);
+                        if (FIRST && ok) {
+                            if (pt.x == g.e0x && pt.y == g.e0y) atomicMin(&H->a_idx, v);
+                            if (pt.x == g.qx && pt.y == g.qy) atomicMin(&H->b_idx, v);
+                        }
+                    }
+                    // phase 2, rare: a thread with an item the filter cannot
+                    // decide classifies all its items with exact signs
+                    if (unc) {
+                        cls = 0;
+#pragma unroll
+                        for (int k = 0; k < kSItems; k++) {
+                            const int v = wbase + k * 32 + lane;
+                            int c = 3;
+                            if (v < v1) {
+                                const int r = v - v0 + shift;
+                                const float2 pt = FIRST ? first_point(s, r, v) : sm.sxy[s][r];
+                                float d = 0.f, e = 0.f;
+                                c = classify2d<P>(g, pt.x, pt.y, FIRST ? -2 : pidx[k], d, e,
+                                                  fallbacks);
+                                dsel[k] = d;
+                                esel[k] = e;
+                            }
+                            cls |= (unsigned)c << (2 * k);
+                        }
+                    }
+                    // phase 3, branch-free: farthest-point keys and counts
+                    int w0 = 0, w1 = 0;
+#pragma unroll
+                    for (int k = 0; k < kSItems; k++) {
+                        const int c = (int)((cls >> (2 * k)) & 3u);
+                        const unsigned long long key = dist_key(dsel[k], pidx[k]);
+                        const unsigned eb = __float_as_uint(esel[k]);
+                        top2_add(ta, c == 0 ? key : 0ull, c == 0 ? eb : 0u);
+                        top2_add(tb, c == 1 ? key : 0ull, c == 1 ? eb : 0u);
+                        w0 += __popc(__ballot_sync(0xffffffffu, c == 0));
+                        w1 += __popc(__ballot_sync(0xffffffffu, c == 1));
+                    }
+                    if (lane == 0) {
+                        off0 = atomicAdd(&sm.tilecnt[p][0], w0);
+                        off1 = atomicAdd(&sm.tilecnt[p][1], w1);
+                    }
+                    off0 = __shfl_sync(0xffffffffu, off0, 0);
+                    off1 = __shfl_sync(0xffffffffu, off1, 0);
+                } else {
+                    multi_tile<P>(sm, seg, acc, sf, m, v0, v1, p, ixy, ii, oxy, oi, fallbacks);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bars.counted[p]);
+            }
+            if (j >= 1) {
+                // scatter tile j-1 with the bases the producer published
+                const int jp = j - 1, sp = jp % kRing, pp = jp & 1;
+                wait(&bars.bases[pp], kPhBases + pp);
+                if (prev_single && !dead) {
+                    const int pv0 = (t_begin + jp) * kSTile;
+                    const int shift = FIRST ? 0 : sm.shift[sp];
+                    const int ps = FIRST ? 0 : sm.sseg[sp].pstart;
+                    const int ln = FIRST ? A.n : sm.sseg[sp].len;
+                    int base0 = sm.gb[pp][0] + off0_prev, base1 = sm.gb[pp][1] + off1_prev;
+                    const int wbase = pv0 + warp * 32 * kSItems;
+#pragma unroll
+                    for (int k = 0; k < kSItems; k++) {
+                        const int c = (int)((cls_prev >> (2 * k)) & 3u);
+                        const unsigned b0 = __ballot_sync(0xffffffffu, c == 0);
+                        const unsigned b1 = __ballot_sync(0xffffffffu, c == 1);
+                        if (c < 2) {
+                            const int v = wbase + k * 32 + lane;
+                            const int r = v - pv0 + shift;
+                            float2 pt;
+                            int idx;
+                            if (FIRST) {
+                                pt = first_point(sp, r, v);
+                                idx = v;
+                            } else {
+                                pt = sm.sxy[sp][r];
+                                idx = sm.sidx[sp][r];
+                            }
+                            const int dst = c == 0 ? ps + base0 + __popc(b0 & lt)
+                                                   : ps + ln - 1 - (base1 + __popc(b1 & lt));
+                            oxy[dst] = pt;
+                            oi[dst] = idx;
+                        }
+                        base0 += __popc(b0);
+                        base1 += __popc(b1);
                     }
                 }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bars.empty[sp]);
             }
+            prev_single = single;
+            cls_prev = cls;
+            off0_prev = off0;
+            off1_prev = off1;
         }
-        if (sm.smode[b]) {
-            if (!mbar_wait(&mbar[b], (ph >> b) & 1u, A.wait_ns) && threadIdx.x == 0)
-                set_status(H, kStTimeout);
-            ph ^= 1u << b;
-        }
-        if (m == 1)
-            pass_tile_pipe<P, true, FIRST>(A, sm, seg, acc, sf, m, v0, v1, b, ixy, ii, oxy, oi,
-                                           fallbacks);
-        else
-            pass_tile_pipe<P, false, false>(A, sm, seg, acc, sf, m, v0, v1, b, ixy, ii, oxy, oi,
-                                            fallbacks);
-        int sfn = -1, mn = 0;
-        if (j + 1 < nt) tmap(j + 1, sfn, mn);
-        merge_slots_pipe(sm, acc, j, sf, m, mn);
-        cp_async_wait_all();
-        __syncthreads();
+        flush();
     }
-    if (threadIdx.x < 2 && nt > 0) {
-        const int cb = nt & 1, cs = sm.carry_seg[cb];
-        if (cs >= 0) acc_merge(acc[2 * cs + threadIdx.x], sm.carry[cb][threadIdx.x]);
-    }
-    unsigned f = __reduce_add_sync(0xffffffffu, fallbacks);
-    if ((threadIdx.x & 31) == 0 && f) atomicAdd(&H->fallbacks, (unsigned long long)f);
+    const unsigned f = __reduce_add_sync(0xffffffffu, fallbacks);
+    if (lane == 0 && f) atomicAdd(&H->fallbacks, (unsigned long long)f);
 }
 
 // ---------------------------------------------------------------- update
@@ -1430,18 +1492,25 @@ __device__ void output2d(const Params2 &A, SmemOut &sm)
 // Shared memory of the persistent kernel (dynamic): the phases' union and the
 // pipelined pass's buffers alias; the bulk-copy barriers stay apart.
 extern __shared__ __align__(16) unsigned char qh2d_dsm[];
-constexpr size_t kPersistSmem = sizeof(SmemAll) > sizeof(SmemPipe) ? sizeof(SmemAll) : sizeof(SmemPipe);
+constexpr size_t kPersistSmem =
+    sizeof(SmemAll) > sizeof(SmemStream) ? sizeof(SmemAll) : sizeof(SmemStream);
 
 template <class P>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_persistent(Params2 A)
 {
     SmemAll &sm = *reinterpret_cast<SmemAll *>(qh2d_dsm);
-    SmemPipe &sp = *reinterpret_cast<SmemPipe *>(qh2d_dsm);
-    __shared__ unsigned long long mbar[2];
-    unsigned ph = 0;  // completed phases of mbar[0], mbar[1] (bit 0, bit 1)
+    SmemStream &sp = *reinterpret_cast<SmemStream *>(qh2d_dsm);
+    __shared__ PipeBars bars;
+    unsigned ph = 0;  // this thread's parities of the pipeline barriers' next phases
     if (threadIdx.x == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        for (int b = 0; b < kRing; b++) {
+            mbar_init(&bars.full[b], 1);
+            mbar_init(&bars.empty[b], kCW);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&bars.counted[b], kCW);
+            mbar_init(&bars.bases[b], 1);
+        }
         fence_mbar_init();
     }
     __syncthreads();
@@ -1473,7 +1542,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_persistent(Params2 A)
     if (*(volatile int *)&H->nonfinite) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(H, kStNonfinite);
     } else if (*(volatile int *)&H->status == 0) {
-        pass2d_pipe<P, true>(A, 0, sp, mbar, ph, blockIdx.x, gridDim.x);
+        pass2d_stream<P, true>(A, 0, sp, bars, ph, blockIdx.x, gridDim.x);
         sync_as(0);
         int t = 0;
         while (*(volatile int *)&H->status == 0) {
@@ -1492,7 +1561,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_persistent(Params2 A)
             }
             if (blockIdx.x == 0 && threadIdx.x == 0) H->iter = t;
             it = t;
-            pass2d_pipe<P, false>(A, t & 1, sp, mbar, ph, blockIdx.x, gridDim.x);
+            pass2d_stream<P, false>(A, t & 1, sp, bars, ph, blockIdx.x, gridDim.x);
             sync_as(0);
         }
     }
