@@ -66,6 +66,12 @@ constexpr int kOutCap = 4096;            // hull slots ranked in one block's sha
 constexpr int kMaxGrid = 4096;
 constexpr int kMinBlocks = QH2D_MINBLOCKS;  // resident CTAs per SM the register budget targets
 constexpr int kTimeline = 64;            // iterations recorded by the diagnostic timeline
+#ifndef QH2D_TAIL
+#define QH2D_TAIL 4096
+#endif
+// below this many live points the persistent kernel finishes the hull in one
+// CTA (block barriers only, no grid barriers)
+constexpr int kTailPoints = QH2D_TAIL;
 
 struct Seg2 {
     float e0x, e0y, qx, qy, e1x, e1y;
@@ -201,60 +207,126 @@ __device__ void init2d(const Params2 &A)
 
 // ---------------------------------------------------------------- extrema
 // Lexicographic min and max of (x, y) over all points (Algorithm 4 step 3,
-// "min and max ... along the x axis", ties broken by y; the index tie-break
-// happens in the first split).  Also flags non-finite input.
-__device__ void extrema2d(const Params2 &A, SmemAll &sm)
+// "min and max ... along the x axis", ties broken by y), each with the lowest
+// index at which it occurs (the block's best pair is returned to thread 0;
+// the persistent kernel settles the index once the global extremes are
+// known).  Also flags non-finite input.
+struct Ext2 {
+    unsigned long long mn, mx;
+    int mni, mxi;
+};
+
+__device__ Ext2 extrema2d(const Params2 &A, SmemAll &sm)
 {
     unsigned long long mn = ~0ull, mx = 0ull;
+    int mni = INT_MAX, mxi = INT_MAX;
     int bad = 0;
+    // each thread visits its points in increasing index order, so a strict
+    // comparison keeps the lowest index of its extreme key
+    auto visit = [&](float xf, float yf, int i) {
+        const float x = canon0(xf), y = canon0(yf);
+        bad |= !(isfinite(x) && isfinite(y));
+        const unsigned long long k = ((unsigned long long)ord_f32(x) << 32) | ord_f32(y);
+        if (k < mn) {
+            mn = k;
+            mni = i;
+        }
+        if (k > mx) {
+            mx = k;
+            mxi = i;
+        }
+    };
     const long long s = A.stride;
     const long long nthr = (long long)gridDim.x * blockDim.x;
-    constexpr int U = 8;  // loads in flight per thread
-    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < A.n; i0 += U * nthr) {
-        float xs[U], ys[U];
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int U = 4;  // vector loads in flight per array and thread
+    if (A.first_tma == 1) {
+        // separate 16-byte aligned x and y arrays: four points per load
+        const float4 *x4 = reinterpret_cast<const float4 *>(A.x);
+        const float4 *y4 = reinterpret_cast<const float4 *>(A.y);
+        const long long n4 = A.n / 4;
+        for (long long q0 = gtid; q0 < n4; q0 += U * nthr) {
+            float4 xs[U], ys[U];
 #pragma unroll
-        for (int u = 0; u < U; u++) {
-            long long i = i0 + u * nthr;
-            xs[u] = i < A.n ? __ldg(A.x + i * s) : 0.0f;
-            ys[u] = i < A.n ? __ldg(A.y + i * s) : 0.0f;
+            for (int u = 0; u < U; u++) {
+                const long long q = q0 + u * nthr;
+                xs[u] = q < n4 ? __ldg(x4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                ys[u] = q < n4 ? __ldg(y4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const long long q = q0 + u * nthr;
+                if (q >= n4) continue;
+                const int i = (int)(4 * q);
+                visit(xs[u].x, ys[u].x, i);
+                visit(xs[u].y, ys[u].y, i + 1);
+                visit(xs[u].z, ys[u].z, i + 2);
+                visit(xs[u].w, ys[u].w, i + 3);
+            }
         }
+        for (long long i = 4 * n4 + gtid; i < A.n; i += nthr) visit(__ldg(A.x + i), __ldg(A.y + i), (int)i);
+    } else {
+        constexpr int V = 8;
+        for (long long i0 = gtid; i0 < A.n; i0 += V * nthr) {
+            float xs[V], ys[V];
 #pragma unroll
-        for (int u = 0; u < U; u++) {
-            if (i0 + u * nthr >= A.n) continue;
-            float x = canon0(xs[u]), y = canon0(ys[u]);
-            bad |= !(isfinite(x) && isfinite(y));
-            unsigned long long k = ((unsigned long long)ord_f32(x) << 32) | ord_f32(y);
-            mn = k < mn ? k : mn;
-            mx = k > mx ? k : mx;
+            for (int u = 0; u < V; u++) {
+                const long long i = i0 + u * nthr;
+                xs[u] = i < A.n ? __ldg(A.x + i * s) : 0.0f;
+                ys[u] = i < A.n ? __ldg(A.y + i * s) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < V; u++)
+                if (i0 + u * nthr < A.n) visit(xs[u], ys[u], (int)(i0 + u * nthr));
         }
     }
+    // (key, index) pairs: smaller key, then smaller index (max: larger key)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long a = __shfl_xor_sync(0xffffffffu, mn, o);
-        unsigned long long b = __shfl_xor_sync(0xffffffffu, mx, o);
-        mn = a < mn ? a : mn;
-        mx = b > mx ? b : mx;
+        const unsigned long long a = __shfl_xor_sync(0xffffffffu, mn, o);
+        const unsigned long long b = __shfl_xor_sync(0xffffffffu, mx, o);
+        const int ai = __shfl_xor_sync(0xffffffffu, mni, o);
+        const int bi = __shfl_xor_sync(0xffffffffu, mxi, o);
+        if (a < mn || (a == mn && ai < mni)) {
+            mn = a;
+            mni = ai;
+        }
+        if (b > mx || (b == mx && bi < mxi)) {
+            mx = b;
+            mxi = bi;
+        }
     }
     bad = __syncthreads_or(bad);
     unsigned long long *red = (unsigned long long *)sm.u.wsum;
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *redi = sm.u.vs;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
         red[w] = mn;
         red[16 + w] = mx;
+        redi[w] = mni;
+        redi[16 + w] = mxi;
     }
     __syncthreads();
+    Ext2 r = {mn, mx, mni, mxi};
     if (threadIdx.x == 0) {
         for (int i = 1; i < (int)(blockDim.x >> 5); i++) {
-            mn = red[i] < mn ? red[i] : mn;
-            mx = red[16 + i] > mx ? red[16 + i] : mx;
+            if (red[i] < r.mn || (red[i] == r.mn && redi[i] < r.mni)) {
+                r.mn = red[i];
+                r.mni = redi[i];
+            }
+            if (red[16 + i] > r.mx || (red[16 + i] == r.mx && redi[16 + i] < r.mxi)) {
+                r.mx = red[16 + i];
+                r.mxi = redi[16 + i];
+            }
         }
         if (A.n > 0) {
-            atomicMin(&A.hdr->lexmin, mn);
-            atomicMax(&A.hdr->lexmax, mx);
+            atomicMin(&A.hdr->lexmin, r.mn);
+            atomicMax(&A.hdr->lexmax, r.mx);
         }
         if (bad) atomicExch(&A.hdr->nonfinite, 1);
     }
     __syncthreads();
+    return r;
 }
 
 // ---------------------------------------------------------------- the pass
@@ -655,7 +727,7 @@ struct SmemStream {
     int run_sf[kRun], run_m[kRun], run_ps[kRun], run_vs[kRun];
     int tilecnt[2][2];                     // survivors per child of a tile (consumers add)
     int gb[2][2];                          // the tile's reserved global base per child
-    int shift[kRing], scnt[kRing];
+    int shift[kRing];
 };
 static_assert(offsetof(SmemStream, sidx) % 16 == 0 && offsetof(SmemStream, sseg) % 16 == 0 &&
                   (sizeof(float2) * kStage) % 16 == 0 && (sizeof(int) * kStage) % 16 == 0,
@@ -887,6 +959,7 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
         // buffers' slack) and the segment record; first pass: the 16-byte
         // multiples of the tile in the caller's x and y (or interleaved xy),
         // never past the caller's arrays.  Other tiles: a plain arrive.
+        // (warp-collective: every lane calls it; lane 0 issues the copies)
         auto issue = [&](int j) {
             const int s = j % kRing;
             const int v0 = (t_begin + j) * kSTile, v1 = min(v0 + kSTile, L), cnt = v1 - v0;
@@ -894,7 +967,21 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                 int c = 0;
                 if (A.first_tma == 1) c = cnt & ~3;
                 else if (A.first_tma == 2) c = cnt & ~1;
-                sm.scnt[s] = c;
+                // the rest of the tile (a ragged end, or all of it when the
+                // caller's layout allows no bulk copies) by plain loads
+                float *xs = reinterpret_cast<float *>(sm.sxy[s]);
+                for (int r = c + lane; r < cnt; r += 32) {
+                    const long long v = (long long)(v0 + r) * A.stride;
+                    const float x = __ldg(A.x + v), y = __ldg(A.y + v);
+                    if (A.first_tma == 2) {
+                        sm.sxy[s][r] = make_float2(x, y);
+                    } else {
+                        xs[r] = x;
+                        xs[kStage + r] = y;
+                    }
+                }
+                __syncwarp();
+                if (lane != 0) return;
                 if (c == 0) {
                     mbar_arrive(&bars.full[s]);
                     return;
@@ -902,7 +989,6 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                 fence_proxy_async();
                 mbar_expect_tx(&bars.full[s], (unsigned)c * 8u);
                 if (A.first_tma == 1) {
-                    float *xs = reinterpret_cast<float *>(sm.sxy[s]);
                     bulk_g2s(xs, A.x + v0, (unsigned)c * 4u, &bars.full[s]);
                     bulk_g2s(xs + kStage, A.y + v0, (unsigned)c * 4u, &bars.full[s]);
                 } else {
@@ -910,6 +996,7 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                 }
                 return;
             }
+            if (lane != 0) return;
             int sf, m, ps, vs;
             if (j < kRun) {
                 sf = sm.run_sf[j];
@@ -934,12 +1021,10 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
             bulk_g2s(sm.sidx[s], ii + a0, (unsigned)nel * 4u, &bars.full[s]);
             bulk_g2s(&sm.sseg[s], seg + sf, (unsigned)sizeof(Seg2), &bars.full[s]);
         };
-        if (lane == 0) {
-            // the point buffers were written by other CTAs' generic stores
-            // before the grid barrier; order them before the bulk copies
-            fence_proxy_async_global();
-            for (int j = 0; j < min(nt, kRing); j++) issue(j);
-        }
+        // the point buffers were written by other CTAs' generic stores
+        // before the grid barrier; order them before the bulk copies
+        if (lane == 0) fence_proxy_async_global();
+        for (int j = 0; j < min(nt, kRing); j++) issue(j);
         __syncwarp();
         for (int j = 0; j < nt; j++) {
             const int p = j & 1;
@@ -967,7 +1052,7 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
             if (j >= 1) {
                 // tile j-1 scattered: its stage takes tile j-1+kRing
                 wait(&bars.empty[(j - 1) % kRing], kPhEmpty + (j - 1) % kRing);
-                if (lane == 0 && j - 1 + kRing < nt) issue(j - 1 + kRing);
+                if (j - 1 + kRing < nt) issue(j - 1 + kRing);
             }
             __syncwarp();
             if (lane == 0) {
@@ -991,18 +1076,12 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
             gfirst.qy = unord_f32((uint32_t)kmx);
             gfirst.q_idx = -1;
         }
-        // point r of stage s in the first pass: bulk-copied part, else the
-        // caller's arrays
-        auto first_point = [&](int s, int r, int v) {
-            if (r < sm.scnt[s]) {
-                if (A.first_tma == 1) {
-                    const float *xs = reinterpret_cast<const float *>(sm.sxy[s]);
-                    return make_float2(xs[r], xs[kStage + r]);
-                }
-                return sm.sxy[s][r];
-            }
-            return make_float2(__ldg(A.x + (long long)v * A.stride),
-                               __ldg(A.y + (long long)v * A.stride));
+        // point r of stage s in the first pass: interleaved xy, or x and y
+        // as two arrays (the producer fills the stage either way)
+        auto first_point = [&](int s, int r) {
+            if (A.first_tma == 2) return sm.sxy[s][r];
+            const float *xs = reinterpret_cast<const float *>(sm.sxy[s]);
+            return make_float2(xs[r], xs[kStage + r]);
         };
         // farthest-point accumulators of segment `cur` (single-segment tiles)
         int cur = FIRST ? 0 : -1;
@@ -1050,7 +1129,7 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                         const int r = ok ? v - v0 + shift : 0;
                         float2 pt;
                         if (FIRST) {
-                            pt = ok ? first_point(s, r, v) : make_float2(g.e0x, g.e0y);
+                            pt = first_point(s, r);
                             pidx[k] = v;
                         } else {
                             pt = sm.sxy[s][r];
@@ -1074,10 +1153,6 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                         dsel[k] = c == 0 ? d0 : d1;
                         esel[k] = c == 0 ? e0 : e1;
                         cls |= (unsigned)c << (2 * k);
-                        if (FIRST && ok) {
-                            if (pt.x == g.e0x && pt.y == g.e0y) atomicMin(&H->a_idx, v);
-                            if (pt.x == g.qx && pt.y == g.qy) atomicMin(&H->b_idx, v);
-                        }
                     }
                     // phase 2, rare: a thread with an item the filter cannot
                     // decide classifies all its items with exact signs
@@ -1089,7 +1164,7 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                             int c = 3;
                             if (v < v1) {
                                 const int r = v - v0 + shift;
-                                const float2 pt = FIRST ? first_point(s, r, v) : sm.sxy[s][r];
+                                const float2 pt = FIRST ? first_point(s, r) : sm.sxy[s][r];
                                 float d = 0.f, e = 0.f;
                                 c = classify2d<P>(g, pt.x, pt.y, FIRST ? -2 : pidx[k], d, e,
                                                   fallbacks);
@@ -1145,7 +1220,7 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                             float2 pt;
                             int idx;
                             if (FIRST) {
-                                pt = first_point(sp, r, v);
+                                pt = first_point(sp, r);
                                 idx = v;
                             } else {
                                 pt = sm.sxy[sp][r];
@@ -1176,7 +1251,11 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
 
 // ---------------------------------------------------------------- update
 // Build the next segment table from the non-empty children (block 0 only).
-__device__ void update2d(const Params2 &A, int par, bool first, SmemU &sm, bool tile_map = true)
+// The tile -> segment map for the next pass is written when that pass has
+// fewer than map_below live points (the passes of the persistent kernel's
+// grid phase find their tiles' segments themselves).
+__device__ void update2d(const Params2 &A, int par, bool first, SmemU &sm,
+                         int map_below = INT_MAX)
 {
     Hdr2 *H = A.hdr;
     Seg2 *so = A.seg[par];
@@ -1295,7 +1374,7 @@ __device__ void update2d(const Params2 &A, int par, bool first, SmemU &sm, bool 
         return lo;
     };
     // (the persistent kernel's passes find their own tiles' segments)
-    for (int t = threadIdx.x; tile_map && t < ntiles; t += blockDim.x) {
+    for (int t = threadIdx.x; L_new < map_below && t < ntiles; t += blockDim.x) {
         int v = t * kTile;
         int vl = min(v + kTile, L_new) - 1;
         int s0 = seg_of(v);
@@ -1495,6 +1574,48 @@ extern __shared__ __align__(16) unsigned char qh2d_dsm[];
 constexpr size_t kPersistSmem =
     sizeof(SmemAll) > sizeof(SmemStream) ? sizeof(SmemAll) : sizeof(SmemStream);
 
+// The last iterations, once fewer than kTailPoints points are live, in one
+// CTA: the same pass, update and exact-argmax steps with block barriers only,
+// while the other CTAs wait at the kernel's final grid barrier.  t is the
+// iteration of the first pass to run; its tile map is in place.
+template <class P>
+__device__ void tail2d(const Params2 &A, int t, SmemAll &sm)
+{
+    Hdr2 *H = A.hdr;
+    const bool clk = threadIdx.x == 0;
+    for (;;) {
+        const unsigned long long t0 = clk ? globaltimer_ns() : 0;
+        if (threadIdx.x == 0) H->iter = t;
+        pass2d<P, false>(A, t & 1, sm.pass, 0, 1);
+        __syncthreads();
+        const unsigned long long t1 = clk ? globaltimer_ns() : 0;
+        update2d(A, t & 1, false, sm.u, INT_MAX);
+        if (clk) {
+            const unsigned long long t2 = globaltimer_ns();
+            H->phase_ns[0] += t1 - t0;
+            H->phase_ns[1] += t2 - t1;
+            if (t < kTimeline) {
+                H->tl[t][0] = *(volatile int *)&H->L[t & 1];
+                H->tl[t][1] = *(volatile int *)&H->S[t & 1];
+                H->tl[t][2] += (long long)(t1 - t0);
+                H->tl[t][3] += (long long)(t2 - t1);
+            }
+        }
+        __syncthreads();
+        if (*(volatile int *)&H->status) break;
+        if (*(volatile int *)&H->n_uncert > 0) {
+            exact2d<P>(A, t & 1, sm.x, 0, 1);
+            __syncthreads();
+        }
+        if (*(volatile int *)&H->S[(t + 1) & 1] == 0) break;
+        t++;
+        if (t > A.max_iters) {
+            if (threadIdx.x == 0) set_status(H, kStNoConv);
+            break;
+        }
+    }
+}
+
 template <class P>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_persistent(Params2 A)
 {
@@ -1537,16 +1658,23 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_persistent(Params2 A)
     };
     init2d(A);
     sync_as(3);
-    extrema2d(A, sm);
+    const Ext2 ext = extrema2d(A, sm);
     sync_as(3);
+    // the lowest index of each global extreme (read by the first update,
+    // after the first pass's grid barrier)
+    if (threadIdx.x == 0 && A.n > 0) {
+        if (ext.mn == *(volatile unsigned long long *)&H->lexmin) atomicMin(&H->a_idx, ext.mni);
+        if (ext.mx == *(volatile unsigned long long *)&H->lexmax) atomicMin(&H->b_idx, ext.mxi);
+    }
     if (*(volatile int *)&H->nonfinite) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(H, kStNonfinite);
     } else if (*(volatile int *)&H->status == 0) {
         pass2d_stream<P, true>(A, 0, sp, bars, ph, blockIdx.x, gridDim.x);
         sync_as(0);
         int t = 0;
+        bool tail = false;
         while (*(volatile int *)&H->status == 0) {
-            if (blockIdx.x == 0) update2d(A, t & 1, t == 0, sm.u, false);
+            if (blockIdx.x == 0) update2d(A, t & 1, t == 0, sm.u, kTailPoints);
             sync_as(1);
             if (*(volatile int *)&H->status) break;
             if (*(volatile int *)&H->n_uncert > 0) {
@@ -1559,10 +1687,19 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_persistent(Params2 A)
                 if (blockIdx.x == 0 && threadIdx.x == 0) set_status(H, kStNoConv);
                 break;
             }
+            if (*(volatile int *)&H->L[t & 1] < kTailPoints) {
+                tail = true;
+                break;
+            }
             if (blockIdx.x == 0 && threadIdx.x == 0) H->iter = t;
             it = t;
             pass2d_stream<P, false>(A, t & 1, sp, bars, ph, blockIdx.x, gridDim.x);
             sync_as(0);
+        }
+        if (tail && blockIdx.x == 0) {
+            tprev = 0;
+            tail2d<P>(A, t, sm);
+            if (clk) tprev = globaltimer_ns();
         }
     }
     sync_as(3);
