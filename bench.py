@@ -45,7 +45,7 @@ WORKLOAD = ("2D at scale: 3 x 16M float32 points (uniform unit square, uniform u
 # profiles/qh2d_persistent_traffic_3x8M.md), keyed by the hash of the kernel's
 # sources it was taken on; the bench scales it by its own algorithmic bytes
 # per launch.  Absent (traffic null) for any other source state.
-NCU_TRAFFIC = {"16d42b7eb15ed134": 1591.59 / 2164.09}
+NCU_TRAFFIC = {"e503a4faae8fb58d": 1526.92 / 2164.09}
 
 
 KERNEL_2D_SOURCES = ("qh2d.cu", "pred2.cuh", "qh_common.cuh")
@@ -549,13 +549,26 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     res = [qh.result_from_tensor(r) for r in results]
-    if args.timeline:
-        for i, (name, _) in enumerate(data):
-            rows = qh.debug_timeline_2d(wss[i], ncl)
+    # per-pass HBM rate of the last timed launch of each cloud (device clock
+    # between the pass's grid barriers): pass t reads its L_t live records
+    # (the first split: the caller's 8-byte coordinates) and writes its
+    # survivors, the L_{t+1} records of the next pass, 12 bytes each
+    passes = []
+    for i, (name, _) in enumerate(data):
+        rows = qh.debug_timeline_2d(wss[i], ncl)
+        if args.timeline:
             print(f"# timeline {name}: iter L S pass_us update_us", file=sys.stderr)
             for r in rows:
                 print(f"#   {r[0]:3d} {r[1]:10d} {r[2]:7d} {r[3] / 1e3:9.2f} "
                       f"{r[4] / 1e3:8.2f}", file=sys.stderr)
+        for t, r in enumerate(rows):
+            L_t, ns = int(r[1]), int(r[3])
+            if L_t < ncl // 2 or ns <= 0:
+                continue
+            S_t = int(rows[t + 1][1]) if t + 1 < len(rows) else 0
+            b = (8 if t == 0 else 12) * L_t + 12 * S_t
+            passes.append({"cloud": name, "iter": t, "live": L_t, "written": S_t,
+                           "us": round(ns / 1e3, 2), "GBps": round(b / ns, 1)})
     pts_per_step = nl * ncl
     value = ws * pts_per_step * args.steps / (total_ms / 1e3) / 1e6
 
@@ -585,6 +598,12 @@ def main():
                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                 "traffic": traffic, "kernel": "qh2d_persistent<PredF32>",
                 "algo_bytes_per_launch": round(algo_tot / nl)}
+    if passes:
+        fr = sorted(p["GBps"] / peak for p in passes)
+        roofline["large_passes"] = {
+            "what": "passes with at least half the cloud live: (read + written bytes) / device time",
+            "n": len(passes), "frac_min": round(fr[0], 4), "frac_median": round(fr[len(fr) // 2], 4),
+            "frac_max": round(fr[-1], 4), "passes": passes}
 
     line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
