@@ -142,7 +142,10 @@ qh_status qh_hull2d_async(const float *d_x, const float *d_y, int64_t n, int64_t
 
 /* Synchronous form of qh_hull2d_async: returns the device status, the hull
  * size in *h_count and, when h_result is not NULL, the full result record.
- * d_result is taken from the workspace. */
+ * d_result is taken from the workspace.  Hulls with more than 4096 hull
+ * slots (the apexes found over all iterations, including points later found
+ * collinear) are finished here by a second, single-block output step;
+ * qh_hull2d_async reports QH_ERR_CAPACITY for them. */
 qh_status qh_hull2d(const float *d_x, const float *d_y, int64_t n, int64_t stride,
                     int32_t *d_out_idx, int64_t *h_count, qh_result *h_result, void *d_ws,
                     size_t ws_bytes, const qh_opts *opts, cudaStream_t stream);

@@ -1739,6 +1739,74 @@ __global__ void __launch_bounds__(kBlock) k_output2d(Params2 A, int nonfinite_ch
     output2d(A, sm.out);
 }
 
+// ---------------------------------------------------------------- large-hull output
+// The output step for hulls with more than kOutCap slots (output2d reports
+// QH_ERR_CAPACITY for them): the same ranking of the hull links by pointer
+// jumping, with the arrays in global memory (the point buffers are free once
+// the last pass is done), by one block; then the collinear filter and the
+// counter-clockwise compaction from a.  A separate launch, made by the
+// synchronous entry point when the first output step reported the capacity.
+__global__ void __launch_bounds__(kBlock) k_output2d_big(Params2 A)
+{
+    __shared__ long long wsum[33];
+    Hdr2 *H = A.hdr;
+    qh_result *R = A.res;
+    const int h = *(volatile int *)&H->hull_count;
+    const unsigned long long kmn = *(volatile unsigned long long *)&H->lexmin;
+    const unsigned long long kmx = *(volatile unsigned long long *)&H->lexmax;
+    if (*(volatile int *)&H->status != 0 || A.n == 0 || kmn == kmx || h <= kOutCap) return;
+    int *sa = A.bi[0], *sb = A.bi[1];
+    int *da = reinterpret_cast<int *>(A.bxy[0]), *db = reinterpret_cast<int *>(A.bxy[1]);
+    for (int i = threadIdx.x; i < h; i += blockDim.x) {
+        const int s = A.next[i];
+        sa[i] = (s == 0) ? -1 : s;
+        da[i] = (s == 0) ? 0 : 1;
+    }
+    __syncthreads();
+    for (int span = 1; span < h; span <<= 1) {
+        for (int i = threadIdx.x; i < h; i += blockDim.x) {
+            int s = sa[i], d = da[i];
+            if (s >= 0) {
+                d += da[s];
+                s = sa[s];
+            }
+            sb[i] = s;
+            db[i] = d;
+        }
+        __syncthreads();
+        int *t = sa;
+        sa = sb;
+        sb = t;
+        t = da;
+        da = db;
+        db = t;
+    }
+    int *order = sb;  // position counter-clockwise from a -> slot
+    for (int i = threadIdx.x; i < h; i += blockDim.x) {
+        const int rank = h - 1 - da[i];
+        order[(h - rank) % h] = i;
+    }
+    __syncthreads();
+    long long off = 0;
+    for (int q = 0; q < h; q += blockDim.x) {
+        const int p = q + threadIdx.x;
+        long long k = 0;
+        if (p < h) {
+            const int sp = order[(p + h - 1) % h], sv = order[p], sx = order[(p + 1) % h];
+            k = orient_exact_sign(A.hull_x[sp], A.hull_y[sp], A.hull_x[sv], A.hull_y[sv],
+                                  A.hull_x[sx], A.hull_y[sx]) != 0;
+        }
+        long long cnt;
+        const long long ex = block_excl_scan64(k, wsum, &cnt);
+        if (k) A.out_idx[off + ex] = A.hull_idx[order[p]];
+        off += cnt;
+    }
+    if (threadIdx.x == 0) {
+        R->count = off;
+        R->status = QH_OK;
+    }
+}
+
 // ---------------------------------------------------------------- host side
 struct Layout2 {
     size_t hdr, bxy[2], bi[2], seg[2], acc[2], tile_seg, tile_m, uncert, hull_idx, hull_x, hull_y,
@@ -1992,6 +2060,19 @@ extern "C" qh_status qh_hull2d(const float *d_x, const float *d_y, int64_t n, in
     if (cudaMemcpyAsync(&r, d_res, sizeof(r), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
         cudaStreamSynchronize(stream) != cudaSuccess)
         return QH_ERR_CUDA;
+    if (r.status == QH_ERR_CAPACITY && n > 0) {
+        // a hull with more slots than the in-kernel output step ranks: the
+        // large-hull output step (it leaves other capacity errors as they are)
+        qh_opts o;
+        qh_default_opts(&o);
+        if (opts) o = *opts;
+        const Params2 A = make_params(d_x, d_y, n, stride, d_out_idx, d_res, (char *)d_ws, L, o);
+        k_output2d_big<<<1, kBlock, 0, stream>>>(A);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(&r, d_res, sizeof(r), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+            cudaStreamSynchronize(stream) != cudaSuccess)
+            return QH_ERR_CUDA;
+    }
     if (h_count) *h_count = r.count;
     if (h_result) *h_result = r;
     return (qh_status)r.status;

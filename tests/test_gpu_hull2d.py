@@ -182,3 +182,40 @@ def test_full_size_bench_clouds(qh, cloud):
     P = torch.from_numpy(np.stack([x, y])).cuda()
     got = qh.hull2d(P)
     assert got.cpu().numpy().tolist() == want.tolist()
+
+
+@pytest.mark.parametrize("loop", ["persistent", "host"])
+def test_hull_larger_than_block_output(qh, loop):
+    # every point of y = x^2 (exact in float32 for |x| < 4096) is a vertex:
+    # 8191 hull vertices, more than one block ranks in shared memory, plus
+    # interior points, shuffled
+    r = np.random.default_rng(11)
+    i = np.arange(-4095, 4096, dtype=np.float64)
+    cx, cy = i, i * i
+    # interior: strictly above the parabola and below the chord y = 4095^2
+    top = 4095.0 * 4095.0
+    ix = np.round(r.uniform(-4000, 4000, 50_000))
+    iy = np.round(ix * ix + 1 + r.uniform(0, 1, ix.size) * (top - 2 - ix * ix))
+    x = np.concatenate([cx, ix]).astype(np.float32)
+    y = np.concatenate([cy, iy]).astype(np.float32)
+    p = r.permutation(x.size)
+    x, y = x[p], y[p]
+    want = oracle.hull2d(x, y)
+    assert len(want) == 8191
+    # (the synchronous entry point finishes such hulls with the large-hull
+    # output step)
+    got, res = _gpu(qh, x, y, pred="f32", loop=loop)
+    assert res["status"] == 0
+    assert got.tolist() == want.tolist()
+
+
+def test_many_vertices_on_circle(qh):
+    # 300k float32 points on the unit circle: thousands of exact extreme points
+    r = np.random.default_rng(12)
+    t = r.uniform(0, 2 * np.pi, 300_000)
+    x, y = np.cos(t).astype(np.float32), np.sin(t).astype(np.float32)
+    want = oracle.hull2d(x, y)
+    assert len(want) > 4096
+    got, res = _gpu(qh, x, y, pred="f32", loop="persistent")
+    assert res["status"] == 0
+    assert got.tolist() == want.tolist()
