@@ -1199,22 +1199,39 @@ __device__ void certify3d(const Params3 &A, int par, int bid, int nb)
 }
 
 // ---------------------------------------------------------------- X: exact apex
+// Chunks per uncertified facet: with fewer such facets than CTAs, each
+// facet's points are split over several CTAs, whose bests (float4 with the
+// index bits in w, -1 when the chunk has no candidate) go to the per-point
+// code buffer, free between the scatter and the next assignment.
+__device__ __forceinline__ int exact_chunks(const Params3 &A, int nu, int nb)
+{
+    if (nu <= 0) return 1;
+    const long long cap = (long long)A.n / 2;  // float4 slots in the code buffer
+    long long per = nb / nu;
+    if (per * nu > cap) per = cap / nu;
+    return per > 1 ? (int)per : 1;
+}
+
 template <int MODE>
-__device__ void exact3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int nb)
+__device__ void exact3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int nb, int per)
 {
     Hdr3 *H = A.hdr;
     const int nu = *(volatile int *)&H->n_uncert;
     const Ent3 *ent = A.ent[par ^ 1];
     const float4 *Q = A.pts[par ^ 1];
-    for (int u = bid; u < nu; u += nb) {
+    float4 *part = reinterpret_cast<float4 *>(A.code);
+    for (int w = bid; w < nu * per; w += nb) {
+        const int u = w / per, ch = w - u * per;
         const Ent3 en = ent[A.uncert[u]];
         const Fac3 F = A.fac[en.f];
         const float *a, *b, *c;
         fac_pts(F, a, b, c);
         const float thr = A.thr[en.f];
+        const int lo = (int)((long long)en.len * ch / per);
+        const int hi = (int)((long long)en.len * (ch + 1) / per);
         int best = -1;
         float4 bp = make_float4(0, 0, 0, 0);
-        for (int i = threadIdx.x; i < en.len; i += blockDim.x) {
+        for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
             const float4 p4 = Q[en.start + i];
             const float p[3] = {p4.x, p4.y, p4.z};
             float d, e;
@@ -1252,8 +1269,48 @@ __device__ void exact3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int nb
             }
             __syncthreads();
         }
-        if (threadIdx.x == 0 && sm.x.idx[0] >= 0) A.apex[en.f] = sm.x.p[0];
+        if (threadIdx.x == 0) {
+            if (per > 1) {
+                float4 r = sm.x.p[0];
+                if (sm.x.idx[0] < 0) r.w = __int_as_float(-1);
+                part[w] = r;
+            } else if (sm.x.idx[0] >= 0) {
+                A.apex[en.f] = sm.x.p[0];
+            }
+        }
         __syncthreads();
+    }
+}
+
+// Split exact phase, second step (after a grid barrier): one thread per
+// uncertified facet merges its chunks' bests with exact comparisons.
+template <int MODE>
+__device__ void exact3d_merge(const Params3 &A, int par, int bid, int nb, int per)
+{
+    Hdr3 *H = A.hdr;
+    const int nu = *(volatile int *)&H->n_uncert;
+    const Ent3 *ent = A.ent[par ^ 1];
+    const float4 *part = reinterpret_cast<const float4 *>(A.code);
+    for (int u = bid * blockDim.x + threadIdx.x; u < nu; u += nb * blockDim.x) {
+        const Ent3 en = ent[A.uncert[u]];
+        const Fac3 F = A.fac[en.f];
+        const float *a, *b, *c;
+        fac_pts(F, a, b, c);
+        int best = -1;
+        float4 bp = make_float4(0, 0, 0, 0);
+        for (int ch = 0; ch < per; ch++) {
+            const float4 p4 = part[u * per + ch];
+            const int idx = __float_as_int(p4.w);
+            if (idx < 0) continue;
+            if (best >= 0) {
+                const float p[3] = {p4.x, p4.y, p4.z}, q[3] = {bp.x, bp.y, bp.z};
+                const int s = cmp_dist3_exact_sign(a, b, c, p, q);
+                if (!(s > 0 || (s == 0 && idx < best))) continue;
+            }
+            best = idx;
+            bp = p4;
+        }
+        if (best >= 0) A.apex[en.f] = bp;
     }
 }
 
@@ -1332,8 +1389,13 @@ __global__ void __launch_bounds__(kMaxBlock) qh3d_persistent(Params3 A)
         certify3d(A, 0, bid, nb);
         sync();
         if (*(volatile int *)&H->n_uncert > 0) {
-            exact3d<MODE>(A, 0, sm, bid, nb);
+            const int per = exact_chunks(A, *(volatile int *)&H->n_uncert, nb);
+            exact3d<MODE>(A, 0, sm, bid, nb, per);
             sync();
+            if (per > 1) {
+                exact3d_merge<MODE>(A, 0, bid, nb, per);
+                sync();
+            }
         }
         setup_mark(3);
     }
@@ -1390,9 +1452,14 @@ __global__ void __launch_bounds__(kMaxBlock) qh3d_persistent(Params3 A)
         sync();
         mark(iter, 7);
         if (*(volatile int *)&H->n_uncert > 0) {
-            exact3d<MODE>(A, cur, sm, bid, nb);
-            if (bid == 0 && threadIdx.x == 0) H->exact_argmax += H->n_uncert;
+            const int per = exact_chunks(A, *(volatile int *)&H->n_uncert, nb);
+            exact3d<MODE>(A, cur, sm, bid, nb, per);
             sync();
+            if (per > 1) {
+                exact3d_merge<MODE>(A, cur, bid, nb, per);
+                sync();
+            }
+            if (bid == 0 && threadIdx.x == 0) H->exact_argmax += H->n_uncert;
         }
         mark(iter, 8);
         cur ^= 1;
