@@ -3,8 +3,10 @@
 Workload (one step): the convex hulls of three seeded 16M-point float32
 clouds in the plane (uniform in the unit square, uniform in the unit disk,
 on the unit circle with N(0, 1e-4) radial jitter), FP32-filtered exact
-predicates, one persistent kernel per hull.  value = points hulled per
-second over the whole job (Mpoints/s), inputs resident in HBM.
+predicates, the three hulls in one persistent launch (qh_hull2d_multi; the
+same clouds as three single-cloud launches are reported beside it).  value =
+points hulled per second over the whole job (Mpoints/s), inputs resident in
+HBM.
 
 Also reported: the 3D hull (8M points in the ball, 1M on the sphere) with the
 FP32 filter and with FP64 predicates; the batched 3D hull (4096 clouds in one
@@ -39,13 +41,15 @@ METRIC = "hull Mpoints/s (2D, 3D, batched) vs plain GPU path; % HBM roofline; bw
 UNIT = "Mpoints/s"
 N_PER_CLOUD = 16 * 1024 * 1024
 WORKLOAD = ("2D at scale: 3 x 16M float32 points (uniform unit square, uniform unit disk, "
-            "unit circle with N(0,1e-4) radial jitter), FP32-filtered exact predicates")
+            "unit circle with N(0,1e-4) radial jitter), FP32-filtered exact predicates, "
+            "the three hulls in one persistent launch")
 # DRAM bytes (read + write) per algorithmic byte of the persistent 2D kernel
-# from one ncu capture of a smaller case (3 clouds x 8M points,
-# profiles/qh2d_persistent_traffic_3x8M.md), keyed by the hash of the kernel's
-# sources it was taken on; the bench scales it by its own algorithmic bytes
-# per launch.  Absent (traffic null) for any other source state.
-NCU_TRAFFIC = {"e503a4faae8fb58d": 1526.92 / 2164.09}
+# (all clouds in one launch) from one ncu capture of a smaller case (3 clouds
+# x 8M points, profiles/qh2d_multi_traffic_3x8M.md), keyed by the hash of the
+# kernel's sources it was taken on; the bench scales it by its own
+# algorithmic bytes per launch.  Absent (traffic null) for any other source
+# state.
+NCU_TRAFFIC = {"f263d4d704095745": 1966.06 / 2164.09}
 
 
 KERNEL_2D_SOURCES = ("qh2d.cu", "pred2.cuh", "qh_common.cuh")
@@ -506,21 +510,29 @@ def main():
     wss = [qh.Workspace(dev) for _ in data]
     opts = qh.make_opts("f32", "persistent")
 
+    # the headline: every cloud of the step in one persistent launch
+    # (qh_hull2d_multi: the clouds share the segment table, the passes and the
+    # grid barriers)
+    mres = torch.zeros(len(data) * qh.RESULT_BYTES, dtype=torch.uint8, device=dev)
+    mws = qh.Workspace(dev)
+    nl = len(dev_pts)
+
     def step():
-        for i, P in enumerate(dev_pts):
-            qh.hull2d_async(P, None, outs[i], results[i], wss[i], opts)
+        qh.hull2d_multi_async(dev_pts, outs, mres, mws, opts)
+
+    def mresults():
+        return [qh.result_from_tensor(mres[i * qh.RESULT_BYTES:(i + 1) * qh.RESULT_BYTES])
+                for i in range(nl)]
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    res = [qh.result_from_tensor(r) for r in results]
-    for r in res:
+    for r in mresults():
         if r.status != 0:
             raise SystemExit(f"hull failed: {qh.status_str(r.status)}")
 
-    # ---- timed region: K steps, per-launch events for the roofline
-    nl = len(dev_pts)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps * nl + 1)]
+    # ---- timed region: K steps (one launch each), events per launch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
@@ -528,80 +540,69 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     ev[0].record(stream)
-    k = 1
-    for _ in range(args.steps):
-        for i, P in enumerate(dev_pts):
-            qh.hull2d_async(P, None, outs[i], results[i], wss[i], opts)
-            ev[k].record(stream)
-            k += 1
+    for k in range(args.steps):
+        step()
+        ev[k + 1].record(stream)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     clocks = sampler.stop()
     total_ms = ev[0].elapsed_time(ev[-1])
-    launch_ms = [[] for _ in range(nl)]
-    for s in range(args.steps):
-        for i in range(nl):
-            j = 1 + s * nl + i
-            launch_ms[i].append(ev[j - 1].elapsed_time(ev[j]))
+    launch_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     if ws > 1:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    res = [qh.result_from_tensor(r) for r in results]
-    # per-pass HBM rate of the last timed launch of each cloud (device clock
-    # between the pass's grid barriers): pass t reads its L_t live records
-    # (the first split: the caller's 8-byte coordinates) and writes its
-    # survivors, the L_{t+1} records of the next pass, 12 bytes each
+    res = mresults()
+    # per-pass HBM rate of the last timed launch (device clock between the
+    # pass's grid barriers): pass t reads its L_t live records (the first
+    # split: the callers' 8-byte coordinates) and writes its survivors, the
+    # L_{t+1} records of the next pass, 12 bytes each; listed for passes with
+    # at least half a cloud's worth of live points
     passes = []
-    for i, (name, _) in enumerate(data):
-        rows = qh.debug_timeline_2d(wss[i], ncl)
-        if args.timeline:
-            print(f"# timeline {name}: iter L S pass_us update_us", file=sys.stderr)
-            for r in rows:
-                print(f"#   {r[0]:3d} {r[1]:10d} {r[2]:7d} {r[3] / 1e3:9.2f} "
-                      f"{r[4] / 1e3:8.2f}", file=sys.stderr)
-        for t, r in enumerate(rows):
-            L_t, ns = int(r[1]), int(r[3])
-            if L_t < ncl // 2 or ns <= 0:
-                continue
-            S_t = int(rows[t + 1][1]) if t + 1 < len(rows) else 0
-            b = (8 if t == 0 else 12) * L_t + 12 * S_t
-            passes.append({"cloud": name, "iter": t, "live": L_t, "written": S_t,
-                           "us": round(ns / 1e3, 2), "GBps": round(b / ns, 1)})
+    rows = qh.debug_timeline_2d(mws, nl * ncl + 2 * nl)
+    if args.timeline:
+        print("# timeline (all clouds): iter L S pass_us update_us", file=sys.stderr)
+        for r in rows:
+            print(f"#   {r[0]:3d} {r[1]:10d} {r[2]:7d} {r[3] / 1e3:9.2f} "
+                  f"{r[4] / 1e3:8.2f}", file=sys.stderr)
+    for t, r in enumerate(rows):
+        L_t, ns = int(r[1]), int(r[3])
+        if L_t < ncl // 2 or ns <= 0:
+            continue
+        S_t = int(rows[t + 1][1]) if t + 1 < len(rows) else 0
+        b = (8 if t == 0 else 12) * L_t + 12 * S_t
+        passes.append({"iter": t, "live": L_t, "written": S_t, "us": round(ns / 1e3, 2),
+                       "GBps": round(b / ns, 1)})
     pts_per_step = nl * ncl
     value = ws * pts_per_step * args.steps / (total_ms / 1e3) / 1e6
 
-    # ---- roofline of the persistent kernel (algorithmic bytes per launch)
+    # ---- roofline of the persistent kernel (algorithmic bytes per launch:
+    # every cloud's extrema and first-split reads, 16 bytes a point, and 24
+    # bytes per survivor of every pass, written once and read once)
     peak, peak_kind = measured_peak()
-    per_cloud = []
-    ach = []
-    for i, (name, _) in enumerate(data):
-        r = res[i]
-        algo = 16 * ncl + 24 * r.survivor_total
-        ms = statistics.mean(launch_ms[i])
-        ach.append((algo, ms))
-        per_cloud.append({"cloud": name, "hull": r.count, "iterations": r.iterations,
-                          "ms": round(ms, 4), "algo_bytes": algo,
-                          "GBps": round(algo / (ms / 1e3) / 1e9, 1),
-                          "fallback_frac": r.filter_fallbacks / max(1, r.live_total),
-                          "exact_argmax_segments": r.exact_argmax,
-                          "phase_us": {"pass": r.extra[0] / 1e3, "update": r.extra[1] / 1e3,
-                                       "exact": r.extra[2] / 1e3, "other": r.extra[3] / 1e3}})
-    algo_tot = sum(a for a, _ in ach)
-    ms_tot = sum(m for _, m in ach)
-    achieved = algo_tot / (ms_tot / 1e3) / 1e9
+    r0 = res[0]
+    algo = 16 * pts_per_step + 24 * r0.survivor_total
+    ms = statistics.mean(launch_ms)
+    achieved = algo / (ms / 1e3) / 1e9
+    per_cloud = [{"cloud": name, "hull": res[i].count, "status": res[i].status}
+                 for i, (name, _) in enumerate(data)]
     sha = kernel_sources_sha()
     ratio = NCU_TRAFFIC.get(sha)
-    traffic = round(ratio * algo_tot / nl) if ratio else None
+    traffic = round(ratio * algo) if ratio else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                "traffic": traffic, "kernel": "qh2d_persistent<PredF32>",
-                "algo_bytes_per_launch": round(algo_tot / nl)}
+                "traffic": traffic, "kernel": "qh2d_multi<PredF32>",
+                "algo_bytes_per_launch": algo, "iterations": r0.iterations,
+                "fallback_frac": r0.filter_fallbacks / max(1, r0.live_total),
+                "exact_argmax_segments": r0.exact_argmax,
+                "phase_us": {"pass": r0.extra[0] / 1e3, "update": r0.extra[1] / 1e3,
+                             "exact": r0.extra[2] / 1e3, "other": r0.extra[3] / 1e3}}
     if passes:
         fr = sorted(p["GBps"] / peak for p in passes)
         roofline["large_passes"] = {
-            "what": "passes with at least half the cloud live: (read + written bytes) / device time",
+            "what": "passes with at least half a cloud's worth of live points: "
+                    "(read + written bytes) / device time",
             "n": len(passes), "frac_min": round(fr[0], 4), "frac_median": round(fr[len(fr) // 2], 4),
             "frac_max": round(fr[-1], 4), "passes": passes}
 
@@ -612,9 +613,29 @@ def main():
             "config": {"workload": WORKLOAD if ncl == N_PER_CLOUD and not args.only else
                        f"reduced: {nl} cloud(s) x {ncl} points", "points_per_step_per_gpu": pts_per_step,
                        "l2": "inputs larger than L2 (3 x 128 MB of coordinates per step)",
-                       "pred": "f32-filter+exact", "loop": "persistent"},
+                       "pred": "f32-filter+exact", "loop": "persistent, one launch for all clouds"},
             "per_cloud": per_cloud, "roofline": roofline, "clocks": clocks,
-            "gpu_launches": args.steps * nl}
+            "gpu_launches": args.steps}
+
+    # ---- the same clouds as separate single-cloud launches (context)
+    sepn = max(3, args.steps // 5)
+    for i, P in enumerate(dev_pts):
+        qh.hull2d_async(P, None, outs[i], results[i], wss[i], opts)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(sepn):
+        for i, P in enumerate(dev_pts):
+            qh.hull2d_async(P, None, outs[i], results[i], wss[i], opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sms = e0.elapsed_time(e1) / sepn
+    sres = [qh.result_from_tensor(r) for r in results]
+    line["separate_launches"] = {
+        "value": round(pts_per_step / (sms / 1e3) / 1e6, 2), "unit": UNIT,
+        "ms_per_step": round(sms, 3), "kernel": "qh2d_persistent<PredF32>, one launch per cloud",
+        "same_hulls": all(sres[i].count == res[i].count for i in range(nl))}
 
     # ---- plain GPU path: FP64 predicates, host loop with per-iteration readback
     if not args.no_plain:
@@ -675,9 +696,9 @@ def main():
     t0 = time.perf_counter()
     for _ in range(esteps):
         d2h = 0
-        for i, hp in enumerate(host_pts):
-            P = hp.to(dev, non_blocking=True)
-            idx = qh.hull2d(P, workspace=wss[i], out=outs[i])   # synchronous C-ABI call
+        P = [hp.to(dev, non_blocking=True) for hp in host_pts]
+        idxs = qh.hull2d_multi(P, workspace=mws)   # synchronous C-ABI call, all clouds
+        for i, idx in enumerate(idxs):
             host_out[i][: idx.numel()].copy_(idx, non_blocking=True)
             d2h += idx.numel() * 4 + qh.RESULT_BYTES
         torch.cuda.synchronize()

@@ -150,6 +150,41 @@ qh_status qh_hull2d(const float *d_x, const float *d_y, int64_t n, int64_t strid
                     int32_t *d_out_idx, int64_t *h_count, qh_result *h_result, void *d_ws,
                     size_t ws_bytes, const qh_opts *opts, cudaStream_t stream);
 
+/*
+ * Several 2D clouds in one persistent launch (no paper counterpart: the
+ * clouds' live points share the segment table, so every iteration's pass,
+ * update and grid barriers serve all of them, and each pass's tiles spread
+ * the clouds' work over the whole GPU).  Each cloud's hull is the one
+ * qh_hull2d_async returns for it alone.
+ *
+ *  k                1 <= k <= QH_MAX_CLOUDS_2D clouds
+ *  h_dx[c], h_dy[c] host arrays of device pointers: cloud c's coordinates,
+ *                   point i at d_x[i*stride] (read only)
+ *  h_n[c]           points of cloud c (>= 0); the total is at most
+ *                   QH_MAX_POINTS - 2 * QH_MAX_CLOUDS_2D
+ *  h_stride[c]      >= 1 (NULL: all 1)
+ *  h_dout[c]        host array of device pointers: int32[max(n_c, 1)] hull
+ *                   indices of cloud c, counter-clockwise from its
+ *                   lexicographically smallest vertex (cloud-local indices)
+ *  d_results        device qh_result[k]: per cloud count and status
+ *                   (QH_ERR_NONFINITE for a cloud with NaN/Inf; a failure of
+ *                   the shared iterations is reported in every record)
+ *  d_ws             device workspace of qh_workspace_bytes_2d_multi bytes,
+ *                   256-byte aligned
+ * Only QH_LOOP_PERSISTENT.  qh_hull2d_multi synchronises, fills h_counts[k]
+ * and h_results[k] (either may be NULL) and returns the first non-OK status
+ * of the clouds. */
+#define QH_MAX_CLOUDS_2D 8
+size_t qh_workspace_bytes_2d_multi(int32_t k, const int64_t *h_n, const qh_opts *opts);
+qh_status qh_hull2d_multi_async(int32_t k, const float *const *h_dx, const float *const *h_dy,
+                                const int64_t *h_n, const int64_t *h_stride,
+                                int32_t *const *h_dout, qh_result *d_results, void *d_ws,
+                                size_t ws_bytes, const qh_opts *opts, cudaStream_t stream);
+qh_status qh_hull2d_multi(int32_t k, const float *const *h_dx, const float *const *h_dy,
+                          const int64_t *h_n, const int64_t *h_stride, int32_t *const *h_dout,
+                          int64_t *h_counts, qh_result *h_results, void *d_ws, size_t ws_bytes,
+                          const qh_opts *opts, cudaStream_t stream);
+
 /* ---------------------------------------------------------------------- */
 /* 3D                                                                      */
 /* ---------------------------------------------------------------------- */

@@ -113,6 +113,74 @@ def hull2d_async(x: torch.Tensor, y: Optional[torch.Tensor], out: torch.Tensor,
         raise QHError(st, "qh_hull2d_async")
 
 
+MAX_CLOUDS_2D = 8
+
+
+def _multi_args(clouds, outs):
+    """Host arrays of the clouds' device pointers, sizes and strides."""
+    k = len(clouds)
+    if not 1 <= k <= MAX_CLOUDS_2D:
+        raise ValueError(f"between 1 and {MAX_CLOUDS_2D} clouds")
+    xs, ys, ns, ss = [], [], [], []
+    for c in clouds:
+        xp, yp, n, stride, _ = _points_2d(*c) if isinstance(c, tuple) else _points_2d(c, None)
+        xs.append(xp)
+        ys.append(yp)
+        ns.append(n)
+        ss.append(stride)
+    P = ctypes.c_void_p * k
+    I = ctypes.c_int64 * k
+    return (k, P(*xs), P(*ys), I(*ns), I(*ss), P(*[o.data_ptr() for o in outs]), ns)
+
+
+def workspace_bytes_2d_multi(ns, opts: Optional[QhOpts] = None) -> int:
+    I = ctypes.c_int64 * len(ns)
+    return int(_native.lib().qh_workspace_bytes_2d_multi(len(ns), I(*ns),
+                                                         ctypes.byref(opts) if opts else None))
+
+
+def hull2d_multi_async(clouds, outs, results: torch.Tensor, workspace: Workspace,
+                       opts: Optional[QhOpts] = None, stream=None) -> None:
+    """Hulls of several 2D clouds in one persistent launch, without
+    synchronising.  `clouds`: up to MAX_CLOUDS_2D CUDA float32 tensors ([n, 2],
+    [2, n]) or (x, y) pairs; `outs`: one int32 CUDA tensor of at least
+    max(n, 1) entries per cloud; `results`: a uint8 CUDA tensor of
+    len(clouds) * RESULT_BYTES bytes for the per-cloud qh_result records."""
+    k, xs, ys, ns, ss, ps, nl = _multi_args(clouds, outs)
+    o = opts if opts is not None else make_opts()
+    ws = workspace.get(workspace_bytes_2d_multi(nl, o))
+    st = _native.lib().qh_hull2d_multi_async(k, xs, ys, ns, ss, ps, results.data_ptr(),
+                                             ws.data_ptr(), ws.numel(), ctypes.byref(o),
+                                             _stream_handle(stream))
+    if st != 0:
+        raise QHError(st, "qh_hull2d_multi_async")
+
+
+def hull2d_multi(clouds, *, pred: str = "f32", workspace: Optional[Workspace] = None,
+                 stream=None, return_results: bool = False):
+    """Hulls of several 2D clouds in one persistent launch (each as hull2d).
+    Returns a list of int32 CUDA index tensors (and the result records)."""
+    if not clouds:
+        return ([], []) if return_results else []
+    first = clouds[0][0] if isinstance(clouds[0], tuple) else clouds[0]
+    dev = first.device
+    sizes = [(_points_2d(*c) if isinstance(c, tuple) else _points_2d(c, None))[2] for c in clouds]
+    outs = [torch.empty(max(n, 1), dtype=torch.int32, device=dev) for n in sizes]
+    k, xs, ys, ns, ss, ps, nl = _multi_args(clouds, outs)
+    o = make_opts(pred, "persistent")
+    if workspace is None:
+        workspace = _default_ws.setdefault(str(dev), Workspace(dev))
+    ws = workspace.get(workspace_bytes_2d_multi(nl, o))
+    counts = (ctypes.c_int64 * k)()
+    res = (QhResult * k)()
+    st = _native.lib().qh_hull2d_multi(k, xs, ys, ns, ss, ps, counts, res, ws.data_ptr(),
+                                       ws.numel(), ctypes.byref(o), _stream_handle(stream))
+    if st not in (0, 2):  # a non-finite cloud is reported in its own record
+        raise QHError(st, "qh_hull2d_multi")
+    out = [outs[c][: counts[c]] for c in range(k)]
+    return (out, [res[c].as_dict() for c in range(k)]) if return_results else out
+
+
 def debug_timeline_2d(workspace: Workspace, n: int, stream=None):
     """Per-iteration rows (iteration, live points, segments, pass ns, update ns)
     of the last persistent-loop 2D call on `workspace` with n points."""

@@ -47,6 +47,11 @@ SIGNATURES = [
     ("qh_hull2d_async", ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp, _sz, _POpts, _vp]),
     ("qh_hull2d", ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, ctypes.POINTER(_i64), _PRes, _vp,
                                  _sz, _POpts, _vp]),
+    ("qh_workspace_bytes_2d_multi", _sz, [ctypes.c_int32, _vp, _POpts]),
+    ("qh_hull2d_multi_async", ctypes.c_int, [ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                             _sz, _POpts, _vp]),
+    ("qh_hull2d_multi", ctypes.c_int, [ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                       _sz, _POpts, _vp]),
     ("qh_workspace_bytes_3d", _sz, [_i64, _POpts]),
     ("qh_hull3d", ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, _vp, ctypes.POINTER(_i64), _vp, _vp,
                                  ctypes.POINTER(_i64), _PRes, _vp, _sz, _POpts, _vp]),

@@ -867,7 +867,11 @@ __device__ __forceinline__ void multi_tile(SmemStream &sm, const Seg2 *seg, Acc2
     mflush();
 }
 
-template <class P, bool FIRST>
+// WEIGHTED: the CTAs' runs split the pass by cost rather than by tiles, a
+// segment start counting as two more tiles (a tile that straddles segments
+// is finished warp by warp with a chain of global round trips), so that runs
+// over many small segments do not fall on a few CTAs.
+template <class P, bool FIRST, bool WEIGHTED = false>
 __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBars &bars,
                               unsigned &ph, int bid, int nb)
 {
@@ -885,8 +889,8 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
     unsigned fallbacks = 0;
     const int ntiles = (L + kSTile - 1) / kSTile;
     const int per = ntiles / nb, rem = ntiles % nb;
-    const int t_begin = bid * per + min(bid, rem);
-    const int nt = per + (bid < rem ? 1 : 0);
+    int t_begin = bid * per + min(bid, rem);
+    int nt = per + (bid < rem ? 1 : 0);
 
     // ---- run map: tile -> (first segment, number of segments, the first
     // segment's physical and virtual start), by binary search of the tile's
@@ -909,8 +913,37 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
         sf = seg_of(v, staged);
         m = seg_of(vl, staged) - sf + 1;
     };
-    if (!FIRST && nt > 0) {
+    if (WEIGHTED && !FIRST && ntiles > 0) {
         if (vs_smem)
+            for (int i = threadIdx.x; i < S; i += blockDim.x) svs[i] = seg[i].vstart;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // cost of tiles [0, t): t plus twice the segment starts before
+            // tile t (strictly increasing in t); run b covers the tiles
+            // whose cost prefix falls in [b W / nb, (b+1) W / nb)
+            auto cost = [&](int t) -> long long {
+                return t == 0 ? 0ll : (long long)t + 2ll * (seg_of(t * kSTile - 1, vs_smem) + 1);
+            };
+            const long long W = cost(ntiles);
+            auto first_at = [&](long long target) {
+                int lo = 0, hi = ntiles;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (cost(mid) >= target) hi = mid;
+                    else lo = mid + 1;
+                }
+                return lo;
+            };
+            const int tb = first_at(W * bid / nb), te = first_at(W * (bid + 1) / nb);
+            sm.shift[0] = tb;  // (the stage shifts are not in use yet)
+            sm.shift[1] = te - tb;
+        }
+        __syncthreads();
+        t_begin = sm.shift[0];
+        nt = sm.shift[1];
+    }
+    if (!FIRST && nt > 0) {
+        if (vs_smem && !WEIGHTED)
             for (int i = threadIdx.x; i < S; i += blockDim.x) svs[i] = seg[i].vstart;
         __syncthreads();
         for (int j = threadIdx.x; j < min(nt, kRun); j += blockDim.x) {
@@ -1706,6 +1739,480 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_persistent(Params2 A)
     if (blockIdx.x == 0) output2d(A, sm.out);
 }
 
+// ---------------------------------------------------------------- several clouds
+// qh_hull2d_multi: K independent clouds in one persistent launch.  The
+// clouds' live points share the segment table and the point buffers (cloud c
+// owns the physical range [off_c, off_c + n_c)), so every pass, update and
+// grid barrier serves all of them, and the tiles of every pass balance the
+// clouds' work over the whole grid.  Point records carry cloud-local
+// indices; a segment carries its cloud (Seg2.pad[0]) for its apex's
+// coordinates, a hull slot its cloud for the output step.  Each cloud has a
+// header of its own for the extrema and the first split (lexmin, lexmax,
+// lowest indices, non-finite flag) and its own output and result record.
+constexpr int kMaxClouds = QH_MAX_CLOUDS_2D;
+
+struct Cloud2 {
+    const float *x, *y;
+    long long stride;
+    int n, first_tma;
+    int off;           // physical start of the cloud's points in the point buffers
+    int *out_idx;
+    qh_result *res;
+    Hdr2 *hdr;         // extrema and first-split state of the cloud
+};
+
+struct Params2M {
+    Params2 A;         // the shared state: all clouds' points (N = sum of n_c)
+    int K;
+    int *hull_cloud;   // cloud of every hull slot
+    Cloud2 c[kMaxClouds];
+};
+
+// Single-cloud parameters of cloud c for its extrema and its first split: its
+// input and header, its accumulator pair, its range of the first buffer.
+__device__ __forceinline__ Params2 cloud_params(const Params2M &M, int c)
+{
+    Params2 a = M.A;
+    const Cloud2 &C = M.c[c];
+    a.x = C.x;
+    a.y = C.y;
+    a.stride = C.stride;
+    a.n = C.n;
+    a.first_tma = C.first_tma;
+    a.hdr = C.hdr;
+    a.acc[0] = M.A.acc[0] + 2 * c;
+    a.bxy[0] = M.A.bxy[0] + C.off;
+    a.bi[0] = M.A.bi[0] + C.off;
+    return a;
+}
+
+__device__ __forceinline__ bool cloud_live(const Params2M &M, int c)
+{
+    return M.c[c].n > 0 && !*(volatile int *)&M.c[c].hdr->nonfinite;
+}
+
+// update2d for several clouds: the first update lays out every cloud's first
+// split (pseudo segment a_c -> b_c -> a_c over its physical range, hull slots
+// 2c and 2c+1); later ones as update2d, with the apex read from the
+// segment's cloud and every new hull slot tagged with it.
+__device__ void update2d_m(const Params2M &M, int par, bool first, SmemU &sm, int map_below)
+{
+    const Params2 &A = M.A;
+    Hdr2 *H = A.hdr;
+    Seg2 *so = A.seg[par];
+    Acc2 *ac = A.acc[par];
+    Seg2 *sn = A.seg[par ^ 1];
+    Acc2 *an = A.acc[par ^ 1];
+    if (first) {
+        for (int c = threadIdx.x; c < M.K; c += blockDim.x) {
+            const Cloud2 &C = M.c[c];
+            Hdr2 *Hc = C.hdr;
+            const unsigned long long kmn = *(volatile unsigned long long *)&Hc->lexmin;
+            const unsigned long long kmx = *(volatile unsigned long long *)&Hc->lexmax;
+            Seg2 g = {};
+            g.e0x = g.e1x = unord_f32((uint32_t)(kmn >> 32));
+            g.e0y = g.e1y = unord_f32((uint32_t)kmn);
+            g.qx = unord_f32((uint32_t)(kmx >> 32));
+            g.qy = unord_f32((uint32_t)kmx);
+            g.q_idx = -1;
+            g.e0_slot = 2 * c;
+            g.q_slot = 2 * c + 1;
+            g.e1_slot = 2 * c;
+            g.pstart = C.off;
+            g.len = C.n;
+            g.pad[0] = c;
+            so[c] = g;
+            A.hull_idx[2 * c] = *(volatile int *)&Hc->a_idx;
+            A.hull_x[2 * c] = g.e0x;
+            A.hull_y[2 * c] = g.e0y;
+            A.hull_idx[2 * c + 1] = *(volatile int *)&Hc->b_idx;
+            A.hull_x[2 * c + 1] = g.qx;
+            A.hull_y[2 * c + 1] = g.qy;
+            A.next[2 * c] = 2 * c + 1;
+            A.next[2 * c + 1] = 2 * c;
+            M.hull_cloud[2 * c] = c;
+            M.hull_cloud[2 * c + 1] = c;
+        }
+        __syncthreads();
+    }
+    const int S_old = *(volatile int *)&H->S[par];
+    const int hull_base = *(volatile int *)&H->hull_count;
+    if (threadIdx.x == 0) H->n_uncert = 0;
+    __syncthreads();
+    const int nslots = 2 * S_old;
+    long long carry_k = 0, carry_v = 0;
+    for (int base = 0; base < nslots; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const unsigned cnt = (i < nslots) ? ac[i].cnt : 0u;
+        const long long packed = ((long long)(cnt > 0) << 32) | (long long)cnt;
+        long long tot;
+        const long long ex = block_excl_scan64(packed, sm.wsum, &tot);
+        if (cnt > 0 && carry_k + (ex >> 32) >= A.cap_seg) {
+            set_status(H, kStCapacity);
+        } else if (cnt > 0) {
+            const int k = (int)(carry_k + (ex >> 32));
+            const int vs = (int)(carry_v + (ex & 0xffffffffll));
+            const int j = i >> 1, c = i & 1;
+            const Seg2 o = so[j];
+            const Acc2 a = ac[i];
+            const int cl = o.pad[0];
+            const Cloud2 &C = M.c[cl];
+            Seg2 g = {};
+            if (c == 0) {
+                g.e0x = o.e0x; g.e0y = o.e0y; g.e0_slot = o.e0_slot;
+                g.e1x = o.qx;  g.e1y = o.qy;  g.e1_slot = o.q_slot;
+                g.pstart = o.pstart;
+            } else {
+                g.e0x = o.qx;  g.e0y = o.qy;  g.e0_slot = o.q_slot;
+                g.e1x = o.e1x; g.e1y = o.e1y; g.e1_slot = o.e1_slot;
+                g.pstart = o.pstart + o.len - (int)cnt;
+            }
+            g.len = (int)cnt;
+            g.vstart = vs;
+            g.pad[0] = cl;
+            const int qi = key_idx(a.key1);
+            g.q_idx = qi;
+            g.qx = __ldg(C.x + (long long)qi * C.stride);
+            g.qy = __ldg(C.y + (long long)qi * C.stride);
+            const int slot = hull_base + k;
+            g.q_slot = slot;
+            // certified when the FP32 gap between the two best keys exceeds
+            // twice the largest error bound of the segment's keys
+            bool cert = true;
+            const float em = __uint_as_float(a.emax);
+            const float d1 = key_dist(a.key1);
+            if (cnt > 1) {
+                const float d2 = unord_f32(a.o2);
+                const double gap = ((double)d1 - (double)d2) * (1.0 - 0x1p-50);
+                cert = gap > 2.0 * (double)em;
+            }
+            if (!cert) {
+                const double thr =
+                    (double)d1 - (double)em - 2.0 * (double)em - fabs((double)d1) * 0x1p-20;
+                g.thr = isfinite(thr) ? __double2float_rd(thr) : -INFINITY;
+                const int u = atomicAdd(&H->n_uncert, 1);
+                A.uncert[u] = k;
+            }
+            A.hull_idx[slot] = qi;
+            A.hull_x[slot] = g.qx;
+            A.hull_y[slot] = g.qy;
+            M.hull_cloud[slot] = cl;
+            A.next[g.e0_slot] = slot;
+            A.next[slot] = g.e1_slot;
+            const Acc2 z = {};
+            an[2 * k] = z;
+            an[2 * k + 1] = z;
+            sn[k] = g;
+            if (k < kTile) sm.vs[k] = vs;
+        }
+        carry_k += tot >> 32;
+        carry_v += tot & 0xffffffffll;
+    }
+    const int S_new = (int)carry_k, L_new = (int)carry_v;
+    __syncthreads();
+    const int ntiles = (L_new + kTile - 1) / kTile;
+    auto seg_of = [&](int v) {
+        int lo = 0, hi = S_new - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            const int vs = (S_new <= kTile) ? sm.vs[mid] : sn[mid].vstart;
+            if (vs <= v) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    };
+    for (int t = threadIdx.x; L_new < map_below && t < ntiles; t += blockDim.x) {
+        const int v = t * kTile;
+        const int vl = min(v + kTile, L_new) - 1;
+        const int s0 = seg_of(v);
+        A.tile_seg[t] = s0;
+        A.tile_m[t] = seg_of(vl) - s0 + 1;
+    }
+    if (threadIdx.x == 0) {
+        H->S[par ^ 1] = S_new;
+        H->L[par ^ 1] = L_new;
+        H->hull_count = hull_base + S_new;
+        H->seg_total += S_new;
+        H->surv_total += L_new;
+        H->exact_argmax += H->n_uncert;
+    }
+    __syncthreads();
+}
+
+// The single-CTA tail (as tail2d) with the several-cloud update.
+template <class P>
+__device__ void tail2d_m(const Params2M &M, int t, SmemAll &sm)
+{
+    const Params2 &A = M.A;
+    Hdr2 *H = A.hdr;
+    const bool clk = threadIdx.x == 0;
+    for (;;) {
+        const unsigned long long t0 = clk ? globaltimer_ns() : 0;
+        if (threadIdx.x == 0) H->iter = t;
+        pass2d<P, false>(A, t & 1, sm.pass, 0, 1);
+        __syncthreads();
+        const unsigned long long t1 = clk ? globaltimer_ns() : 0;
+        update2d_m(M, t & 1, false, sm.u, INT_MAX);
+        if (clk) {
+            const unsigned long long t2 = globaltimer_ns();
+            H->phase_ns[0] += t1 - t0;
+            H->phase_ns[1] += t2 - t1;
+            if (t < kTimeline) {
+                H->tl[t][0] = *(volatile int *)&H->L[t & 1];
+                H->tl[t][1] = *(volatile int *)&H->S[t & 1];
+                H->tl[t][2] += (long long)(t1 - t0);
+                H->tl[t][3] += (long long)(t2 - t1);
+            }
+        }
+        __syncthreads();
+        if (*(volatile int *)&H->status) break;
+        if (*(volatile int *)&H->n_uncert > 0) {
+            exact2d<P>(A, t & 1, sm.x, 0, 1);
+            __syncthreads();
+        }
+        if (*(volatile int *)&H->S[(t + 1) & 1] == 0) break;
+        t++;
+        if (t > A.max_iters) {
+            if (threadIdx.x == 0) set_status(H, kStNoConv);
+            break;
+        }
+    }
+}
+
+// Output of every cloud (block 0): the hull links of all clouds ranked at
+// once by pointer jumping in global memory (each cloud's cycle ends at the
+// link back to its slot a_c = 2c), then per cloud the collinear filter and
+// the counter-clockwise compaction from a_c into its output.
+__device__ void output2d_m(const Params2M &M, SmemOut &sm)
+{
+    const Params2 &A = M.A;
+    Hdr2 *H = A.hdr;
+    const int st = *(volatile int *)&H->status;
+    const int h = *(volatile int *)&H->hull_count;
+    int *hc = sm.succ;         // per cloud: hull slots of its cycle
+    int *hbase = sm.succ + kMaxClouds;  // per cloud: first position of its order
+    if (st == 0) {
+        int *sa = A.bi[0], *sb = A.bi[1];
+        int *da = reinterpret_cast<int *>(A.bxy[0]), *db = reinterpret_cast<int *>(A.bxy[1]);
+        for (int i = threadIdx.x; i < h; i += blockDim.x) {
+            const int s = A.next[i];
+            const bool end = s == 2 * M.hull_cloud[i];
+            sa[i] = end ? -1 : s;
+            da[i] = end ? 0 : 1;
+        }
+        __syncthreads();
+        for (int span = 1; span < h; span <<= 1) {
+            for (int i = threadIdx.x; i < h; i += blockDim.x) {
+                int s = sa[i], d = da[i];
+                if (s >= 0) {
+                    d += da[s];
+                    s = sa[s];
+                }
+                sb[i] = s;
+                db[i] = d;
+            }
+            __syncthreads();
+            int *t = sa;
+            sa = sb;
+            sb = t;
+            t = da;
+            da = db;
+            db = t;
+        }
+        if (threadIdx.x == 0) {
+            int b = 0;
+            for (int c = 0; c < M.K; c++) {
+                hc[c] = da[2 * c] + 1;  // a_c is the farthest from its cycle's end
+                hbase[c] = b;
+                b += hc[c];
+            }
+        }
+        __syncthreads();
+        int *order = sb;  // hbase[c] + position counter-clockwise from a_c -> slot
+        for (int i = threadIdx.x; i < h; i += blockDim.x) {
+            const int c = M.hull_cloud[i], hh = hc[c];
+            const int rank = hh - 1 - da[i];
+            order[hbase[c] + (hh - rank) % hh] = i;
+        }
+        __syncthreads();
+        for (int c = 0; c < M.K; c++) {
+            const Cloud2 &C = M.c[c];
+            Hdr2 *Hc = C.hdr;
+            const bool nonfinite = C.n > 0 && *(volatile int *)&Hc->nonfinite;
+            long long count = 0;
+            if (C.n > 0 && !nonfinite) {
+                const unsigned long long kmn = *(volatile unsigned long long *)&Hc->lexmin;
+                const unsigned long long kmx = *(volatile unsigned long long *)&Hc->lexmax;
+                if (kmn == kmx) {
+                    if (threadIdx.x == 0) C.out_idx[0] = *(volatile int *)&Hc->a_idx;
+                    count = 1;
+                } else {
+                    const int hh = hc[c], b0 = hbase[c];
+                    long long off = 0;
+                    for (int q = 0; q < hh; q += blockDim.x) {
+                        const int p = q + threadIdx.x;
+                        long long k = 0;
+                        if (p < hh) {
+                            if (hh <= 2) {
+                                k = 1;
+                            } else {
+                                const int sp = order[b0 + (p + hh - 1) % hh], sv = order[b0 + p],
+                                          sx = order[b0 + (p + 1) % hh];
+                                k = orient_exact_sign(A.hull_x[sp], A.hull_y[sp], A.hull_x[sv],
+                                                      A.hull_y[sv], A.hull_x[sx],
+                                                      A.hull_y[sx]) != 0;
+                            }
+                        }
+                        long long cnt;
+                        const long long ex = block_excl_scan64(k, sm.wsum, &cnt);
+                        if (k) C.out_idx[off + ex] = A.hull_idx[order[b0 + p]];
+                        off += cnt;
+                    }
+                    count = off;
+                }
+            }
+            if (threadIdx.x == 0) {
+                qh_result *R = C.res;
+                const int cst = nonfinite ? (int)QH_ERR_NONFINITE : 0;
+                R->count = cst == 0 ? count : 0;
+                R->status = cst;
+                R->iterations = *(volatile int *)&H->iter;
+                R->survivor_total = *(volatile long long *)&H->surv_total;
+                R->live_total = (long long)A.n + R->survivor_total;
+                R->segments_total = *(volatile long long *)&H->seg_total;
+                R->filter_fallbacks = (long long)(*(volatile unsigned long long *)&H->fallbacks +
+                                                  *(volatile unsigned long long *)&Hc->fallbacks);
+                R->exact_argmax = *(volatile unsigned long long *)&H->exact_argmax;
+                for (int i = 0; i < 4; i++)
+                    R->extra[i] = (long long)*(volatile unsigned long long *)&H->phase_ns[i];
+            }
+            __syncthreads();
+        }
+    } else if (threadIdx.x == 0) {
+        for (int c = 0; c < M.K; c++) {
+            qh_result *R = M.c[c].res;
+            R->count = 0;
+            R->status = st;
+            R->iterations = *(volatile int *)&H->iter;
+        }
+    }
+}
+
+template <class P>
+__global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_multi(Params2M M)
+{
+    const Params2 &A = M.A;
+    SmemAll &sm = *reinterpret_cast<SmemAll *>(qh2d_dsm);
+    SmemStream &sp = *reinterpret_cast<SmemStream *>(qh2d_dsm);
+    __shared__ PipeBars bars;
+    __shared__ Ext2 ext_m[kMaxClouds];
+    unsigned ph = 0;
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < kRing; b++) {
+            mbar_init(&bars.full[b], 1);
+            mbar_init(&bars.empty[b], kCW);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&bars.counted[b], kCW);
+            mbar_init(&bars.bases[b], 1);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    Hdr2 *H = A.hdr;
+    int *fail = &H->status;
+    const bool clk = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long tprev = clk ? globaltimer_ns() : 0;
+    int it = 0;
+    auto sync_as = [&](int cat) {
+        grid_sync(&H->bar, fail, A.wait_ns);
+        if (clk) {
+            const unsigned long long t = globaltimer_ns();
+            H->phase_ns[cat] += t - tprev;
+            if (it < kTimeline && cat < 2) {
+                H->tl[it][2 + cat] += (long long)(t - tprev);
+                if (cat == 0) {
+                    H->tl[it][0] = *(volatile int *)&H->L[it & 1];
+                    H->tl[it][1] = *(volatile int *)&H->S[it & 1];
+                }
+            }
+            tprev = t;
+        }
+    };
+    // headers: the shared one (K pseudo segments, N live points, 2K hull
+    // slots) and each cloud's
+    if (blockIdx.x == 0) {
+        for (int c = 0; c < M.K; c++) init2d(cloud_params(M, c));
+        if (threadIdx.x == 0) {
+            H->S[0] = M.K;
+            H->L[0] = A.n;
+            H->hull_count = 2 * M.K;
+        }
+    }
+    sync_as(3);
+    for (int c = 0; c < M.K; c++) {
+        if (M.c[c].n == 0) continue;
+        const Ext2 e = extrema2d(cloud_params(M, c), sm);
+        if (threadIdx.x == 0) ext_m[c] = e;
+    }
+    sync_as(3);
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < M.K; c++) {
+            if (M.c[c].n == 0) continue;
+            Hdr2 *Hc = M.c[c].hdr;
+            if (ext_m[c].mn == *(volatile unsigned long long *)&Hc->lexmin)
+                atomicMin(&Hc->a_idx, ext_m[c].mni);
+            if (ext_m[c].mx == *(volatile unsigned long long *)&Hc->lexmax)
+                atomicMin(&Hc->b_idx, ext_m[c].mxi);
+        }
+    }
+    // the first split of every finite cloud, one after the other (each over
+    // the whole grid; no barrier between them)
+    for (int c = 0; c < M.K; c++)
+        if (cloud_live(M, c))
+            pass2d_stream<P, true>(cloud_params(M, c), 0, sp, bars, ph, blockIdx.x, gridDim.x);
+    sync_as(0);
+    // a bounded wait that expired in a cloud's first split stops every cloud
+    bool first_ok = true;
+    for (int c = 0; c < M.K; c++) first_ok &= *(volatile int *)&M.c[c].hdr->status == 0;
+    if (!first_ok) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(H, kStTimeout);
+    } else {
+        int t = 0;
+        bool tail = false;
+        while (*(volatile int *)&H->status == 0) {
+            if (blockIdx.x == 0) update2d_m(M, t & 1, t == 0, sm.u, kTailPoints);
+            sync_as(1);
+            if (*(volatile int *)&H->status) break;
+            if (*(volatile int *)&H->n_uncert > 0) {
+                exact2d<P>(A, t & 1, sm.x, blockIdx.x, gridDim.x);
+                sync_as(2);
+            }
+            if (*(volatile int *)&H->S[(t + 1) & 1] == 0) break;
+            t++;
+            if (t > A.max_iters) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) set_status(H, kStNoConv);
+                break;
+            }
+            if (*(volatile int *)&H->L[t & 1] < kTailPoints) {
+                tail = true;
+                break;
+            }
+            if (blockIdx.x == 0 && threadIdx.x == 0) H->iter = t;
+            it = t;
+            pass2d_stream<P, false, true>(A, t & 1, sp, bars, ph, blockIdx.x, gridDim.x);
+            sync_as(0);
+        }
+        if (tail && blockIdx.x == 0) {
+            tprev = 0;
+            tail2d_m<P>(M, t, sm);
+            if (clk) tprev = globaltimer_ns();
+        }
+    }
+    sync_as(3);
+    if (blockIdx.x == 0) output2d_m(M, sm.out);
+}
+
 // ---------------------------------------------------------------- host-loop kernels
 __global__ void __launch_bounds__(kBlock) k_init2d(Params2 A) { init2d(A); }
 __global__ void __launch_bounds__(kBlock) k_extrema2d(Params2 A)
@@ -1953,7 +2460,181 @@ static qh_status run2d(const Params2 &A, const qh_opts &o, cudaStream_t st)
     return cudaGetLastError() == cudaSuccess ? QH_OK : QH_ERR_CUDA;
 }
 
+
+// ---------------------------------------------------------------- several clouds: host side
+struct Layout2M {
+    Layout2 L;        // shared state for N points (+ two hull slots per cloud)
+    size_t chdr;      // K cloud headers
+    size_t hull_cloud;
+    size_t res;       // K result records (used by the synchronous entry point)
+    size_t total;
+};
+
+static Layout2M layout2d_multi(int k, int64_t N)
+{
+    Layout2M M;
+    M.L = layout2d(N + 2 * (int64_t)k);
+    size_t o = M.L.total;
+    M.chdr = o;
+    o = align_up(o + (size_t)k * align_up(sizeof(Hdr2)));
+    M.hull_cloud = o;
+    o = align_up(o + (size_t)(N + 2 * (int64_t)k + 2) * 4);
+    M.res = o;
+    o = align_up(o + (size_t)k * sizeof(qh_result));
+    M.total = o;
+    return M;
+}
+
+template <class P>
+static qh_status run2d_multi(const Params2M &M, const Layout2M &LM, char *ws, const qh_opts &o,
+                             cudaStream_t st)
+{
+    if (cudaMemsetAsync(ws + LM.L.hdr, 0, sizeof(Hdr2), st) != cudaSuccess ||
+        cudaMemsetAsync(ws + LM.chdr, 0, (size_t)M.K * align_up(sizeof(Hdr2)), st) != cudaSuccess)
+        return QH_ERR_CUDA;
+    const void *fn = (const void *)qh2d_multi<P>;
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [&]() {
+        attr_err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kPersistSmem);
+    });
+    if (attr_err != cudaSuccess) return QH_ERR_CUDA;
+    int grid = persistent_grid_smem(fn, kBlock, o.blocks_per_sm, kPersistSmem);
+    if (grid <= 0) return QH_ERR_CUDA;
+    grid = grid > kMaxGrid ? kMaxGrid : grid;
+    if (o.max_ctas > 0 && grid > o.max_ctas) grid = o.max_ctas;
+    const int first_tiles = (int)((M.A.n + kTile - 1) / kTile);
+    if (grid > first_tiles) grid = first_tiles > 0 ? first_tiles : 1;
+    Params2M m = M;
+    void *args[] = {&m};
+    const cudaError_t e =
+        cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, kPersistSmem, st);
+    return e == cudaSuccess ? QH_OK : QH_ERR_CUDA;
+}
+
+// Checks the clouds and fills the several-cloud parameters (NOMEM when the
+// workspace is too small or misaligned).
+static qh_status multi_params(int32_t k, const float *const *h_dx, const float *const *h_dy,
+                              const int64_t *h_n, const int64_t *h_stride, int32_t *const *h_dout,
+                              qh_result *d_results, void *d_ws, size_t ws_bytes,
+                              const qh_opts &o, Params2M &M, Layout2M &LM, int64_t &N)
+{
+    if (k < 1 || k > kMaxClouds || !h_n || !d_results || !d_ws) return QH_ERR_INVALID_ARG;
+    if (o.pred_mode != QH_PRED_F32 && o.pred_mode != QH_PRED_F64) return QH_ERR_INVALID_ARG;
+    if (o.loop_mode != QH_LOOP_PERSISTENT) return QH_ERR_INVALID_ARG;
+    N = 0;
+    for (int c = 0; c < k; c++) {
+        const int64_t n = h_n[c];
+        const int64_t s = h_stride ? h_stride[c] : 1;
+        if (n < 0 || n > QH_MAX_POINTS || s < 1) return QH_ERR_INVALID_ARG;
+        if (n > 0 && (!h_dx || !h_dy || !h_dout || !h_dx[c] || !h_dy[c] || !h_dout[c]))
+            return QH_ERR_INVALID_ARG;
+        if ((n - 1) * s > (int64_t)1 << 40) return QH_ERR_INVALID_ARG;
+        N += n;
+    }
+    if (N > QH_MAX_POINTS - 2 * kMaxClouds) return QH_ERR_INVALID_ARG;
+    LM = layout2d_multi(k, N);
+    if (ws_bytes < LM.total || ((uintptr_t)d_ws & 255)) return QH_ERR_NOMEM;
+    char *ws = (char *)d_ws;
+    M = Params2M{};
+    M.A = make_params(nullptr, nullptr, N, 1, nullptr, nullptr, ws, LM.L, o);
+    M.A.first_tma = 0;
+    M.K = k;
+    M.hull_cloud = (int *)(ws + LM.hull_cloud);
+    int64_t off = 0;
+    for (int c = 0; c < k; c++) {
+        Cloud2 &C = M.c[c];
+        const int64_t n = h_n[c];
+        const int64_t s = h_stride ? h_stride[c] : 1;
+        C.n = (int)n;
+        C.stride = s;
+        C.off = (int)off;
+        C.x = n > 0 ? h_dx[c] : nullptr;
+        C.y = n > 0 ? h_dy[c] : nullptr;
+        C.out_idx = n > 0 ? h_dout[c] : nullptr;
+        C.res = d_results + c;
+        C.hdr = (Hdr2 *)(ws + LM.chdr + (size_t)c * align_up(sizeof(Hdr2)));
+        C.first_tma = 0;
+        if (n > 0) {
+            if (s == 1 && ((uintptr_t)C.x & 15) == 0 && ((uintptr_t)C.y & 15) == 0)
+                C.first_tma = 1;
+            else if (s == 2 && C.y == C.x + 1 && ((uintptr_t)C.x & 15) == 0)
+                C.first_tma = 2;
+        }
+        off += n;
+    }
+    return QH_OK;
+}
+
 }  // namespace qh
+
+extern "C" size_t qh_workspace_bytes_2d_multi(int32_t k, const int64_t *h_n, const qh_opts *opts)
+{
+    (void)opts;
+    if (k < 1 || k > qh::kMaxClouds || !h_n) return 0;
+    int64_t N = 0;
+    for (int c = 0; c < k; c++) {
+        if (h_n[c] < 0 || h_n[c] > QH_MAX_POINTS) return 0;
+        N += h_n[c];
+    }
+    if (N > QH_MAX_POINTS - 2 * qh::kMaxClouds) return 0;
+    return qh::layout2d_multi(k, N).total;
+}
+
+extern "C" qh_status qh_hull2d_multi_async(int32_t k, const float *const *h_dx,
+                                           const float *const *h_dy, const int64_t *h_n,
+                                           const int64_t *h_stride, int32_t *const *h_dout,
+                                           qh_result *d_results, void *d_ws, size_t ws_bytes,
+                                           const qh_opts *opts, cudaStream_t stream)
+{
+    using namespace qh;
+    qh_opts o;
+    qh_default_opts(&o);
+    if (opts) o = *opts;
+    Params2M M;
+    Layout2M LM;
+    int64_t N = 0;
+    const qh_status s = multi_params(k, h_dx, h_dy, h_n, h_stride, h_dout, d_results, d_ws,
+                                     ws_bytes, o, M, LM, N);
+    if (s != QH_OK) return s;
+    if (N == 0)
+        return cudaMemsetAsync(d_results, 0, (size_t)k * sizeof(qh_result), stream) == cudaSuccess
+                   ? QH_OK
+                   : QH_ERR_CUDA;
+    if (o.pred_mode == QH_PRED_F32) return run2d_multi<PredF32>(M, LM, (char *)d_ws, o, stream);
+    return run2d_multi<PredF64>(M, LM, (char *)d_ws, o, stream);
+}
+
+extern "C" qh_status qh_hull2d_multi(int32_t k, const float *const *h_dx, const float *const *h_dy,
+                                     const int64_t *h_n, const int64_t *h_stride,
+                                     int32_t *const *h_dout, int64_t *h_counts,
+                                     qh_result *h_results, void *d_ws, size_t ws_bytes,
+                                     const qh_opts *opts, cudaStream_t stream)
+{
+    using namespace qh;
+    if (k < 1 || k > kMaxClouds || !h_n || !d_ws) return QH_ERR_INVALID_ARG;
+    int64_t N = 0;
+    for (int c = 0; c < k; c++) N += h_n[c] > 0 ? h_n[c] : 0;
+    const Layout2M LM = layout2d_multi(k, N);
+    if (ws_bytes < LM.total || ((uintptr_t)d_ws & 255)) return QH_ERR_NOMEM;
+    qh_result *d_res = (qh_result *)((char *)d_ws + LM.res);
+    qh_status s = qh_hull2d_multi_async(k, h_dx, h_dy, h_n, h_stride, h_dout, d_res, d_ws,
+                                        ws_bytes, opts, stream);
+    if (s != QH_OK) return s;
+    qh_result r[kMaxClouds];
+    if (cudaMemcpyAsync(r, d_res, (size_t)k * sizeof(qh_result), cudaMemcpyDeviceToHost, stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return QH_ERR_CUDA;
+    qh_status worst = QH_OK;
+    for (int c = 0; c < k; c++) {
+        if (h_counts) h_counts[c] = r[c].count;
+        if (h_results) h_results[c] = r[c];
+        if (r[c].status != QH_OK && worst == QH_OK) worst = (qh_status)r[c].status;
+    }
+    return worst;
+}
 
 using namespace qh;
 

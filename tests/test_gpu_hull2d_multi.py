@@ -1,0 +1,98 @@
+"""GPU parity for several 2D clouds in one persistent launch: each cloud's
+hull (through the C ABI) against the oracle's hull of that cloud alone,
+index for index, on seeded inputs of mixed distributions and sizes, with the
+degenerate clouds (empty, one point, identical points, collinear points,
+non-finite) beside normal ones."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1201_2936_gb300 import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qh():
+    from paper_1201_2936_gb300 import build
+    build.build()
+    oracle.build()
+    import paper_1201_2936_gb300 as q
+    return q
+
+
+def _dev(x, y):
+    return (torch.from_numpy(np.asarray(x, np.float32)).cuda(),
+            torch.from_numpy(np.asarray(y, np.float32)).cuda())
+
+
+def _check(qh, clouds, pred="f32"):
+    got, res = qh.hull2d_multi([_dev(x, y) for x, y in clouds], pred=pred, return_results=True)
+    for c, (x, y) in enumerate(clouds):
+        if len(x) and not (np.isfinite(x).all() and np.isfinite(y).all()):
+            assert res[c]["status"] == 2, c  # QH_ERR_NONFINITE
+            continue
+        assert res[c]["status"] == 0, (c, res[c])
+        want = oracle.hull2d(np.asarray(x, np.float32), np.asarray(y, np.float32)) if len(x) else []
+        assert got[c].cpu().numpy().tolist() == list(want), c
+
+
+@pytest.mark.parametrize("pred", ["f32", "f64"])
+def test_mixed_clouds_match_oracle(qh, pred):
+    r = np.random.default_rng(3)
+    g = r.normal(size=(2, 50_001)).astype(np.float32)
+    clouds = [w.uniform_square(100_000, 11), w.uniform_disk(300_001, 12),
+              w.circle_jitter(250_037, 13, 1e-4), (g[0], g[1]), w.uniform_disk(2047, 14),
+              w.uniform_square(5, 15)]
+    _check(qh, clouds, pred)
+
+
+def test_degenerate_clouds_beside_normal_ones(qh):
+    x, y = w.uniform_disk(70_001, 21)
+    bad = np.array([0.5, np.nan, 0.25], np.float32)
+    clouds = [
+        (x, y),
+        (np.zeros(0, np.float32), np.zeros(0, np.float32)),   # empty
+        (np.array([0.3], np.float32), np.array([0.7], np.float32)),  # one point
+        (np.full(1000, 2.5, np.float32), np.full(1000, -1.0, np.float32)),  # identical
+        (np.arange(100, dtype=np.float32), 2 * np.arange(100, dtype=np.float32)),  # collinear
+        (bad, np.array([0.1, 0.2, 0.3], np.float32)),  # non-finite
+        w.circle_jitter(9_999, 22, 1e-4),
+        w.uniform_square(33_333, 23),
+    ]
+    _check(qh, clouds)
+
+
+def test_single_cloud_equals_hull2d(qh):
+    x, y = w.circle_jitter(400_000, 31, 1e-4)
+    X, Y = _dev(x, y)
+    one = qh.hull2d_multi([(X, Y)])[0]
+    assert one.cpu().numpy().tolist() == qh.hull2d(X, Y).cpu().numpy().tolist()
+
+
+def test_layouts_and_large_hull(qh):
+    # an interleaved [n, 2] cloud, an unaligned one and a hull with 8191
+    # vertices (more hull slots than one block ranks in shared memory)
+    i = np.arange(-4095, 4096, dtype=np.float64)
+    px, py = i.astype(np.float32), (i * i).astype(np.float32)
+    x1, y1 = w.uniform_disk(60_001, 41)
+    x2, y2 = w.uniform_square(80_000, 42)
+    P1 = torch.from_numpy(np.stack([x1, y1], 1).copy()).cuda()
+    X2 = torch.from_numpy(np.concatenate([[0.0], x2]).astype(np.float32)).cuda()[1:]
+    Y2 = torch.from_numpy(np.concatenate([[0.0], y2]).astype(np.float32)).cuda()[1:]
+    got = qh.hull2d_multi([_dev(px, py), P1, (X2, Y2)])
+    assert got[0].cpu().numpy().tolist() == oracle.hull2d(px, py).tolist()
+    assert got[1].cpu().numpy().tolist() == oracle.hull2d(x1, y1).tolist()
+    assert got[2].cpu().numpy().tolist() == oracle.hull2d(x2, y2).tolist()
+
+
+def test_full_size_bench_clouds_in_one_launch(qh):
+    # the 2D benchmark workload (three 16M-point clouds) in the launch the
+    # benchmark times
+    s = w.SEED_BASE + 1
+    clouds = [w.uniform_square(w.N_LARGE_2D, s), w.uniform_disk(w.N_LARGE_2D, s + 10),
+              w.circle_jitter(w.N_LARGE_2D, s + 20, 1e-4)]
+    got = qh.hull2d_multi([torch.from_numpy(np.stack([x, y])).cuda() for x, y in clouds])
+    for c, (x, y) in enumerate(clouds):
+        assert got[c].cpu().numpy().tolist() == oracle.hull2d(x, y).tolist(), c
