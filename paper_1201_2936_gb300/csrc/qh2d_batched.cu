@@ -12,8 +12,9 @@
 //     certify   each segment's farthest point from its FP32 top-2 keys, or
 //               resolve it exactly (block-wide, exact comparisons);
 //               link it into the hull list between the segment's ends;
-//     scatter   every live point: child 0 (s, q) if strictly outside s->q,
-//               child 1 (q, e) if strictly outside q->e, else discarded
+//     scatter   every live point (read segment by segment from the live
+//               ranges, never the holes): child 0 (s, q) if strictly outside
+//               s->q, child 1 (q, e) if strictly outside q->e, else discarded
 //               (flagPermute with k = 3 states, Section 4.1); child 0 fills
 //               the parent's range from the left, child 1 from the right, so
 //               no scan is needed to place them (compact, Section 4.2, is the
@@ -45,7 +46,7 @@ struct Rec {  // a live point: coordinates, index, raw id of its segment
 struct SegB {
     float sx, sy, qx, qy, ex, ey;
     int si, qi, ei;
-    int start, len, pad;
+    int start, len, vstart;  // physical range of its points; virtual start (live order)
     unsigned long long key1;
     unsigned o2, emax;
 };
@@ -74,7 +75,6 @@ struct ParamsB {
     Rec *rec[2];
     SegB *tab[2];
     AccB *acc[2];
-    int *remap[2];
     int *cur0, *cur1;  // child cursors per segment
     int *next, *order, *unc;
 };
@@ -164,17 +164,28 @@ __device__ void exact_argmax(const ParamsB &A, Smem &sm, SegB &T, const Rec *buf
 
 // One pass over the live points of the cloud: classify against their
 // segment's apex, place in the child range, accumulate the child's
-// farthest-point key.  FIRST: the input points against the pseudo segment.
+// farthest-point key.  FIRST: the nc input points against the pseudo
+// segment; else the nc live points of the m segments of T, in their virtual
+// order (segment S covers [T[S].vstart, + len), physically from T[S].start;
+// the starts are staged in shared memory when they fit), so that the holes
+// the discarded points left are never read.
 template <class P, bool FIRST>
-__device__ void scatter_pass(const ParamsB &A, Smem &sm, int lo, int nc, int par,
+__device__ void scatter_pass(const ParamsB &A, Smem &sm, int lo, int nc, int m, int par,
                              const SegB *T, unsigned &fb)
 {
     const Rec *src = A.rec[par];
     Rec *dst = A.rec[par ^ 1];
-    const int *remap = A.remap[par];
     AccB *acc = A.acc[par ^ 1];
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
+    int *vst = reinterpret_cast<int *>(sm.pa);
+    constexpr int kVstCap = (int)(2 * sizeof(sm.pa) / sizeof(int));  // pa and pb
+    const bool staged = m <= kVstCap;
+    if (!FIRST) {
+        if (staged)
+            for (int i = threadIdx.x; i < m; i += blockDim.x) vst[i] = T[i].vstart;
+        __syncthreads();
+    }
     for (int v0 = 0; v0 < nc; v0 += blockDim.x) {
         const int v = v0 + threadIdx.x;
         int child = -1, S = 0;
@@ -188,10 +199,16 @@ __device__ void scatter_pass(const ParamsB &A, Smem &sm, int lo, int nc, int par
                 r.idx = lo + v;
                 r.raw = 0;
             } else {
-                r = src[lo + v];
+                int a = 0, b = m - 1;
+                while (a < b) {
+                    const int mid = (a + b + 1) >> 1;
+                    if ((staged ? vst[mid] : T[mid].vstart) <= v) a = mid;
+                    else b = mid - 1;
+                }
+                S = a;
+                r = src[lo + T[S].start + (v - T[S].vstart)];
             }
-            if (r.raw >= 0) {
-                S = FIRST ? 0 : remap[r.raw];
+            {
                 const SegB &G = T[S];
                 if (r.idx != G.qi) {
                     float d0, e0;
@@ -328,20 +345,16 @@ __global__ void __launch_bounds__(kBlock) qh2d_batched_kernel(ParamsB A)
             A.cur1[tb] = 0;
         }
         for (int i = threadIdx.x; i < 2; i += blockDim.x) A.acc[0][rb + i] = AccB{0ull, 0u, 0u};
-        for (int i = threadIdx.x; i < nc; i += blockDim.x) A.rec[0][lo + i].raw = -1;
         __syncthreads();
         // table parity: tab[p] holds the segments of the records in rec[p]
         // (the pseudo segment: parity 1, the input as source)
         ParamsB Ac = A;
         Ac.cur0 = A.cur0 + tb;
         Ac.cur1 = A.cur1 + tb;
-        for (int q = 0; q < 2; q++) {
-            Ac.acc[q] = A.acc[q] + rb;
-            Ac.remap[q] = A.remap[q] + rb;
-        }
-        scatter_pass<P, true>(Ac, sm, lo, nc, 1, tab[1], fb);
+        for (int q = 0; q < 2; q++) Ac.acc[q] = A.acc[q] + rb;
+        scatter_pass<P, true>(Ac, sm, lo, nc, 1, 1, tab[1], fb);
         __syncthreads();
-        int par = 0;  // records now in rec[0]; their raw ids index acc[0] / remap[0]
+        int par = 0;  // records now in rec[0], by the segments of tab[par ^ 1]
         int m_par = 1;
         int iter = 0;
         long long segs = 0;
@@ -349,6 +362,8 @@ __global__ void __launch_bounds__(kBlock) qh2d_batched_kernel(ParamsB A)
             // ---- compact the children of tab[par ^ 1] (m_par parents) into tab[par]
             const SegB *Tp = tab[par ^ 1];
             SegB *Tn = tab[par];
+            // (segment index, virtual start) of every non-empty child: one
+            // packed scan
             long long carry = 0;
             unsigned long long nsurv = 0;
             for (int base = 0; base < 2 * m_par; base += blockDim.x) {
@@ -357,7 +372,9 @@ __global__ void __launch_bounds__(kBlock) qh2d_batched_kernel(ParamsB A)
                 if (raw < 2 * m_par) cnt = (raw & 1) ? Ac.cur1[raw >> 1] : Ac.cur0[raw >> 1];
                 nsurv += (unsigned long long)cnt;
                 long long tot;
-                const long long ex = block_excl_scan64(cnt > 0 ? 1 : 0, sm.wsum, &tot) + carry;
+                const long long packed = ((long long)(cnt > 0) << 32) | (long long)cnt;
+                const long long exp = block_excl_scan64(packed, sm.wsum, &tot) + carry;
+                const long long ex = exp >> 32;
                 if (raw < 2 * m_par) {
                     if (cnt > 0) {
                         const SegB &G = Tp[raw >> 1];
@@ -372,20 +389,18 @@ __global__ void __launch_bounds__(kBlock) qh2d_batched_kernel(ParamsB A)
                             T.start = G.start;
                         }
                         T.len = cnt;
+                        T.vstart = (int)(exp & 0xffffffffll);
                         const AccB ac = Ac.acc[par][raw];
                         T.key1 = ac.key1;
                         T.o2 = ac.o2;
                         T.emax = ac.emax;
                         T.qi = -1;
                         Tn[ex] = T;
-                        Ac.remap[par][raw] = (int)ex;
-                    } else {
-                        Ac.remap[par][raw] = -1;
                     }
                 }
                 carry += tot;
             }
-            const int m = (int)carry;
+            const int m = (int)(carry >> 32), live = (int)(carry & 0xffffffffll);
             nsurv = __reduce_add_sync(0xffffffffu, (unsigned)nsurv);
             if ((threadIdx.x & 31) == 0 && nsurv) atomicAdd(&sm.surv, nsurv);
             __syncthreads();
@@ -431,11 +446,9 @@ __global__ void __launch_bounds__(kBlock) qh2d_batched_kernel(ParamsB A)
                 A.next[T.si] = T.qi;
                 A.next[T.qi] = T.ei;
             }
-            // ---- scatter into the other buffer
-            for (int i = threadIdx.x; i < nc; i += blockDim.x) A.rec[par ^ 1][lo + i].raw = -1;
+            // ---- scatter the live points into the other buffer
             __syncthreads();
-            // records of rec[par] carry raw ids of the previous round: remap[par]
-            scatter_pass<P, false>(Ac, sm, lo, nc, par, Tn, fb);
+            scatter_pass<P, false>(Ac, sm, lo, live, m, par, Tn, fb);
             __syncthreads();
             // children counts are in cur0/cur1 of Tn's segments; their keys in
             // acc[par ^ 1]; records in rec[par ^ 1] carry raw ids 2S + k
@@ -533,7 +546,7 @@ __global__ void k_status_b2(ParamsB A)
 static size_t au(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct LayoutB {
-    size_t hdr, rec[2], tab[2], acc[2], remap[2], cur0, cur1, next, order, unc, total;
+    size_t hdr, rec[2], tab[2], acc[2], cur0, cur1, next, order, unc, total;
 };
 
 static LayoutB layout_b2(int64_t n, int ncloud)
@@ -552,7 +565,6 @@ static LayoutB layout_b2(int64_t n, int ncloud)
         L.rec[p] = take(np * sizeof(Rec));
         L.tab[p] = take(ts * sizeof(SegB));
         L.acc[p] = take(2 * ts * sizeof(AccB));
-        L.remap[p] = take(2 * ts * 4);
     }
     L.cur0 = take(ts * 4);
     L.cur1 = take(ts * 4);
@@ -609,7 +621,6 @@ extern "C" qh_status qh_hull2d_batched(const float *d_x, const float *d_y, int64
         A.rec[p] = (Rec *)(ws + L.rec[p]);
         A.tab[p] = (SegB *)(ws + L.tab[p]);
         A.acc[p] = (AccB *)(ws + L.acc[p]);
-        A.remap[p] = (int *)(ws + L.remap[p]);
     }
     A.cur0 = (int *)(ws + L.cur0);
     A.cur1 = (int *)(ws + L.cur1);
