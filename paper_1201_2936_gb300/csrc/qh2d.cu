@@ -15,23 +15,29 @@
 //     always form the current hull polygon, clockwise from a.
 //
 // One iteration (the hot loop of Algorithm 4):
-//   P  (pass2d)   every live point: classify against its segment's apex
+//   P  (pass2d_stream) every live point: classify against its segment's apex
 //                 (outside edge e0-q -> child 0, outside q-e1 -> child 1,
 //                 else discarded: inside the triangle, Algorithm 4 step 12),
-//                 block-local ranks by warp ballots, one atomic per
-//                 (tile, segment, child) for the global base, scatter of the
-//                 survivors, and the child's farthest-point reduction
-//                 (distance to the child edge is the classification value).
-//                 This fuses compact (Algorithm 3) and the 2-state
-//                 flagPermute (Algorithm 2) with the next iteration's
-//                 distance + segmented argmax (Algorithm 4 steps 9-14).
+//                 place it in its child's range and add it to the child's
+//                 farthest-point reduction (the distance to the child edge
+//                 is the classification value).  This fuses compact
+//                 (Algorithm 3) and the 2-state flagPermute (Algorithm 2)
+//                 with the next iteration's distance + segmented argmax
+//                 (Algorithm 4 steps 9-14).  Warp-specialised: a producer
+//                 warp streams tiles through a TMA ring and reserves each
+//                 tile's output range with one atomic per child; consumer
+//                 warps classify tile j and scatter tile j-1 (mbarrier
+//                 hand-offs, no block barrier inside the pass).
 //   U  (update2d) new segment table from the non-empty children, apex of
 //                 each (certified exact when the FP32 top-2 gap exceeds the
-//                 error bound), hull slots and links, tile -> segment map.
+//                 error bound), hull slots and links.
 //   X  (exact2d)  only for uncertified segments: exact farthest point.
-// The persistent kernel runs all iterations with grid barriers; the host
-// loop variant launches each phase and reads the live counts back every
-// iteration, as the paper's implementation does (Section 5 cost analysis).
+// The persistent kernel runs all iterations with grid barriers; below
+// kTailPoints live points block 0 finishes alone (tail2d) with the
+// synchronous pass (pass2d).  The host-loop variant launches each phase and
+// reads the live counts back every iteration, as the paper's implementation
+// does (Section 5 cost analysis).  qh2d_multi runs several clouds' hulls in
+// one persistent launch over a shared segment table.
 
 #include <climits>
 #include <cstddef>
