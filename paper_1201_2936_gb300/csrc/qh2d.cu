@@ -873,11 +873,43 @@ __device__ __forceinline__ void multi_tile(SmemStream &sm, const Seg2 *seg, Acc2
     mflush();
 }
 
+// A thread's farthest-point record of one child in the lean pass: the order
+// bits (ord_f32) of its best and second-best distance (0 = none: no distance
+// that arithmetic produces maps to 0), the best point's index (the first one
+// met among equal distances; a tie leaves o2 == o1, so the segment is never
+// certified and its apex is found by the exact argmax) and the largest error
+// bound.  Unsigned min/max order NaN distances like the 64-bit keys do.
+struct Far2 {
+    unsigned o1, o2, em;
+    int i1;
+};
+__device__ __forceinline__ void far2_add(Far2 &a, unsigned o, int idx, unsigned eb)
+{
+    const bool gt = o > a.o1;
+    a.o2 = max(a.o2, min(a.o1, o));
+    a.o1 = max(a.o1, o);
+    a.i1 = gt ? idx : a.i1;
+    a.em = max(a.em, eb);
+}
+__device__ __forceinline__ Top2 far2_top2(const Far2 &a)
+{
+    Top2 t;
+    t.k1 = a.o1 ? (((unsigned long long)a.o1 << 32) | (unsigned long long)(0xffffffffu - (uint32_t)a.i1))
+                : 0ull;
+    t.o2 = a.o2;
+    t.em = a.em;
+    return t;
+}
+
 // WEIGHTED: the CTAs' runs split the pass by cost rather than by tiles, a
 // segment start counting as two more tiles (a tile that straddles segments
 // is finished warp by warp with a chain of global round trips), so that runs
 // over many small segments do not fall on a few CTAs.
-template <class P, bool FIRST, bool WEIGHTED = false>
+// LEAN: single-segment tiles keep per-thread Far2 records and counts instead
+// of 64-bit keys and per-row ballots, the scatter loads a warp's items before
+// storing them, and the producer publishes a tile's bases as soon as they are
+// reserved.
+template <class P, bool FIRST, bool WEIGHTED = false, bool LEAN = false>
 __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBars &bars,
                               unsigned &ph, int bid, int nb)
 {
@@ -923,14 +955,44 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
         if (vs_smem)
             for (int i = threadIdx.x; i < S; i += blockDim.x) svs[i] = seg[i].vstart;
         __syncthreads();
+        // cost of tiles [0, t): t plus twice the segment starts before
+        // tile t (strictly increasing in t); run b covers the tiles
+        // whose cost prefix falls in [b W / nb, (b+1) W / nb)
+        auto cost = [&](int t) -> long long {
+            return t == 0 ? 0ll : (long long)t + 2ll * (seg_of(t * kSTile - 1, vs_smem) + 1);
+        };
+        const long long W = cost(ntiles);
+        if constexpr (LEAN) {
+            // the first tile with cost >= target, for the run's two ends at
+            // once (threads 0-127: its start, 128-255: its end): each round
+            // probes 128 evenly spaced tiles of the interval [lo, hi] that
+            // holds the answer and keeps the gap between the last probe
+            // below the target and the first one at or above it
+            static_assert(kBlock == 256, "two halves of 128 probes");
+            const int half = threadIdx.x >> 7, hl = threadIdx.x & 127;
+            const long long target = W * (bid + half) / nb;
+            int *nbelow = sm.run_sf;  // per-warp counts (the run map is built later)
+            int lo = 0, hi = ntiles;
+            auto probe = [&](int i) { return lo + (int)(((long long)(i + 1) * (hi - lo)) >> 7); };
+            for (int span = ntiles; span > 0; span >>= 7) {
+                const bool below = cost(probe(hl)) < target;
+                const unsigned b = __ballot_sync(0xffffffffu, below);
+                if (lane == 0) nbelow[warp] = __popc(b);
+                __syncthreads();
+                const int q = half * 4;
+                const int nf = nbelow[q] + nbelow[q + 1] + nbelow[q + 2] + nbelow[q + 3];
+                __syncthreads();
+                // probes 0..nf-1 are below the target, probe nf (<= 127) is not
+                const int nlo = nf == 0 ? lo : probe(nf - 1) + 1, nhi = probe(nf);
+                lo = nlo;
+                hi = nhi;
+            }
+            if (hl == 0) sm.shift[half] = lo;  // (the stage shifts are not in use yet)
+            __syncthreads();
+            t_begin = sm.shift[0];
+            nt = sm.shift[1] - sm.shift[0];
+        } else {
         if (threadIdx.x == 0) {
-            // cost of tiles [0, t): t plus twice the segment starts before
-            // tile t (strictly increasing in t); run b covers the tiles
-            // whose cost prefix falls in [b W / nb, (b+1) W / nb)
-            auto cost = [&](int t) -> long long {
-                return t == 0 ? 0ll : (long long)t + 2ll * (seg_of(t * kSTile - 1, vs_smem) + 1);
-            };
-            const long long W = cost(ntiles);
             auto first_at = [&](long long target) {
                 int lo = 0, hi = ntiles;
                 while (lo < hi) {
@@ -947,6 +1009,7 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
         __syncthreads();
         t_begin = sm.shift[0];
         nt = sm.shift[1];
+        }
     }
     if (!FIRST && nt > 0) {
         if (vs_smem && !WEIGHTED)
@@ -1088,18 +1151,35 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                     sm.sem[p][ls][c] = 0u;
                 }
             }
-            if (j >= 1) {
-                // tile j-1 scattered: its stage takes tile j-1+kRing
-                wait(&bars.empty[(j - 1) % kRing], kPhEmpty + (j - 1) % kRing);
-                if (j - 1 + kRing < nt) issue(j - 1 + kRing);
+            if constexpr (LEAN) {
+                // every consumer warp has scattered tile j-2 (it did so
+                // before classifying tile j): the bases of parity p are free
+                __syncwarp();
+                if (lane == 0) {
+                    sm.gb[p][0] = (int)r0;
+                    sm.gb[p][1] = (int)r1;
+                    mbar_arrive(&bars.bases[p]);
+                }
+                __syncwarp();
+                if (j >= 1) {
+                    wait(&bars.empty[(j - 1) % kRing], kPhEmpty + (j - 1) % kRing);
+                    if (j - 1 + kRing < nt) issue(j - 1 + kRing);
+                }
+                __syncwarp();
+            } else {
+                if (j >= 1) {
+                    // tile j-1 scattered: its stage takes tile j-1+kRing
+                    wait(&bars.empty[(j - 1) % kRing], kPhEmpty + (j - 1) % kRing);
+                    if (j - 1 + kRing < nt) issue(j - 1 + kRing);
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    sm.gb[p][0] = (int)r0;
+                    sm.gb[p][1] = (int)r1;
+                    mbar_arrive(&bars.bases[p]);
+                }
+                __syncwarp();
             }
-            __syncwarp();
-            if (lane == 0) {
-                sm.gb[p][0] = (int)r0;
-                sm.gb[p][1] = (int)r1;
-                mbar_arrive(&bars.bases[p]);
-            }
-            __syncwarp();
         }
         if (nt > 0) wait(&bars.empty[(nt - 1) % kRing], kPhEmpty + (nt - 1) % kRing);
     } else {
@@ -1125,8 +1205,14 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
         // farthest-point accumulators of segment `cur` (single-segment tiles)
         int cur = FIRST ? 0 : -1;
         Top2 ta = {0ull, 0u, 0u}, tb = {0ull, 0u, 0u};
+        Far2 fa = {0u, 0u, 0u, 0}, fb = {0u, 0u, 0u, 0};
+        const int first_tma = A.first_tma;
         auto flush = [&]() {
             if (cur < 0) return;
+            if constexpr (LEAN) {
+                ta = far2_top2(fa);
+                tb = far2_top2(fb);
+            }
             top2_warp(ta);
             top2_warp(tb);
             if (lane == 0) {
@@ -1153,6 +1239,8 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                         cur = sf;
                         ta = {0ull, 0u, 0u};
                         tb = {0ull, 0u, 0u};
+                        fa = {0u, 0u, 0u, 0};
+                        fb = {0u, 0u, 0u, 0};
                     }
                     // phase 1, branch-free: filter values and classes of all
                     // items (independent chains the compiler interleaves)
@@ -1215,6 +1303,21 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                     }
                     // phase 3, branch-free: farthest-point keys and counts
                     int w0 = 0, w1 = 0;
+                    if constexpr (LEAN) {
+                        int n0 = 0, n1 = 0;
+#pragma unroll
+                        for (int k = 0; k < kSItems; k++) {
+                            const int c = (int)((cls >> (2 * k)) & 3u);
+                            const unsigned o = ord_f32(dsel[k]);
+                            const unsigned eb = __float_as_uint(esel[k]);
+                            far2_add(fa, c == 0 ? o : 0u, pidx[k], c == 0 ? eb : 0u);
+                            far2_add(fb, c == 1 ? o : 0u, pidx[k], c == 1 ? eb : 0u);
+                            n0 += c == 0;
+                            n1 += c == 1;
+                        }
+                        w0 = __reduce_add_sync(0xffffffffu, n0);
+                        w1 = __reduce_add_sync(0xffffffffu, n1);
+                    } else {
 #pragma unroll
                     for (int k = 0; k < kSItems; k++) {
                         const int c = (int)((cls >> (2 * k)) & 3u);
@@ -1224,6 +1327,7 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                         top2_add(tb, c == 1 ? key : 0ull, c == 1 ? eb : 0u);
                         w0 += __popc(__ballot_sync(0xffffffffu, c == 0));
                         w1 += __popc(__ballot_sync(0xffffffffu, c == 1));
+                    }
                     }
                     if (lane == 0) {
                         off0 = atomicAdd(&sm.tilecnt[p][0], w0);
@@ -1248,6 +1352,44 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                     const int ln = FIRST ? A.n : sm.sseg[sp].len;
                     int base0 = sm.gb[pp][0] + off0_prev, base1 = sm.gb[pp][1] + off1_prev;
                     const int wbase = pv0 + warp * 32 * kSItems;
+                    if constexpr (LEAN) {
+                        // destinations and stage reads of all items, then the stores
+                        int dst[kSItems];
+                        float2 spt[kSItems];
+                        int sidx[kSItems];
+                        const int r0 = wbase - pv0 + shift + lane;
+                        int lo = ps + base0, hi = ps + ln - 1 - base1;
+#pragma unroll
+                        for (int k = 0; k < kSItems; k++) {
+                            const int c = (int)((cls_prev >> (2 * k)) & 3u);
+                            const unsigned b0 = __ballot_sync(0xffffffffu, c == 0);
+                            const unsigned b1 = __ballot_sync(0xffffffffu, c == 1);
+                            dst[k] = c == 0 ? lo + __popc(b0 & lt)
+                                            : (c == 1 ? hi - __popc(b1 & lt) : -1);
+                            lo += __popc(b0);
+                            hi -= __popc(b1);
+                            const int r = r0 + k * 32;
+                            if (FIRST) {
+                                if (first_tma == 2) {
+                                    spt[k] = sm.sxy[sp][r];
+                                } else {
+                                    const float *xs = reinterpret_cast<const float *>(sm.sxy[sp]);
+                                    spt[k] = make_float2(xs[r], xs[kStage + r]);
+                                }
+                                sidx[k] = wbase + k * 32 + lane;
+                            } else {
+                                spt[k] = sm.sxy[sp][r];
+                                sidx[k] = sm.sidx[sp][r];
+                            }
+                        }
+#pragma unroll
+                        for (int k = 0; k < kSItems; k++) {
+                            if (dst[k] >= 0) {
+                                oxy[dst[k]] = spt[k];
+                                oi[dst[k]] = sidx[k];
+                            }
+                        }
+                    } else {
 #pragma unroll
                     for (int k = 0; k < kSItems; k++) {
                         const int c = (int)((cls_prev >> (2 * k)) & 3u);
@@ -1272,6 +1414,7 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                         }
                         base0 += __popc(b0);
                         base1 += __popc(b1);
+                    }
                     }
                 }
                 __syncwarp();
@@ -2176,7 +2319,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_multi(Params2M M)
     // the whole grid; no barrier between them)
     for (int c = 0; c < M.K; c++)
         if (cloud_live(M, c))
-            pass2d_stream<P, true>(cloud_params(M, c), 0, sp, bars, ph, blockIdx.x, gridDim.x);
+            pass2d_stream<P, true, false, true>(cloud_params(M, c), 0, sp, bars, ph, blockIdx.x,
+                                                gridDim.x);
     sync_as(0);
     // a bounded wait that expired in a cloud's first split stops every cloud
     bool first_ok = true;
@@ -2206,7 +2350,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_multi(Params2M M)
             }
             if (blockIdx.x == 0 && threadIdx.x == 0) H->iter = t;
             it = t;
-            pass2d_stream<P, false, true>(A, t & 1, sp, bars, ph, blockIdx.x, gridDim.x);
+            pass2d_stream<P, false, true, true>(A, t & 1, sp, bars, ph, blockIdx.x, gridDim.x);
             sync_as(0);
         }
         if (tail && blockIdx.x == 0) {
