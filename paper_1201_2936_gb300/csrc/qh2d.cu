@@ -781,11 +781,12 @@ __device__ __forceinline__ int classify2d(const Geo2 &g, float x, float y, int i
 // kSItems rows, classified, reserved per (segment, child) group and
 // scattered.  Keys of the tile's first kMSlot segments go to the slots of
 // parity p (merged by the producer), the others to the accumulators.
-template <class P>
+// STAGED: the virtual starts of the tile's m segments are in tvs (shared).
+template <class P, bool STAGED = false>
 __device__ __forceinline__ void multi_tile(SmemStream &sm, const Seg2 *seg, Acc2 *acc, int sf,
                                            int m, int v0, int v1, int p, const float2 *ixy,
                                            const int *ii, float2 *oxy, int *oi,
-                                           unsigned &fallbacks)
+                                           unsigned &fallbacks, const int *tvs = nullptr)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
@@ -820,7 +821,7 @@ __device__ __forceinline__ void multi_tile(SmemStream &sm, const Seg2 *seg, Acc2
                 int lo = 0, hi = m - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
-                    if (seg[sf + mid].vstart <= v) lo = mid;
+                    if ((STAGED ? tvs[mid] : seg[sf + mid].vstart) <= v) lo = mid;
                     else hi = mid - 1;
                 }
                 ls = lo;
@@ -1098,6 +1099,23 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                 }
                 return;
             }
+            if constexpr (LEAN) {
+                // a tile that straddles segments: its segments' virtual
+                // starts go to the stage's index area
+                int sf, m;
+                if (j < kRun) {
+                    sf = sm.run_sf[j];
+                    m = sm.run_m[j];
+                } else {
+                    tile_segs(j, sf, m, false);
+                }
+                if (m != 1) {
+                    for (int i = lane; i < m; i += 32) sm.sidx[s][i] = seg[sf + i].vstart;
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&bars.full[s]);
+                    return;
+                }
+            }
             if (lane != 0) return;
             int sf, m, ps, vs;
             if (j < kRun) {
@@ -1335,6 +1353,9 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                     }
                     off0 = __shfl_sync(0xffffffffu, off0, 0);
                     off1 = __shfl_sync(0xffffffffu, off1, 0);
+                } else if constexpr (LEAN) {
+                    multi_tile<P, true>(sm, seg, acc, sf, m, v0, v1, p, ixy, ii, oxy, oi,
+                                        fallbacks, sm.sidx[s]);
                 } else {
                     multi_tile<P>(sm, seg, acc, sf, m, v0, v1, p, ixy, ii, oxy, oi, fallbacks);
                 }
@@ -2274,7 +2295,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_multi(Params2M M)
     unsigned long long tprev = clk ? globaltimer_ns() : 0;
     int it = 0;
     auto sync_as = [&](int cat) {
-        grid_sync(&H->bar, fail, A.wait_ns);
+        grid_sync_count(&H->bar, fail, A.wait_ns);
         if (clk) {
             const unsigned long long t = globaltimer_ns();
             H->phase_ns[cat] += t - tprev;

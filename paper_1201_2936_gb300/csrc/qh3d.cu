@@ -1322,7 +1322,7 @@ __global__ void __launch_bounds__(kMaxBlock) qh3d_persistent(Params3 A)
     Hdr3 *H = A.hdr;
     int *fail = &H->status;
     const int bid = blockIdx.x, nb = gridDim.x;
-    auto sync = [&]() { grid_sync(&H->bar, fail, A.wait_ns); };
+    auto sync = [&]() { grid_sync_count(&H->bar, fail, A.wait_ns); };
     auto ok = [&]() { return *(volatile int *)&H->status == 0; };
     // phase clock of block 0, thread 0 (per-iteration record)
     const bool clk = bid == 0 && threadIdx.x == 0;

@@ -103,6 +103,38 @@ __device__ __forceinline__ void grid_sync(GridBarrier *b, int *fail, long long w
     __syncthreads();
 }
 
+// The same barrier with one global atomic per CTA and round: count only grows
+// (zero at launch), arrival k of the grid belongs to round k / gridDim.x, and
+// round r is complete once count reaches (r + 1) * gridDim.x.  The arrival
+// releases the CTA's writes (ordered before it by the block barrier) and the
+// polling load acquires the other CTAs'.  A kernel uses either this barrier
+// or grid_sync on a given GridBarrier, never both.
+__device__ __forceinline__ void grid_sync_count(GridBarrier *b, int *fail, long long wait_ns)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int old;
+        asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;"
+                     : "=r"(old)
+                     : "l"(&b->count)
+                     : "memory");
+        const unsigned int target = (old / gridDim.x + 1u) * gridDim.x;
+        unsigned long long t0 = 0;
+        for (unsigned int spins = 0;; spins++) {
+            unsigned int cur;
+            asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(&b->count) : "memory");
+            if ((int)(cur - target) >= 0) break;
+            if (spins == 0) {
+                t0 = globaltimer_ns();
+            } else if ((spins & 255u) == 0u && (long long)(globaltimer_ns() - t0) > wait_ns) {
+                atomicCAS(fail, 0, kStTimeout);
+                break;
+            }
+        }
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------- async copies
 // Per-thread asynchronous global -> shared copies (completed by cp_async_wait_all
 // in the issuing thread, then visible to the CTA after a barrier).
