@@ -96,3 +96,42 @@ def test_full_size_bench_clouds_in_one_launch(qh):
     got = qh.hull2d_multi([torch.from_numpy(np.stack([x, y])).cuda() for x, y in clouds])
     for c, (x, y) in enumerate(clouds):
         assert got[c].cpu().numpy().tolist() == oracle.hull2d(x, y).tolist(), c
+
+
+def _tie_and_overflow_clouds():
+    r = np.random.default_rng(51)
+    # integer parabola y = x^2 (every point a hull vertex) with interior
+    # points above it: the farthest points of a segment whose ends are
+    # (a, a^2), (b, b^2) with a + b odd tie exactly, (i - a)(b - i) at
+    # i = (a + b -+ 1) / 2; all coordinates are exact in float32
+    i = np.arange(-1500, 1501)
+    ix = r.integers(-1400, 1401, 30_000)
+    iy = ix * ix + 1 + r.integers(0, 10_000, 30_000)
+    x = np.concatenate([i, ix]).astype(np.float32)
+    y = np.concatenate([i * i, np.minimum(iy, 1500 * 1500 - 1)]).astype(np.float32)
+    p = r.permutation(len(x))
+    parabola = (x[p], y[p])
+    # hull vertices of a disk repeated at higher and lower indices
+    dx, dy = w.uniform_disk(50_000, 52)
+    hv = oracle.hull2d(dx, dy)[:12]
+    dup = (np.concatenate([dx[hv], dx, dx[hv]]).astype(np.float32),
+           np.concatenate([dy[hv], dy, dy[hv]]).astype(np.float32))
+    # coordinates near 1e37: the FP32 filter overflows, the exact path decides
+    hx, hy = w.uniform_disk(20_000, 53)
+    huge = ((hx * np.float32(1e37)).astype(np.float32), (hy * np.float32(1e37)).astype(np.float32))
+    # a shuffled integer grid: collinear points on every hull edge, equal
+    # distances everywhere
+    gx, gy = np.meshgrid(np.arange(300, dtype=np.float32), np.arange(300, dtype=np.float32))
+    q = r.permutation(300 * 300)
+    grid = (gx.ravel()[q].copy(), gy.ravel()[q].copy())
+    return [parabola, dup, huge, grid]
+
+
+@pytest.mark.parametrize("pred", ["f32", "f64"])
+def test_exact_ties_and_filter_overflow(qh, pred):
+    clouds = _tie_and_overflow_clouds()
+    _check(qh, clouds, pred)
+    for c, (x, y) in enumerate(clouds):
+        X, Y = _dev(x, y)
+        got = qh.hull2d(X, Y, pred=pred)
+        assert got.cpu().numpy().tolist() == oracle.hull2d(x, y).tolist(), c
