@@ -37,7 +37,8 @@
 // synchronous pass (pass2d).  The host-loop variant launches each phase and
 // reads the live counts back every iteration, as the paper's implementation
 // does (Section 5 cost analysis).  qh2d_multi runs several clouds' hulls in
-// one persistent launch over a shared segment table.
+// one persistent launch over a shared segment table, with the lean variant
+// of the pass (pass2d_stream<..., LEAN>) and the one-atomic grid barrier.
 
 #include <climits>
 #include <cstddef>
@@ -908,8 +909,9 @@ __device__ __forceinline__ Top2 far2_top2(const Far2 &a)
 // over many small segments do not fall on a few CTAs.
 // LEAN: single-segment tiles keep per-thread Far2 records and counts instead
 // of 64-bit keys and per-row ballots, the scatter loads a warp's items before
-// storing them, and the producer publishes a tile's bases as soon as they are
-// reserved.
+// storing them, the producer publishes a tile's bases as soon as they are
+// reserved and stages the segment starts of a tile that straddles segments,
+// and the cost-weighted run ends are found by all threads at once.
 template <class P, bool FIRST, bool WEIGHTED = false, bool LEAN = false>
 __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBars &bars,
                               unsigned &ph, int bid, int nb)
