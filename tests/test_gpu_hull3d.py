@@ -112,3 +112,43 @@ def test_full_size_matches_oracle(qh, gen):
         assert np.array_equal(v.cpu().numpy(), ov), pred
         assert np.array_equal(off.cpu().numpy(), oo), pred
         assert np.array_equal(idx.cpu().numpy(), oi), pred
+
+
+def _paraboloid_dup_huge():
+    r = np.random.default_rng(61)
+    # integer paraboloid z = x^2 + y^2: the four points of every grid cell
+    # are coplanar, and the farthest points of many facets tie exactly
+    i, j = np.meshgrid(np.arange(-30, 31), np.arange(-30, 31))
+    i, j = i.ravel(), j.ravel()
+    ix, iy = r.integers(-29, 30, (2, 20_000))
+    iz = ix * ix + iy * iy + 1 + r.integers(0, 500, 20_000)
+    P = np.concatenate([np.stack([i, j, i * i + j * j], 1),
+                        np.stack([ix, iy, np.minimum(iz, 1799)], 1)]).astype(np.float32)
+    P = P[r.permutation(len(P))]
+    para = (P[:, 0].copy(), P[:, 1].copy(), P[:, 2].copy())
+    # hull vertices of a ball repeated at lower and higher indices
+    bx, by, bz = w.uniform_ball(40_000, 62)
+    hv = oracle.hull3d(bx, by, bz)[0][:16]
+    dup = tuple(np.concatenate([c[hv], c, c[hv]]).astype(np.float32) for c in (bx, by, bz))
+    # coordinates near 1e13: the FP32 orientation overflows, the exact path decides
+    hx, hy, hz = w.uniform_ball(20_000, 63)
+    huge = tuple((c * np.float32(1e13)).astype(np.float32) for c in (hx, hy, hz))
+    return [para, dup, huge]
+
+
+@pytest.mark.parametrize("pred", ["f32", "f64"])
+def test_exact_ties_duplicates_and_filter_overflow(qh, pred):
+    for k, (x, y, z) in enumerate(_paraboloid_dup_huge()):
+        want = _oracle(x, y, z)
+        v, f, _ = _gpu(qh, x, y, z, pred=pred)
+        assert (v, f) == (want[0], want[1]), (k, pred)
+
+
+def test_non_finite_input(qh):
+    x, y, z = w.uniform_ball(1000, 64)
+    for bad in (np.nan, np.inf):
+        zz = z.copy()
+        zz[123] = bad
+        with pytest.raises(qh.QHError) as ei:
+            _gpu(qh, x, y, zz)
+        assert ei.value.status == 2
