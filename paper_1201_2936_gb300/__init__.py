@@ -157,9 +157,10 @@ def hull2d_multi_async(clouds, outs, results: torch.Tensor, workspace: Workspace
 
 
 def hull2d_multi(clouds, *, pred: str = "f32", workspace: Optional[Workspace] = None,
-                 stream=None, return_results: bool = False):
+                 stream=None, opts: Optional[QhOpts] = None, return_results: bool = False):
     """Hulls of several 2D clouds in one persistent launch (each as hull2d).
-    Returns a list of int32 CUDA index tensors (and the result records)."""
+    Returns a list of int32 CUDA index tensors (and the result records).
+    `opts` (make_opts) replaces the defaults built from `pred`."""
     if not clouds:
         return ([], []) if return_results else []
     first = clouds[0][0] if isinstance(clouds[0], tuple) else clouds[0]
@@ -167,7 +168,7 @@ def hull2d_multi(clouds, *, pred: str = "f32", workspace: Optional[Workspace] = 
     sizes = [(_points_2d(*c) if isinstance(c, tuple) else _points_2d(c, None))[2] for c in clouds]
     outs = [torch.empty(max(n, 1), dtype=torch.int32, device=dev) for n in sizes]
     k, xs, ys, ns, ss, ps, nl = _multi_args(clouds, outs)
-    o = make_opts(pred, "persistent")
+    o = opts if opts is not None else make_opts(pred, "persistent")
     if workspace is None:
         workspace = _default_ws.setdefault(str(dev), Workspace(dev))
     ws = workspace.get(workspace_bytes_2d_multi(nl, o))

@@ -135,3 +135,14 @@ def test_exact_ties_and_filter_overflow(qh, pred):
         X, Y = _dev(x, y)
         got = qh.hull2d(X, Y, pred=pred)
         assert got.cpu().numpy().tolist() == oracle.hull2d(x, y).tolist(), c
+
+
+@pytest.mark.parametrize("ctas", [1, 2, 3])
+def test_capped_grid_long_runs(qh, ctas):
+    # few CTAs: each one's run of tiles is longer than the tile map it stages,
+    # so the producer searches the starts of straddling tiles' segments itself
+    clouds = [w.uniform_disk(700_001, 71), w.circle_jitter(500_003, 72, 1e-4),
+              w.uniform_square(300_007, 73)]
+    got = qh.hull2d_multi([_dev(x, y) for x, y in clouds], opts=qh.make_opts("f32", max_ctas=ctas))
+    for c, (x, y) in enumerate(clouds):
+        assert got[c].cpu().numpy().tolist() == oracle.hull2d(x, y).tolist(), (ctas, c)
