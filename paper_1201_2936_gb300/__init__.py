@@ -235,15 +235,17 @@ def _points_3d(x, y, z):
 
 def hull3d(x: torch.Tensor, y: Optional[torch.Tensor] = None, z: Optional[torch.Tensor] = None,
            *, pred: str = "f32", workspace: Optional[Workspace] = None, stream=None,
-           return_result: bool = False):
+           opts: Optional[QhOpts] = None, return_result: bool = False):
     """Convex hull of 3D float32 points on the GPU.
 
     Returns (vertices, face_offsets, face_indices) as int32 CUDA tensors:
     sorted vertex indices and the faces as CSR polygons (maximal coplanar
     faces, counter-clockwise from outside, starting at their smallest index,
-    sorted lexicographically).  Points are [n, 3], [3, n] or x, y, z."""
+    sorted lexicographically).  Points are [n, 3], [3, n] or x, y, z.
+    `opts` (make_opts: launch shape, limits) replaces the defaults built from
+    `pred`."""
     xp, yp, zp, n, stride, dev = _points_3d(x, y, z)
-    o = make_opts(pred, "persistent")
+    o = opts if opts is not None else make_opts(pred, "persistent")
     if workspace is None:
         workspace = _default_ws.setdefault(str(dev), Workspace(dev))
     ws = workspace.get(workspace_bytes_3d(n, o))

@@ -15,7 +15,10 @@ namespace d3 {
 // Launch shape of the persistent kernel: threads per CTA (runtime, up to
 // kMaxBlock) and points per thread of the assign pass (template: 2, 4, 8).
 constexpr int kMaxBlock = 512;
-constexpr int kDefBlock = 256;
+// default threads per CTA by predicate mode: the fastest of 128/256/512 on
+// the 8M ball and the 1M sphere (FP32 filter: 512, FP64: 256)
+constexpr int kDefBlockF32 = 512;
+constexpr int kDefBlockF64 = 256;
 constexpr int kDefItems = 4;
 constexpr int kMaxTile = 4096;           // points per assign tile (block x items), upper bound
 constexpr int kMinTile = 256;            // lower bound (sizes the tile maps)

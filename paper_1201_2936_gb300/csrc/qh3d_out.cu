@@ -144,7 +144,7 @@ Params3 make_params3(const float *x, const float *y, const float *z, int64_t n, 
     A.blk_i = (int *)(ws + L.blk_i);
     A.max_iters = o.max_iters > 0 ? o.max_iters : 4 * n + 16;
     A.wait_ns = o.wait_ns > 0 ? o.wait_ns : 2000000000ll;
-    const int block = o.block > 0 ? o.block : kDefBlock;
+    const int block = o.block > 0 ? o.block : (o.pred_mode == QH_PRED_F64 ? kDefBlockF64 : kDefBlockF32);
     const int items = o.items > 0 ? o.items : kDefItems;
     A.tile = block * items;
     return A;
@@ -673,7 +673,7 @@ static qh_status enqueue3d(Params3 &A, const Layout3 &L, char *ws, const qh_opts
                            int32_t *d_verts, int32_t *d_face_off, int32_t *d_face_idx,
                            int32_t *cloud_voff, int32_t *cloud_foff, cudaStream_t st)
 {
-    const int block = o.block > 0 ? o.block : kDefBlock;
+    const int block = o.block > 0 ? o.block : (o.pred_mode == QH_PRED_F64 ? kDefBlockF64 : kDefBlockF32);
     const int items = o.items > 0 ? o.items : kDefItems;
     if ((block != 128 && block != 256 && block != 512) || (items != 2 && items != 4 && items != 8))
         return QH_ERR_INVALID_ARG;
