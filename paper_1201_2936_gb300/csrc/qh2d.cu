@@ -38,7 +38,9 @@
 // reads the live counts back every iteration, as the paper's implementation
 // does (Section 5 cost analysis).  qh2d_multi runs several clouds' hulls in
 // one persistent launch over a shared segment table, with the lean variant
-// of the pass (pass2d_stream<..., LEAN>) and the one-atomic grid barrier.
+// of the pass (pass2d_stream<..., LEAN>), a warp-per-segment pass once the
+// segments are short (pass2d_warpseg) instead of the tail, and the one-atomic
+// grid barrier.
 
 #include <climits>
 #include <cstddef>
@@ -79,6 +81,11 @@ constexpr int kTimeline = 64;            // iterations recorded by the diagnosti
 // below this many live points the persistent kernel finishes the hull in one
 // CTA (block barriers only, no grid barriers)
 constexpr int kTailPoints = QH2D_TAIL;
+// several-cloud kernel: a pass whose segments average at most kWarpSegAvg
+// points, none longer than kWarpSegMax, gives each segment to one warp
+// (pass2d_warpseg); it has no single-CTA tail
+constexpr int kWarpSegAvg = 64;
+constexpr int kWarpSegMax = 2048;
 
 struct Seg2 {
     float e0x, e0y, qx, qy, e1x, e1y;
@@ -109,7 +116,7 @@ struct Hdr2 {
     int hull_count;
     int n_uncert;
     int iter;
-    int pad0;
+    int maxlen;         // longest segment of the next pass (several-cloud kernel)
     long long seg_total, surv_total;
     unsigned long long fallbacks, exact_argmax;
     unsigned long long phase_ns[4];  // pass, update, exact, other (persistent kernel)
@@ -2009,13 +2016,18 @@ __device__ void update2d_m(const Params2M &M, int par, bool first, SmemU &sm, in
     }
     const int S_old = *(volatile int *)&H->S[par];
     const int hull_base = *(volatile int *)&H->hull_count;
-    if (threadIdx.x == 0) H->n_uncert = 0;
+    if (threadIdx.x == 0) {
+        H->n_uncert = 0;
+        H->maxlen = 0;
+    }
     __syncthreads();
+    unsigned longest = 0;
     const int nslots = 2 * S_old;
     long long carry_k = 0, carry_v = 0;
     for (int base = 0; base < nslots; base += blockDim.x) {
         const int i = base + threadIdx.x;
         const unsigned cnt = (i < nslots) ? ac[i].cnt : 0u;
+        longest = max(longest, cnt);
         const long long packed = ((long long)(cnt > 0) << 32) | (long long)cnt;
         long long tot;
         const long long ex = block_excl_scan64(packed, sm.wsum, &tot);
@@ -2081,6 +2093,8 @@ __device__ void update2d_m(const Params2M &M, int par, bool first, SmemU &sm, in
         carry_v += tot & 0xffffffffll;
     }
     const int S_new = (int)carry_k, L_new = (int)carry_v;
+    longest = __reduce_max_sync(0xffffffffu, longest);
+    if ((threadIdx.x & 31) == 0 && longest) atomicMax(&H->maxlen, (int)longest);
     __syncthreads();
     const int ntiles = (L_new + kTile - 1) / kTile;
     auto seg_of = [&](int v) {
@@ -2111,44 +2125,86 @@ __device__ void update2d_m(const Params2M &M, int par, bool first, SmemU &sm, in
     __syncthreads();
 }
 
-// The single-CTA tail (as tail2d) with the several-cloud update.
+// A pass over short segments (several-cloud kernel): one warp per segment
+// classifies its points 32 at a time (the next 32 loaded before the current
+// ones are stored), writes child 0 from the left end of the segment's range
+// and child 1 from the right end with ballot ranks, and stores both
+// children's accumulators itself: the warp owns the segment, so there are no
+// reservation or key atomics.
 template <class P>
-__device__ void tail2d_m(const Params2M &M, int t, SmemAll &sm)
+__device__ void pass2d_warpseg(const Params2 &A, int par, int bid, int nb)
 {
-    const Params2 &A = M.A;
     Hdr2 *H = A.hdr;
-    const bool clk = threadIdx.x == 0;
-    for (;;) {
-        const unsigned long long t0 = clk ? globaltimer_ns() : 0;
-        if (threadIdx.x == 0) H->iter = t;
-        pass2d<P, false>(A, t & 1, sm.pass, 0, 1);
-        __syncthreads();
-        const unsigned long long t1 = clk ? globaltimer_ns() : 0;
-        update2d_m(M, t & 1, false, sm.u, INT_MAX);
-        if (clk) {
-            const unsigned long long t2 = globaltimer_ns();
-            H->phase_ns[0] += t1 - t0;
-            H->phase_ns[1] += t2 - t1;
-            if (t < kTimeline) {
-                H->tl[t][0] = *(volatile int *)&H->L[t & 1];
-                H->tl[t][1] = *(volatile int *)&H->S[t & 1];
-                H->tl[t][2] += (long long)(t1 - t0);
-                H->tl[t][3] += (long long)(t2 - t1);
+    const int S = vload_i(&H->S[par]);
+    const Seg2 *seg = A.seg[par];
+    Acc2 *acc = A.acc[par];
+    const float2 *ixy = A.bxy[par ^ 1];
+    const int *ii = A.bi[par ^ 1];
+    float2 *oxy = A.bxy[par];
+    int *oi = A.bi[par];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const int wpb = blockDim.x >> 5;
+    unsigned fallbacks = 0;
+    for (int sg = bid * wpb + (threadIdx.x >> 5); sg < S; sg += nb * wpb) {
+        const Geo2 g = geo_of(seg[sg]);
+        const int ps = g.pstart, len = g.len;
+        Far2 fa = {0u, 0u, 0u, 0}, fb = {0u, 0u, 0u, 0};
+        int n0 = 0, n1 = 0;
+        float2 cp = make_float2(0.f, 0.f);
+        int ci = 0;
+        if (lane < len) {
+            cp = ixy[ps + lane];
+            ci = ii[ps + lane];
+        }
+        for (int b = 0; b < len; b += 32) {
+            const int i = b + lane;
+            float2 np = make_float2(0.f, 0.f);
+            int ni = 0;
+            if (i + 32 < len) {
+                np = ixy[ps + i + 32];
+                ni = ii[ps + i + 32];
             }
+            int c = 3;
+            float d = 0.f, e = 0.f;
+            if (i < len) c = classify2d<P>(g, cp.x, cp.y, ci, d, e, fallbacks);
+            const unsigned b0 = __ballot_sync(0xffffffffu, c == 0);
+            const unsigned b1 = __ballot_sync(0xffffffffu, c == 1);
+            if (c == 0) {
+                const int dst = ps + n0 + __popc(b0 & lt);
+                oxy[dst] = cp;
+                oi[dst] = ci;
+                far2_add(fa, ord_f32(d), ci, __float_as_uint(e));
+            } else if (c == 1) {
+                const int dst = ps + len - 1 - (n1 + __popc(b1 & lt));
+                oxy[dst] = cp;
+                oi[dst] = ci;
+                far2_add(fb, ord_f32(d), ci, __float_as_uint(e));
+            }
+            n0 += __popc(b0);
+            n1 += __popc(b1);
+            cp = np;
+            ci = ni;
         }
-        __syncthreads();
-        if (*(volatile int *)&H->status) break;
-        if (*(volatile int *)&H->n_uncert > 0) {
-            exact2d<P>(A, t & 1, sm.x, 0, 1);
-            __syncthreads();
-        }
-        if (*(volatile int *)&H->S[(t + 1) & 1] == 0) break;
-        t++;
-        if (t > A.max_iters) {
-            if (threadIdx.x == 0) set_status(H, kStNoConv);
-            break;
+        Top2 ta = far2_top2(fa), tb = far2_top2(fb);
+        top2_warp(ta);
+        top2_warp(tb);
+        if (lane == 0) {
+            Acc2 a0 = {}, a1 = {};
+            a0.key1 = ta.k1;
+            a0.o2 = ta.o2;
+            a0.cnt = (unsigned)n0;
+            a0.emax = ta.em;
+            a1.key1 = tb.k1;
+            a1.o2 = tb.o2;
+            a1.cnt = (unsigned)n1;
+            a1.emax = tb.em;
+            acc[2 * sg] = a0;
+            acc[2 * sg + 1] = a1;
         }
     }
+    const unsigned f = __reduce_add_sync(0xffffffffu, fallbacks);
+    if (lane == 0 && f) atomicAdd(&H->fallbacks, (unsigned long long)f);
 }
 
 // Output of every cloud (block 0): the hull links of all clouds ranked at
@@ -2352,9 +2408,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_multi(Params2M M)
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(H, kStTimeout);
     } else {
         int t = 0;
-        bool tail = false;
         while (*(volatile int *)&H->status == 0) {
-            if (blockIdx.x == 0) update2d_m(M, t & 1, t == 0, sm.u, kTailPoints);
+            if (blockIdx.x == 0) update2d_m(M, t & 1, t == 0, sm.u, 0);
             sync_as(1);
             if (*(volatile int *)&H->status) break;
             if (*(volatile int *)&H->n_uncert > 0) {
@@ -2367,19 +2422,15 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_multi(Params2M M)
                 if (blockIdx.x == 0 && threadIdx.x == 0) set_status(H, kStNoConv);
                 break;
             }
-            if (*(volatile int *)&H->L[t & 1] < kTailPoints) {
-                tail = true;
-                break;
-            }
+            const int Lt = *(volatile int *)&H->L[t & 1], St = *(volatile int *)&H->S[t & 1];
             if (blockIdx.x == 0 && threadIdx.x == 0) H->iter = t;
             it = t;
-            pass2d_stream<P, false, true, true>(A, t & 1, sp, bars, ph, blockIdx.x, gridDim.x);
+            if ((long long)Lt <= (long long)kWarpSegAvg * St &&
+                *(volatile int *)&H->maxlen <= kWarpSegMax)
+                pass2d_warpseg<P>(A, t & 1, blockIdx.x, gridDim.x);
+            else
+                pass2d_stream<P, false, true, true>(A, t & 1, sp, bars, ph, blockIdx.x, gridDim.x);
             sync_as(0);
-        }
-        if (tail && blockIdx.x == 0) {
-            tprev = 0;
-            tail2d_m<P>(M, t, sm);
-            if (clk) tprev = globaltimer_ns();
         }
     }
     sync_as(3);
