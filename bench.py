@@ -643,7 +643,7 @@ def main():
     sres = [qh.result_from_tensor(r) for r in results]
     line["separate_launches"] = {
         "value": round(pts_per_step / (sms / 1e3) / 1e6, 2), "unit": UNIT,
-        "ms_per_step": round(sms, 3), "kernel": "qh2d_persistent<PredF32>, one launch per cloud",
+        "ms_per_step": round(sms, 3), "kernel": "qh2d_multi<PredF32>, one cloud per launch (qh_hull2d)",
         "same_hulls": all(sres[i].count == res[i].count for i in range(nl))}
 
     # ---- plain GPU path: FP64 predicates, host loop with per-iteration readback

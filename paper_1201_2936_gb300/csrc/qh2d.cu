@@ -32,15 +32,14 @@
 //                 each (certified exact when the FP32 top-2 gap exceeds the
 //                 error bound), hull slots and links.
 //   X  (exact2d)  only for uncertified segments: exact farthest point.
-// The persistent kernel runs all iterations with grid barriers; below
-// kTailPoints live points block 0 finishes alone (tail2d) with the
-// synchronous pass (pass2d).  The host-loop variant launches each phase and
+// The persistent kernel (qh2d_multi) runs all iterations of up to
+// QH_MAX_CLOUDS_2D clouds with grid barriers over a shared segment table (a
+// single-cloud call is one cloud): the streaming pass (pass2d_stream), a
+// warp-per-segment pass once the segments are short (pass2d_warpseg), the
+// update, and the exact argmax split over CTAs (exact2d_split).  The
+// host-loop variant launches each phase (the synchronous pass pass2d) and
 // reads the live counts back every iteration, as the paper's implementation
-// does (Section 5 cost analysis).  qh2d_multi runs several clouds' hulls in
-// one persistent launch over a shared segment table, with the lean variant
-// of the pass (pass2d_stream<..., LEAN>), a warp-per-segment pass once the
-// segments are short (pass2d_warpseg) instead of the tail, and the one-atomic
-// grid barrier.
+// does (Section 5 cost analysis).
 
 #include <climits>
 #include <cstddef>
@@ -75,15 +74,8 @@ constexpr int kOutCap = 4096;            // hull slots ranked in one block's sha
 constexpr int kMaxGrid = 4096;
 constexpr int kMinBlocks = QH2D_MINBLOCKS;  // resident CTAs per SM the register budget targets
 constexpr int kTimeline = 64;            // iterations recorded by the diagnostic timeline
-#ifndef QH2D_TAIL
-#define QH2D_TAIL 4096
-#endif
-// below this many live points the persistent kernel finishes the hull in one
-// CTA (block barriers only, no grid barriers)
-constexpr int kTailPoints = QH2D_TAIL;
-// several-cloud kernel: a pass whose segments average at most kWarpSegAvg
-// points, none longer than kWarpSegMax, gives each segment to one warp
-// (pass2d_warpseg); it has no single-CTA tail
+// a pass whose segments average at most kWarpSegAvg points, none longer than
+// kWarpSegMax, gives each segment to one warp (pass2d_warpseg)
 constexpr int kWarpSegAvg = 64;
 constexpr int kWarpSegMax = 2048;
 
@@ -1786,138 +1778,6 @@ extern __shared__ __align__(16) unsigned char qh2d_dsm[];
 constexpr size_t kPersistSmem =
     sizeof(SmemAll) > sizeof(SmemStream) ? sizeof(SmemAll) : sizeof(SmemStream);
 
-// The last iterations, once fewer than kTailPoints points are live, in one
-// CTA: the same pass, update and exact-argmax steps with block barriers only,
-// while the other CTAs wait at the kernel's final grid barrier.  t is the
-// iteration of the first pass to run; its tile map is in place.
-template <class P>
-__device__ void tail2d(const Params2 &A, int t, SmemAll &sm)
-{
-    Hdr2 *H = A.hdr;
-    const bool clk = threadIdx.x == 0;
-    for (;;) {
-        const unsigned long long t0 = clk ? globaltimer_ns() : 0;
-        if (threadIdx.x == 0) H->iter = t;
-        pass2d<P, false>(A, t & 1, sm.pass, 0, 1);
-        __syncthreads();
-        const unsigned long long t1 = clk ? globaltimer_ns() : 0;
-        update2d(A, t & 1, false, sm.u, INT_MAX);
-        if (clk) {
-            const unsigned long long t2 = globaltimer_ns();
-            H->phase_ns[0] += t1 - t0;
-            H->phase_ns[1] += t2 - t1;
-            if (t < kTimeline) {
-                H->tl[t][0] = *(volatile int *)&H->L[t & 1];
-                H->tl[t][1] = *(volatile int *)&H->S[t & 1];
-                H->tl[t][2] += (long long)(t1 - t0);
-                H->tl[t][3] += (long long)(t2 - t1);
-            }
-        }
-        __syncthreads();
-        if (*(volatile int *)&H->status) break;
-        if (*(volatile int *)&H->n_uncert > 0) {
-            exact2d<P>(A, t & 1, sm.x, 0, 1);
-            __syncthreads();
-        }
-        if (*(volatile int *)&H->S[(t + 1) & 1] == 0) break;
-        t++;
-        if (t > A.max_iters) {
-            if (threadIdx.x == 0) set_status(H, kStNoConv);
-            break;
-        }
-    }
-}
-
-template <class P>
-__global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_persistent(Params2 A)
-{
-    SmemAll &sm = *reinterpret_cast<SmemAll *>(qh2d_dsm);
-    SmemStream &sp = *reinterpret_cast<SmemStream *>(qh2d_dsm);
-    __shared__ PipeBars bars;
-    unsigned ph = 0;  // this thread's parities of the pipeline barriers' next phases
-    if (threadIdx.x == 0) {
-        for (int b = 0; b < kRing; b++) {
-            mbar_init(&bars.full[b], 1);
-            mbar_init(&bars.empty[b], kCW);
-        }
-        for (int b = 0; b < 2; b++) {
-            mbar_init(&bars.counted[b], kCW);
-            mbar_init(&bars.bases[b], 1);
-        }
-        fence_mbar_init();
-    }
-    __syncthreads();
-    Hdr2 *H = A.hdr;
-    int *fail = &H->status;
-    // phase clock (block 0, thread 0): time from one barrier exit to the next
-    const bool clk = blockIdx.x == 0 && threadIdx.x == 0;
-    unsigned long long tprev = clk ? globaltimer_ns() : 0;
-    int it = 0;  // iteration being recorded (0 = first split)
-    auto sync_as = [&](int cat) {
-        grid_sync(&H->bar, fail, A.wait_ns);
-        if (clk) {
-            unsigned long long t = globaltimer_ns();
-            H->phase_ns[cat] += t - tprev;
-            if (it < kTimeline && cat < 2) {
-                H->tl[it][2 + cat] += (long long)(t - tprev);
-                if (cat == 0) {
-                    H->tl[it][0] = *(volatile int *)&H->L[it & 1];
-                    H->tl[it][1] = *(volatile int *)&H->S[it & 1];
-                }
-            }
-            tprev = t;
-        }
-    };
-    init2d(A);
-    sync_as(3);
-    const Ext2 ext = extrema2d(A, sm);
-    sync_as(3);
-    // the lowest index of each global extreme (read by the first update,
-    // after the first pass's grid barrier)
-    if (threadIdx.x == 0 && A.n > 0) {
-        if (ext.mn == *(volatile unsigned long long *)&H->lexmin) atomicMin(&H->a_idx, ext.mni);
-        if (ext.mx == *(volatile unsigned long long *)&H->lexmax) atomicMin(&H->b_idx, ext.mxi);
-    }
-    if (*(volatile int *)&H->nonfinite) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(H, kStNonfinite);
-    } else if (*(volatile int *)&H->status == 0) {
-        pass2d_stream<P, true>(A, 0, sp, bars, ph, blockIdx.x, gridDim.x);
-        sync_as(0);
-        int t = 0;
-        bool tail = false;
-        while (*(volatile int *)&H->status == 0) {
-            if (blockIdx.x == 0) update2d(A, t & 1, t == 0, sm.u, kTailPoints);
-            sync_as(1);
-            if (*(volatile int *)&H->status) break;
-            if (*(volatile int *)&H->n_uncert > 0) {
-                exact2d<P>(A, t & 1, sm.x, blockIdx.x, gridDim.x);
-                sync_as(2);
-            }
-            if (*(volatile int *)&H->S[(t + 1) & 1] == 0) break;
-            t++;
-            if (t > A.max_iters) {
-                if (blockIdx.x == 0 && threadIdx.x == 0) set_status(H, kStNoConv);
-                break;
-            }
-            if (*(volatile int *)&H->L[t & 1] < kTailPoints) {
-                tail = true;
-                break;
-            }
-            if (blockIdx.x == 0 && threadIdx.x == 0) H->iter = t;
-            it = t;
-            pass2d_stream<P, false>(A, t & 1, sp, bars, ph, blockIdx.x, gridDim.x);
-            sync_as(0);
-        }
-        if (tail && blockIdx.x == 0) {
-            tprev = 0;
-            tail2d<P>(A, t, sm);
-            if (clk) tprev = globaltimer_ns();
-        }
-    }
-    sync_as(3);
-    if (blockIdx.x == 0) output2d(A, sm.out);
-}
-
 // ---------------------------------------------------------------- several clouds
 // qh_hull2d_multi: K independent clouds in one persistent launch.  The
 // clouds' live points share the segment table and the point buffers (cloud c
@@ -2123,6 +1983,146 @@ __device__ void update2d_m(const Params2M &M, int par, bool first, SmemU &sm, in
         H->exact_argmax += H->n_uncert;
     }
     __syncthreads();
+}
+
+// The exact argmax of the several-cloud kernel.  With fewer uncertified
+// segments than CTAs each segment's points are split into `per` chunks, one
+// CTA each (a tie at the top of a large segment, e.g. a duplicated extreme
+// point, would otherwise leave millions of points to one CTA).  A chunk's
+// best (exact comparison, then lowest index) goes to slot w of the point
+// buffers of the other parity, free until the next pass writes them, and
+// exact2d_merge reduces the chunks after a grid barrier.  per = 1 is exact2d.
+// Chunks of at least kExactChunk points (of the longest such segment): a
+// shorter segment costs a CTA less than the extra barrier and merge.  Every
+// CTA reads the same lengths, so all agree on per.
+constexpr int kExactChunk = 65536;
+__device__ int exact_chunks2d(const Params2 &A, int par, SmemX &sm, int nu, int nb)
+{
+    if (nu <= 0) return 1;
+    long long cap = nb / nu;
+    if (cap * nu > (long long)A.n) cap = A.n / nu;
+    if (cap <= 1) return 1;
+    const Seg2 *sn = A.seg[par ^ 1];
+    int mx = 0;
+    for (int u = threadIdx.x; u < nu; u += blockDim.x) mx = max(mx, sn[A.uncert[u]].len);
+    mx = (int)__reduce_max_sync(0xffffffffu, (unsigned)mx);
+    if ((threadIdx.x & 31) == 0) sm.bidx[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    int m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = max(m, sm.bidx[w]);
+    __syncthreads();
+    const long long want = ((long long)m + kExactChunk - 1) / kExactChunk;
+    return (int)max(1ll, min(cap, want));
+}
+
+template <class P>
+__device__ void exact2d_split(const Params2 &A, int par, SmemX &sm, int bid, int nb, int per)
+{
+    Hdr2 *H = A.hdr;
+    const int nu = *(volatile int *)&H->n_uncert;
+    Seg2 *sn = A.seg[par ^ 1];
+    const float2 *bxy = A.bxy[par];
+    const int *bi = A.bi[par];
+    float2 *cxy = A.bxy[par ^ 1];
+    int *ci = A.bi[par ^ 1];
+    for (int w = bid; w < nu * per; w += nb) {
+        const int u = w / per, q = w - u * per;
+        const int k = A.uncert[u];
+        const Seg2 g = sn[k];
+        const int i0 = (int)((long long)g.len * q / per), i1 = (int)((long long)g.len * (q + 1) / per);
+        int best = -1;
+        float bxv = 0.f, byv = 0.f;
+        for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const int pos = g.pstart + i;
+            const float2 p = bxy[pos];
+            const int idx = bi[pos];
+            float d, e;
+            orient_value<P>(g.e0x, g.e0y, g.e1x, g.e1y, p.x, p.y, d, e);
+            if ((double)d + (double)e < (double)g.thr) continue;
+            if (best >= 0) {
+                const int c = cmp_dist_exact(g.e0x, g.e0y, g.e1x, g.e1y, p.x, p.y, bxv, byv);
+                if (!(c > 0 || (c == 0 && idx < best))) continue;
+            }
+            best = idx;
+            bxv = p.x;
+            byv = p.y;
+        }
+        sm.bidx[threadIdx.x] = best;
+        sm.bx[threadIdx.x] = bxv;
+        sm.by[threadIdx.x] = byv;
+        __syncthreads();
+        for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+            if (threadIdx.x < st) {
+                const int o = threadIdx.x + st;
+                const int oi = sm.bidx[o];
+                if (oi >= 0) {
+                    const int mi = sm.bidx[threadIdx.x];
+                    bool take = mi < 0;
+                    if (!take) {
+                        const int c = cmp_dist_exact(g.e0x, g.e0y, g.e1x, g.e1y, sm.bx[o], sm.by[o],
+                                                     sm.bx[threadIdx.x], sm.by[threadIdx.x]);
+                        take = c > 0 || (c == 0 && oi < mi);
+                    }
+                    if (take) {
+                        sm.bidx[threadIdx.x] = oi;
+                        sm.bx[threadIdx.x] = sm.bx[o];
+                        sm.by[threadIdx.x] = sm.by[o];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            if (per > 1) {
+                ci[w] = sm.bidx[0];
+                cxy[w] = make_float2(sm.bx[0], sm.by[0]);
+            } else if (sm.bidx[0] >= 0) {
+                sn[k].q_idx = sm.bidx[0];
+                sn[k].qx = sm.bx[0];
+                sn[k].qy = sm.by[0];
+                A.hull_idx[g.q_slot] = sm.bidx[0];
+                A.hull_x[g.q_slot] = sm.bx[0];
+                A.hull_y[g.q_slot] = sm.by[0];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// The chunks' bests of each uncertified segment, one thread per segment.
+__device__ void exact2d_merge(const Params2 &A, int par, int bid, int nb, int per)
+{
+    Hdr2 *H = A.hdr;
+    const int nu = *(volatile int *)&H->n_uncert;
+    Seg2 *sn = A.seg[par ^ 1];
+    const float2 *cxy = A.bxy[par ^ 1];
+    const int *ci = A.bi[par ^ 1];
+    for (int u = bid * blockDim.x + threadIdx.x; u < nu; u += nb * blockDim.x) {
+        const int k = A.uncert[u];
+        const Seg2 g = sn[k];
+        int best = -1;
+        float bxv = 0.f, byv = 0.f;
+        for (int q = 0; q < per; q++) {
+            const int idx = ci[u * per + q];
+            if (idx < 0) continue;
+            const float2 p = cxy[u * per + q];
+            if (best >= 0) {
+                const int c = cmp_dist_exact(g.e0x, g.e0y, g.e1x, g.e1y, p.x, p.y, bxv, byv);
+                if (!(c > 0 || (c == 0 && idx < best))) continue;
+            }
+            best = idx;
+            bxv = p.x;
+            byv = p.y;
+        }
+        if (best >= 0) {
+            sn[k].q_idx = best;
+            sn[k].qx = bxv;
+            sn[k].qy = byv;
+            A.hull_idx[g.q_slot] = best;
+            A.hull_x[g.q_slot] = bxv;
+            A.hull_y[g.q_slot] = byv;
+        }
+    }
 }
 
 // A pass over short segments (several-cloud kernel): one warp per segment
@@ -2412,9 +2412,15 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_multi(Params2M M)
             if (blockIdx.x == 0) update2d_m(M, t & 1, t == 0, sm.u, 0);
             sync_as(1);
             if (*(volatile int *)&H->status) break;
-            if (*(volatile int *)&H->n_uncert > 0) {
-                exact2d<P>(A, t & 1, sm.x, blockIdx.x, gridDim.x);
+            const int nu = *(volatile int *)&H->n_uncert;
+            if (nu > 0) {
+                const int per = exact_chunks2d(A, t & 1, sm.x, nu, gridDim.x);
+                exact2d_split<P>(A, t & 1, sm.x, blockIdx.x, gridDim.x, per);
                 sync_as(2);
+                if (per > 1) {
+                    exact2d_merge(A, t & 1, blockIdx.x, gridDim.x, per);
+                    sync_as(2);
+                }
             }
             if (*(volatile int *)&H->S[(t + 1) & 1] == 0) break;
             t++;
@@ -2622,29 +2628,6 @@ static qh_status run2d(const Params2 &A, const qh_opts &o, cudaStream_t st)
 {
     if (cudaMemsetAsync(A.hdr, 0, sizeof(Hdr2), st) != cudaSuccess) return QH_ERR_CUDA;
     int grid = 0;
-    if (o.loop_mode == QH_LOOP_PERSISTENT) {
-        const void *fn = (const void *)qh2d_persistent<P>;
-        static std::once_flag attr_once;
-        static cudaError_t attr_err = cudaSuccess;
-        std::call_once(attr_once, [&]() {
-            attr_err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)kPersistSmem);
-        });
-        if (attr_err != cudaSuccess) return QH_ERR_CUDA;
-        grid = persistent_grid_smem(fn, kBlock, o.blocks_per_sm, kPersistSmem);
-        if (grid <= 0) return QH_ERR_CUDA;
-        grid = grid > kMaxGrid ? kMaxGrid : grid;
-        if (o.max_ctas > 0 && grid > o.max_ctas) grid = o.max_ctas;
-        // no more CTAs than the first pass has tiles: a small hull's grid
-        // barriers then involve few CTAs
-        const int first_tiles = (int)((A.n + kTile - 1) / kTile);
-        if (grid > first_tiles) grid = first_tiles > 0 ? first_tiles : 1;
-        Params2 a = A;
-        void *args[] = {&a};
-        cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args,
-                                                    kPersistSmem, st);
-        return e == cudaSuccess ? QH_OK : QH_ERR_CUDA;
-    }
     // host-driven loop: one launch per phase, live counts read back each iteration
     grid = persistent_grid((const void *)k_pass2d<P, false>, kBlock, o.blocks_per_sm);
     if (grid <= 0) return QH_ERR_CUDA;
@@ -2757,7 +2740,7 @@ static qh_status multi_params(int32_t k, const float *const *h_dx, const float *
         if ((n - 1) * s > (int64_t)1 << 40) return QH_ERR_INVALID_ARG;
         N += n;
     }
-    if (N > QH_MAX_POINTS - 2 * kMaxClouds) return QH_ERR_INVALID_ARG;
+    if (N > QH_MAX_POINTS - 2 * (int64_t)k) return QH_ERR_INVALID_ARG;
     LM = layout2d_multi(k, N);
     if (ws_bytes < LM.total || ((uintptr_t)d_ws & 255)) return QH_ERR_NOMEM;
     char *ws = (char *)d_ws;
@@ -2866,7 +2849,9 @@ extern "C" size_t qh_workspace_bytes_2d(int64_t n, const qh_opts *opts)
 {
     (void)opts;
     if (n < 0 || n > QH_MAX_POINTS) return 0;
-    return layout2d(n).total;
+    // the persistent loop runs the several-cloud kernel with one cloud
+    const size_t a = layout2d(n).total, b = layout2d_multi(1, n).total;
+    return a > b ? a : b;
 }
 
 extern "C" qh_status qh_hull2d_async(const float *d_x, const float *d_y, int64_t n, int64_t stride,
@@ -2881,11 +2866,18 @@ extern "C" qh_status qh_hull2d_async(const float *d_x, const float *d_y, int64_t
     if (o.pred_mode != QH_PRED_F32 && o.pred_mode != QH_PRED_F64) return QH_ERR_INVALID_ARG;
     if (o.loop_mode != QH_LOOP_PERSISTENT && o.loop_mode != QH_LOOP_HOST) return QH_ERR_INVALID_ARG;
     if ((n - 1) * stride > (int64_t)1 << 40) return QH_ERR_INVALID_ARG;
-    Layout2 L = layout2d(n);
-    if (ws_bytes < L.total || ((uintptr_t)d_ws & 255)) return QH_ERR_NOMEM;
+    if (ws_bytes < qh_workspace_bytes_2d(n, &o) || ((uintptr_t)d_ws & 255)) return QH_ERR_NOMEM;
     if (n == 0)
         return cudaMemsetAsync(d_result, 0, sizeof(qh_result), stream) == cudaSuccess ? QH_OK
                                                                                      : QH_ERR_CUDA;
+    if (o.loop_mode == QH_LOOP_PERSISTENT) {
+        // the several-cloud persistent kernel with one cloud
+        const float *xs[1] = {d_x}, *ys[1] = {d_y};
+        const int64_t ns[1] = {n}, ss[1] = {stride};
+        int32_t *os[1] = {d_out_idx};
+        return qh_hull2d_multi_async(1, xs, ys, ns, ss, os, d_result, d_ws, ws_bytes, &o, stream);
+    }
+    Layout2 L = layout2d(n);
     Params2 A = make_params(d_x, d_y, n, stride, d_out_idx, d_result, (char *)d_ws, L, o);
     if (o.pred_mode == QH_PRED_F32) return run2d<PredF32>(A, o, stream);
     return run2d<PredF64>(A, o, stream);
@@ -2909,8 +2901,7 @@ extern "C" qh_status qh_hull2d_noalloc(const float *d_x, const float *d_y, int64
 {
     if (n < 0 || n > QH_NOALLOC_MAX_POINTS || stride < 1 || !h_count) return QH_ERR_INVALID_ARG;
     if (n > 0 && (!d_x || !d_y || !d_out_idx)) return QH_ERR_INVALID_ARG;
-    Layout2 L = layout2d(n);
-    if (L.total > kNoAllocBytes) return QH_ERR_CAPACITY;
+    if (qh_workspace_bytes_2d(n, nullptr) > kNoAllocBytes) return QH_ERR_CAPACITY;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return QH_ERR_CUDA;
     void *ws = nullptr;
@@ -2956,21 +2947,24 @@ extern "C" qh_status qh_hull2d(const float *d_x, const float *d_y, int64_t n, in
                                cudaStream_t stream)
 {
     if (n < 0 || n > QH_MAX_POINTS || !d_ws) return QH_ERR_INVALID_ARG;
+    qh_opts o;
+    qh_default_opts(&o);
+    if (opts) o = *opts;
+    if (ws_bytes < qh_workspace_bytes_2d(n, &o) || ((uintptr_t)d_ws & 255)) return QH_ERR_NOMEM;
+    const bool host_loop = o.loop_mode == QH_LOOP_HOST;
     Layout2 L = layout2d(n);
-    if (ws_bytes < L.total || ((uintptr_t)d_ws & 255)) return QH_ERR_NOMEM;
-    qh_result *d_res = (qh_result *)((char *)d_ws + L.res);
-    qh_status s = qh_hull2d_async(d_x, d_y, n, stride, d_out_idx, d_res, d_ws, ws_bytes, opts, stream);
+    // the result record: a slot of the workspace the chosen loop leaves free
+    qh_result *d_res =
+        (qh_result *)((char *)d_ws + (host_loop ? L.res : layout2d_multi(1, n).res));
+    qh_status s = qh_hull2d_async(d_x, d_y, n, stride, d_out_idx, d_res, d_ws, ws_bytes, &o, stream);
     if (s != QH_OK) return s;
     qh_result r;
     if (cudaMemcpyAsync(&r, d_res, sizeof(r), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
         cudaStreamSynchronize(stream) != cudaSuccess)
         return QH_ERR_CUDA;
-    if (r.status == QH_ERR_CAPACITY && n > 0) {
-        // a hull with more slots than the in-kernel output step ranks: the
+    if (host_loop && r.status == QH_ERR_CAPACITY && n > 0) {
+        // a hull with more slots than the host loop's output step ranks: the
         // large-hull output step (it leaves other capacity errors as they are)
-        qh_opts o;
-        qh_default_opts(&o);
-        if (opts) o = *opts;
         const Params2 A = make_params(d_x, d_y, n, stride, d_out_idx, d_res, (char *)d_ws, L, o);
         k_output2d_big<<<1, kBlock, 0, stream>>>(A);
         if (cudaGetLastError() != cudaSuccess ||

@@ -146,3 +146,19 @@ def test_capped_grid_long_runs(qh, ctas):
     got = qh.hull2d_multi([_dev(x, y) for x, y in clouds], opts=qh.make_opts("f32", max_ctas=ctas))
     for c, (x, y) in enumerate(clouds):
         assert got[c].cpu().numpy().tolist() == oracle.hull2d(x, y).tolist(), (ctas, c)
+
+
+def test_duplicated_hull_vertices_large(qh):
+    # every hull vertex of a 4M-point disk repeated at a higher index: each
+    # segment's farthest point ties, so no apex is certified and the large
+    # early segments go through the exact argmax split over many CTAs; the
+    # hull keeps the lower index of every pair
+    x, y = w.uniform_disk(4_000_000, 81)
+    h = oracle.hull2d(x, y)
+    xd = np.concatenate([x, x[h]]).astype(np.float32)
+    yd = np.concatenate([y, y[h]]).astype(np.float32)
+    sq = w.uniform_square(1_000_000, 82)
+    got, res = qh.hull2d_multi([_dev(xd, yd), _dev(*sq)], return_results=True)
+    assert got[0].cpu().numpy().tolist() == oracle.hull2d(xd, yd).tolist() == h.tolist()
+    assert got[1].cpu().numpy().tolist() == oracle.hull2d(*sq).tolist()
+    assert res[0]["exact_argmax"] > 0
