@@ -781,12 +781,12 @@ __device__ __forceinline__ int classify2d(const Geo2 &g, float x, float y, int i
 // kSItems rows, classified, reserved per (segment, child) group and
 // scattered.  Keys of the tile's first kMSlot segments go to the slots of
 // parity p (merged by the producer), the others to the accumulators.
-// STAGED: the virtual starts of the tile's m segments are in tvs (shared).
-template <class P, bool STAGED = false>
+// The virtual starts of the tile's m segments are in tvs (shared memory).
+template <class P>
 __device__ __forceinline__ void multi_tile(SmemStream &sm, const Seg2 *seg, Acc2 *acc, int sf,
                                            int m, int v0, int v1, int p, const float2 *ixy,
                                            const int *ii, float2 *oxy, int *oi,
-                                           unsigned &fallbacks, const int *tvs = nullptr)
+                                           unsigned &fallbacks, const int *tvs)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
@@ -821,7 +821,7 @@ __device__ __forceinline__ void multi_tile(SmemStream &sm, const Seg2 *seg, Acc2
                 int lo = 0, hi = m - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
-                    if ((STAGED ? tvs[mid] : seg[sf + mid].vstart) <= v) lo = mid;
+                    if (tvs[mid] <= v) lo = mid;
                     else hi = mid - 1;
                 }
                 ls = lo;
@@ -906,12 +906,12 @@ __device__ __forceinline__ Top2 far2_top2(const Far2 &a)
 // segment start counting as two more tiles (a tile that straddles segments
 // is finished warp by warp with a chain of global round trips), so that runs
 // over many small segments do not fall on a few CTAs.
-// LEAN: single-segment tiles keep per-thread Far2 records and counts instead
-// of 64-bit keys and per-row ballots, the scatter loads a warp's items before
-// storing them, the producer publishes a tile's bases as soon as they are
-// reserved and stages the segment starts of a tile that straddles segments,
-// and the cost-weighted run ends are found by all threads at once.
-template <class P, bool FIRST, bool WEIGHTED = false, bool LEAN = false>
+// Single-segment tiles keep per-thread Far2 records and counts, the scatter
+// loads a warp's items before storing them, the producer publishes a tile's
+// bases as soon as they are reserved and stages the segment starts of a tile
+// that straddles segments, and the cost-weighted run ends are found by all
+// threads at once.
+template <class P, bool FIRST, bool WEIGHTED = false>
 __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBars &bars,
                               unsigned &ph, int bid, int nb)
 {
@@ -964,54 +964,34 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
             return t == 0 ? 0ll : (long long)t + 2ll * (seg_of(t * kSTile - 1, vs_smem) + 1);
         };
         const long long W = cost(ntiles);
-        if constexpr (LEAN) {
-            // the first tile with cost >= target, for the run's two ends at
-            // once (threads 0-127: its start, 128-255: its end): each round
-            // probes 128 evenly spaced tiles of the interval [lo, hi] that
-            // holds the answer and keeps the gap between the last probe
-            // below the target and the first one at or above it
-            static_assert(kBlock == 256, "two halves of 128 probes");
-            const int half = threadIdx.x >> 7, hl = threadIdx.x & 127;
-            const long long target = W * (bid + half) / nb;
-            int *nbelow = sm.run_sf;  // per-warp counts (the run map is built later)
-            int lo = 0, hi = ntiles;
-            auto probe = [&](int i) { return lo + (int)(((long long)(i + 1) * (hi - lo)) >> 7); };
-            for (int span = ntiles; span > 0; span >>= 7) {
-                const bool below = cost(probe(hl)) < target;
-                const unsigned b = __ballot_sync(0xffffffffu, below);
-                if (lane == 0) nbelow[warp] = __popc(b);
-                __syncthreads();
-                const int q = half * 4;
-                const int nf = nbelow[q] + nbelow[q + 1] + nbelow[q + 2] + nbelow[q + 3];
-                __syncthreads();
-                // probes 0..nf-1 are below the target, probe nf (<= 127) is not
-                const int nlo = nf == 0 ? lo : probe(nf - 1) + 1, nhi = probe(nf);
-                lo = nlo;
-                hi = nhi;
-            }
-            if (hl == 0) sm.shift[half] = lo;  // (the stage shifts are not in use yet)
+        // the first tile with cost >= target, for the run's two ends at
+        // once (threads 0-127: its start, 128-255: its end): each round
+        // probes 128 evenly spaced tiles of the interval [lo, hi] that
+        // holds the answer and keeps the gap between the last probe
+        // below the target and the first one at or above it
+        static_assert(kBlock == 256, "two halves of 128 probes");
+        const int half = threadIdx.x >> 7, hl = threadIdx.x & 127;
+        const long long target = W * (bid + half) / nb;
+        int *nbelow = sm.run_sf;  // per-warp counts (the run map is built later)
+        int lo = 0, hi = ntiles;
+        auto probe = [&](int i) { return lo + (int)(((long long)(i + 1) * (hi - lo)) >> 7); };
+        for (int span = ntiles; span > 0; span >>= 7) {
+            const bool below = cost(probe(hl)) < target;
+            const unsigned b = __ballot_sync(0xffffffffu, below);
+            if (lane == 0) nbelow[warp] = __popc(b);
             __syncthreads();
-            t_begin = sm.shift[0];
-            nt = sm.shift[1] - sm.shift[0];
-        } else {
-        if (threadIdx.x == 0) {
-            auto first_at = [&](long long target) {
-                int lo = 0, hi = ntiles;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (cost(mid) >= target) hi = mid;
-                    else lo = mid + 1;
-                }
-                return lo;
-            };
-            const int tb = first_at(W * bid / nb), te = first_at(W * (bid + 1) / nb);
-            sm.shift[0] = tb;  // (the stage shifts are not in use yet)
-            sm.shift[1] = te - tb;
+            const int q = half * 4;
+            const int nf = nbelow[q] + nbelow[q + 1] + nbelow[q + 2] + nbelow[q + 3];
+            __syncthreads();
+            // probes 0..nf-1 are below the target, probe nf (<= 127) is not
+            const int nlo = nf == 0 ? lo : probe(nf - 1) + 1, nhi = probe(nf);
+            lo = nlo;
+            hi = nhi;
         }
+        if (hl == 0) sm.shift[half] = lo;  // (the stage shifts are not in use yet)
         __syncthreads();
         t_begin = sm.shift[0];
-        nt = sm.shift[1];
-        }
+        nt = sm.shift[1] - sm.shift[0];
     }
     if (!FIRST && nt > 0) {
         if (vs_smem && !WEIGHTED)
@@ -1100,39 +1080,24 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                 }
                 return;
             }
-            if constexpr (LEAN) {
-                // a tile that straddles segments: its segments' virtual
-                // starts go to the stage's index area
-                int sf, m;
-                if (j < kRun) {
-                    sf = sm.run_sf[j];
-                    m = sm.run_m[j];
-                } else {
-                    tile_segs(j, sf, m, false);
-                }
-                if (m != 1) {
-                    for (int i = lane; i < m; i += 32) sm.sidx[s][i] = seg[sf + i].vstart;
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&bars.full[s]);
-                    return;
-                }
-            }
-            if (lane != 0) return;
-            int sf, m, ps, vs;
+            int sf, m;
             if (j < kRun) {
                 sf = sm.run_sf[j];
                 m = sm.run_m[j];
-                ps = sm.run_ps[j];
-                vs = sm.run_vs[j];
             } else {
                 tile_segs(j, sf, m, false);
-                ps = seg[sf].pstart;
-                vs = seg[sf].vstart;
             }
             if (m != 1) {
-                mbar_arrive(&bars.full[s]);
+                // a tile that straddles segments: its segments' virtual
+                // starts go to the stage's index area
+                for (int i = lane; i < m; i += 32) sm.sidx[s][i] = seg[sf + i].vstart;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bars.full[s]);
                 return;
             }
+            if (lane != 0) return;
+            const int ps = j < kRun ? sm.run_ps[j] : seg[sf].pstart;
+            const int vs = j < kRun ? sm.run_vs[j] : seg[sf].vstart;
             const int pos0 = ps + (v0 - vs);
             const int a0 = pos0 & ~3, a1 = (pos0 + cnt + 3) & ~3, nel = a1 - a0;
             sm.shift[s] = pos0 - a0;
@@ -1170,35 +1135,20 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                     sm.sem[p][ls][c] = 0u;
                 }
             }
-            if constexpr (LEAN) {
-                // every consumer warp has scattered tile j-2 (it did so
-                // before classifying tile j): the bases of parity p are free
-                __syncwarp();
-                if (lane == 0) {
-                    sm.gb[p][0] = (int)r0;
-                    sm.gb[p][1] = (int)r1;
-                    mbar_arrive(&bars.bases[p]);
-                }
-                __syncwarp();
-                if (j >= 1) {
-                    wait(&bars.empty[(j - 1) % kRing], kPhEmpty + (j - 1) % kRing);
-                    if (j - 1 + kRing < nt) issue(j - 1 + kRing);
-                }
-                __syncwarp();
-            } else {
-                if (j >= 1) {
-                    // tile j-1 scattered: its stage takes tile j-1+kRing
-                    wait(&bars.empty[(j - 1) % kRing], kPhEmpty + (j - 1) % kRing);
-                    if (j - 1 + kRing < nt) issue(j - 1 + kRing);
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    sm.gb[p][0] = (int)r0;
-                    sm.gb[p][1] = (int)r1;
-                    mbar_arrive(&bars.bases[p]);
-                }
-                __syncwarp();
+            // every consumer warp has scattered tile j-2 (it did so
+            // before classifying tile j): the bases of parity p are free
+            __syncwarp();
+            if (lane == 0) {
+                sm.gb[p][0] = (int)r0;
+                sm.gb[p][1] = (int)r1;
+                mbar_arrive(&bars.bases[p]);
             }
+            __syncwarp();
+            if (j >= 1) {
+                wait(&bars.empty[(j - 1) % kRing], kPhEmpty + (j - 1) % kRing);
+                if (j - 1 + kRing < nt) issue(j - 1 + kRing);
+            }
+            __syncwarp();
         }
         if (nt > 0) wait(&bars.empty[(nt - 1) % kRing], kPhEmpty + (nt - 1) % kRing);
     } else {
@@ -1228,10 +1178,8 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
         const int first_tma = A.first_tma;
         auto flush = [&]() {
             if (cur < 0) return;
-            if constexpr (LEAN) {
-                ta = far2_top2(fa);
-                tb = far2_top2(fb);
-            }
+            ta = far2_top2(fa);
+            tb = far2_top2(fb);
             top2_warp(ta);
             top2_warp(tb);
             if (lane == 0) {
@@ -1256,8 +1204,6 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                     if (!FIRST && sf != cur) {
                         flush();
                         cur = sf;
-                        ta = {0ull, 0u, 0u};
-                        tb = {0ull, 0u, 0u};
                         fa = {0u, 0u, 0u, 0};
                         fb = {0u, 0u, 0u, 0};
                     }
@@ -1322,43 +1268,28 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                     }
                     // phase 3, branch-free: farthest-point keys and counts
                     int w0 = 0, w1 = 0;
-                    if constexpr (LEAN) {
-                        int n0 = 0, n1 = 0;
-#pragma unroll
-                        for (int k = 0; k < kSItems; k++) {
-                            const int c = (int)((cls >> (2 * k)) & 3u);
-                            const unsigned o = ord_f32(dsel[k]);
-                            const unsigned eb = __float_as_uint(esel[k]);
-                            far2_add(fa, c == 0 ? o : 0u, pidx[k], c == 0 ? eb : 0u);
-                            far2_add(fb, c == 1 ? o : 0u, pidx[k], c == 1 ? eb : 0u);
-                            n0 += c == 0;
-                            n1 += c == 1;
-                        }
-                        w0 = __reduce_add_sync(0xffffffffu, n0);
-                        w1 = __reduce_add_sync(0xffffffffu, n1);
-                    } else {
+                    int n0 = 0, n1 = 0;
 #pragma unroll
                     for (int k = 0; k < kSItems; k++) {
                         const int c = (int)((cls >> (2 * k)) & 3u);
-                        const unsigned long long key = dist_key(dsel[k], pidx[k]);
+                        const unsigned o = ord_f32(dsel[k]);
                         const unsigned eb = __float_as_uint(esel[k]);
-                        top2_add(ta, c == 0 ? key : 0ull, c == 0 ? eb : 0u);
-                        top2_add(tb, c == 1 ? key : 0ull, c == 1 ? eb : 0u);
-                        w0 += __popc(__ballot_sync(0xffffffffu, c == 0));
-                        w1 += __popc(__ballot_sync(0xffffffffu, c == 1));
+                        far2_add(fa, c == 0 ? o : 0u, pidx[k], c == 0 ? eb : 0u);
+                        far2_add(fb, c == 1 ? o : 0u, pidx[k], c == 1 ? eb : 0u);
+                        n0 += c == 0;
+                        n1 += c == 1;
                     }
-                    }
+                    w0 = __reduce_add_sync(0xffffffffu, n0);
+                    w1 = __reduce_add_sync(0xffffffffu, n1);
                     if (lane == 0) {
                         off0 = atomicAdd(&sm.tilecnt[p][0], w0);
                         off1 = atomicAdd(&sm.tilecnt[p][1], w1);
                     }
                     off0 = __shfl_sync(0xffffffffu, off0, 0);
                     off1 = __shfl_sync(0xffffffffu, off1, 0);
-                } else if constexpr (LEAN) {
-                    multi_tile<P, true>(sm, seg, acc, sf, m, v0, v1, p, ixy, ii, oxy, oi,
-                                        fallbacks, sm.sidx[s]);
                 } else {
-                    multi_tile<P>(sm, seg, acc, sf, m, v0, v1, p, ixy, ii, oxy, oi, fallbacks);
+                    multi_tile<P>(sm, seg, acc, sf, m, v0, v1, p, ixy, ii, oxy, oi, fallbacks,
+                                  sm.sidx[s]);
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bars.counted[p]);
@@ -1374,69 +1305,41 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                     const int ln = FIRST ? A.n : sm.sseg[sp].len;
                     int base0 = sm.gb[pp][0] + off0_prev, base1 = sm.gb[pp][1] + off1_prev;
                     const int wbase = pv0 + warp * 32 * kSItems;
-                    if constexpr (LEAN) {
-                        // destinations and stage reads of all items, then the stores
-                        int dst[kSItems];
-                        float2 spt[kSItems];
-                        int sidx[kSItems];
-                        const int r0 = wbase - pv0 + shift + lane;
-                        int lo = ps + base0, hi = ps + ln - 1 - base1;
-#pragma unroll
-                        for (int k = 0; k < kSItems; k++) {
-                            const int c = (int)((cls_prev >> (2 * k)) & 3u);
-                            const unsigned b0 = __ballot_sync(0xffffffffu, c == 0);
-                            const unsigned b1 = __ballot_sync(0xffffffffu, c == 1);
-                            dst[k] = c == 0 ? lo + __popc(b0 & lt)
-                                            : (c == 1 ? hi - __popc(b1 & lt) : -1);
-                            lo += __popc(b0);
-                            hi -= __popc(b1);
-                            const int r = r0 + k * 32;
-                            if (FIRST) {
-                                if (first_tma == 2) {
-                                    spt[k] = sm.sxy[sp][r];
-                                } else {
-                                    const float *xs = reinterpret_cast<const float *>(sm.sxy[sp]);
-                                    spt[k] = make_float2(xs[r], xs[kStage + r]);
-                                }
-                                sidx[k] = wbase + k * 32 + lane;
-                            } else {
-                                spt[k] = sm.sxy[sp][r];
-                                sidx[k] = sm.sidx[sp][r];
-                            }
-                        }
-#pragma unroll
-                        for (int k = 0; k < kSItems; k++) {
-                            if (dst[k] >= 0) {
-                                oxy[dst[k]] = spt[k];
-                                oi[dst[k]] = sidx[k];
-                            }
-                        }
-                    } else {
+                    // destinations and stage reads of all items, then the stores
+                    int dst[kSItems];
+                    float2 spt[kSItems];
+                    int sidx[kSItems];
+                    const int r0 = wbase - pv0 + shift + lane;
+                    int lo = ps + base0, hi = ps + ln - 1 - base1;
 #pragma unroll
                     for (int k = 0; k < kSItems; k++) {
                         const int c = (int)((cls_prev >> (2 * k)) & 3u);
                         const unsigned b0 = __ballot_sync(0xffffffffu, c == 0);
                         const unsigned b1 = __ballot_sync(0xffffffffu, c == 1);
-                        if (c < 2) {
-                            const int v = wbase + k * 32 + lane;
-                            const int r = v - pv0 + shift;
-                            float2 pt;
-                            int idx;
-                            if (FIRST) {
-                                pt = first_point(sp, r);
-                                idx = v;
+                        dst[k] = c == 0 ? lo + __popc(b0 & lt)
+                                        : (c == 1 ? hi - __popc(b1 & lt) : -1);
+                        lo += __popc(b0);
+                        hi -= __popc(b1);
+                        const int r = r0 + k * 32;
+                        if (FIRST) {
+                            if (first_tma == 2) {
+                                spt[k] = sm.sxy[sp][r];
                             } else {
-                                pt = sm.sxy[sp][r];
-                                idx = sm.sidx[sp][r];
+                                const float *xs = reinterpret_cast<const float *>(sm.sxy[sp]);
+                                spt[k] = make_float2(xs[r], xs[kStage + r]);
                             }
-                            const int dst = c == 0 ? ps + base0 + __popc(b0 & lt)
-                                                   : ps + ln - 1 - (base1 + __popc(b1 & lt));
-                            oxy[dst] = pt;
-                            oi[dst] = idx;
+                            sidx[k] = wbase + k * 32 + lane;
+                        } else {
+                            spt[k] = sm.sxy[sp][r];
+                            sidx[k] = sm.sidx[sp][r];
                         }
-                        base0 += __popc(b0);
-                        base1 += __popc(b1);
                     }
+#pragma unroll
+                    for (int k = 0; k < kSItems; k++) {
+                        if (dst[k] >= 0) {
+                            oxy[dst[k]] = spt[k];
+                            oi[dst[k]] = sidx[k];
+                        }
                     }
                 }
                 __syncwarp();
@@ -2398,8 +2301,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_multi(Params2M M)
     // the whole grid; no barrier between them)
     for (int c = 0; c < M.K; c++)
         if (cloud_live(M, c))
-            pass2d_stream<P, true, false, true>(cloud_params(M, c), 0, sp, bars, ph, blockIdx.x,
-                                                gridDim.x);
+            pass2d_stream<P, true>(cloud_params(M, c), 0, sp, bars, ph, blockIdx.x, gridDim.x);
     sync_as(0);
     // a bounded wait that expired in a cloud's first split stops every cloud
     bool first_ok = true;
@@ -2435,7 +2337,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_multi(Params2M M)
                 *(volatile int *)&H->maxlen <= kWarpSegMax)
                 pass2d_warpseg<P>(A, t & 1, blockIdx.x, gridDim.x);
             else
-                pass2d_stream<P, false, true, true>(A, t & 1, sp, bars, ph, blockIdx.x, gridDim.x);
+                pass2d_stream<P, false, true>(A, t & 1, sp, bars, ph, blockIdx.x, gridDim.x);
             sync_as(0);
         }
     }
