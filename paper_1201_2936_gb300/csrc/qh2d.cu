@@ -874,7 +874,7 @@ __device__ __forceinline__ void multi_tile(SmemStream &sm, const Seg2 *seg, Acc2
     mflush();
 }
 
-// A thread's farthest-point record of one child in the lean pass: the order
+// A thread's farthest-point record of one child in the streaming pass: the order
 // bits (ord_f32) of its best and second-best distance (0 = none: no distance
 // that arithmetic produces maps to 0), the best point's index (the first one
 // met among equal distances; a tie leaves o2 == o1, so the segment is never
