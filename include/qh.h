@@ -134,6 +134,8 @@ size_t qh_workspace_bytes_2d(int64_t n, const qh_opts *opts);
  *  opts       may be NULL (defaults)
  * Host-side argument errors are returned directly; data-dependent errors
  * (QH_ERR_NONFINITE, QH_ERR_TIMEOUT, ...) appear in d_result->status.
+ * QH_LOOP_PERSISTENT (the default) runs the persistent kernel of
+ * qh_hull2d_multi_async with this one cloud (n <= QH_MAX_POINTS - 2);
  * QH_LOOP_HOST synchronises the stream once per iteration.
  */
 qh_status qh_hull2d_async(const float *d_x, const float *d_y, int64_t n, int64_t stride,
@@ -142,10 +144,11 @@ qh_status qh_hull2d_async(const float *d_x, const float *d_y, int64_t n, int64_t
 
 /* Synchronous form of qh_hull2d_async: returns the device status, the hull
  * size in *h_count and, when h_result is not NULL, the full result record.
- * d_result is taken from the workspace.  Hulls with more than 4096 hull
- * slots (the apexes found over all iterations, including points later found
- * collinear) are finished here by a second, single-block output step;
- * qh_hull2d_async reports QH_ERR_CAPACITY for them. */
+ * d_result is taken from the workspace.  With QH_LOOP_HOST, hulls with more
+ * than 4096 hull slots (the apexes found over all iterations, including
+ * points later found collinear) are finished here by a second, single-block
+ * output step; qh_hull2d_async reports QH_ERR_CAPACITY for them there (the
+ * persistent loop returns them directly). */
 qh_status qh_hull2d(const float *d_x, const float *d_y, int64_t n, int64_t stride,
                     int32_t *d_out_idx, int64_t *h_count, qh_result *h_result, void *d_ws,
                     size_t ws_bytes, const qh_opts *opts, cudaStream_t stream);
@@ -161,7 +164,7 @@ qh_status qh_hull2d(const float *d_x, const float *d_y, int64_t n, int64_t strid
  *  h_dx[c], h_dy[c] host arrays of device pointers: cloud c's coordinates,
  *                   point i at d_x[i*stride] (read only)
  *  h_n[c]           points of cloud c (>= 0); the total is at most
- *                   QH_MAX_POINTS - 2 * QH_MAX_CLOUDS_2D
+ *                   QH_MAX_POINTS - 2 * k
  *  h_stride[c]      >= 1 (NULL: all 1)
  *  h_dout[c]        host array of device pointers: int32[max(n_c, 1)] hull
  *                   indices of cloud c, counter-clockwise from its
