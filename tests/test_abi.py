@@ -63,3 +63,20 @@ def test_host_side_argument_errors(lib):
     # workspace too small
     assert L.qh_hull2d_async(ctypes.c_void_p(256), ctypes.c_void_p(256), 10, 1, ctypes.c_void_p(256),
                              res, ctypes.c_void_p(256), 16, None, None) == 4
+
+
+def test_single_cloud_workspace_covers_the_persistent_kernel(lib):
+    # the persistent loop of qh_hull2d runs the several-cloud kernel with one
+    # cloud: the single-cloud size covers that layout, and the fixed scratch of
+    # qh_hull2d_noalloc covers its largest call
+    from paper_1201_2936_gb300 import _native
+    L = _native.lib()
+    one = ctypes.c_int64 * 1
+    for n in (0, 1, 2, 1000, 4097, 131072, 1 << 24):
+        assert L.qh_workspace_bytes_2d(n, None) >= L.qh_workspace_bytes_2d_multi(1, one(n), None) > 0
+    assert L.qh_workspace_bytes_2d(131072, None) <= 32 << 20
+    # one byte short of the size is refused before any device work
+    need = L.qh_workspace_bytes_2d(10, None)
+    res = ctypes.c_void_p(16)
+    assert L.qh_hull2d_async(ctypes.c_void_p(256), ctypes.c_void_p(256), 10, 1, ctypes.c_void_p(256),
+                             res, ctypes.c_void_p(256), need - 1, None, None) == 4
