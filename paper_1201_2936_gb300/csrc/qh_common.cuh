@@ -38,27 +38,6 @@ __device__ __forceinline__ unsigned long long dist_key(float d, int idx)
 __device__ __forceinline__ int key_idx(unsigned long long k) { return (int)(0xffffffffu - (uint32_t)(k & 0xffffffffu)); }
 __device__ __forceinline__ float key_dist(unsigned long long k) { return unord_f32((uint32_t)(k >> 32)); }
 
-// Insert key k into a (top1, top2) pair held in memory with atomics: after any
-// set of insertions *t1 is the largest key and *t2 the largest of the others.
-// Every key displaced from, or refused by, *t1 is offered to *t2.
-template <class T>
-__device__ __forceinline__ void top2_insert(T *t1, T *t2, T k)
-{
-    if (k == 0) return;
-    T old = atomicMax(t1, k);
-    atomicMax(t2, old < k ? old : k);
-}
-
-__device__ __forceinline__ void top2_merge(unsigned long long &a1, unsigned long long &a2,
-                                           unsigned long long b1, unsigned long long b2)
-{
-    unsigned long long hi = a1 > b1 ? a1 : b1;
-    unsigned long long lo = a1 > b1 ? b1 : a1;
-    unsigned long long o2 = a2 > b2 ? a2 : b2;
-    a1 = hi;
-    a2 = lo > o2 ? lo : o2;
-}
-
 __device__ __forceinline__ unsigned long long globaltimer_ns()
 {
     unsigned long long t;
@@ -67,48 +46,17 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
 }
 
 struct GridBarrier {
-    unsigned int count;
-    unsigned int gen;
+    unsigned int count;  // arrivals since the launch
 };
 
-// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The
-// wait is bounded by wait_ns; on expiry the barrier raises *fail (status
-// QH_ERR_TIMEOUT) and returns so that the kernel can leave cleanly.
-__device__ __forceinline__ void grid_sync(GridBarrier *b, int *fail, long long wait_ns)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned int *vgen = &b->gen;
-        unsigned int g = *vgen;
-        __threadfence();
-        unsigned int arrived = atomicAdd(&b->count, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            atomicExch(&b->count, 0u);
-            __threadfence();
-            atomicAdd(&b->gen, 1u);
-        } else {
-            unsigned long long t0 = globaltimer_ns();
-            unsigned int spins = 0;
-            while (*vgen == g) {
-                __nanosleep(64);
-                if (((++spins) & 255u) == 0u &&
-                    (long long)(globaltimer_ns() - t0) > wait_ns) {
-                    atomicCAS(fail, 0, kStTimeout);
-                    break;
-                }
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-}
-
-// The same barrier with one global atomic per CTA and round: count only grows
-// (zero at launch), arrival k of the grid belongs to round k / gridDim.x, and
-// round r is complete once count reaches (r + 1) * gridDim.x.  The arrival
-// releases the CTA's writes (ordered before it by the block barrier) and the
-// polling load acquires the other CTAs'.  A kernel uses either this barrier
-// or grid_sync on a given GridBarrier, never both.
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident), one
+// global atomic per CTA and round: count only grows (zero at launch), arrival
+// k of the grid belongs to round k / gridDim.x, and round r is complete once
+// count reaches (r + 1) * gridDim.x.  The arrival releases the CTA's writes
+// (ordered before it by the block barrier) and the polling load acquires the
+// other CTAs'.  The wait is bounded by wait_ns; on expiry the barrier raises
+// *fail (status QH_ERR_TIMEOUT) and returns so that the kernel can leave
+// cleanly.
 __device__ __forceinline__ void grid_sync_count(GridBarrier *b, int *fail, long long wait_ns)
 {
     __syncthreads();
@@ -135,25 +83,11 @@ __device__ __forceinline__ void grid_sync_count(GridBarrier *b, int *fail, long 
     __syncthreads();
 }
 
-// ---------------------------------------------------------------- async copies
-// Per-thread asynchronous global -> shared copies (completed by cp_async_wait_all
-// in the issuing thread, then visible to the CTA after a barrier).
+// ---------------------------------------------------------------- shared addresses
 __device__ __forceinline__ unsigned smem_u32(const void *p)
 {
     return (unsigned)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ void cp_async16(void *dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Bulk copy engine (TMA, non-tensor form): `bytes` (a multiple of 16) from a
 // 16-byte aligned global address to a 16-byte aligned shared address,
@@ -212,18 +146,6 @@ __device__ __forceinline__ unsigned lanemask_lt()
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
-}
-
-// Inclusive warp scan of an int.
-__device__ __forceinline__ int warp_incl_scan(int v)
-{
-    int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += t;
-    }
-    return v;
 }
 
 __device__ __forceinline__ long long warp_incl_scan64(long long v)
