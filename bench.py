@@ -29,6 +29,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -97,12 +98,12 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = None
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.fh = open(self.path, "w")
+            fd, self.path = tempfile.mkstemp(prefix=f"qh_clocks_gpu{self.gpu}_", suffix=".csv")
+            self.fh = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "100"],
@@ -133,6 +134,10 @@ class ClockSampler:
             for nm, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
@@ -563,6 +568,8 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     res = mresults()
+    # the headline's hulls, index for index, for the comparisons below
+    head_idx = [outs[i][: res[i].count].clone() for i in range(nl)]
     # per-pass HBM rate of the last timed launch (device clock between the
     # pass's grid barriers): pass t reads its L_t live records (the first
     # split: the callers' 8-byte coordinates) and writes its survivors, the
@@ -644,7 +651,8 @@ def main():
     line["separate_launches"] = {
         "value": round(pts_per_step / (sms / 1e3) / 1e6, 2), "unit": UNIT,
         "ms_per_step": round(sms, 3), "kernel": "qh2d_multi<PredF32>, one cloud per launch (qh_hull2d)",
-        "same_hulls": all(sres[i].count == res[i].count for i in range(nl))}
+        "same_hulls": all(sres[i].count == res[i].count and
+                          torch.equal(outs[i][: sres[i].count], head_idx[i]) for i in range(nl))}
 
     # ---- plain GPU path: FP64 predicates, host loop with per-iteration readback
     if not args.no_plain:
@@ -664,11 +672,12 @@ def main():
         torch.cuda.synchronize()
         pms = e0.elapsed_time(e1) / ksteps
         pres = [qh.result_from_tensor(r) for r in results]
-        same = all(pres[i].count == res[i].count for i in range(nl))
+        same = all(pres[i].count == res[i].count and
+                   torch.equal(outs[i][: pres[i].count], head_idx[i]) for i in range(nl))
         line["plain_gpu"] = {"value": round(pts_per_step / (pms / 1e3) / 1e6, 2), "unit": UNIT,
                              "ms_per_step": round(pms, 3), "pred": "f64-filter+exact",
                              "loop": "host (live count read back every iteration)",
-                             "same_hull_sizes": same,
+                             "same_hulls": same,
                              "speedup_of_fast_path": round(pms / (total_ms / args.steps), 2)}
 
     # ---- 3D (8M points uniform in the ball, 1M points on the sphere): FP32

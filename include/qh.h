@@ -76,10 +76,18 @@ typedef struct qh_opts {
     int32_t blocks_per_sm;/* persistent grid: CTAs per SM (0 = as many as fit) */
     int32_t block;        /* 3D: threads per CTA, 128, 256 or 512 (0 = 256) */
     int64_t max_iters;    /* iteration cap (0 = n + 8 in 2D, 4n + 16 in 3D) */
-    int64_t wait_ns;      /* bound of every device-side wait (0 = 2 s) */
+    int64_t wait_ns;      /* bound of every grid-barrier wait (0 = 2 s); a CTA's wait for its
+                             own bulk copies has a fixed 2 s bound */
     int32_t items;        /* 3D: points per thread of the assign pass, 2, 4 or 8 (0 = 4) */
     int32_t max_ctas;     /* 2D persistent grid: at most this many CTAs (0 = no cap); lets
                              several hulls share the GPU on different streams */
+    int32_t test_hold;    /* tests of the bounded waits only (0 = off): 1 = CTA 0 of the
+                             persistent kernel does not arrive at its first grid barrier, so
+                             that round never completes, every CTA's wait runs out after
+                             wait_ns and the call reports QH_ERR_TIMEOUT.  The kernel then
+                             leaves without starting another phase; the workspace is
+                             reusable for the next call. */
+    int32_t reserved;
 } qh_opts;
 
 /* Result record written by the device (async calls) and copied back by the
@@ -365,13 +373,20 @@ qh_status qh_hull3d_backward(const float *d_x, const float *d_y, const float *d_
  * argument: the scratch is one fixed array of 32 MiB in device memory that
  * every device holds once the library is loaded on it, until the process
  * exits.  n may not exceed QH_NOALLOC_MAX_POINTS; larger n returns
- * QH_ERR_INVALID_ARG without touching the device.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.
- * Every call on a device shares the array: calls that overlap on the GPU
- * (other streams, other host threads) race and must be serialised by the
- * caller.  Nothing here calls cudaMalloc, cudaFree or an allocating library
- * routine.  Synchronises `stream`.
+ * QH_ERR_INVALID_ARG without touching the device.  Set-up happens on the
+ * first call made on a device, with that device current: it looks up the
+ * array's device address (cudaGetSymbolAddress) and keeps it for the
+ * device.  That lookup is also what loads the library's module on the
+ * device (CUDA loads modules lazily) and so reserves the 32 MiB; a device
+ * without room for it gives QH_ERR_NOMEM.  Make that first call at start-up
+ * and before any stream capture.  The kept address belongs to the device's
+ * current context: after cudaDeviceReset (or any teardown of the primary
+ * context) this entry point may not be called again in the process.  Every
+ * call on a device shares the array and finds it as the last call left it
+ * (the hull clears what it needs): calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Nothing here calls cudaMalloc, cudaFree or an allocating library routine.
+ * Synchronises `stream`.
  */
 #define QH_NOALLOC_MAX_POINTS ((int64_t)131072)
 qh_status qh_hull2d_noalloc(const float *d_x, const float *d_y, int64_t n, int64_t stride,

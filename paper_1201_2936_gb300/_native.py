@@ -17,7 +17,8 @@ class QhOpts(ctypes.Structure):
     _fields_ = [("pred_mode", ctypes.c_int32), ("loop_mode", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("max_iters", ctypes.c_int64), ("wait_ns", ctypes.c_int64),
-                ("items", ctypes.c_int32), ("max_ctas", ctypes.c_int32)]
+                ("items", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
+                ("test_hold", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class QhResult(ctypes.Structure):

@@ -136,6 +136,7 @@ struct Params2 {
     int *next;
     long long max_iters;
     long long wait_ns;
+    int test_hold;  // CTA 0 skips its first grid-barrier arrival (tests of the bounded wait)
     int cap_seg;
     int first_tma;  // first pass bulk copies: 0 none, 1 separate x, y arrays, 2 interleaved xy
 };
@@ -927,6 +928,9 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
     float2 *oxy = A.bxy[par];
     int *oi = A.bi[par];
     unsigned fallbacks = 0;
+    // a pass never starts after a failure: no copy is issued that nobody
+    // waits for (the same decision in every thread of the CTA)
+    if (status_uniform(&H->status) != 0) return;
     const int ntiles = (L + kSTile - 1) / kSTile;
     const int per = ntiles / nb, rem = ntiles % nb;
     int t_begin = bid * per + min(bid, rem);
@@ -1025,11 +1029,12 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
             tile_segs(j, sf, m, false);  // runs longer than kRun tiles: searched again
         }
     };
-    // bounded waits: after one has expired the others return at once and no
-    // scatter uses a base that may not have been published
-    bool dead = vload_i(&H->status) != 0;
+    // bounded waits: after one has expired the others return at once, the
+    // warp reads no staged data and no scatter uses a base that may not have
+    // been published; the barrier arrivals go on, so no warp waits on this one
+    bool dead = false;
     auto wait = [&](unsigned long long *bar, int bit) {
-        if (!dead && !mbar_wait(bar, (ph >> bit) & 1u, A.wait_ns)) {
+        if (!dead && !mbar_wait(bar, (ph >> bit) & 1u, kCopyWaitNs)) {
             dead = true;
             set_status(H, kStTimeout);
         }
@@ -1287,7 +1292,7 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                     }
                     off0 = __shfl_sync(0xffffffffu, off0, 0);
                     off1 = __shfl_sync(0xffffffffu, off1, 0);
-                } else {
+                } else if (!dead) {
                     multi_tile<P>(sm, seg, acc, sf, m, v0, v1, p, ixy, ii, oxy, oi, fallbacks,
                                   sm.sidx[s]);
                 }
@@ -1351,6 +1356,14 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
             off1_prev = off1;
         }
         flush();
+    }
+    // after an expired wait, copies into the stage ring may still be in
+    // flight: the CTA stays until the last copy issued to every stage has
+    // landed (warp 0 counted every tile's phase of the full barriers, waited
+    // for or not), bounded again; past that bound the CTA leaves best-effort
+    if (__syncthreads_or(dead) && threadIdx.x == 0) {
+        for (int s = 0; s < kRing; s++)
+            mbar_wait(&bars.full[s], ((ph >> (kPhFull + s)) & 1u) ^ 1u, kCopyWaitNs);
     }
     const unsigned f = __reduce_add_sync(0xffffffffu, fallbacks);
     if (lane == 0 && f) atomicAdd(&H->fallbacks, (unsigned long long)f);
@@ -2255,8 +2268,14 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_multi(Params2M M)
     const bool clk = blockIdx.x == 0 && threadIdx.x == 0;
     unsigned long long tprev = clk ? globaltimer_ns() : 0;
     int it = 0;
+    // every grid barrier returns the status as one value for the whole CTA:
+    // a phase starts only when it is zero, so after a failure (an expired
+    // wait, a non-finite input) no CTA reads results another CTA has not
+    // finished writing
+    bool hold = A.test_hold != 0 && blockIdx.x == 0;
     auto sync_as = [&](int cat) {
-        grid_sync_count(&H->bar, fail, A.wait_ns);
+        const int st = grid_sync_count(&H->bar, fail, A.wait_ns, hold);
+        hold = false;
         if (clk) {
             const unsigned long long t = globaltimer_ns();
             H->phase_ns[cat] += t - tprev;
@@ -2269,6 +2288,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_multi(Params2M M)
             }
             tprev = t;
         }
+        return st;
     };
     // headers: the shared one (K pseudo segments, N live points, 2K hull
     // slots) and each cloud's
@@ -2280,67 +2300,74 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) qh2d_multi(Params2M M)
             H->hull_count = 2 * M.K;
         }
     }
-    sync_as(3);
-    for (int c = 0; c < M.K; c++) {
-        if (M.c[c].n == 0) continue;
-        const Ext2 e = extrema2d(cloud_params(M, c), sm);
-        if (threadIdx.x == 0) ext_m[c] = e;
-    }
-    sync_as(3);
-    if (threadIdx.x == 0) {
+    if (sync_as(3) == 0) {
         for (int c = 0; c < M.K; c++) {
             if (M.c[c].n == 0) continue;
-            Hdr2 *Hc = M.c[c].hdr;
-            if (ext_m[c].mn == *(volatile unsigned long long *)&Hc->lexmin)
-                atomicMin(&Hc->a_idx, ext_m[c].mni);
-            if (ext_m[c].mx == *(volatile unsigned long long *)&Hc->lexmax)
-                atomicMin(&Hc->b_idx, ext_m[c].mxi);
+            const Ext2 e = extrema2d(cloud_params(M, c), sm);
+            if (threadIdx.x == 0) ext_m[c] = e;
         }
-    }
-    // the first split of every finite cloud, one after the other (each over
-    // the whole grid; no barrier between them)
-    for (int c = 0; c < M.K; c++)
-        if (cloud_live(M, c))
-            pass2d_stream<P, true>(cloud_params(M, c), 0, sp, bars, ph, blockIdx.x, gridDim.x);
-    sync_as(0);
-    // a bounded wait that expired in a cloud's first split stops every cloud
-    bool first_ok = true;
-    for (int c = 0; c < M.K; c++) first_ok &= *(volatile int *)&M.c[c].hdr->status == 0;
-    if (!first_ok) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(H, kStTimeout);
-    } else {
-        int t = 0;
-        while (*(volatile int *)&H->status == 0) {
-            if (blockIdx.x == 0) update2d_m(M, t & 1, t == 0, sm.u, 0);
-            sync_as(1);
-            if (*(volatile int *)&H->status) break;
-            const int nu = *(volatile int *)&H->n_uncert;
-            if (nu > 0) {
-                const int per = exact_chunks2d(A, t & 1, sm.x, nu, gridDim.x);
-                exact2d_split<P>(A, t & 1, sm.x, blockIdx.x, gridDim.x, per);
-                sync_as(2);
-                if (per > 1) {
-                    exact2d_merge(A, t & 1, blockIdx.x, gridDim.x, per);
-                    sync_as(2);
+        if (sync_as(3) == 0) {
+            if (threadIdx.x == 0) {
+                for (int c = 0; c < M.K; c++) {
+                    if (M.c[c].n == 0) continue;
+                    Hdr2 *Hc = M.c[c].hdr;
+                    if (ext_m[c].mn == *(volatile unsigned long long *)&Hc->lexmin)
+                        atomicMin(&Hc->a_idx, ext_m[c].mni);
+                    if (ext_m[c].mx == *(volatile unsigned long long *)&Hc->lexmax)
+                        atomicMin(&Hc->b_idx, ext_m[c].mxi);
                 }
             }
-            if (*(volatile int *)&H->S[(t + 1) & 1] == 0) break;
-            t++;
-            if (t > A.max_iters) {
-                if (blockIdx.x == 0 && threadIdx.x == 0) set_status(H, kStNoConv);
-                break;
+            // the first split of every finite cloud, one after the other
+            // (each over the whole grid; no barrier between them)
+            for (int c = 0; c < M.K; c++)
+                if (cloud_live(M, c))
+                    pass2d_stream<P, true>(cloud_params(M, c), 0, sp, bars, ph, blockIdx.x,
+                                           gridDim.x);
+            int st = sync_as(0);
+            // a bounded wait that expired in a cloud's first split stops every cloud
+            if (st == 0) {
+                int cst = 0;
+                if (threadIdx.x == 0)
+                    for (int c = 0; c < M.K; c++) cst |= *(volatile int *)&M.c[c].hdr->status;
+                if (__syncthreads_or(cst != 0)) {
+                    if (blockIdx.x == 0 && threadIdx.x == 0) set_status(H, kStTimeout);
+                    st = kStTimeout;
+                }
             }
-            const int Lt = *(volatile int *)&H->L[t & 1], St = *(volatile int *)&H->S[t & 1];
-            if (blockIdx.x == 0 && threadIdx.x == 0) H->iter = t;
-            it = t;
-            if ((long long)Lt <= (long long)kWarpSegAvg * St &&
-                *(volatile int *)&H->maxlen <= kWarpSegMax)
-                pass2d_warpseg<P>(A, t & 1, blockIdx.x, gridDim.x);
-            else
-                pass2d_stream<P, false, true>(A, t & 1, sp, bars, ph, blockIdx.x, gridDim.x);
-            sync_as(0);
+            int t = 0;
+            while (st == 0) {
+                if (blockIdx.x == 0) update2d_m(M, t & 1, t == 0, sm.u, 0);
+                if (sync_as(1) != 0) break;
+                const int nu = *(volatile int *)&H->n_uncert;
+                if (nu > 0) {
+                    const int per = exact_chunks2d(A, t & 1, sm.x, nu, gridDim.x);
+                    exact2d_split<P>(A, t & 1, sm.x, blockIdx.x, gridDim.x, per);
+                    if (sync_as(2) != 0) break;
+                    if (per > 1) {
+                        exact2d_merge(A, t & 1, blockIdx.x, gridDim.x, per);
+                        if (sync_as(2) != 0) break;
+                    }
+                }
+                if (*(volatile int *)&H->S[(t + 1) & 1] == 0) break;
+                t++;
+                if (t > A.max_iters) {
+                    if (blockIdx.x == 0 && threadIdx.x == 0) set_status(H, kStNoConv);
+                    break;
+                }
+                const int Lt = *(volatile int *)&H->L[t & 1], St = *(volatile int *)&H->S[t & 1];
+                if (blockIdx.x == 0 && threadIdx.x == 0) H->iter = t;
+                it = t;
+                if ((long long)Lt <= (long long)kWarpSegAvg * St &&
+                    *(volatile int *)&H->maxlen <= kWarpSegMax)
+                    pass2d_warpseg<P>(A, t & 1, blockIdx.x, gridDim.x);
+                else
+                    pass2d_stream<P, false, true>(A, t & 1, sp, bars, ph, blockIdx.x, gridDim.x);
+                st = sync_as(0);
+            }
         }
     }
+    // the output step reads the status itself and writes only the result
+    // records when it is not zero
     sync_as(3);
     if (blockIdx.x == 0) output2d_m(M, sm.out);
 }
@@ -2522,6 +2549,7 @@ static Params2 make_params(const float *x, const float *y, int64_t n, int64_t st
     if (stride == 1 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)y & 15) == 0) A.first_tma = 1;
     else if (stride == 2 && y == x + 1 && ((uintptr_t)x & 15) == 0) A.first_tma = 2;
     A.wait_ns = o.wait_ns > 0 ? o.wait_ns : 2000000000ll;
+    A.test_hold = o.test_hold;
     return A;
 }
 
@@ -2602,13 +2630,11 @@ static qh_status run2d_multi(const Params2M &M, const Layout2M &LM, char *ws, co
         cudaMemsetAsync(ws + LM.chdr, 0, (size_t)M.K * align_up(sizeof(Hdr2)), st) != cudaSuccess)
         return QH_ERR_CUDA;
     const void *fn = (const void *)qh2d_multi<P>;
-    static std::once_flag attr_once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(attr_once, [&]() {
-        attr_err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)kPersistSmem);
-    });
-    if (attr_err != cudaSuccess) return QH_ERR_CUDA;
+    // the attribute belongs to the current device's context: set it on every
+    // call (cheap), so that a process that uses several devices gets it on each
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kPersistSmem) != cudaSuccess)
+        return QH_ERR_CUDA;
     int grid = persistent_grid_smem(fn, kBlock, o.blocks_per_sm, kPersistSmem);
     if (grid <= 0) return QH_ERR_CUDA;
     grid = grid > kMaxGrid ? kMaxGrid : grid;
@@ -2787,9 +2813,10 @@ extern "C" qh_status qh_hull2d_async(const float *d_x, const float *d_y, int64_t
 
 // ---------------------------------------------------------------- no-alloc variant
 // Scratch for qh_hull2d_noalloc: a fixed array in device memory, created when
-// the module is loaded on a device and kept until the process exits.  Host
-// code may not use the symbol as a pointer; its device address is looked up
-// once per device with cudaGetSymbolAddress.
+// the module is loaded on a device and kept until the process exits.  In host
+// code the array's name is a host-side stand-in, not a device address: the
+// device address is looked up once per device, with that device current,
+// with cudaGetSymbolAddress (set-up on the first call made on the device).
 constexpr size_t kNoAllocBytes = (size_t)32 << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -2810,9 +2837,15 @@ extern "C" qh_status qh_hull2d_noalloc(const float *d_x, const float *d_y, int64
     {
         std::lock_guard<std::mutex> g(g_noalloc_mu);
         if (!g_noalloc_ptr[dev]) {
-            // first call on this device: resolve the array's device address
+            // set-up, first call on this device: this lookup loads the
+            // module there (CUDA loads modules lazily), which reserves the
+            // array; a device without room for it gives NOMEM
             void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return QH_ERR_CUDA;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                (void)cudaGetLastError();
+                return e == cudaErrorMemoryAllocation ? QH_ERR_NOMEM : QH_ERR_CUDA;
+            }
             g_noalloc_ptr[dev] = p;
         }
         ws = g_noalloc_ptr[dev];

@@ -1322,8 +1322,15 @@ __global__ void __launch_bounds__(kMaxBlock) qh3d_persistent(Params3 A)
     Hdr3 *H = A.hdr;
     int *fail = &H->status;
     const int bid = blockIdx.x, nb = gridDim.x;
-    auto sync = [&]() { grid_sync_count(&H->bar, fail, A.wait_ns); };
-    auto ok = [&]() { return *(volatile int *)&H->status == 0; };
+    // every grid barrier returns the status, the same value in the whole
+    // CTA; a phase runs only while it is zero, so after a failure no CTA
+    // reads results that another CTA has not finished writing
+    bool hold = A.test_hold != 0 && bid == 0;
+    auto sync = [&]() {
+        const int st = grid_sync_count(&H->bar, fail, A.wait_ns, hold);
+        hold = false;
+        return st == 0;
+    };
     // phase clock of block 0, thread 0 (per-iteration record)
     const bool clk = bid == 0 && threadIdx.x == 0;
     unsigned long long tprev = clk ? globaltimer_ns() : 0;
@@ -1341,60 +1348,74 @@ __global__ void __launch_bounds__(kMaxBlock) qh3d_persistent(Params3 A)
         H->setup_ns[k] = (long long)(t - tprev);
         tprev = t;
     };
+    bool go = status_uniform(fail) == 0;
     // ---- initial simplex: grid-wide for one cloud, one block per cloud for
     // a batch
     if (A.cloud_off) {
-        if (ok()) init_clouds(A, sm, bid, nb);  // offsets checked before the launch
-        sync();
+        if (go) init_clouds(A, sm, bid, nb);  // offsets checked before the launch
+        go = sync() && go;
     } else {
-        extrema3d(A, sm, bid, nb);
-        sync();
-        if (bid == 0) simplex_step(A, sm, 0, nb);
-        sync();
-        if (*(volatile int *)&H->nonfinite) {
-            if (bid == 0 && threadIdx.x == 0) set_status(H, QH_ERR_NONFINITE);
+        if (go) {
+            extrema3d(A, sm, bid, nb);
+            go = sync();
         }
-        for (int step = 1; step <= 2 && ok(); step++) {
+        if (go) {
+            if (bid == 0) simplex_step(A, sm, 0, nb);
+            go = sync();
+        }
+        if (go && *(volatile int *)&H->nonfinite) {
+            if (bid == 0 && threadIdx.x == 0) set_status(H, QH_ERR_NONFINITE);
+            go = sync();
+        }
+        for (int step = 1; step <= 2 && go; step++) {
             farthest3d(A, sm, bid, nb, step - 1);
-            sync();
+            if (!(go = sync())) break;
             if (bid == 0) simplex_step(A, sm, step, nb);
-            sync();
+            if (!(go = sync())) break;
             if (!*(volatile int *)&H->cand_ok) {
                 exact_search3d(A, bid, nb, step - 1);
-                sync();
+                if (!(go = sync())) break;
             }
             if (bid == 0) simplex_take(A, step);
-            sync();
+            go = sync();
         }
-        if (ok()) {
+        if (go) {
             if (bid == 0) build_tetra(A);
-            sync();
+            go = sync();
         }
     }
     setup_mark(0);
-    if (ok()) {
+    if (go) {
         // ---- first assignment: every input point against the tetrahedron;
         // table 1 / buffer 1 receive the result
         assign3d<MODE, ITEMS, true>(A, 0, sm, bid, nb);
-        sync();
+        go = sync();
         setup_mark(1);
-        table_sum(A, 0, true, sm, bid, nb);
-        sync();
-        table_write(A, 0, true, sm, bid, nb);
-        if (bid == 0 && threadIdx.x == 0) H->n_uncert = 0;
-        sync();
+        if (go) {
+            table_sum(A, 0, true, sm, bid, nb);
+            go = sync();
+        }
+        if (go) {
+            table_write(A, 0, true, sm, bid, nb);
+            if (bid == 0 && threadIdx.x == 0) H->n_uncert = 0;
+            go = sync();
+        }
         setup_mark(2);
-        scatter3d<true>(A, 0, bid, nb);
-        sync();
-        certify3d(A, 0, bid, nb);
-        sync();
-        if (*(volatile int *)&H->n_uncert > 0) {
+        if (go) {
+            scatter3d<true>(A, 0, bid, nb);
+            go = sync();
+        }
+        if (go) {
+            certify3d(A, 0, bid, nb);
+            go = sync();
+        }
+        if (go && *(volatile int *)&H->n_uncert > 0) {
             const int per = exact_chunks(A, *(volatile int *)&H->n_uncert, nb);
             exact3d<MODE>(A, 0, sm, bid, nb, per);
-            sync();
-            if (per > 1) {
+            go = sync();
+            if (go && per > 1) {
                 exact3d_merge<MODE>(A, 0, bid, nb, per);
-                sync();
+                go = sync();
             }
         }
         setup_mark(3);
@@ -1402,7 +1423,7 @@ __global__ void __launch_bounds__(kMaxBlock) qh3d_persistent(Params3 A)
     // ---- iterations: table `cur` describes the live points in buffer `cur`
     int cur = 1;
     int iter = 0;
-    while (ok() && *(volatile int *)&H->nent[cur] > 0) {
+    while (go && *(volatile int *)&H->nent[cur] > 0) {
         iter++;
         if (iter > A.max_iters) {
             if (bid == 0 && threadIdx.x == 0) set_status(H, QH_ERR_NO_CONVERGENCE);
@@ -1419,45 +1440,45 @@ __global__ void __launch_bounds__(kMaxBlock) qh3d_persistent(Params3 A)
         }
         mark(0, 0);
         select3d<MODE>(A, cur, bid, nb);
-        sync();
+        if (!sync()) break;
         mark(iter, 3);
         if (bid == 0 && threadIdx.x == 0) H->nactive[0] = 0;
-        sync();
-        for (int round = 0; round < kRounds; round++) {
+        if (!sync()) break;
+        for (int round = 0; round < kRounds && go; round++) {
             claim3d(A, cur, iter, round, bid, nb);
-            sync();
+            if (!(go = sync())) break;
             if (*(volatile int *)&H->nactive[round & 1] == 0) break;
             cone3d(A, cur, iter, round, bid, nb);
-            sync();
+            go = sync();
         }
+        if (!go) break;
         if (*(volatile int *)&H->nwin == 0) {
             if (bid == 0) fallback3d<MODE>(A, cur, iter);
-            sync();
+            if (!sync()) break;
         }
         if (clk && iter <= kTimeline3) H->tl[iter - 1][2] = H->nwin;
         mark(iter, 4);
-        if (!ok()) break;
         assign3d<MODE, ITEMS, false>(A, cur, sm, bid, nb);
-        sync();
+        if (!sync()) break;
         mark(iter, 5);
         table_sum(A, cur, false, sm, bid, nb);
-        sync();
+        if (!sync()) break;
         table_write(A, cur, false, sm, bid, nb);
         if (bid == 0 && threadIdx.x == 0) H->n_uncert = 0;
-        sync();
+        if (!sync()) break;
         mark(iter, 6);
         scatter3d<false>(A, cur, bid, nb);
         certify3d(A, cur, bid, nb);  // reads the table and accumulators only
         if (bid == 0 && threadIdx.x == 0) H->surv_total += H->L[cur ^ 1];
-        sync();
+        if (!sync()) break;
         mark(iter, 7);
         if (*(volatile int *)&H->n_uncert > 0) {
             const int per = exact_chunks(A, *(volatile int *)&H->n_uncert, nb);
             exact3d<MODE>(A, cur, sm, bid, nb, per);
-            sync();
+            if (!sync()) break;
             if (per > 1) {
                 exact3d_merge<MODE>(A, cur, bid, nb, per);
-                sync();
+                if (!sync()) break;
             }
             if (bid == 0 && threadIdx.x == 0) H->exact_argmax += H->n_uncert;
         }

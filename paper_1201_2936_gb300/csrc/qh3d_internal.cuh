@@ -120,6 +120,7 @@ struct Params3 {
     float *blk_v;
     int *blk_i;
     long long max_iters, wait_ns;
+    int test_hold;                // CTA 0 skips its first grid-barrier arrival (tests)
 };
 
 // The pseudo facet of cloud c in the first assignment (every point of the

@@ -32,7 +32,8 @@ namespace d3 {
 static size_t au(size_t v) { return (v + 255) & ~(size_t)255; }
 
 constexpr int kScanTile = 2048;  // elements per tile of the scan and sort kernels
-constexpr int kOutGrid = 152 * 4;  // CTAs of the grid-stride output kernels
+// CTAs of the grid-stride output kernels: four per SM of the current device
+static long long out_grid() { return 4ll * sm_count(); }
 
 Layout3 layout3d(int64_t n, int ncloud)
 {
@@ -144,6 +145,7 @@ Params3 make_params3(const float *x, const float *y, const float *z, int64_t n, 
     A.blk_i = (int *)(ws + L.blk_i);
     A.max_iters = o.max_iters > 0 ? o.max_iters : 4 * n + 16;
     A.wait_ns = o.wait_ns > 0 ? o.wait_ns : 2000000000ll;
+    A.test_hold = o.test_hold;
     const int block = o.block > 0 ? o.block : (o.pred_mode == QH_PRED_F64 ? kDefBlockF64 : kDefBlockF32);
     const int items = o.items > 0 ? o.items : kDefItems;
     A.tile = block * items;
@@ -227,13 +229,13 @@ __global__ void __launch_bounds__(256) k_scan_apply(const int *in, const int *m_
 static int grid_for(long long items, int block)
 {
     const long long g = (items + block - 1) / block;
-    return (int)std::max(1ll, std::min(g, (long long)kOutGrid));
+    return (int)std::max(1ll, std::min(g, out_grid()));
 }
 
 static int tiles_grid(long long cap)
 {
     const long long t = (cap + kScanTile - 1) / kScanTile;
-    return (int)std::max(1ll, std::min(t, (long long)kOutGrid));
+    return (int)std::max(1ll, std::min(t, out_grid()));
 }
 
 // m_cap: an upper bound of the count (sizes the grid).
@@ -690,7 +692,7 @@ static qh_status enqueue3d(Params3 &A, const Layout3 &L, char *ws, const qh_opts
     OutBufs O = out_bufs(ws, L);
     Hdr3 *H = A.hdr;
     const long long fcap = L.fcap, ecap = 3ll * (L.fcap + 1), n = A.n;
-    const int gf = (int)std::min<long long>(kOutGrid, (fcap + 255) / 256);
+    const int gf = (int)std::min<long long>(out_grid(), (fcap + 255) / 256);
     k_alive<<<gf, 256, 0, st>>>(A, O);
     k_uf_union<<<gf, 256, 0, st>>>(A, O);
     k_uf_compress<<<gf, 256, 0, st>>>(A, O);
@@ -699,13 +701,13 @@ static qh_status enqueue3d(Params3 &A, const Layout3 &L, char *ws, const qh_opts
     while ((1ll << lbits) <= fcap) lbits++;
     radix_sort(O.ekey[0], O.eval[0], O.ekey[1], O.eval[1], &H->nbedge, ecap, 32 + lbits, O.hist,
                O.hist_off, O.scan_tmp, &H->sort_m, st);
-    const int ge = (int)std::min<long long>(kOutGrid, (ecap + 255) / 256);
+    const int ge = (int)std::min<long long>(out_grid(), (ecap + 255) / 256);
     k_gmark<<<ge, 256, 0, st>>>(A, O);
     // start-flag scan -> group index (the edge-sort scratch keys are free now)
     long long *gscan = (long long *)O.ekey[1];
     scan_counts(O.poly, &H->nbedge, 0, ecap, gscan, O.scan_tmp, nullptr, st);
     k_gwrite<<<ge, 256, 0, st>>>(A, O, gscan);
-    k_walk<<<(int)std::min<long long>(kOutGrid * 2, (fcap + 127) / 128), 128, 0, st>>>(A, O);
+    k_walk<<<(int)std::min<long long>(out_grid() * 2, (fcap + 127) / 128), 128, 0, st>>>(A, O);
     int vbits = 1;
     while ((1ll << vbits) <= n) vbits++;
     radix_sort(O.fkey[0], O.fval[0], O.fkey[1], O.fval[1], &H->ngroup, fcap + 1, 32 + vbits,
@@ -713,7 +715,7 @@ static qh_status enqueue3d(Params3 &A, const Layout3 &L, char *ws, const qh_opts
     k_fsizes<<<gf, 256, 0, st>>>(A, O);
     long long *foff = (long long *)O.ekey[1];
     scan_counts(O.eval[1], &H->ngroup, 0, fcap + 1, foff, O.scan_tmp, &H->nfidx, st);
-    const int gn = (int)std::min<long long>(kOutGrid, (n + 255) / 256);
+    const int gn = (int)std::min<long long>(out_grid(), (n + 255) / 256);
     k_vclear<<<gn, 256, 0, st>>>(A, O);
     k_fcopy<<<gf, 256, 0, st>>>(A, O, foff, d_face_off, d_face_idx);
     long long *voff = (long long *)O.eval[1];  // n long longs fit: eval[1] holds 3 * fcap ints

@@ -57,15 +57,27 @@ struct GridBarrier {
 // other CTAs'.  The wait is bounded by wait_ns; on expiry the barrier raises
 // *fail (status QH_ERR_TIMEOUT) and returns so that the kernel can leave
 // cleanly.
-__device__ __forceinline__ void grid_sync_count(GridBarrier *b, int *fail, long long wait_ns)
+//
+// Returns *fail as read by thread 0 after the wait, the same value in every
+// thread of the CTA: callers branch on it without splitting the CTA around
+// later block barriers.  skip_arrive (tests of the bounded wait only): this
+// CTA waits without arriving, so the round cannot complete and every CTA's
+// wait runs out.
+__device__ __forceinline__ int grid_sync_count(GridBarrier *b, int *fail, long long wait_ns,
+                                               bool skip_arrive = false)
 {
+    __shared__ int st_bcast;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned int old;
-        asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;"
-                     : "=r"(old)
-                     : "l"(&b->count)
-                     : "memory");
+        if (skip_arrive) {
+            asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(old) : "l"(&b->count) : "memory");
+        } else {
+            asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;"
+                         : "=r"(old)
+                         : "l"(&b->count)
+                         : "memory");
+        }
         const unsigned int target = (old / gridDim.x + 1u) * gridDim.x;
         unsigned long long t0 = 0;
         for (unsigned int spins = 0;; spins++) {
@@ -79,9 +91,27 @@ __device__ __forceinline__ void grid_sync_count(GridBarrier *b, int *fail, long 
                 break;
             }
         }
+        st_bcast = *(volatile int *)fail;
     }
     __syncthreads();
+    return st_bcast;
 }
+
+// CTA-uniform read of a status word (thread 0 reads; block barriers on both
+// sides).
+__device__ __forceinline__ int status_uniform(const int *st)
+{
+    __shared__ int st_u;
+    __syncthreads();
+    if (threadIdx.x == 0) st_u = *(volatile const int *)st;
+    __syncthreads();
+    return st_u;
+}
+
+// Bound of a CTA's wait for its own bulk copies (a few KB from device
+// memory: microseconds).  Fixed, not the caller's wait_ns: an expired wait
+// means the copy engine failed, not that another CTA is slow.
+constexpr long long kCopyWaitNs = 2000000000ll;
 
 // ---------------------------------------------------------------- shared addresses
 __device__ __forceinline__ unsigned smem_u32(const void *p)

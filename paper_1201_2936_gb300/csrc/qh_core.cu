@@ -43,6 +43,25 @@ int persistent_grid_smem(const void *func, int block, int blocks_per_sm, size_t 
     return per_sm * sms;
 }
 
+int sm_count()
+{
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = cache.find(dev);
+        if (it != cache.end()) return it->second;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        return 1;
+    std::lock_guard<std::mutex> g(mu);
+    cache[dev] = sms;
+    return sms;
+}
+
 }  // namespace qh
 
 extern "C" const char *qh_status_str(qh_status s)

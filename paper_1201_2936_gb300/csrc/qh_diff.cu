@@ -21,6 +21,7 @@
 #include <algorithm>
 
 #include "qh.h"
+#include "qh_internal.h"
 
 namespace qh {
 namespace diff {
@@ -224,8 +225,12 @@ __global__ void __launch_bounds__(kBlock) k_round3d(const double *acc, long long
     }
 }
 
-static int cloud_grid(int ncloud) { return std::max(1, std::min(ncloud, 152 * 8)); }
-static int pts_grid(long long n) { return (int)std::max(1ll, std::min((n + 255) / 256, 152ll * 8)); }
+// grid-stride kernels: at most eight CTAs per SM of the current device
+static int cloud_grid(int ncloud) { return std::max(1, std::min(ncloud, 8 * sm_count())); }
+static int pts_grid(long long n)
+{
+    return (int)std::max(1ll, std::min((n + 255) / 256, 8ll * sm_count()));
+}
 
 }  // namespace diff
 }  // namespace qh

@@ -13,5 +13,8 @@ namespace qh {
 int persistent_grid(const void *func, int block, int blocks_per_sm);
 // The same for a kernel launched with `dsmem` bytes of dynamic shared memory.
 int persistent_grid_smem(const void *func, int block, int blocks_per_sm, size_t dsmem);
+// Streaming multiprocessors of the current device (cached per device; 1 on
+// a CUDA error, so that grid sizes stay valid).
+int sm_count();
 
 }  // namespace qh

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "qh.h"
+#include "qh_internal.h"
 
 namespace qh {
 namespace seg {
@@ -28,7 +29,8 @@ namespace seg {
 constexpr int kBlock = 256;
 constexpr int kTileE = 4096;        // elements per scan tile
 constexpr int kMaxK = 7;            // states (the eighth counter numbers the segments)
-constexpr int kGrid = 152 * 4;
+// grid-stride kernels: four CTAs per SM of the current device
+static long long seg_grid() { return 4ll * sm_count(); }
 
 struct Cnt8 {
     int c[8];
@@ -276,7 +278,7 @@ static LayoutS layout_s(long long n)
 
 static int grid_of(long long items)
 {
-    return (int)std::max(1ll, std::min((items + kBlock - 1) / kBlock, (long long)kGrid));
+    return (int)std::max(1ll, std::min((items + kBlock - 1) / kBlock, seg_grid()));
 }
 
 // The scan behind both primitives: segment numbers and counts.
@@ -285,7 +287,7 @@ static void scan_states(const int32_t *f, const int32_t *s, long long n, char *w
 {
     const long long nt = (n + kTileE - 1) / kTileE;
     Cnt8 *tt = (Cnt8 *)(ws + L.tt);
-    const int g = (int)std::max(1ll, std::min(nt, (long long)kGrid));
+    const int g = (int)std::max(1ll, std::min(nt, seg_grid()));
     k_tile_tot<<<g, kBlock, 0, st>>>(f, s, n, tt);
     k_tile_scan<<<1, kBlock, 0, st>>>(tt, nt);
     k_apply<<<g, kBlock, 0, st>>>(f, s, n, tt, (int32_t *)(ws + L.segid),
