@@ -85,15 +85,26 @@ __device__ void extrema3d(const Params3 &A, SmemAll3 &sm, int bid, int nb)
     float4 mn = make_float4(INFINITY, INFINITY, INFINITY, __int_as_float(INT_MAX));
     float4 mx = make_float4(-INFINITY, -INFINITY, -INFINITY, __int_as_float(INT_MAX));
     int bad = 0;
-    for (long long i = (long long)bid * blockDim.x + threadIdx.x; i < A.n;
-         i += (long long)nb * blockDim.x) {
-        float4 p = load_input(A, i);
-        p.x = canon0(p.x);
-        p.y = canon0(p.y);
-        p.z = canon0(p.z);
-        bad |= !(isfinite(p.x) && isfinite(p.y) && isfinite(p.z));
-        if (lex_less(p, mn)) mn = p;
-        if (lex_greater_lowidx(p, mx)) mx = p;
+    constexpr int kU = 4;  // points per thread in flight
+    const long long step = (long long)nb * blockDim.x * kU;
+    for (long long i0 = (long long)bid * blockDim.x * kU + threadIdx.x; i0 < A.n; i0 += step) {
+        float4 q[kU];
+#pragma unroll
+        for (int k = 0; k < kU; k++) {
+            const long long i = i0 + (long long)k * blockDim.x;
+            q[k] = i < A.n ? load_input(A, i) : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+        }
+#pragma unroll
+        for (int k = 0; k < kU; k++) {
+            if (__float_as_int(q[k].w) < 0) continue;
+            float4 p = q[k];
+            p.x = canon0(p.x);
+            p.y = canon0(p.y);
+            p.z = canon0(p.z);
+            bad |= !(isfinite(p.x) && isfinite(p.y) && isfinite(p.z));
+            if (lex_less(p, mn)) mn = p;
+            if (lex_greater_lowidx(p, mx)) mx = p;
+        }
     }
     bad = __syncthreads_or(bad);
     sm.red.a[threadIdx.x] = mn;
@@ -126,9 +137,20 @@ __device__ void farthest3d(const Params3 &A, SmemAll3 &sm, int bid, int nb, int 
     const float c[3] = {H->pc.x, H->pc.y, H->pc.z};
     float best = -1.0f;
     int bi = INT_MAX;
-    for (long long i = (long long)bid * blockDim.x + threadIdx.x; i < A.n;
-         i += (long long)nb * blockDim.x) {
-        float4 p = load_input(A, i);
+    constexpr int kU = 4;  // points per thread in flight
+    const long long step = (long long)nb * blockDim.x * kU;
+    for (long long i0 = (long long)bid * blockDim.x * kU + threadIdx.x; i0 < A.n; i0 += step) {
+      float4 q[kU];
+#pragma unroll
+      for (int k = 0; k < kU; k++) {
+          const long long i = i0 + (long long)k * blockDim.x;
+          q[k] = i < A.n ? load_input(A, i) : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+      }
+#pragma unroll
+      for (int k = 0; k < kU; k++) {
+        const long long i = i0 + (long long)k * blockDim.x;
+        if (i >= A.n) continue;
+        const float4 p = q[k];
         float v;
         if (kind == 0) {
             float ux = b[0] - a[0], uy = b[1] - a[1], uz = b[2] - a[2];
@@ -147,6 +169,7 @@ __device__ void farthest3d(const Params3 &A, SmemAll3 &sm, int bid, int nb, int 
                 bi = (int)i;
             }
         }
+      }
     }
     sm.red.v[threadIdx.x] = best;
     sm.red.i[threadIdx.x] = bi;
@@ -195,42 +218,86 @@ __device__ void exact_search3d(const Params3 &A, int bid, int nb, int kind)
     }
 }
 
-// Block 0: reduce the per-block candidates of the previous phase.
+// Block 0: reduce the per-block candidates of the previous phase (every
+// thread of the block takes a stride of them, then a tree in shared memory).
 __device__ void simplex_step(const Params3 &A, SmemAll3 &sm, int step, int nblk)
 {
     Hdr3 *H = A.hdr;
-    if (threadIdx.x != 0) return;
+    const int t = threadIdx.x;
     if (step == 0) {
-        float4 mn = A.blk_a[0], mx = A.blk_b[0];
-        for (int b = 1; b < nblk; b++) {
-            if (lex_less(A.blk_a[b], mn)) mn = A.blk_a[b];
-            if (lex_greater_lowidx(A.blk_b[b], mx)) mx = A.blk_b[b];
+        float4 mn = make_float4(INFINITY, INFINITY, INFINITY, __int_as_float(INT_MAX));
+        float4 mx = make_float4(-INFINITY, -INFINITY, -INFINITY, __int_as_float(INT_MAX));
+        bool any = false;
+        for (int b = t; b < nblk; b += blockDim.x) {
+            const float4 a = A.blk_a[b], c = A.blk_b[b];
+            if (!any || lex_less(a, mn)) mn = a;
+            if (!any || lex_greater_lowidx(c, mx)) mx = c;
+            any = true;
         }
-        H->pa = mn;
-        H->pb = mx;
-        if (mn.x == mx.x && mn.y == mx.y && mn.z == mx.z) set_status(H, QH_ERR_DEGENERATE);
+        sm.red.a[t] = mn;
+        sm.red.b[t] = mx;
+        sm.red.i[t] = any;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (t < s && sm.red.i[t + s]) {
+                const bool mine = sm.red.i[t] != 0;
+                if (!mine || lex_less(sm.red.a[t + s], sm.red.a[t])) sm.red.a[t] = sm.red.a[t + s];
+                if (!mine || lex_greater_lowidx(sm.red.b[t + s], sm.red.b[t]))
+                    sm.red.b[t] = sm.red.b[t + s];
+                sm.red.i[t] = 1;
+            }
+            __syncthreads();
+        }
+        if (t == 0) {
+            mn = sm.red.a[0];
+            mx = sm.red.b[0];
+            H->pa = mn;
+            H->pb = mx;
+            if (mn.x == mx.x && mn.y == mx.y && mn.z == mx.z) set_status(H, QH_ERR_DEGENERATE);
+        }
+        __syncthreads();
     } else {
-        float bv = A.blk_v[0];
-        int bi = A.blk_i[0];
-        for (int b = 1; b < nblk; b++) {
-            if (A.blk_v[b] > bv || (A.blk_v[b] == bv && A.blk_i[b] < bi)) {
-                bv = A.blk_v[b];
-                bi = A.blk_i[b];
+        float bv = -2.0f;
+        int bi = INT_MAX;
+        for (int b = t; b < nblk; b += blockDim.x) {
+            const float v = A.blk_v[b];
+            const int i = A.blk_i[b];
+            if (v > bv || (v == bv && i < bi)) {
+                bv = v;
+                bi = i;
             }
         }
-        H->search_idx = INT_MAX;
-        H->cand_idx = bi;
-        // exact check of the FP32 choice
-        bool ok = false;
-        if (bi >= 0 && bi < A.n) {
-            float4 p = load_input(A, bi);
-            const float a[3] = {H->pa.x, H->pa.y, H->pa.z};
-            const float b[3] = {H->pb.x, H->pb.y, H->pb.z};
-            const float c[3] = {H->pc.x, H->pc.y, H->pc.z};
-            float q[3] = {p.x, p.y, p.z};
-            ok = step == 1 ? !collinear3_exact(a, b, q) : orient3d_exact_sign(a, b, c, q) != 0;
+        sm.red.v[t] = bv;
+        sm.red.i[t] = bi;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (t < s) {
+                const float ov = sm.red.v[t + s];
+                const int oi = sm.red.i[t + s];
+                if (ov > sm.red.v[t] || (ov == sm.red.v[t] && oi < sm.red.i[t])) {
+                    sm.red.v[t] = ov;
+                    sm.red.i[t] = oi;
+                }
+            }
+            __syncthreads();
         }
-        H->cand_ok = ok;
+        if (t == 0) {
+            bi = sm.red.i[0];
+            H->search_idx = INT_MAX;
+            H->cand_idx = bi;
+            // exact check of the FP32 choice
+            bool ok = false;
+            if (bi >= 0 && bi < A.n) {
+                float4 p = load_input(A, bi);
+                const float a[3] = {H->pa.x, H->pa.y, H->pa.z};
+                const float b[3] = {H->pb.x, H->pb.y, H->pb.z};
+                const float c[3] = {H->pc.x, H->pc.y, H->pc.z};
+                float q[3] = {p.x, p.y, p.z};
+                ok = step == 1 ? !collinear3_exact(a, b, q) : orient3d_exact_sign(a, b, c, q) != 0;
+            }
+            H->cand_ok = ok;
+        }
+        __syncthreads();
     }
 }
 
@@ -278,7 +345,8 @@ __device__ void build_tetra_at(const Params3 &A, int base, const float4 *t, int 
         A.fac[base + o] = f;
         Acc3 z = {};
         A.acc[base + o] = z;
-        A.claim[base + o] = 0ull;
+        A.claim[0][base + o] = 0ull;
+        A.claim[1][base + o] = 0ull;
         A.taken[base + o] = 0;
         A.big_mark[base + o] = -1;
     }
@@ -304,7 +372,8 @@ __device__ void dead_tetra_at(const Params3 &A, int base, int pseudo)
         A.fac[base + o] = f;
         Acc3 z = {};
         A.acc[base + o] = z;
-        A.claim[base + o] = 0ull;
+        A.claim[0][base + o] = 0ull;
+        A.claim[1][base + o] = 0ull;
         A.taken[base + o] = 0;
         A.big_mark[base + o] = -1;
     }
@@ -502,16 +571,21 @@ __device__ void init_clouds(const Params3 &A, SmemAll3 &sm, int bid, int nb)
 
 // ---------------------------------------------------------------- S: select
 // One thread per segment (candidate): visible-set BFS from its facet with
-// exact tests.  V: visible facets, N: their non-visible neighbours.
+// exact tests.  V: visible facets, N: their non-visible neighbours.  A
+// candidate whose lists fit claims its visible facets for round 0 at once.
 template <int MODE>
-__device__ void select3d(const Params3 &A, int par, int bid, int nb)
+__device__ void select3d(const Params3 &A, int par, int iter, int bid, int nb)
 {
     Hdr3 *H = A.hdr;
-    const int ne = *(volatile int *)&H->nent[par];
+    const int ne = (int)(*(volatile unsigned long long *)&H->tab[par] >> 32);
     const Ent3 *ent = A.ent[par];
     unsigned fallbacks = 0;
-    for (int e = bid * blockDim.x + threadIdx.x; e < ne; e += nb * blockDim.x) {
-        const int f0 = ent[e].f;
+    int nact = 0;
+    const int per = (ne + nb - 1) / nb;
+    const int e_lo = min(ne, bid * per), e_hi = min(ne, e_lo + per);
+    for (int e = e_lo + threadIdx.x; e < e_hi; e += blockDim.x) {
+        const Ent3 en = ent[e];
+        const int f0 = en.f;
         const float4 q4 = A.apex[f0];
         const float q[3] = {q4.x, q4.y, q4.z};
         // the lists live in thread-local memory during the search (the
@@ -547,49 +621,108 @@ __device__ void select3d(const Params3 &A, int par, int bid, int nb)
             int *Ng = A.npool + (size_t)e * kNCap;
             for (int j = 0; j < nv; j++) Vg[j] = V[j];
             for (int j = 0; j < nn; j++) Ng[j] = N[j];
+            const unsigned long long mine = claim_key(iter, 0, f0, en.len);
+            for (int j = 0; j < nv; j++) atomicMax(&A.claim[0][V[j]], mine);
+            nact++;
         }
         A.vn[e] = over ? make_int2(-1, -1) : make_int2(nv, nn);
         A.cstate[e] = over ? 2 : 0;
     }
     unsigned f = __reduce_add_sync(0xffffffffu, fallbacks);
     if ((threadIdx.x & 31) == 0 && f) atomicAdd(&H->fallbacks, (unsigned long long)f);
+    const int na = __reduce_add_sync(0xffffffffu, nact);
+    if ((threadIdx.x & 31) == 0 && na) atomicAdd(&H->nact[0], na);
 }
 
-// Round `round` of the selection: every still-active candidate drops out if
-// a winner of an earlier round deleted a facet of V or N (their regions would
-// touch), else claims its visible facets.
-__device__ void claim3d(const Params3 &A, int par, int iter, int round, int bid, int nb)
+// The same search with one warp per candidate, level by level: the lanes
+// take the unexpanded visible facets' neighbour slots of a level at once;
+// a neighbour met by several lanes is tested by the lowest, one already
+// listed is skipped; visible ones join V (expanded at the next level), the
+// others N.  The lists (sets) are those of select3d.  Used when there are
+// no more candidates than warps in the grid.
+template <int MODE>
+__device__ void select3d_warp(const Params3 &A, int par, int iter, SmemAll3 &sm, int bid, int nb)
 {
     Hdr3 *H = A.hdr;
-    if (bid == 0 && threadIdx.x == 0) H->nactive[(round + 1) & 1] = 0;  // next round's counter
-    const int ne = *(volatile int *)&H->nent[par];
+    const int ne = (int)(*(volatile unsigned long long *)&H->tab[par] >> 32);
     const Ent3 *ent = A.ent[par];
-    for (int e = bid * blockDim.x + threadIdx.x; e < ne; e += nb * blockDim.x) {
-        if (A.cstate[e] != 0) continue;
-        const int2 c = A.vn[e];
-        const int *V = A.vpool + (size_t)e * kVCap;
-        const int *N = A.npool + (size_t)e * kNCap;
-        bool touched = false;
-        if (round > 0) {
-            for (int j = 0; j < c.x && !touched; j++) touched = A.taken[V[j]] == iter;
-            for (int j = 0; j < c.y && !touched; j++) touched = A.taken[N[j]] == iter;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const unsigned lt = lanemask_lt();
+    int *V = sm.bfs.V[warp];
+    int *N = sm.bfs.N[warp];
+    unsigned fallbacks = 0;
+    int nact = 0;
+    for (int e = bid * nwarp + warp; e < ne; e += nb * nwarp) {
+        const Ent3 en = ent[e];
+        const int f0 = en.f;
+        const float4 q4 = A.apex[f0];
+        const float q[3] = {q4.x, q4.y, q4.z};
+        if (lane == 0) V[0] = f0;
+        int nv = 1, nn = 0, done = 0;
+        bool over = false;
+        __syncwarp();
+        while (done < nv && !over) {
+            const int lo = done, cnt = 3 * (nv - done);
+            done = nv;
+            for (int b0 = 0; b0 < cnt && !over; b0 += 32) {
+                const int it = b0 + lane;
+                int g = -1;
+                if (it < cnt) g = A.fac[V[lo + it / 3]].nb[it - 3 * (it / 3)];
+                const unsigned same = __match_any_sync(0xffffffffu, g);
+                bool keep = g >= 0 && lane == __ffs(same) - 1;
+                for (int j = 0; j < nv && keep; j++) keep = V[j] != g;
+                for (int j = 0; j < nn && keep; j++) keep = N[j] != g;
+                bool vis = false;
+                if (keep) {
+                    const Fac3 &G = A.fac[g];
+                    const float *a, *b, *c;
+                    fac_pts(G, a, b, c);
+                    float d, err;
+                    orient3d_value<MODE>(a, b, c, q, d, err);
+                    vis = orient3d_sign<MODE>(d, err, a, b, c, q, fallbacks) > 0;
+                }
+                const unsigned bv = __ballot_sync(0xffffffffu, keep && vis);
+                const unsigned bn = __ballot_sync(0xffffffffu, keep && !vis);
+                if (nv + __popc(bv) > kVCap || nn + __popc(bn) > kNCap) {
+                    over = true;
+                } else {
+                    if (keep && vis) V[nv + __popc(bv & lt)] = g;
+                    if (keep && !vis) N[nn + __popc(bn & lt)] = g;
+                    nv += __popc(bv);
+                    nn += __popc(bn);
+                }
+                __syncwarp();
+            }
         }
-        if (touched) {
-            A.cstate[e] = 2;
-            continue;
+        if (!over) {
+            int *Vg = A.vpool + (size_t)e * kVCap;
+            int *Ng = A.npool + (size_t)e * kNCap;
+            const unsigned long long mine = claim_key(iter, 0, f0, en.len);
+            for (int j = lane; j < nv; j += 32) {
+                Vg[j] = V[j];
+                atomicMax(&A.claim[0][V[j]], mine);
+            }
+            for (int j = lane; j < nn; j += 32) Ng[j] = N[j];
+            nact += lane == 0;
         }
-        const unsigned long long mine = claim_key(iter, round, ent[e].f, ent[e].len);
-        for (int j = 0; j < c.x; j++) atomicMax(&A.claim[V[j]], mine);
-        atomicAdd(&H->nactive[round & 1], 1);
+        if (lane == 0) {
+            A.vn[e] = over ? make_int2(-1, -1) : make_int2(nv, nn);
+            A.cstate[e] = over ? 2 : 0;
+        }
+        __syncwarp();
     }
+    unsigned f = __reduce_add_sync(0xffffffffu, fallbacks);
+    if (lane == 0 && f) atomicAdd(&H->fallbacks, (unsigned long long)f);
+    const int na = __reduce_add_sync(0xffffffffu, nact);
+    if (lane == 0 && na) atomicAdd(&H->nact[0], na);
 }
 
 // Cone of one winner: horizon edges of V (edges whose neighbour is not in V),
 // one facet (u, v, q) per horizon edge, neighbours relinked.  V and N are the
 // winner's visible facets and horizon neighbours; hz is scratch for the
-// horizon (capacity >= |V| + 2).
+// horizon (capacity >= |V| + 2); cl holds the claims of `round`.
 __device__ bool build_cone(const Params3 &A, int f0, int len, const int *V, int nv, int *hz,
-                           int hcap, int iter, int round)
+                           int hcap, int iter, int round, const unsigned long long *cl)
 {
     Hdr3 *H = A.hdr;
     const unsigned long long mine = claim_key(iter, round, f0, len);
@@ -600,7 +733,7 @@ __device__ bool build_cone(const Params3 &A, int f0, int len, const int *V, int 
         const Fac3 &F = A.fac[V[i]];
         for (int k = 0; k < 3; k++) {
             int g = F.nb[k];
-            if (A.claim[g] == mine) continue;  // g is in V
+            if (cl[g] == mine) continue;  // g is in V
             if (nh == hcap) {  // a visible region that is not a disk: cannot happen
                 set_status(H, QH_ERR_CAPACITY);
                 return false;
@@ -632,7 +765,8 @@ __device__ bool build_cone(const Params3 &A, int f0, int len, const int *V, int 
         A.fac[base + j] = C;
         Acc3 z = {};
         A.acc[base + j] = z;
-        A.claim[base + j] = 0ull;
+        A.claim[0][base + j] = 0ull;
+        A.claim[1][base + j] = 0ull;
         A.taken[base + j] = 0;
         A.big_mark[base + j] = -1;
         // the horizon neighbour now points at the cone facet
@@ -661,13 +795,13 @@ __device__ bool build_cone(const Params3 &A, int f0, int len, const int *V, int 
 }
 
 // ---------------------------------------------------------------- C: winners
-// One warp per candidate that claimed in this round.  A winner owns every
-// facet of V and no facet of N carries a higher claim; it builds its cone at
-// once: horizon edges found by the lanes (ballot-compacted), one cone facet
-// per horizon edge, the horizon neighbours relinked, and the cone facets
-// linked around the apex by matching edge ends across lanes (shuffles).
+// One warp builds one winner's cone: horizon edges found by the lanes
+// (ballot-compacted; g is in V exactly when it carries the winner's claim
+// of this round in cl), one cone facet per horizon edge, the horizon
+// neighbours relinked, and the cone facets linked around the apex by
+// matching edge ends across lanes (shuffles).
 __device__ void cone_warp(const Params3 &A, int e, int f0, int len, const int *V, int nv,
-                          int *hz, int iter, int round)
+                          int *hz, int iter, int round, const unsigned long long *cl)
 {
     Hdr3 *H = A.hdr;
     const int lane = threadIdx.x & 31;
@@ -681,7 +815,7 @@ __device__ void cone_warp(const Params3 &A, int e, int f0, int len, const int *V
         bool is_h = false;
         if (p < 3 * nv) {
             const int i = p / 3, k = p - 3 * (p / 3);
-            is_h = A.claim[A.fac[V[i]].nb[k]] != mine;
+            is_h = cl[A.fac[V[i]].nb[k]] != mine;
         }
         const unsigned b = __ballot_sync(0xffffffffu, is_h);
         if (is_h) {
@@ -726,7 +860,8 @@ __device__ void cone_warp(const Params3 &A, int e, int f0, int len, const int *V
         A.fac[base + j] = C;
         Acc3 z = {};
         A.acc[base + j] = z;
-        A.claim[base + j] = 0ull;
+        A.claim[0][base + j] = 0ull;
+        A.claim[1][base + j] = 0ull;
         A.taken[base + j] = 0;
         A.big_mark[base + j] = -1;
         Fac3 &G = A.fac[g];
@@ -770,54 +905,74 @@ __device__ void cone_warp(const Params3 &A, int e, int f0, int len, const int *V
     }
 }
 
-__device__ void cone3d(const Params3 &A, int par, int iter, int round, int bid, int nb)
+// Round r of the selection, one phase: every still-active candidate drops out
+// if a winner of an earlier round deleted a facet of V or N (their regions
+// would touch); else it wins when it owns every facet of V in this round's
+// claims (claim[r & 1]) and no facet of N carries a higher claim.  A
+// candidate that lost claims its visible facets for round r + 1 in the
+// other claim array, which this round's checks and cones never read.  The
+// CTA's winners are collected in shared memory and their cones built one
+// warp per winner.  Winners of one round touch disjoint, non-adjacent facet
+// sets (a facet of V_u in N_w would carry u's claim above w's, and one of
+// V_w in N_u w's above u's), so their cones commute; a later round's winner
+// re-checks against every earlier round's deletions.
+__device__ void round3d(const Params3 &A, int par, int iter, int r, bool last, SmemAll3 &sm,
+                        int bid, int nb)
 {
     Hdr3 *H = A.hdr;
-    const int ne = *(volatile int *)&H->nent[par];
+    const int ne = (int)(*(volatile unsigned long long *)&H->tab[par] >> 32);
     const Ent3 *ent = A.ent[par];
-    const int lane = threadIdx.x & 31;
-    const int gw = (bid * blockDim.x + threadIdx.x) >> 5, nw = (nb * blockDim.x) >> 5;
-    // Candidates in groups of G per warp, G ~ candidates / warps (1..32): with
-    // few candidates every candidate gets a warp (its lists checked by all
-    // lanes, its cone built at once); with many, each lane checks one
-    // candidate and the warp then builds the cones of the group's winners.
-    const int G = min(32, max(1, (ne + nw - 1) / nw));
-    for (int base = gw * G; base < ne; base += nw * G) {
-        unsigned wins;
-        if (G == 1) {
-            const int e = base;
-            bool ok = A.cstate[e] == 0;
-            if (ok) {
-                const int2 c = A.vn[e];
-                const unsigned long long mine = claim_key(iter, round, ent[e].f, ent[e].len);
-                const int *V = A.vpool + (size_t)e * kVCap;
-                const int *N = A.npool + (size_t)e * kNCap;
-                for (int j = lane; j < c.x; j += 32) ok &= A.claim[V[j]] == mine;
-                for (int j = lane; j < c.y; j += 32) ok &= A.claim[N[j]] < mine;
+    const unsigned long long *cl = A.claim[r & 1];
+    unsigned long long *cn = A.claim[(r + 1) & 1];
+    const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    int nact = 0;
+    // a contiguous chunk of candidates per CTA: few candidates spread over
+    // every SM (their winners' cones are built by the CTA's warps)
+    const int per = (ne + nb - 1) / nb;
+    const int e_lo = min(ne, bid * per), e_hi = min(ne, e_lo + per);
+    for (int base = e_lo; base < e_hi; base += blockDim.x) {
+        if (threadIdx.x == 0) sm.w.n = 0;
+        __syncthreads();
+        const int e = base + threadIdx.x;
+        if (e < e_hi && A.cstate[e] == 0) {
+            const int2 c = A.vn[e];
+            const int *V = A.vpool + (size_t)e * kVCap;
+            const int *N = A.npool + (size_t)e * kNCap;
+            const Ent3 en = ent[e];
+            bool touched = false;
+            if (r > 0) {
+                for (int j = 0; j < c.x && !touched; j++) touched = A.taken[V[j]] == iter;
+                for (int j = 0; j < c.y && !touched; j++) touched = A.taken[N[j]] == iter;
             }
-            wins = __all_sync(0xffffffffu, ok) ? 1u : 0u;
-        } else {
-            const int e = base + lane;
-            bool win = false;
-            if (lane < G && e < ne && A.cstate[e] == 0) {
-                const int2 c = A.vn[e];
-                const unsigned long long mine = claim_key(iter, round, ent[e].f, ent[e].len);
-                const int *V = A.vpool + (size_t)e * kVCap;
-                const int *N = A.npool + (size_t)e * kNCap;
-                win = true;
-                for (int j = 0; j < c.x && win; j++) win = A.claim[V[j]] == mine;
-                for (int j = 0; j < c.y && win; j++) win = A.claim[N[j]] < mine;
+            if (touched) {
+                A.cstate[e] = 2;
+            } else {
+                const unsigned long long mine = claim_key(iter, r, en.f, en.len);
+                bool win = true;
+                for (int j = 0; j < c.x && win; j++) win = cl[V[j]] == mine;
+                for (int j = 0; j < c.y && win; j++) win = cl[N[j]] < mine;
+                if (win) {
+                    sm.w.list[atomicAdd(&sm.w.n, 1)] = e;
+                } else if (!last) {
+                    const unsigned long long next = claim_key(iter, r + 1, en.f, en.len);
+                    for (int j = 0; j < c.x; j++) atomicMax(&cn[V[j]], next);
+                    nact++;
+                }
             }
-            wins = __ballot_sync(0xffffffffu, win);
         }
-        while (wins) {
-            const int l = __ffs(wins) - 1;
-            wins &= wins - 1;
-            const int ew = base + l;
+        __syncthreads();
+        const int nw = sm.w.n;
+        for (int i = warp; i < nw; i += nwarp) {
+            const int ew = sm.w.list[i];
             // the horizon list reuses the candidate's neighbour slice (>= |V| + 2)
-            cone_warp(A, ew, ent[ew].f, ent[ew].len, A.vpool + (size_t)ew * kVCap,
-                      A.vn[ew].x, A.npool + (size_t)ew * kNCap, iter, round);
+            cone_warp(A, ew, ent[ew].f, ent[ew].len, A.vpool + (size_t)ew * kVCap, A.vn[ew].x,
+                      A.npool + (size_t)ew * kNCap, iter, r, cl);
         }
+        __syncthreads();  // the list is reused by the next chunk
+    }
+    if (!last) {
+        const int na = __reduce_add_sync(0xffffffffu, nact);
+        if ((threadIdx.x & 31) == 0 && na) atomicAdd(&H->nact[r + 1], na);
     }
 }
 
@@ -828,7 +983,7 @@ __device__ void fallback3d(const Params3 &A, int par, int iter)
 {
     Hdr3 *H = A.hdr;
     if (threadIdx.x != 0) return;
-    const int ne = H->nent[par];
+    const int ne = (int)(H->tab[par] >> 32);
     const Ent3 *ent = A.ent[par];
     int f0 = INT_MAX, len = 0;
     for (int e = 0; e < ne; e++)
@@ -843,46 +998,58 @@ __device__ void fallback3d(const Params3 &A, int par, int iter)
     int nv = 1;
     V[0] = f0;
     const unsigned long long mine = claim_key(iter, kRounds, f0, len);
-    A.claim[f0] = mine;
+    unsigned long long *cl = A.claim[kRounds & 1];  // round kRounds: above every claim
+    cl[f0] = mine;
     unsigned fb = 0;
     for (int i = 0; i < nv; i++) {
         const Fac3 &F = A.fac[V[i]];
         for (int k = 0; k < 3; k++) {
             const int g = F.nb[k];
-            if (A.claim[g] == mine || A.big_mark[g] == iter) continue;
+            if (cl[g] == mine || A.big_mark[g] == iter) continue;
             const Fac3 &G = A.fac[g];
             const float *a, *b, *c;
             fac_pts(G, a, b, c);
             float d, err;
             orient3d_value<MODE>(a, b, c, q, d, err);
             if (orient3d_sign<MODE>(d, err, a, b, c, q, fb) > 0) {
-                A.claim[g] = mine;
+                cl[g] = mine;
                 V[nv++] = g;
             } else {
                 A.big_mark[g] = iter;
             }
         }
     }
-    build_cone(A, f0, len, V, nv, A.big_h, A.fcap, iter, kRounds);
+    build_cone(A, f0, len, V, nv, A.big_h, A.fcap, iter, kRounds, cl);
 }
 
 // ---------------------------------------------------------------- A: assign
-// Target of every live point: its own facet if that facet survives (rank =
-// position in the segment), else the first cone facet of its winner that it
-// is strictly above (warp-aggregated count, rank and farthest-point key), else
-// discarded (-1).  FIRST: the input points against the tetrahedron.
+// Target of every live point whose facet was deleted this iteration: the
+// first cone facet of its winner that it is strictly above (warp-aggregated
+// count, rank and farthest-point key), else discarded (-1); code[v] receives
+// (target, rank).  Points of surviving facets are left alone (the scatter
+// moves their segments whole), and a tile that meets no deleted facet is
+// skipped.  FIRST: the input points against the tetrahedron.
 template <int MODE, int ITEMS, bool FIRST>
-__device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int nb)
+__device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, SmemSlots &ss, int bid, int nb)
 {
     Hdr3 *H = A.hdr;
-    const int L = FIRST ? A.n : *(volatile int *)&H->L[par];
+    const int L = FIRST ? A.n : (int)(*(volatile unsigned long long *)&H->tab[par] & 0xffffffffull);
     const Ent3 *ent = A.ent[par];
     const float4 *P = A.pts[par];
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     unsigned fallbacks = 0;
-    const int T = A.tile;  // blockDim.x * ITEMS
+    // points per tile: blockDim.x * ITEMS, or fewer for a small table (so
+    // that its tiles spread over the SMs)
+    const int T = FIRST ? A.tile : *(volatile int *)&H->tile_sz[par];
     const int ntiles = (L + T - 1) / T;
+    for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
+        ss.skey[i] = -1;
+        ss.scnt[i] = 0;
+        ss.sk1[i] = 0ull;
+        ss.so2[i] = 0u;
+        ss.sem[i] = 0u;
+    }
     for (int tile = bid; tile < ntiles; tile += nb) {
         const int v0 = tile * T, v1 = min(v0 + T, L);
         __syncthreads();
@@ -892,34 +1059,56 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int n
                 sm.a.e0 = c0;
                 sm.a.m = cloud_of(A, v1 - 1) - c0 + 1;
             } else {
-                sm.a.e0 = A.tile_ent[tile];
-                sm.a.m = A.tile_m[tile];
+                sm.a.e0 = A.tile_ent[par][tile];
+                sm.a.m = A.tile_m[par][tile];
             }
-        }
-        for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
-            sm.a.skey[i] = -1;
-            sm.a.scnt[i] = 0;
-            sm.a.sk1[i] = 0ull;
-            sm.a.so2[i] = 0u;
-            sm.a.sem[i] = 0u;
         }
         __syncthreads();
         const int e0 = sm.a.e0, m = sm.a.m;
         // FIRST: a tile that meets more clouds than the stage holds (runs of
         // empty clouds) searches the cloud offsets in global memory instead
+        // entries: start, and the facet (>= 0) when it was deleted, -1 - facet
+        // when it survives
         const bool staged = m <= kMaxTile;
+        int dead = FIRST ? 1 : 0;
         for (int i = threadIdx.x; i < m && i < kMaxTile; i += blockDim.x) {
             if (FIRST) {
                 sm.a.start[i] = cloud_start(A, e0 + i);
                 sm.a.f[i] = A.fcap + e0 + i;
             } else {
-                sm.a.start[i] = ent[e0 + i].start;
-                sm.a.f[i] = ent[e0 + i].f;
+                const Ent3 en = ent[e0 + i];
+                const bool alive = A.fac[en.f].alive != 0;
+                sm.a.start[i] = en.start;
+                sm.a.f[i] = alive ? -1 - en.f : en.f;
+                dead |= !alive;
             }
         }
-        __syncthreads();
-        // ---- classify; cone targets get a tile-local slot (shared hash table)
-        int tgt[ITEMS], rk[ITEMS], slot[ITEMS];
+        if (!__syncthreads_or(dead)) continue;  // every facet of the tile survives
+        // ---- each item's facet (>= 0: deleted, to classify) and point,
+        // every load issued before the first classification
+        int fit[ITEMS];
+        float4 pit[ITEMS];
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            const int v = v0 + k * blockDim.x + threadIdx.x;
+            fit[k] = -1;
+            if (v < v1) {
+                int lo = 0, hi = m - 1;
+                if (FIRST && !staged) {
+                    fit[k] = A.fcap + cloud_of(A, v);
+                } else {
+                    while (lo < hi) {
+                        int mid = (lo + hi + 1) >> 1;
+                        if (sm.a.start[mid] <= v) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    fit[k] = sm.a.f[lo];
+                }
+            }
+            if (fit[k] >= 0) pit[k] = FIRST ? load_input(A, v) : P[v];
+        }
+        // ---- classify; cone targets get a slot of the CTA's table (shared
+        // hash), or go straight to the global accumulator when it is full
 #pragma unroll
         for (int k = 0; k < ITEMS; k++) {
             const int v = v0 + k * blockDim.x + threadIdx.x;
@@ -927,27 +1116,14 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int n
             int target = -1, rank = 0, s = -1;
             float d = 0.0f, err = 0.0f;
             int idx = 0;
-            bool cone_t = false;
+            bool cone_t = false, f_dead = false;
             if (valid) {
-                int lo = 0, hi = m - 1, f;
-                if (FIRST && !staged) {
-                    lo = cloud_of(A, v) - e0;
-                    f = A.fcap + e0 + lo;
-                } else {
-                    while (lo < hi) {
-                        int mid = (lo + hi + 1) >> 1;
-                        if (sm.a.start[mid] <= v) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    f = sm.a.f[lo];
-                }
-                const float4 p4 = FIRST ? load_input(A, v) : P[v];
-                idx = __float_as_int(p4.w);
-                const float p[3] = {p4.x, p4.y, p4.z};
-                if (!FIRST && A.fac[f].alive) {
-                    target = f;
-                    rank = v - sm.a.start[lo];
-                } else {
+                const int f = fit[k];
+                f_dead = f >= 0;
+                if (f_dead) {
+                    const float4 p4 = pit[k];
+                    idx = __float_as_int(p4.w);
+                    const float p[3] = {p4.x, p4.y, p4.z};
                     const int4 cn = A.cone[f];
                     bool skip = idx == cn.z;  // the apex itself
                     if (FIRST && cn.y == 4) {
@@ -988,7 +1164,7 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int n
                     // find or insert the target's slot (linear probing)
                     int h = (int)(((unsigned)target * 0x9E3779B1u) >> (32 - kSlotBits));
                     for (int probe = 0; probe < kSlots; probe++) {
-                        const int prev = atomicCAS(&sm.a.skey[h], -1, target);
+                        const int prev = atomicCAS(&ss.skey[h], -1, target);
                         if (prev == -1 || prev == target) {
                             s = h;
                             break;
@@ -998,12 +1174,12 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int n
                     const unsigned long long k1 =
                         ((unsigned long long)top_o << 32) | (0xffffffffu - top_i);
                     if (s >= 0) {
-                        base = atomicAdd(&sm.a.scnt[s], __popc(grp));
-                        const unsigned long long old = atomicMax(&sm.a.sk1[s], k1);
+                        base = atomicAdd(&ss.scnt[s], __popc(grp));
+                        const unsigned long long old = atomicMax(&ss.sk1[s], k1);
                         const unsigned long long lo2 = old < k1 ? old : k1;
                         const unsigned lo_o = (unsigned)(lo2 >> 32);
-                        atomicMax(&sm.a.so2[s], lo_o > sec_o ? lo_o : sec_o);
-                        atomicMax(&sm.a.sem[s], em);
+                        atomicMax(&ss.so2[s], lo_o > sec_o ? lo_o : sec_o);
+                        atomicMax(&ss.sem[s], em);
                     } else {
                         // table full: straight to the global accumulator
                         Acc3 &ac = A.acc[target];
@@ -1019,99 +1195,103 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, int bid, int n
                 s = __shfl_sync(grp, s, leader);
                 rank = base + __popc(grp & lt);
             }
-            tgt[k] = valid ? target : -2;
-            rk[k] = rank;
-            slot[k] = s;
+            // code: (target, (slot << kLocalBits) | rank in the CTA's count),
+            // (target, -1 - global rank) past a full table, (-1, 0) discarded
+            if (valid && f_dead) {
+                const int r = !cone_t ? 0 : (s >= 0 ? (s << kLocalBits) | rank : -1 - rank);
+                A.code[v] = make_int2(target, r);
+            }
         }
-        __syncthreads();
-        // ---- one global reservation and key merge per (tile, target)
-        for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
-            const int t = sm.a.skey[i];
-            if (t < 0) continue;
-            Acc3 &ac = A.acc[t];
-            sm.a.sbase[i] = (int)atomicAdd(&ac.cnt, (unsigned)sm.a.scnt[i]);
-            const unsigned long long k1 = sm.a.sk1[i];
-            const unsigned long long old = atomicMax(&ac.key1, k1);
-            const unsigned long long lo2 = old < k1 ? old : k1;
-            const unsigned lo_o = (unsigned)(lo2 >> 32);
-            const unsigned o2 = sm.a.so2[i];
-            atomicMax(&ac.o2, lo_o > o2 ? lo_o : o2);
-            atomicMax(&ac.emax, sm.a.sem[i]);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < ITEMS; k++) {
-            const int v = v0 + k * blockDim.x + threadIdx.x;
-            if (tgt[k] == -2) continue;
-            const int r = (slot[k] >= 0) ? sm.a.sbase[slot[k]] + rk[k] : rk[k];
-            A.code[v] = make_int2(tgt[k], r);
-        }
+    }
+    // ---- one reservation and key merge per (CTA, target)
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
+        const int t = ss.skey[i];
+        if (t < 0) continue;
+        if (ss.scnt[i] >= (1 << kLocalBits)) set_status(H, QH_ERR_CAPACITY);
+        Acc3 &ac = A.acc[t];
+        ss.sbase[i] = (int)atomicAdd(&ac.cnt, (unsigned)ss.scnt[i]);
+        const unsigned long long k1 = ss.sk1[i];
+        const unsigned long long old = atomicMax(&ac.key1, k1);
+        const unsigned long long lo2 = old < k1 ? old : k1;
+        const unsigned lo_o = (unsigned)(lo2 >> 32);
+        const unsigned o2 = ss.so2[i];
+        atomicMax(&ac.o2, lo_o > o2 ? lo_o : o2);
+        atomicMax(&ac.emax, ss.sem[i]);
     }
     unsigned fsum = __reduce_add_sync(0xffffffffu, fallbacks);
     if (lane == 0 && fsum) atomicAdd(&H->fallbacks, (unsigned long long)fsum);
 }
 
+// Destination of a point classified into a cone facet (code from assign3d,
+// slot bases of the CTA that classified it: the same CTA as the caller).
+__device__ __forceinline__ int code_dst(const Params3 &A, const SmemSlots &ss, int2 cr)
+{
+    if (cr.x < 0) return -1;
+    const int r = cr.y >= 0 ? ss.sbase[cr.y >> kLocalBits] + (cr.y & ((1 << kLocalBits) - 1))
+                            : -1 - cr.y;
+    return A.nstart[cr.x] + r;
+}
+
 // ---------------------------------------------------------------- T: table
-// New segment table: the old segments whose facet survives (in order), then
-// the cone facets created this iteration that received points.  Grid-wide
-// exclusive scan in two steps (block sums, then offsets).
-__device__ __forceinline__ int table_item_len(const Params3 &A, int par, int ne, int fc0, int j,
-                                              int &f)
-{
-    if (j < ne) {
-        const Ent3 en = A.ent[par][j];
-        f = en.f;
-        return A.fac[en.f].alive ? en.len : 0;
-    }
-    f = fc0 + (j - ne);
-    return (int)A.acc[f].cnt;
-}
-
-__device__ void table_sum(const Params3 &A, int par, bool first, SmemAll3 &sm, int bid, int nb)
+// New segment table (the other parity): the old segments whose facet
+// survives and the cone facets created this iteration that received points.
+// Each CTA takes blocks of items, scans a block in shared memory and
+// reserves its entries and points with one 64-bit atomic ((entries << 32) |
+// points), so entries come out sorted by start (the order of the blocks is
+// whatever the atomics give; no hull result depends on it).  A new facet's
+// FP32 farthest point is certified here (top-2 gap against twice the largest
+// error bound) or queued for the exact phase; its apex is recorded.
+__device__ void certify_new(const Params3 &A, int f, int e)
 {
     Hdr3 *H = A.hdr;
-    const int ne = first ? 0 : *(volatile int *)&H->nent[par];
+    const Acc3 a = A.acc[f];
+    const int qi = key_idx(a.key1);
+    A.apex[f] = load_input(A, qi);
+    bool cert = true;
+    const float em = __uint_as_float(a.emax);
+    const float d1 = key_dist(a.key1);
+    if (a.cnt > 1) {
+        const float d2 = unord_f32(a.o2);
+        const double gap = ((double)d1 - (double)d2) * (1.0 - 0x1p-50);
+        cert = gap > 2.0 * (double)em;
+    }
+    if (!cert) {
+        const double thr = (double)d1 - 3.0 * (double)em - fabs((double)d1) * 0x1p-20;
+        A.thr[f] = isfinite(thr) ? __double2float_rd(thr) : -INFINITY;
+        A.uncert[atomicAdd(&H->n_uncert, 1)] = e;
+    }
+}
+
+__device__ void table3d(const Params3 &A, int par, bool first, SmemAll3 &sm, int bid, int nb)
+{
+    Hdr3 *H = A.hdr;
+    const int ne = first ? 0 : (int)(*(volatile unsigned long long *)&H->tab[par] >> 32);
     const int fc0 = first ? 0 : *(volatile int *)&H->fc_iter[par];
     const int fc1 = *(volatile int *)&H->fcount;
     const int m = ne + (fc1 - fc0);
-    const int chunk = (m + nb - 1) / nb;
-    const int j0 = bid * chunk, j1 = min(j0 + chunk, m);
-    long long s = 0;
-    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-        int f;
-        int len = table_item_len(A, par, ne, fc0, j, f);
-        s += ((long long)(len > 0) << 32) | (long long)len;
-    }
-    long long tot;
-    block_excl_scan64(s, sm.t.wsum, &tot);
-    if (threadIdx.x == 0) A.part[bid] = tot;
-}
-
-__device__ void table_write(const Params3 &A, int par, bool first, SmemAll3 &sm, int bid, int nb)
-{
-    Hdr3 *H = A.hdr;
-    const int ne = first ? 0 : *(volatile int *)&H->nent[par];
-    const int fc0 = first ? 0 : *(volatile int *)&H->fc_iter[par];
-    const int fc1 = *(volatile int *)&H->fcount;
-    const int m = ne + (fc1 - fc0);
-    const int chunk = (m + nb - 1) / nb;
-    const int j0 = bid * chunk, j1 = min(j0 + chunk, m);
-    // prefix of the earlier blocks
-    long long pre = 0;
-    for (int b = threadIdx.x; b < bid; b += blockDim.x) pre += A.part[b];
-    long long pre_tot;
-    block_excl_scan64(pre, sm.t.wsum, &pre_tot);
-    long long carry = pre_tot;
+    const Ent3 *old = A.ent[par];
     Ent3 *out = A.ent[par ^ 1];
-    for (int base = j0; base < j1; base += blockDim.x) {
+    for (int base = bid * blockDim.x; base < m; base += nb * blockDim.x) {
         const int j = base + threadIdx.x;
         int f = -1, len = 0;
-        if (j < j1) len = table_item_len(A, par, ne, fc0, j, f);
-        long long s = ((long long)(len > 0) << 32) | (long long)len;
+        if (j < ne) {
+            const Ent3 en = old[j];
+            f = en.f;
+            len = A.fac[f].alive ? en.len : 0;
+        } else if (j < m) {
+            f = fc0 + (j - ne);
+            len = (int)A.acc[f].cnt;
+        }
+        const long long s = len > 0 ? ((1ll << 32) | (long long)len) : 0ll;
         long long tot;
-        long long ex = block_excl_scan64(s, sm.t.wsum, &tot) + carry;
+        const long long ex = block_excl_scan64(s, sm.t.wsum, &tot);
+        if (threadIdx.x == 0)
+            sm.t.base = tot ? atomicAdd(&H->tab[par ^ 1], (unsigned long long)tot) : 0ull;
+        __syncthreads();
         if (len > 0) {
-            const int k = (int)(ex >> 32), st = (int)(ex & 0xffffffffll);
+            const unsigned long long b = sm.t.base + (unsigned long long)ex;
+            const int k = (int)(b >> 32), st = (int)(b & 0xffffffffull);
             Ent3 en;
             en.f = f;
             en.start = st;
@@ -1119,82 +1299,126 @@ __device__ void table_write(const Params3 &A, int par, bool first, SmemAll3 &sm,
             en.pad = 0;
             out[k] = en;
             A.nstart[f] = st;
+            if (j >= ne) certify_new(A, f, k);
         }
-        carry += tot;
+        __syncthreads();  // sm.t.base is rewritten by the next block
     }
-    if (bid == nb - 1 && threadIdx.x == 0) {
-        H->nent[par ^ 1] = (int)(carry >> 32);
-        H->L[par ^ 1] = (int)(carry & 0xffffffffll);
+    if (bid == 0 && threadIdx.x == 0) {
         H->fc_lo_last = fc0;
         H->fc_iter[par ^ 1] = fc1;  // read by the next table phase (other parity)
+        // round counters of the next iteration (its select counts round 0)
+        for (int r = 0; r < kRounds; r++) H->nact[r] = 0;
     }
 }
 
 // ---------------------------------------------------------------- B: scatter
+// Every live point of table `par` to its place in the other buffer: a point
+// of a surviving facet keeps its offset in its segment (the segment moves
+// whole, nstart[f] - start), a point of a deleted facet goes where its code
+// says (or nowhere).  Then the tile map of the new table, for the next
+// assign and scatter.  FIRST: the input points and their codes.
 template <bool FIRST>
-__device__ void scatter3d(const Params3 &A, int par, int bid, int nb)
+__device__ void scatter3d(const Params3 &A, int par, SmemAll3 &sm, const SmemSlots &ss, int bid,
+                          int nb)
 {
     Hdr3 *H = A.hdr;
-    const int L = FIRST ? A.n : *(volatile int *)&H->L[par];
+    const int L = FIRST ? A.n : (int)(*(volatile unsigned long long *)&H->tab[par] & 0xffffffffull);
+    const Ent3 *ent = A.ent[par];
     const float4 *P = A.pts[par];
     float4 *Q = A.pts[par ^ 1];
-    for (long long v = (long long)bid * blockDim.x + threadIdx.x; v < L;
-         v += (long long)nb * blockDim.x) {
-        const int2 cr = A.code[v];
-        if (cr.x < 0) continue;
-        const float4 p = FIRST ? load_input(A, v) : P[v];
-        Q[A.nstart[cr.x] + cr.y] = p;
-    }
-}
-
-// New facets: certify the FP32 farthest point (top-2 gap against twice the
-// largest error bound) or queue it for the exact phase; record the apex.
-// Also the tile -> entry map of the next assign phase.
-__device__ void certify3d(const Params3 &A, int par, int bid, int nb)
-{
-    Hdr3 *H = A.hdr;
-    const int ne = *(volatile int *)&H->nent[par ^ 1];
-    const int L = *(volatile int *)&H->L[par ^ 1];
-    const Ent3 *ent = A.ent[par ^ 1];
-    for (int e = bid * blockDim.x + threadIdx.x; e < ne; e += nb * blockDim.x) {
-        const int f = ent[e].f;
-        const Acc3 a = A.acc[f];
-        if (f >= *(volatile int *)&H->fc_lo_last) {
-            // a facet created this iteration: its apex is new
-            const int qi = key_idx(a.key1);
-            const float4 q = load_input(A, qi);
-            A.apex[f] = q;
-            bool cert = true;
-            const float em = __uint_as_float(a.emax);
-            const float d1 = key_dist(a.key1);
-            if (a.cnt > 1) {
-                const float d2 = unord_f32(a.o2);
-                const double gap = ((double)d1 - (double)d2) * (1.0 - 0x1p-50);
-                cert = gap > 2.0 * (double)em;
+    const int T = FIRST ? A.tile : *(volatile int *)&H->tile_sz[par];
+    constexpr int kSc = 4;  // points per thread in flight
+    // the tiles of the assign phase, each on the CTA that classified it (the
+    // codes' ranks are relative to that CTA's slot bases)
+    if (FIRST) {
+        const int ntiles = (L + T - 1) / T;
+        for (int tile = bid; tile < ntiles; tile += nb) {
+            const int v0 = tile * T, v1 = min(v0 + T, L);
+            for (int vb = v0 + threadIdx.x; vb < v1; vb += blockDim.x * kSc) {
+                int dst[kSc];
+                float4 p[kSc];
+#pragma unroll
+                for (int k = 0; k < kSc; k++) {
+                    const int v = vb + k * blockDim.x;
+                    dst[k] = v < v1 ? code_dst(A, ss, A.code[v]) : -1;
+                }
+#pragma unroll
+                for (int k = 0; k < kSc; k++)
+                    if (dst[k] >= 0) p[k] = load_input(A, vb + k * blockDim.x);
+#pragma unroll
+                for (int k = 0; k < kSc; k++)
+                    if (dst[k] >= 0) Q[dst[k]] = p[k];
             }
-            if (!cert) {
-                const double thr = (double)d1 - 3.0 * (double)em - fabs((double)d1) * 0x1p-20;
-                A.thr[f] = isfinite(thr) ? __double2float_rd(thr) : -INFINITY;
-                A.uncert[atomicAdd(&H->n_uncert, 1)] = e;
+        }
+    } else {
+        const int ntiles = (L + T - 1) / T;
+        for (int tile = bid; tile < ntiles; tile += nb) {
+            const int v0 = tile * T, v1 = min(v0 + T, L);
+            __syncthreads();
+            const int e0 = A.tile_ent[par][tile], m = A.tile_m[par][tile];
+            // per entry: start, and the shift of a surviving segment (INT_MIN:
+            // the facet was deleted, its points follow their codes)
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                const Ent3 en = ent[e0 + i];
+                sm.a.start[i] = en.start;
+                sm.a.f[i] = A.fac[en.f].alive ? A.nstart[en.f] - en.start : INT_MIN;
+            }
+            __syncthreads();
+            for (int vb = v0 + threadIdx.x; vb < v1; vb += blockDim.x * kSc) {
+                int dst[kSc];
+                float4 p[kSc];
+#pragma unroll
+                for (int k = 0; k < kSc; k++) {
+                    const int v = vb + k * blockDim.x;
+                    dst[k] = -1;
+                    if (v >= v1) continue;
+                    int lo = 0, hi = m - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (sm.a.start[mid] <= v) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    const int sh = sm.a.f[lo];
+                    if (sh != INT_MIN) {
+                        dst[k] = v + sh;
+                    } else {
+                        dst[k] = code_dst(A, ss, A.code[v]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < kSc; k++) {
+                    const int v = vb + k * blockDim.x;
+                    if (dst[k] >= 0) p[k] = P[v];
+                }
+#pragma unroll
+                for (int k = 0; k < kSc; k++)
+                    if (dst[k] >= 0) Q[dst[k]] = p[k];
             }
         }
     }
-    const int T = A.tile;
-    const int ntiles = (L + T - 1) / T;
-    for (int t = bid * blockDim.x + threadIdx.x; t < ntiles; t += nb * blockDim.x) {
-        const int v = t * T, vl = min(v + T, L) - 1;
+    // tile size and tile -> entries map of the new table: the largest tile
+    // (blockDim.x * ITEMS) halved, down to kMinTile, until every CTA gets one
+    const unsigned long long tb = *(volatile unsigned long long *)&H->tab[par ^ 1];
+    const int ne1 = (int)(tb >> 32), L1 = (int)(tb & 0xffffffffull);
+    const Ent3 *ent1 = A.ent[par ^ 1];
+    int T1 = A.tile;
+    while (T1 > kMinTile && (L1 + T1 - 1) / T1 < nb) T1 >>= 1;
+    if (bid == 0 && threadIdx.x == 0) H->tile_sz[par ^ 1] = T1;
+    const int nt1 = (L1 + T1 - 1) / T1;
+    for (int t = bid * blockDim.x + threadIdx.x; t < nt1; t += nb * blockDim.x) {
+        const int v = t * T1, vl = min(v + T1, L1) - 1;
         auto ent_of = [&](int x) {
-            int lo = 0, hi = ne - 1;
+            int lo = 0, hi = ne1 - 1;
             while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (ent[mid].start <= x) lo = mid;
+                const int mid = (lo + hi + 1) >> 1;
+                if (ent1[mid].start <= x) lo = mid;
                 else hi = mid - 1;
             }
             return lo;
         };
         const int s0 = ent_of(v);
-        A.tile_ent[t] = s0;
-        A.tile_m[t] = ent_of(vl) - s0 + 1;
+        A.tile_ent[par ^ 1][t] = s0;
+        A.tile_m[par ^ 1][t] = ent_of(vl) - s0 + 1;
     }
 }
 
@@ -1319,6 +1543,7 @@ template <int MODE, int ITEMS>
 __global__ void __launch_bounds__(kMaxBlock) qh3d_persistent(Params3 A)
 {
     __shared__ SmemAll3 sm;
+    __shared__ SmemSlots ss;  // an assign phase's targets, read by the following scatter
     Hdr3 *H = A.hdr;
     int *fail = &H->status;
     const int bid = blockIdx.x, nb = gridDim.x;
@@ -1385,45 +1610,53 @@ __global__ void __launch_bounds__(kMaxBlock) qh3d_persistent(Params3 A)
         }
     }
     setup_mark(0);
+    auto tab_ne = [&](int p) { return (int)(*(volatile unsigned long long *)&H->tab[p] >> 32); };
+    auto tab_L = [&](int p) {
+        return (int)(*(volatile unsigned long long *)&H->tab[p] & 0xffffffffull);
+    };
+    // exact farthest points of the facets the table phase left uncertified
+    // (their points must be in place: after a scatter and a barrier); p is
+    // the parity of the table the phase read (the new one is p ^ 1)
+    auto exact_phase = [&](int p) {
+        const int nu = *(volatile int *)&H->n_uncert;
+        if (nu <= 0) return true;
+        const int per = exact_chunks(A, nu, nb);
+        exact3d<MODE>(A, p, sm, bid, nb, per);
+        if (!sync()) return false;
+        if (per > 1) {
+            exact3d_merge<MODE>(A, p, bid, nb, per);
+            if (!sync()) return false;
+        }
+        if (bid == 0 && threadIdx.x == 0) H->exact_argmax += nu;
+        return true;
+    };
     if (go) {
         // ---- first assignment: every input point against the tetrahedron;
         // table 1 / buffer 1 receive the result
-        assign3d<MODE, ITEMS, true>(A, 0, sm, bid, nb);
+        assign3d<MODE, ITEMS, true>(A, 0, sm, ss, bid, nb);
         go = sync();
         setup_mark(1);
         if (go) {
-            table_sum(A, 0, true, sm, bid, nb);
-            go = sync();
-        }
-        if (go) {
-            table_write(A, 0, true, sm, bid, nb);
-            if (bid == 0 && threadIdx.x == 0) H->n_uncert = 0;
+            table3d(A, 0, true, sm, bid, nb);
             go = sync();
         }
         setup_mark(2);
         if (go) {
-            scatter3d<true>(A, 0, bid, nb);
+            scatter3d<true>(A, 0, sm, ss, bid, nb);
             go = sync();
         }
-        if (go) {
-            certify3d(A, 0, bid, nb);
-            go = sync();
-        }
-        if (go && *(volatile int *)&H->n_uncert > 0) {
-            const int per = exact_chunks(A, *(volatile int *)&H->n_uncert, nb);
-            exact3d<MODE>(A, 0, sm, bid, nb, per);
-            go = sync();
-            if (go && per > 1) {
-                exact3d_merge<MODE>(A, 0, bid, nb, per);
-                go = sync();
-            }
-        }
+        if (go) go = exact_phase(0);
         setup_mark(3);
     }
-    // ---- iterations: table `cur` describes the live points in buffer `cur`
+    // ---- iterations: table `cur` describes the live points in buffer `cur`.
+    // Phases: [scatter of the previous iteration +] select with the claims of
+    // round 0 | rounds 0 .. kRounds-1 (winners' cones, next round's claims) |
+    // [lone-apex fallback] | assign | table (+ certification) | [scatter |
+    // exact, when some apex is uncertified].
     int cur = 1;
     int iter = 0;
-    while (go && *(volatile int *)&H->nent[cur] > 0) {
+    bool scatter_due = false;  // the points of table `cur` are still in buffer cur ^ 1
+    while (go && tab_ne(cur) > 0) {
         iter++;
         if (iter > A.max_iters) {
             if (bid == 0 && threadIdx.x == 0) set_status(H, QH_ERR_NO_CONVERGENCE);
@@ -1431,24 +1664,27 @@ __global__ void __launch_bounds__(kMaxBlock) qh3d_persistent(Params3 A)
         }
         if (bid == 0 && threadIdx.x == 0) {
             H->iter = iter;
-            H->nwin = 0;
-            H->seg_total += H->nent[cur];
+            H->nwin = 0;  // counted from the rounds on (after this phase's barrier)
+            H->seg_total += tab_ne(cur);
+            H->surv_total += tab_L(cur);
             if (iter <= kTimeline3) {
-                H->tl[iter - 1][0] = H->L[cur];
-                H->tl[iter - 1][1] = H->nent[cur];
+                H->tl[iter - 1][0] = tab_L(cur);
+                H->tl[iter - 1][1] = tab_ne(cur);
             }
         }
         mark(0, 0);
-        select3d<MODE>(A, cur, bid, nb);
+        if (scatter_due) scatter3d<false>(A, cur ^ 1, sm, ss, bid, nb);
+        if (tab_ne(cur) <= nb * (int)(blockDim.x >> 5)) {
+            __syncthreads();  // the scatter's staging and the warps' lists share memory
+            select3d_warp<MODE>(A, cur, iter, sm, bid, nb);
+        } else {
+            select3d<MODE>(A, cur, iter, bid, nb);
+        }
         if (!sync()) break;
         mark(iter, 3);
-        if (bid == 0 && threadIdx.x == 0) H->nactive[0] = 0;
-        if (!sync()) break;
-        for (int round = 0; round < kRounds && go; round++) {
-            claim3d(A, cur, iter, round, bid, nb);
-            if (!(go = sync())) break;
-            if (*(volatile int *)&H->nactive[round & 1] == 0) break;
-            cone3d(A, cur, iter, round, bid, nb);
+        for (int r = 0; r < kRounds && go; r++) {
+            if (*(volatile int *)&H->nact[r] == 0) break;
+            round3d(A, cur, iter, r, r == kRounds - 1, sm, bid, nb);
             go = sync();
         }
         if (!go) break;
@@ -1458,29 +1694,25 @@ __global__ void __launch_bounds__(kMaxBlock) qh3d_persistent(Params3 A)
         }
         if (clk && iter <= kTimeline3) H->tl[iter - 1][2] = H->nwin;
         mark(iter, 4);
-        assign3d<MODE, ITEMS, false>(A, cur, sm, bid, nb);
+        assign3d<MODE, ITEMS, false>(A, cur, sm, ss, bid, nb);
+        if (bid == 0 && threadIdx.x == 0) {
+            H->tab[cur ^ 1] = 0ull;  // the table of two iterations ago
+            H->n_uncert = 0;
+        }
         if (!sync()) break;
         mark(iter, 5);
-        table_sum(A, cur, false, sm, bid, nb);
-        if (!sync()) break;
-        table_write(A, cur, false, sm, bid, nb);
-        if (bid == 0 && threadIdx.x == 0) H->n_uncert = 0;
+        table3d(A, cur, false, sm, bid, nb);
         if (!sync()) break;
         mark(iter, 6);
-        scatter3d<false>(A, cur, bid, nb);
-        certify3d(A, cur, bid, nb);  // reads the table and accumulators only
-        if (bid == 0 && threadIdx.x == 0) H->surv_total += H->L[cur ^ 1];
-        if (!sync()) break;
-        mark(iter, 7);
+        if (tab_ne(cur ^ 1) == 0) break;  // no point left outside the hull
         if (*(volatile int *)&H->n_uncert > 0) {
-            const int per = exact_chunks(A, *(volatile int *)&H->n_uncert, nb);
-            exact3d<MODE>(A, cur, sm, bid, nb, per);
+            scatter3d<false>(A, cur, sm, ss, bid, nb);
             if (!sync()) break;
-            if (per > 1) {
-                exact3d_merge<MODE>(A, cur, bid, nb, per);
-                if (!sync()) break;
-            }
-            if (bid == 0 && threadIdx.x == 0) H->exact_argmax += H->n_uncert;
+            mark(iter, 7);
+            if (!(go = exact_phase(cur))) break;
+            scatter_due = false;
+        } else {
+            scatter_due = true;
         }
         mark(iter, 8);
         cur ^= 1;

@@ -59,8 +59,12 @@ struct Hdr3 {
     int fc_iter[2];         // facet count when the table of that parity was built
     int fc_lo_last;         // first facet id created in the last iteration
     int hull_vertices;
-    int nwin, iter, nactive[2];
-    int nent[2], L[2];
+    int nwin, iter;
+    int nact[8];            // candidates that claimed in round r (r < kRounds)
+    // segment table of each parity: (entries << 32) | points, counted by the
+    // table phase with one atomic per 512 items
+    unsigned long long tab[2];
+    int tile_sz[2];         // points per assign / scatter tile of each table
     int n_uncert;
     int next_cloud;         // queue of the per-cloud setup
     long long seg_total, surv_total;
@@ -97,7 +101,7 @@ struct Params3 {
     Fac3 *fac;
     Acc3 *acc;
     float4 *apex;                 // apex (farthest point) of each facet with a segment
-    unsigned long long *claim;    // (iteration << 32) | ~candidate facet
+    unsigned long long *claim[2]; // claims of the even / odd selection rounds (claim_key)
     int4 *cone;                   // deleted facet: (first cone facet, count, apex index, iteration)
     float *thr;                   // exact-apex candidate threshold
     int *nstart;                  // new segment start of a facet
@@ -105,7 +109,7 @@ struct Params3 {
     int *big_v, *big_h;
     // segments
     Ent3 *ent[2];
-    int *tile_ent, *tile_m;
+    int *tile_ent[2], *tile_m[2];  // per table: tile -> first entry, entries the tile meets
     int2 *vn;                     // (|V|, |N|) of a candidate, (-1,-1) on overflow
     int *cstate;                  // candidate state in an iteration: 0 active, 1 won, 2 out
     int *taken;                   // iteration whose winner deleted the facet
@@ -134,7 +138,11 @@ struct Params3 {
 // a bijective pseudo-random permutation of the facet ids (28 bits), which
 // keeps keys unique and makes each round's winners a Luby-style independent
 // set.  Bits: iteration 28 | round 4 | size class 4 | permutation 28.
-constexpr int kRounds = 4;
+#ifndef QH3D_ROUNDS
+#define QH3D_ROUNDS 3
+#endif
+constexpr int kRounds = QH3D_ROUNDS;
+static_assert(kRounds >= 1 && kRounds <= 7, "round numbers fit the claim key and nact[]");
 __device__ __forceinline__ unsigned long long claim_key(int iter, int round, int f, int len)
 {
     const unsigned perm = (((unsigned)f ^ ((unsigned)iter * 0x9E37u)) * 0x0B5AD4Bu) & 0x0FFFFFFFu;
@@ -155,12 +163,31 @@ struct SmemAssign {
     int e0, m;
     int start[kMaxTile];
     int f[kMaxTile];
+};
+// The cone targets a CTA met in one assign phase, over all of its tiles (it
+// lives outside the union: the scatter after the table phase, which visits
+// the same tiles on the same CTA, reads the bases): points counted and
+// farthest-point keys merged in shared memory, one reservation and key merge
+// per (CTA, target) at the end of the phase.  A point's code then carries
+// its slot and rank within the CTA's count.
+constexpr int kLocalBits = 24;           // rank within a CTA's count of one target
+struct SmemSlots {
     int skey[kSlots], scnt[kSlots], sbase[kSlots];
     unsigned long long sk1[kSlots];
     unsigned so2[kSlots], sem[kSlots];
 };
 struct SmemTable {
     long long wsum[33];
+    unsigned long long base;
+};
+struct SmemWin {
+    int n;
+    int list[kMaxBlock];
+};
+// Visible-set search with one warp per candidate: the warp's lists.
+struct SmemBfs {
+    int V[kMaxBlock / 32][kVCap];
+    int N[kMaxBlock / 32][kNCap];
 };
 struct SmemX3 {
     int idx[kMaxBlock];
@@ -171,11 +198,13 @@ union SmemAll3 {
     SmemAssign a;
     SmemTable t;
     SmemX3 x;
+    SmemWin w;
+    SmemBfs bfs;
 };
 
 struct Layout3 {
-    size_t hdr, res, fac, acc, apex, claim, cone, thr, nstart, big_mark, big_v, big_h;
-    size_t ent[2], tile_ent, tile_m, vn, cstate, taken, vpool, npool, uncert, pts[2], code, part,
+    size_t hdr, res, fac, acc, apex, claim[2], cone, thr, nstart, big_mark, big_v, big_h;
+    size_t ent[2], tile_ent[2], tile_m[2], vn, cstate, taken, vpool, npool, uncert, pts[2], code, part,
         blk_a, blk_b, blk_v, blk_i;
     // output stage
     size_t alive, label, cop, ekey[2], eval[2], hist, hist_off, gstart, poly, glen, fkey[2], fval[2],

@@ -55,7 +55,7 @@ Layout3 layout3d(int64_t n, int ncloud)
     L.fac = take(fc * sizeof(Fac3));
     L.acc = take(fc * sizeof(Acc3));
     L.apex = take(fc * sizeof(float4));
-    L.claim = take(fc * 8);
+    for (int b = 0; b < 2; b++) L.claim[b] = take(fc * 8);
     L.cone = take((fc + nc) * sizeof(int4));  // + the clouds' pseudo facets
     L.thr = take(fc * 4);
     L.nstart = take(fc * 4);
@@ -63,8 +63,10 @@ Layout3 layout3d(int64_t n, int ncloud)
     L.big_v = take(fc * 4);
     L.big_h = take(fc * 4);
     for (int b = 0; b < 2; b++) L.ent[b] = take((size_t)L.ecap * sizeof(Ent3));
-    L.tile_ent = take((np / kMinTile + 2) * 4);
-    L.tile_m = take((np / kMinTile + 2) * 4);
+    for (int b = 0; b < 2; b++) {
+        L.tile_ent[b] = take((np / kMinTile + 2) * 4);
+        L.tile_m[b] = take((np / kMinTile + 2) * 4);
+    }
     L.vn = take((size_t)L.ecap * sizeof(int2));
     L.cstate = take((size_t)L.ecap * 4);
     L.taken = take(fc * 4);
@@ -118,7 +120,7 @@ Params3 make_params3(const float *x, const float *y, const float *z, int64_t n, 
     A.fac = (Fac3 *)(ws + L.fac);
     A.acc = (Acc3 *)(ws + L.acc);
     A.apex = (float4 *)(ws + L.apex);
-    A.claim = (unsigned long long *)(ws + L.claim);
+    for (int b = 0; b < 2; b++) A.claim[b] = (unsigned long long *)(ws + L.claim[b]);
     A.cone = (int4 *)(ws + L.cone);
     A.thr = (float *)(ws + L.thr);
     A.nstart = (int *)(ws + L.nstart);
@@ -129,8 +131,10 @@ Params3 make_params3(const float *x, const float *y, const float *z, int64_t n, 
         A.ent[b] = (Ent3 *)(ws + L.ent[b]);
         A.pts[b] = (float4 *)(ws + L.pts[b]);
     }
-    A.tile_ent = (int *)(ws + L.tile_ent);
-    A.tile_m = (int *)(ws + L.tile_m);
+    for (int b = 0; b < 2; b++) {
+        A.tile_ent[b] = (int *)(ws + L.tile_ent[b]);
+        A.tile_m[b] = (int *)(ws + L.tile_m[b]);
+    }
     A.vn = (int2 *)(ws + L.vn);
     A.cstate = (int *)(ws + L.cstate);
     A.taken = (int *)(ws + L.taken);
