@@ -187,6 +187,53 @@ __device__ __forceinline__ void orient3d_value(const float *a, const float *b, c
     }
 }
 
+// A facet's plane for the FP32 filter of many points against one facet.
+// The same determinant det[u; v; w] (u = b - a, v = c - a, w = p - a)
+// expanded along w instead: D = (w0 n0 + w1 n1) + w2 n2 with the minors
+// n_i = u_j v_k - u_k v_j (each product and the difference rounded) and
+// m_i = |u_j v_k| + |u_k v_j|.  Every monomial u_j v_k w_i still passes
+// through eight roundings (w_i, u_j, v_k, the product u_j v_k, the minor's
+// difference, the product with w_i, two sums), so the bound of det3_f32
+// holds with its roles permuted: |det - D| <= 8u(1 + 2^-10) perm, perm =
+// sum_i |w_i| m_i.  The minors are computed once per facet; a point then
+// costs three differences and two short dot products.  a.w = 1 marks a facet
+// with a non-zero component of u or v below 2^-40 (the filter never decides
+// then, as in det3_f32); the same test on w is made per point.
+struct Plane3 {
+    float4 a, n, m;
+};
+
+__device__ __forceinline__ Plane3 make_plane3(const float *a, const float *b, const float *c)
+{
+    const float u0 = __fsub_rn(b[0], a[0]), u1 = __fsub_rn(b[1], a[1]), u2 = __fsub_rn(b[2], a[2]);
+    const float v0 = __fsub_rn(c[0], a[0]), v1 = __fsub_rn(c[1], a[1]), v2 = __fsub_rn(c[2], a[2]);
+    const float p0a = __fmul_rn(u1, v2), p0b = __fmul_rn(u2, v1);
+    const float p1a = __fmul_rn(u2, v0), p1b = __fmul_rn(u0, v2);
+    const float p2a = __fmul_rn(u0, v1), p2b = __fmul_rn(u1, v0);
+    auto small = [](float t) { return t != 0.0f && fabsf(t) < kTiny3; };
+    const bool never = small(u0) || small(u1) || small(u2) || small(v0) || small(v1) || small(v2);
+    Plane3 P;
+    P.a = make_float4(a[0], a[1], a[2], never ? 1.0f : 0.0f);
+    P.n = make_float4(__fsub_rn(p0a, p0b), __fsub_rn(p1a, p1b), __fsub_rn(p2a, p2b), 0.0f);
+    P.m = make_float4(__fadd_rn(fabsf(p0a), fabsf(p0b)), __fadd_rn(fabsf(p1a), fabsf(p1b)),
+                      __fadd_rn(fabsf(p2a), fabsf(p2b)), 0.0f);
+    return P;
+}
+
+// FP32 value of vol(a, b, c, p) and its bound from the facet's plane
+// (e = +inf when the filter cannot decide).
+__device__ __forceinline__ void plane3_value(const Plane3 &P, float px, float py, float pz,
+                                             float &d, float &e)
+{
+    const float w0 = __fsub_rn(px, P.a.x), w1 = __fsub_rn(py, P.a.y), w2 = __fsub_rn(pz, P.a.z);
+    d = __fadd_rn(__fadd_rn(__fmul_rn(w0, P.n.x), __fmul_rn(w1, P.n.y)), __fmul_rn(w2, P.n.z));
+    const float perm = __fadd_rn(__fadd_rn(__fmul_rn(fabsf(w0), P.m.x), __fmul_rn(fabsf(w1), P.m.y)),
+                                 __fmul_rn(fabsf(w2), P.m.z));
+    e = __fmul_rn(kC32_3, perm);
+    auto small = [](float t) { return t != 0.0f && fabsf(t) < kTiny3; };
+    if (P.a.w != 0.0f || small(w0) || small(w1) || small(w2)) e = INFINITY;
+}
+
 // Exact sign of vol(a, b, c, p) given its filter value.
 template <int MODE>
 __device__ __forceinline__ int orient3d_sign(float d, float e, const float *a, const float *b,

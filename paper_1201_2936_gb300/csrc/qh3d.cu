@@ -76,6 +76,21 @@ __device__ __forceinline__ bool lex_greater_lowidx(float4 p, float4 q)
     return __float_as_int(p.w) < __float_as_int(q.w);
 }
 
+// Filter value of vol(facet g, p): the facet's plane in FP32 mode, the
+// vertices (FP64 filter) in the plain mode.
+template <int MODE>
+__device__ __forceinline__ void facet_value(const Params3 &A, int g, const float *p, float &d,
+                                            float &e)
+{
+    if (MODE == QH_PRED_F32) {
+        const Plane3 P = A.plane[g];
+        plane3_value(P, p[0], p[1], p[2], d, e);
+    } else {
+        const Fac3 &G = A.fac[g];
+        orient3d_value<MODE>(G.p, G.p + 3, G.p + 6, p, d, e);
+    }
+}
+
 // ---------------------------------------------------------------- initial simplex
 // Block-level reductions write one candidate per block; block 0 reduces them
 // after a grid barrier.
@@ -343,6 +358,7 @@ __device__ void build_tetra_at(const Params3 &A, int base, const float4 *t, int 
         f.nb[0] = f.nb[1] = f.nb[2] = -1;
         f.alive = 1;
         A.fac[base + o] = f;
+        A.plane[base + o] = make_plane3(f.p, f.p + 3, f.p + 6);
         Acc3 z = {};
         A.acc[base + o] = z;
         A.claim[0][base + o] = 0ull;
@@ -370,6 +386,7 @@ __device__ void dead_tetra_at(const Params3 &A, int base, int pseudo)
         Fac3 f = {};
         f.nb[0] = f.nb[1] = f.nb[2] = base + o;
         A.fac[base + o] = f;
+        A.plane[base + o] = make_plane3(f.p, f.p + 3, f.p + 6);
         Acc3 z = {};
         A.acc[base + o] = z;
         A.claim[0][base + o] = 0ull;
@@ -602,12 +619,14 @@ __device__ void select3d(const Params3 &A, int par, int iter, int bid, int nb)
                 for (int j = 0; j < nv && !seen; j++) seen = V[j] == g;
                 for (int j = 0; j < nn && !seen; j++) seen = N[j] == g;
                 if (seen) continue;
-                const Fac3 &G = A.fac[g];
-                const float *a, *b, *c;
-                fac_pts(G, a, b, c);
                 float d, err;
-                orient3d_value<MODE>(a, b, c, q, d, err);
-                if (orient3d_sign<MODE>(d, err, a, b, c, q, fallbacks) > 0) {
+                facet_value<MODE>(A, g, q, d, err);
+                bool vis = d > err;
+                if (!vis && !(-d > err)) {
+                    const Fac3 &G = A.fac[g];
+                    vis = orient3d_sign<MODE>(d, err, G.p, G.p + 3, G.p + 6, q, fallbacks) > 0;
+                }
+                if (vis) {
                     if (nv == kVCap) over = true;
                     else V[nv++] = g;
                 } else {
@@ -674,12 +693,13 @@ __device__ void select3d_warp(const Params3 &A, int par, int iter, SmemAll3 &sm,
                 for (int j = 0; j < nn && keep; j++) keep = N[j] != g;
                 bool vis = false;
                 if (keep) {
-                    const Fac3 &G = A.fac[g];
-                    const float *a, *b, *c;
-                    fac_pts(G, a, b, c);
                     float d, err;
-                    orient3d_value<MODE>(a, b, c, q, d, err);
-                    vis = orient3d_sign<MODE>(d, err, a, b, c, q, fallbacks) > 0;
+                    facet_value<MODE>(A, g, q, d, err);
+                    vis = d > err;
+                    if (!vis && !(-d > err)) {
+                        const Fac3 &G = A.fac[g];
+                        vis = orient3d_sign<MODE>(d, err, G.p, G.p + 3, G.p + 6, q, fallbacks) > 0;
+                    }
                 }
                 const unsigned bv = __ballot_sync(0xffffffffu, keep && vis);
                 const unsigned bn = __ballot_sync(0xffffffffu, keep && !vis);
@@ -763,6 +783,7 @@ __device__ bool build_cone(const Params3 &A, int f0, int len, const int *V, int 
         C.nb[2] = -1;
         C.alive = 1;
         A.fac[base + j] = C;
+        A.plane[base + j] = make_plane3(C.p, C.p + 3, C.p + 6);
         Acc3 z = {};
         A.acc[base + j] = z;
         A.claim[0][base + j] = 0ull;
@@ -858,6 +879,7 @@ __device__ void cone_warp(const Params3 &A, int e, int f0, int len, const int *V
         u[r] = C.v[0];
         w[r] = C.v[1];
         A.fac[base + j] = C;
+        A.plane[base + j] = make_plane3(C.p, C.p + 3, C.p + 6);
         Acc3 z = {};
         A.acc[base + j] = z;
         A.claim[0][base + j] = 0ull;
@@ -1134,15 +1156,32 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, SmemSlots &ss,
                                idx == F1.v[0] || idx == F1.v[1] || idx == F1.v[2];
                     }
                     if (!skip) {
-                        for (int c = 0; c < cn.y; c++) {
-                            const Fac3 &C = A.fac[cn.x + c];
-                            const float *a, *b, *cc;
-                            fac_pts(C, a, b, cc);
-                            orient3d_value<MODE>(a, b, cc, p, d, err);
-                            if (orient3d_sign<MODE>(d, err, a, b, cc, p, fallbacks) > 0) {
-                                target = cn.x + c;
-                                cone_t = true;
-                                break;
+                        // the first cone facet strictly below p: filter values
+                        // four facets at a time (independent chains), then in
+                        // order, an undecided one settled exactly
+                        for (int c0 = 0; c0 < cn.y && !cone_t; c0 += 4) {
+                            float dd[4], ee[4];
+#pragma unroll
+                            for (int j = 0; j < 4; j++) {
+                                dd[j] = 0.0f;
+                                ee[j] = 0.0f;
+                                if (c0 + j < cn.y) facet_value<MODE>(A, cn.x + c0 + j, p, dd[j], ee[j]);
+                            }
+#pragma unroll
+                            for (int j = 0; j < 4; j++) {
+                                if (cone_t || c0 + j >= cn.y || -dd[j] > ee[j]) continue;
+                                bool pos = dd[j] > ee[j];
+                                if (!pos) {
+                                    const Fac3 &C = A.fac[cn.x + c0 + j];
+                                    pos = orient3d_sign<MODE>(dd[j], ee[j], C.p, C.p + 3, C.p + 6, p,
+                                                              fallbacks) > 0;
+                                }
+                                if (pos) {
+                                    target = cn.x + c0 + j;
+                                    d = dd[j];
+                                    err = ee[j];
+                                    cone_t = true;
+                                }
                             }
                         }
                     }

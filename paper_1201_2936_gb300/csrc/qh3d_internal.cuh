@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "qh.h"
+#include "pred3.cuh"
 #include "qh_common.cuh"
 
 namespace qh {
@@ -99,6 +100,7 @@ struct Params3 {
     qh_result *res;
     // facets
     Fac3 *fac;
+    Plane3 *plane;                // FP32 filter plane of each facet (written with the facet)
     Acc3 *acc;
     float4 *apex;                 // apex (farthest point) of each facet with a segment
     unsigned long long *claim[2]; // claims of the even / odd selection rounds (claim_key)
@@ -203,7 +205,7 @@ union SmemAll3 {
 };
 
 struct Layout3 {
-    size_t hdr, res, fac, acc, apex, claim[2], cone, thr, nstart, big_mark, big_v, big_h;
+    size_t hdr, res, fac, plane, acc, apex, claim[2], cone, thr, nstart, big_mark, big_v, big_h;
     size_t ent[2], tile_ent[2], tile_m[2], vn, cstate, taken, vpool, npool, uncert, pts[2], code, part,
         blk_a, blk_b, blk_v, blk_i;
     // output stage

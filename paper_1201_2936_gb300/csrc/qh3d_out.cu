@@ -53,6 +53,7 @@ Layout3 layout3d(int64_t n, int ncloud)
     L.hdr = take(sizeof(Hdr3));
     L.res = take(sizeof(qh_result));
     L.fac = take(fc * sizeof(Fac3));
+    L.plane = take(fc * sizeof(Plane3));
     L.acc = take(fc * sizeof(Acc3));
     L.apex = take(fc * sizeof(float4));
     for (int b = 0; b < 2; b++) L.claim[b] = take(fc * 8);
@@ -118,6 +119,7 @@ Params3 make_params3(const float *x, const float *y, const float *z, int64_t n, 
     A.hdr = (Hdr3 *)(ws + L.hdr);
     A.res = (qh_result *)(ws + L.res);
     A.fac = (Fac3 *)(ws + L.fac);
+    A.plane = (Plane3 *)(ws + L.plane);
     A.acc = (Acc3 *)(ws + L.acc);
     A.apex = (float4 *)(ws + L.apex);
     for (int b = 0; b < 2; b++) A.claim[b] = (unsigned long long *)(ws + L.claim[b]);
