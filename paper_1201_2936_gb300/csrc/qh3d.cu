@@ -1065,16 +1065,48 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, SmemSlots &ss,
     // that its tiles spread over the SMs)
     const int T = FIRST ? A.tile : *(volatile int *)&H->tile_sz[par];
     const int ntiles = (L + T - 1) / T;
-    for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
-        ss.skey[i] = -1;
-        ss.scnt[i] = 0;
-        ss.sk1[i] = 0ull;
-        ss.so2[i] = 0u;
-        ss.sem[i] = 0u;
-    }
+    // Aggregation scope.  Few targets in the phase (the first assignment of
+    // one cloud, the early iterations): the CTA's table spans all of its
+    // tiles, so the few hot accumulators see one reservation per CTA instead
+    // of one per tile.  Many targets: a table per tile, reserved at the
+    // tile's end (contention is low, and the table would not hold them).
+    const int ntarget = FIRST ? 4 * A.ncloud
+                              : *(volatile int *)&H->fcount - *(volatile int *)&H->fc_iter[par];
+    const bool per_tile = ntarget > (3 * kSlots) / 4;
+    auto reset_slots = [&]() {
+        for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
+            ss.skey[i] = -1;
+            ss.scnt[i] = 0;
+            ss.sk1[i] = 0ull;
+            ss.so2[i] = 0u;
+            ss.sem[i] = 0u;
+        }
+    };
+    // one reservation and key merge per used slot
+    auto reserve_slots = [&]() {
+        for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
+            const int t = ss.skey[i];
+            if (t < 0) continue;
+            if (ss.scnt[i] >= (1 << kLocalBits)) set_status(H, QH_ERR_CAPACITY);
+            Acc3 &ac = A.acc[t];
+            ss.sbase[i] = (int)atomicAdd(&ac.cnt, (unsigned)ss.scnt[i]);
+            const unsigned long long k1 = ss.sk1[i];
+            const unsigned long long old = atomicMax(&ac.key1, k1);
+            const unsigned long long lo2 = old < k1 ? old : k1;
+            const unsigned lo_o = (unsigned)(lo2 >> 32);
+            const unsigned o2 = ss.so2[i];
+            atomicMax(&ac.o2, lo_o > o2 ? lo_o : o2);
+            atomicMax(&ac.emax, ss.sem[i]);
+        }
+    };
+    reset_slots();
     for (int tile = bid; tile < ntiles; tile += nb) {
         const int v0 = tile * T, v1 = min(v0 + T, L);
         __syncthreads();
+        if (per_tile) {
+            reset_slots();
+            __syncthreads();
+        }
         if (threadIdx.x == 0) {
             if (FIRST) {  // entries = the clouds the tile meets
                 const int c0 = cloud_of(A, v0);
@@ -1129,8 +1161,9 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, SmemSlots &ss,
             }
             if (fit[k] >= 0) pit[k] = FIRST ? load_input(A, v) : P[v];
         }
-        // ---- classify; cone targets get a slot of the CTA's table (shared
-        // hash), or go straight to the global accumulator when it is full
+        // ---- classify; cone targets get a slot of the table (shared hash),
+        // or go straight to the global accumulator when it is full
+        int tgt[ITEMS], rk[ITEMS], slot[ITEMS];
 #pragma unroll
         for (int k = 0; k < ITEMS; k++) {
             const int v = v0 + k * blockDim.x + threadIdx.x;
@@ -1200,9 +1233,10 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, SmemSlots &ss,
                 const unsigned em = __reduce_max_sync(grp, __float_as_uint(err));
                 int base = 0;
                 if (lane == leader) {
-                    // find or insert the target's slot (linear probing)
+                    // find or insert the target's slot (linear probing, a
+                    // bounded number of probes)
                     int h = (int)(((unsigned)target * 0x9E3779B1u) >> (32 - kSlotBits));
-                    for (int probe = 0; probe < kSlots; probe++) {
+                    for (int probe = 0; probe < 16; probe++) {
                         const int prev = atomicCAS(&ss.skey[h], -1, target);
                         if (prev == -1 || prev == target) {
                             s = h;
@@ -1235,29 +1269,32 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, SmemSlots &ss,
                 rank = base + __popc(grp & lt);
             }
             // code: (target, (slot << kLocalBits) | rank in the CTA's count),
-            // (target, -1 - global rank) past a full table, (-1, 0) discarded
-            if (valid && f_dead) {
+            // (target, -1 - global rank) with a per-tile table or past a full
+            // one, (-1, 0) discarded
+            tgt[k] = (valid && f_dead) ? target : -2;
+            rk[k] = rank;
+            slot[k] = cone_t ? s : -1;
+            if (!per_tile && valid && f_dead) {
                 const int r = !cone_t ? 0 : (s >= 0 ? (s << kLocalBits) | rank : -1 - rank);
                 A.code[v] = make_int2(target, r);
             }
         }
+        if (per_tile) {
+            __syncthreads();
+            reserve_slots();
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < ITEMS; k++) {
+                const int v = v0 + k * blockDim.x + threadIdx.x;
+                if (tgt[k] == -2) continue;
+                const int r = tgt[k] < 0 ? 0 : -1 - (slot[k] >= 0 ? ss.sbase[slot[k]] + rk[k] : rk[k]);
+                A.code[v] = make_int2(tgt[k], r);
+            }
+        }
     }
-    // ---- one reservation and key merge per (CTA, target)
+    // ---- CTA-wide table: one reservation and key merge per (CTA, target)
     __syncthreads();
-    for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
-        const int t = ss.skey[i];
-        if (t < 0) continue;
-        if (ss.scnt[i] >= (1 << kLocalBits)) set_status(H, QH_ERR_CAPACITY);
-        Acc3 &ac = A.acc[t];
-        ss.sbase[i] = (int)atomicAdd(&ac.cnt, (unsigned)ss.scnt[i]);
-        const unsigned long long k1 = ss.sk1[i];
-        const unsigned long long old = atomicMax(&ac.key1, k1);
-        const unsigned long long lo2 = old < k1 ? old : k1;
-        const unsigned lo_o = (unsigned)(lo2 >> 32);
-        const unsigned o2 = ss.so2[i];
-        atomicMax(&ac.o2, lo_o > o2 ? lo_o : o2);
-        atomicMax(&ac.emax, ss.sem[i]);
-    }
+    if (!per_tile) reserve_slots();
     unsigned fsum = __reduce_add_sync(0xffffffffu, fallbacks);
     if (lane == 0 && fsum) atomicAdd(&H->fallbacks, (unsigned long long)fsum);
 }
