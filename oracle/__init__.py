@@ -22,7 +22,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
-_SRC = os.path.join(_HERE, "qh_oracle.c")
+_SRCS = [os.path.join(_HERE, "qh_oracle.c"), os.path.join(_HERE, "qh_oracle4.c")]
 _lock = threading.Lock()
 _lib = None
 
@@ -38,10 +38,11 @@ class OracleError(RuntimeError):
 def build(force: bool = False) -> str:
     """Compile the C oracle (gcc, -ffp-contract=off so the FP64 error bounds hold)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_SO) or \
+            any(os.path.getmtime(_SO) < os.path.getmtime(src) for src in _SRCS):
         tmp = _SO + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-o", tmp, _SRC, "-lm"]
+               "-shared", "-o", tmp] + _SRCS + ["-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _SO)
     return _SO
@@ -58,8 +59,12 @@ def _load():
             lib.oracle_hull2d.restype = ctypes.c_int
             lib.oracle_hull3d.argtypes = [fp, fp, fp, ctypes.c_int64, fp, i64p, fp, fp, i64p, i64p]
             lib.oracle_hull3d.restype = ctypes.c_int
+            lib.oracle_hull4d.argtypes = [fp, fp, fp, fp, ctypes.c_int64, fp, i64p, fp,
+                                          ctypes.c_int64, fp, ctypes.c_int64, i64p, i64p]
+            lib.oracle_hull4d.restype = ctypes.c_int
             for name, k in (("oracle_orient2d", 3), ("oracle_cmp_dist2", 4),
-                            ("oracle_orient3d", 4), ("oracle_cmp_dist3", 5)):
+                            ("oracle_orient3d", 4), ("oracle_cmp_dist3", 5),
+                            ("oracle_orient4", 5), ("oracle_cmp_dist4", 6)):
                 f = getattr(lib, name)
                 f.argtypes = [fp] * k
                 f.restype = ctypes.c_int
@@ -109,6 +114,30 @@ def hull3d(x, y, z, return_iterations: bool = False):
         raise OracleError(rc, "hull3d")
     faces = [fidx[foff[i]:foff[i + 1]].copy() for i in range(nf.value)]
     res = (verts[: nv.value].copy(), faces)
+    return (res, it.value) if return_iterations else res
+
+
+def hull4d(x, y, z, w, return_iterations: bool = False):
+    """Canonical 4D hull: (vertices, facets) where vertices is the sorted
+    int32 array of extreme points and facets a list of int32 arrays, each the
+    sorted extreme points on one facet (maximal set of boundary points on a
+    supporting hyperplane), sorted lexicographically.  Raises OracleError with
+    code ERR_DEGENERATE when the points do not span R^4."""
+    lib = _load()
+    x, y, z, w = _f32(x), _f32(y), _f32(z), _f32(w)
+    n = x.shape[0]
+    verts = np.empty(max(n, 1), dtype=np.int32)
+    fcap, icap = 64 * n + 64, 256 * n + 256
+    foff = np.empty(fcap, dtype=np.int32)
+    fidx = np.empty(icap, dtype=np.int32)
+    nv, nf, it = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = lib.oracle_hull4d(_ptr(x), _ptr(y), _ptr(z), _ptr(w), n, _ptr(verts), ctypes.byref(nv),
+                           _ptr(foff), fcap, _ptr(fidx), icap, ctypes.byref(nf),
+                           ctypes.byref(it))
+    if rc != OK:
+        raise OracleError(rc, "hull4d")
+    facets = [fidx[foff[i]:foff[i + 1]].copy() for i in range(nf.value)]
+    res = (verts[: nv.value].copy(), facets)
     return (res, it.value) if return_iterations else res
 
 
@@ -177,6 +206,16 @@ def cmp_dist2(a, b, p1, p2) -> int:
 def orient3d(a, b, c, p) -> int:
     """Exact sign of det[b-a; c-a; p-a]."""
     return _load().oracle_orient3d(*(_ptr(_pt(v)) for v in (a, b, c, p)))
+
+
+def orient4(a, b, c, d, p) -> int:
+    """Exact sign of det[b-a; c-a; d-a; p-a] (points as 4 float32 values)."""
+    return _load().oracle_orient4(*(_ptr(_pt(q)) for q in (a, b, c, d, p)))
+
+
+def cmp_dist4(a, b, c, d, p1, p2) -> int:
+    """Exact sign of orient4 at p1 minus orient4 at p2."""
+    return _load().oracle_cmp_dist4(*(_ptr(_pt(q)) for q in (a, b, c, d, p1, p2)))
 
 
 def cmp_dist3(a, b, c, p1, p2) -> int:

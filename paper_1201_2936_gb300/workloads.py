@@ -76,6 +76,24 @@ def near_sphere(n: int, seed: int, sigma: float = 1e-4):
     return _soa(g[0], g[1], g[2])
 
 
+def uniform_ball_4d(n: int, seed: int):
+    """Uniform in the unit 4-ball: Gaussian direction times u^(1/4)."""
+    r = _rng(seed)
+    g = r.standard_normal((4, n))
+    g /= np.linalg.norm(g, axis=0)
+    g *= r.random(n) ** 0.25
+    return _soa(g[0], g[1], g[2], g[3])
+
+
+def near_sphere_4d(n: int, seed: int, sigma: float = 1e-3):
+    """Near the unit 3-sphere in R^4: normalised Gaussian, radius 1 + sigma N(0, 1)."""
+    r = _rng(seed)
+    g = r.standard_normal((4, n))
+    g /= np.linalg.norm(g, axis=0)
+    g *= 1.0 + sigma * r.standard_normal(n)
+    return _soa(g[0], g[1], g[2], g[3])
+
+
 def _random_rotation(r: np.random.Generator) -> np.ndarray:
     q, rr = np.linalg.qr(r.standard_normal((3, 3)))
     q = q * np.sign(np.diag(rr))

@@ -190,3 +190,95 @@ def brute_hull3d(x, y, z):
     result.sort()
     verts = sorted({v for f in result for v in f})
     return verts, result
+
+
+# ---------------------------------------------------------------- 4D
+
+def det4(rows) -> Fraction:
+    """Determinant of a 4x4 matrix of Fractions by cofactor expansion."""
+    def det3r(m):
+        return det3(m[0], m[1], m[2])
+    tot = Fraction(0)
+    for j in range(4):
+        minor = [[rows[i][k] for k in range(4) if k != j] for i in range(1, 4)]
+        term = rows[0][j] * det3r(minor)
+        tot += term if j % 2 == 0 else -term
+    return tot
+
+
+def orient4(a, b, c, d, p) -> int:
+    """Sign of det[b-a; c-a; d-a; p-a] in exact rationals."""
+    A, B, C, D, P = ([F(t) for t in q] for q in (a, b, c, d, p))
+    d4 = det4([[B[i] - A[i] for i in range(4)], [C[i] - A[i] for i in range(4)],
+               [D[i] - A[i] for i in range(4)], [P[i] - A[i] for i in range(4)]])
+    return (d4 > 0) - (d4 < 0)
+
+
+def _normal4(A, B, C, D):
+    """A normal of the hyperplane through four points (Fractions): the
+    generalised cross product of b-a, c-a, d-a (zero vector when they are
+    affinely dependent)."""
+    u = [B[i] - A[i] for i in range(4)]
+    v = [C[i] - A[i] for i in range(4)]
+    w = [D[i] - A[i] for i in range(4)]
+    n = []
+    for j in range(4):
+        cols = [k for k in range(4) if k != j]
+        m = det3([u[k] for k in cols], [v[k] for k in cols], [w[k] for k in cols])
+        n.append(m if j % 2 == 0 else -m)
+    return n
+
+
+def _rank(vecs) -> int:
+    """Rank of a list of Fraction vectors (Gaussian elimination)."""
+    rows = [list(v) for v in vecs]
+    rank, col = 0, 0
+    ncol = len(rows[0]) if rows else 0
+    while rank < len(rows) and col < ncol:
+        piv = next((r for r in range(rank, len(rows)) if rows[r][col] != 0), None)
+        if piv is None:
+            col += 1
+            continue
+        rows[rank], rows[piv] = rows[piv], rows[rank]
+        for r in range(len(rows)):
+            if r != rank and rows[r][col] != 0:
+                f = rows[r][col] / rows[rank][col]
+                rows[r] = [x - f * y for x, y in zip(rows[r], rows[rank])]
+        rank += 1
+        col += 1
+    return rank
+
+
+def brute_hull4d(x, y, z, w):
+    """The 4D hull by definition, in exact rationals: every hyperplane through
+    four affinely independent input locations with all points on one side is
+    a supporting hyperplane, the points on it form a facet; a point is a
+    vertex when the normals of the facets through it span R^4.  Returns
+    (sorted vertex indices, sorted list of facet tuples of the vertices on
+    each facet), or None when the points do not span R^4."""
+    pts = list(zip(*(np.asarray(c, np.float64).tolist() for c in (x, y, z, w))))
+    loc = unique_lowest(pts)
+    ids = sorted(loc.values())
+    P = {i: [F(t) for t in pts[i]] for i in ids}
+    facets = {}
+    for quad in combinations(ids, 4):
+        A, B, C, D = (P[i] for i in quad)
+        nrm = _normal4(A, B, C, D)
+        if all(t == 0 for t in nrm):
+            continue
+        s = {i: sum(nrm[k] * (P[i][k] - A[k]) for k in range(4)) for i in ids}
+        if all(v >= 0 for v in s.values()) or all(v <= 0 for v in s.values()):
+            on = frozenset(i for i in ids if s[i] == 0)
+            if len(on) == len(ids):
+                return None  # every point on one hyperplane
+            facets[on] = nrm
+    if not facets:
+        return None
+    verts = []
+    for i in ids:
+        normals = [nrm for on, nrm in facets.items() if i in on]
+        if normals and _rank(normals) == 4:
+            verts.append(i)
+    vset = set(verts)
+    out = sorted(tuple(sorted(i for i in on if i in vset)) for on in facets)
+    return verts, out
