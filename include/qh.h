@@ -362,6 +362,49 @@ qh_status qh_hull3d_backward(const float *d_x, const float *d_y, const float *d_
                              const double *d_grad, float *d_gx, float *d_gy, float *d_gz,
                              int64_t gstride, double *d_scratch, cudaStream_t stream);
 
+/* ---------------------------------------------------------------------- */
+/* 4D                                                                      */
+/* ---------------------------------------------------------------------- */
+
+/* Bytes of device workspace qh_hull4d needs for n points (0 when n is out
+ * of range: 0 <= n <= 8,000,000). */
+size_t qh_workspace_bytes_4d(int64_t n, const qh_opts *opts);
+
+/*
+ * qh_hull4d: convex hull of n float32 points in R^4 (Section 4.3, "3D and
+ * Higher Dimensions": the recursion with a k-state flagPermute in higher
+ * dimensions; read as Barber et al.'s Quickhull in R^4, several
+ * non-conflicting apexes inserted per iteration, horizon ridges are
+ * triangles).  The iterations are driven from the host (one launch per
+ * phase, the table sizes read back once per iteration).
+ *
+ *  d_x .. d_w     device, coordinate i at d_c[i*stride] (read only)
+ *  d_verts        device int32[max(n,1)]: the extreme points, increasing index
+ *                 (a location present several times: its lowest index)
+ *  h_nv           host: number of vertices
+ *  d_facet_off    device int32[max_facets + 1]: CSR offsets of the facets
+ *  d_facet_idx    device int32[max_idx]: for every facet (a maximal set of
+ *                 boundary points on one supporting hyperplane), the sorted
+ *                 extreme points on it; facets in lexicographic order of
+ *                 these lists (compared on their first eight entries; lists
+ *                 equal there appear in an unspecified order)
+ *  h_nf           host: number of facets (also set when the capacities are
+ *                 too small: then QH_ERR_CAPACITY, *h_nf and h_result->extra[2]
+ *                 give the sizes needed)
+ *  h_result       optional host qh_result (extra[0..2] = vertices, facets,
+ *                 facet index total)
+ * Points that do not span R^4 (n < 5 included) give QH_ERR_DEGENERATE;
+ * n = 0 gives QH_OK with no facets; a non-finite coordinate gives
+ * QH_ERR_NONFINITE.  The workspace holds up to 32 n + 1024 facets created
+ * over the run (QH_ERR_CAPACITY beyond; inputs whose hull grows faster than
+ * that are not supported).  Synchronises `stream`.
+ */
+qh_status qh_hull4d(const float *d_x, const float *d_y, const float *d_z, const float *d_w,
+                    int64_t n, int64_t stride, int32_t *d_verts, int64_t *h_nv,
+                    int32_t *d_facet_off, int64_t max_facets, int32_t *d_facet_idx,
+                    int64_t max_idx, int64_t *h_nf, qh_result *h_result, void *d_ws,
+                    size_t ws_bytes, const qh_opts *opts, cudaStream_t stream);
+
 /*
  * qh_hull2d_noalloc: qh_hull2d for callers that cannot allocate device
  * memory while they run: plugins whose host owns every device allocation,

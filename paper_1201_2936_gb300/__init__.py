@@ -266,6 +266,70 @@ def hull3d(x: torch.Tensor, y: Optional[torch.Tensor] = None, z: Optional[torch.
     return (out, res.as_dict()) if return_result else out
 
 
+def workspace_bytes_4d(n: int, opts: Optional[QhOpts] = None) -> int:
+    return int(_native.lib().qh_workspace_bytes_4d(int(n), ctypes.byref(opts) if opts else None))
+
+
+def hull4d(x: torch.Tensor, y: Optional[torch.Tensor] = None, z: Optional[torch.Tensor] = None,
+           w: Optional[torch.Tensor] = None, *, workspace: Optional[Workspace] = None,
+           stream=None, opts: Optional[QhOpts] = None, return_result: bool = False):
+    """Convex hull of 4D float32 points on the GPU (qh_hull4d).
+
+    Returns (vertices, facet_offsets, facet_indices) as int32 CUDA tensors:
+    the sorted extreme points and, as CSR lists, every facet's sorted extreme
+    points, facets in lexicographic order.  Points are a [n, 4] tensor, a
+    [4, n] tensor, or x, y, z, w."""
+    if y is None and z is None and w is None:
+        t = x
+        if t.dtype != torch.float32 or not t.is_cuda or t.dim() != 2:
+            raise ValueError("points must be a CUDA float32 tensor of shape [n, 4] or [4, n]")
+        if t.shape[1] == 4 and t.stride(1) == 1 and (t.shape[0] <= 1 or t.stride(0) == 4):
+            p = t.data_ptr()
+            xp, yp, zp, wp, n, stride = p, p + 4, p + 8, p + 12, t.shape[0], 4
+        elif t.shape[0] == 4 and t.stride(1) == 1:
+            xp, yp, zp, wp, n, stride = (t[0].data_ptr(), t[1].data_ptr(), t[2].data_ptr(),
+                                         t[3].data_ptr(), t.shape[1], 1)
+        else:
+            raise ValueError("points must be contiguous [n, 4] or row-contiguous [4, n]")
+        dev = t.device
+    else:
+        for c in (x, y, z, w):
+            if c is None or c.dtype != torch.float32 or not c.is_cuda or c.dim() != 1 or \
+                    (c.numel() > 1 and c.stride(0) != 1):
+                raise ValueError("x, y, z, w must be contiguous 1-D CUDA float32 tensors")
+        if not (x.shape == y.shape == z.shape == w.shape):
+            raise ValueError("x, y, z, w must have the same length")
+        xp, yp, zp, wp, n, stride = (x.data_ptr(), y.data_ptr(), z.data_ptr(), w.data_ptr(),
+                                     x.shape[0], 1)
+        dev = x.device
+    o = opts if opts is not None else make_opts("f32", "persistent")
+    if workspace is None:
+        workspace = _default_ws.setdefault(str(dev), Workspace(dev))
+    nb = workspace_bytes_4d(n, o)
+    if nb == 0:
+        raise QHError(1, "qh_workspace_bytes_4d")
+    ws = workspace.get(nb)
+    verts = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    cap_f, cap_i = 8 * n + 64, 32 * n + 256
+    for _ in range(2):
+        foff = torch.empty(cap_f + 1, dtype=torch.int32, device=dev)
+        fidx = torch.empty(cap_i, dtype=torch.int32, device=dev)
+        nv, nf = ctypes.c_int64(0), ctypes.c_int64(0)
+        res = QhResult()
+        st = _native.lib().qh_hull4d(xp, yp, zp, wp, n, stride, verts.data_ptr(), ctypes.byref(nv),
+                                     foff.data_ptr(), cap_f, fidx.data_ptr(), cap_i,
+                                     ctypes.byref(nf), ctypes.byref(res), ws.data_ptr(),
+                                     ws.numel(), ctypes.byref(o), _stream_handle(stream))
+        if st == 5 and (nf.value > cap_f or res.extra[2] > cap_i):  # QH_ERR_CAPACITY: grow once
+            cap_f, cap_i = max(cap_f, nf.value), max(cap_i, int(res.extra[2]))
+            continue
+        break
+    if st != 0:
+        raise QHError(st, "qh_hull4d")
+    out = (verts[: nv.value], foff[: nf.value + 1], fidx[: int(res.extra[2])])
+    return (out, res.as_dict()) if return_result else out
+
+
 NOALLOC_MAX_POINTS = 131072
 
 

@@ -54,6 +54,10 @@ SIGNATURES = [
     ("qh_hull2d_multi", ctypes.c_int, [ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                        _sz, _POpts, _vp]),
     ("qh_workspace_bytes_3d", _sz, [_i64, _POpts]),
+    ("qh_workspace_bytes_4d", _sz, [_i64, _POpts]),
+    ("qh_hull4d", ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _i64, _vp, ctypes.POINTER(_i64), _vp,
+                                 _i64, _vp, _i64, ctypes.POINTER(_i64), _PRes, _vp, _sz, _POpts,
+                                 _vp]),
     ("qh_hull3d", ctypes.c_int, [_vp, _vp, _vp, _i64, _i64, _vp, ctypes.POINTER(_i64), _vp, _vp,
                                  ctypes.POINTER(_i64), _PRes, _vp, _sz, _POpts, _vp]),
     ("qh_debug_timeline_3d", ctypes.c_int, [_vp, _i64, _vp, ctypes.c_int32,

@@ -216,6 +216,19 @@ struct Layout3 {
 };
 
 Layout3 layout3d(int64_t n, int ncloud = 1);
+
+// Device-sized scan and radix sort (qh3d_out.cu), shared with the 4D output
+// stage.  Counts are read on the device (*m_ptr, or m_fix when m_ptr is
+// null); m_cap bounds them and sizes the grids.  Scratch: tmp holds
+// (256 * tiles(m_cap) + m_cap) / kScanTile + 64 long longs, hist 256 *
+// tiles(m_cap) ints and hist_off as many long longs, tiles(m) = ceil(m /
+// kScanTile).
+constexpr int kScanTile = 2048;
+void scan_counts(const int *in, const int *m_ptr, int m_fix, long long m_cap, long long *out,
+                 long long *tmp, long long *d_total, cudaStream_t st);
+void radix_sort(unsigned long long *key, int *val, unsigned long long *tkey, int *tval,
+                const int *m_ptr, long long m_cap, int bits, int *hist, long long *hist_off,
+                long long *tmp, int *hist_m, cudaStream_t st);
 const void *persistent_kernel(int mode, int items);
 Params3 make_params3(const float *x, const float *y, const float *z, int64_t n, int64_t stride,
                      char *ws, const Layout3 &L, const qh_opts &o);

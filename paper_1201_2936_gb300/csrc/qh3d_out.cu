@@ -31,7 +31,6 @@ namespace d3 {
 // ---------------------------------------------------------------- layout
 static size_t au(size_t v) { return (v + 255) & ~(size_t)255; }
 
-constexpr int kScanTile = 2048;  // elements per tile of the scan and sort kernels
 // CTAs of the grid-stride output kernels: four per SM of the current device
 static long long out_grid() { return 4ll * sm_count(); }
 
@@ -245,7 +244,7 @@ static int tiles_grid(long long cap)
 }
 
 // m_cap: an upper bound of the count (sizes the grid).
-static void scan_counts(const int *in, const int *m_ptr, int m_fix, long long m_cap,
+void scan_counts(const int *in, const int *m_ptr, int m_fix, long long m_cap,
                         long long *out, long long *tmp, long long *d_total, cudaStream_t st)
 {
     const int g = tiles_grid(m_cap);
@@ -319,7 +318,7 @@ __global__ void __launch_bounds__(256) k_rs_scatter(const unsigned long long *ke
 
 // Sorts keys/vals in place (ping-pong through tkey/tval); bits: key bits to
 // sort; the count is *m_ptr (at most m_cap).
-static void radix_sort(unsigned long long *key, int *val, unsigned long long *tkey, int *tval,
+void radix_sort(unsigned long long *key, int *val, unsigned long long *tkey, int *tval,
                        const int *m_ptr, long long m_cap, int bits, int *hist, long long *hist_off,
                        long long *tmp, int *hist_m, cudaStream_t st)
 {
