@@ -169,7 +169,8 @@ def clouds_3d(rank: int, scale: int = 1):
     from paper_1201_2936_gb300 import workloads as w
     s = w.SEED_BASE + 2 + 1000 * rank
     return [("ball8M", w.uniform_ball(w.N_BALL_3D // scale, s)),
-            ("sphere1M", w.on_sphere(w.N_SPHERE_3D // scale, s + 10))]
+            ("sphere1M", w.on_sphere(w.N_SPHERE_3D // scale, s + 10)),
+            ("nearsphere8M", w.near_sphere(w.N_BALL_3D // scale, s + 20, 1e-4))]
 
 
 def bench_3d(args, qh, dev, rank, peak, peak_kind):
@@ -214,8 +215,48 @@ def bench_3d(args, qh, dev, rank, peak, peak_kind):
         out.append(row)
         del P, ws
         torch.cuda.empty_cache()
-    return {"workload": "3D: 8M uniform in the unit ball, 1M on the unit sphere (float32)",
+    return {"workload": "3D: 8M uniform in the unit ball, 1M on the unit sphere, 8M near the "
+                        "unit sphere (radius 1 + 1e-4 N(0,1)) (float32)",
             "peak": peak, "peak_kind": peak_kind, "reps": reps, "clouds": out}
+
+
+def bench_4d(args, qh, dev, rank, peak, peak_kind):
+    """The 4D hull (qh_hull4d, host-driven iterations): device time per call
+    on 1M points uniform in the 4-ball and 100K near the 3-sphere.
+    Algorithmic bytes: 16 B per point for the extrema and first-assignment
+    reads, 20 B (x, y, z, w, index) per live point read and per survivor
+    written afterwards."""
+    import torch
+    from paper_1201_2936_gb300 import workloads as w
+    s = w.SEED_BASE + 7 + 1000 * rank
+    out = []
+    for name, pts in (("ball4d_1M", w.uniform_ball_4d(1 << 20, s)),
+                      ("nearsphere4d_100K", w.near_sphere_4d(100_000, s + 1, 1e-3))):
+        n = len(pts[0])
+        P = torch.from_numpy(np.stack(pts)).to(dev)
+        ws = qh.Workspace(dev)
+        for _ in range(2):
+            (v, off, idx), r = qh.hull4d(P, workspace=ws, return_result=True)
+        reps = 3
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+        torch.cuda.synchronize()
+        e[0].record()
+        for k in range(reps):
+            qh.hull4d(P, workspace=ws)
+            e[k + 1].record()
+        torch.cuda.synchronize()
+        ms = statistics.median(e[k].elapsed_time(e[k + 1]) for k in range(reps))
+        algo = 32 * n + 40 * r["survivor_total"]
+        out.append({"cloud": name, "n": n, "ms": round(ms, 3), "Mpoints_s": round(n / ms / 1e3, 1),
+                    "iterations": r["iterations"], "vertices": int(v.numel()),
+                    "facets": int(off.numel() - 1), "algo_bytes": algo,
+                    "frac": round(algo / (ms / 1e3) / 1e9 / peak, 4),
+                    "fallback_frac": r["filter_fallbacks"] / max(1, r["live_total"])})
+        del P, ws
+        torch.cuda.empty_cache()
+    return {"workload": "4D: 1M uniform in the unit 4-ball, 100K near the unit 3-sphere (float32)",
+            "loop": "host-driven (one launch per phase, sizes read back each iteration)",
+            "peak": peak, "peak_kind": peak_kind, "clouds": out}
 
 
 def bench_batched(args, qh, dev, rank, peak, peak_kind):
@@ -264,8 +305,34 @@ def bench_batched(args, qh, dev, rank, peak, peak_kind):
            "frac": round(algo / (ms / 1e3) / 1e9 / peak, 4), "peak_kind": peak_kind,
            "fallback_frac": r["filter_fallbacks"] / max(1, r["live_total"]),
            "tuned": {"block": b.opts.block, "items": b.opts.items,
-                     "ctas_per_sm": b.opts.blocks_per_sm},
-           "tune_table_ms": [[bl, it, c, round(t, 3)] for bl, it, c, t in table]}
+                     "ctas_per_sm": b.opts.blocks_per_sm, "small_cloud": b.opts.small_cloud},
+           "tune_table_ms": [[bl, it, c, sc, round(t, 3)] for bl, it, c, sc, t in table]}
+    # the switchover: the tuned launch with and without the small-cloud route
+    # (clouds of at most small_cloud points hulled whole by one warp)
+    sc_rows = {int(sc): round(t, 3) for bl, it, c, sc, t in table
+               if (bl, it, c) == (b.opts.block, b.opts.items, b.opts.blocks_per_sm)}
+    out["small_cloud_route"] = {
+        "what": "batched 3D: clouds of 4..threshold points hulled whole by one warp in the "
+                "setup, the rest by the segmented iterations; threshold chosen by the autotuner",
+        "threshold_ms": sc_rows, "chosen": int(b.opts.small_cloud),
+        "clouds_on_route": int(((np.diff(off) >= 4) & (np.diff(off) <= b.opts.small_cloud)).sum())
+        if b.opts.small_cloud > 0 else 0}
+    # the switchover on a batch of many small clouds (32768 clouds, sizes
+    # log-uniform in [16, 256]): tuned launch, route on and off
+    xs, ys, zs, offs = w.batched_clouds_3d(32768, w.SEED_BASE + 13 + 1000 * rank, nmin=16,
+                                           nmax=256)
+    Ps = torch.from_numpy(np.stack([xs, ys, zs])).to(dev)
+    Os = torch.from_numpy(offs).to(dev)
+    bs = qh.Hull3DBatch(Ps, cloud_off=Os)
+    stab = bs.tune(reps=2)
+    sc_small = {int(sc): round(t, 3) for bl, it, c, sc, t in stab
+                if (bl, it, c) == (bs.opts.block, bs.opts.items, bs.opts.blocks_per_sm)}
+    out["small_cloud_route"]["many_small_clouds"] = {
+        "workload": "32768 clouds, sizes log-uniform in [16, 256], anisotropic Gaussian",
+        "points": int(len(xs)), "threshold_ms": sc_small, "chosen": int(bs.opts.small_cloud),
+        "speedup_of_route": round(sc_small.get(0, 0.0) /
+                                  max(1e-9, sc_small.get(int(bs.opts.small_cloud), 1.0)), 2)}
+    del bs, Ps, Os
     # plain path on a bounded sample of clouds
     ns = min(args.batch_clouds, args.plain_clouds)
     ws = qh.Workspace(dev)
@@ -394,39 +461,55 @@ def bench_select(args, qh, dev, rank):
 
 
 def bench_switchover(args, qh, dev):
-    """CPU/GPU switchover (Section 6's open question): wall time of one
-    synchronous 2D hull call through the C ABI (device-resident points)
-    against the oracle on the host, over n; the smallest n from which the GPU
-    call is faster."""
+    """CPU/GPU switchover (Section 6's open question), per dimension: wall
+    time of one synchronous hull call through the C ABI (device-resident
+    points) against the oracle on the host, over n; the smallest n from which
+    the GPU call is faster.  (Inside a batch the switchover is the small-cloud
+    route's threshold, reported with the batched workload.)"""
     import torch
     import oracle
     from paper_1201_2936_gb300 import workloads as w
-    rows = []
     ws = qh.Workspace(dev)
-    cross = None
-    for n in (64, 256, 1024, 4096, 16384, 65536, 262144, 1048576):
-        x, y = w.uniform_disk(n, 1208 + n)
-        P = torch.from_numpy(np.stack([x, y])).to(dev)
-        for _ in range(3):
-            qh.hull2d(P, workspace=ws)
-        reps = 20
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            qh.hull2d(P, workspace=ws)
-        g = (time.perf_counter() - t0) / reps * 1e6
-        reps_c = max(1, min(50, 2_000_000 // n))
-        t0 = time.perf_counter()
-        for _ in range(reps_c):
-            oracle.hull2d(x, y)
-        c = (time.perf_counter() - t0) / reps_c * 1e6
-        rows.append({"n": n, "gpu_us": round(g, 1), "cpu_oracle_us": round(c, 1)})
-        if cross is None and g < c:
-            cross = n
-    return {"workload": "2D uniform disk, one hull per call", "rows": rows,
-            "gpu_faster_from_n": cross,
-            "note": "GPU: synchronous qh_hull2d incl. launch and result readback; "
-                    "CPU: the exact FP64 oracle, one thread"}
+
+    def sweep(sizes, gen, gpu, cpu):
+        rows, cross = [], None
+        for n in sizes:
+            pts = gen(n)
+            P = torch.from_numpy(np.stack(pts)).to(dev)
+            for _ in range(2):
+                gpu(P)
+            reps = 10
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                gpu(P)
+            torch.cuda.synchronize()
+            g = (time.perf_counter() - t0) / reps * 1e6
+            reps_c = max(1, min(20, 1_000_000 // n))
+            t0 = time.perf_counter()
+            for _ in range(reps_c):
+                cpu(*pts)
+            c = (time.perf_counter() - t0) / reps_c * 1e6
+            rows.append({"n": n, "gpu_us": round(g, 1), "cpu_oracle_us": round(c, 1)})
+            if cross is None and g < c:
+                cross = n
+        return rows, cross
+
+    out = {"note": "GPU: one synchronous call incl. launch and result readback; CPU: the exact "
+                   "FP64 oracle, one thread"}
+    r2, c2 = sweep((64, 256, 1024, 4096, 16384, 65536, 262144, 1048576),
+                   lambda n: w.uniform_disk(n, 1208 + n),
+                   lambda P: qh.hull2d(P, workspace=ws), oracle.hull2d)
+    out["2d"] = {"workload": "uniform disk", "rows": r2, "gpu_faster_from_n": c2}
+    r3, c3 = sweep((64, 256, 1024, 4096, 16384, 65536, 262144),
+                   lambda n: w.uniform_ball(n, 1218 + n),
+                   lambda P: qh.hull3d(P, workspace=ws), oracle.hull3d)
+    out["3d"] = {"workload": "uniform ball", "rows": r3, "gpu_faster_from_n": c3}
+    r4, c4 = sweep((64, 256, 1024, 4096, 16384, 65536),
+                   lambda n: w.uniform_ball_4d(n, 1228 + n),
+                   lambda P: qh.hull4d(P, workspace=ws), oracle.hull4d)
+    out["4d"] = {"workload": "uniform 4-ball", "rows": r4, "gpu_faster_from_n": c4}
+    return out
 
 
 def run_reference(args, ws, rank):
@@ -470,6 +553,7 @@ def main():
     ap.add_argument("--only", default="", help="comma-separated cloud names to keep")
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-4d", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--no-select", action="store_true")
     ap.add_argument("--no-switchover", action="store_true")
@@ -480,7 +564,7 @@ def main():
     ap.add_argument("--timeline", action="store_true",
                     help="print the per-iteration device timeline of each cloud to stderr")
     ap.add_argument("--sections", default="",
-                    help="comma-separated subset of 3d,batched,diff,select,switchover,plain,e2e,cpu to run "
+                    help="comma-separated subset of 3d,4d,batched,diff,select,switchover,plain,e2e,cpu to run "
                          "besides the 2D headline (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -488,6 +572,7 @@ def main():
         keep = set(args.sections.split(","))
         args.no_3d = "3d" not in keep
         args.no_batched = "batched" not in keep
+        args.no_4d = "4d" not in keep
         args.no_diff = "diff" not in keep
         args.no_select = "select" not in keep
         args.no_switchover = "switchover" not in keep
@@ -685,6 +770,10 @@ def main():
     if not args.no_3d:
         line["hull3d"] = bench_3d(args, qh, dev, rank, peak, peak_kind)
 
+    # ---- 4D (the higher-dimensional extension): 1M in the 4-ball, 100K near the 3-sphere
+    if not args.no_4d:
+        line["hull4d"] = bench_4d(args, qh, dev, rank, peak, peak_kind)
+
     # ---- batched 3D: one persistent launch per batch, CUDA graph, autotuned shape
     if not args.no_batched:
         line["batched3d"] = bench_batched(args, qh, dev, rank, peak, peak_kind)
@@ -697,7 +786,7 @@ def main():
     if not args.no_select:
         line["selection"] = bench_select(args, qh, dev, rank)
 
-    # ---- CPU/GPU switchover of the 2D hull
+    # ---- CPU/GPU switchover, per dimension
     if rank == 0 and not args.no_switchover:
         line["switchover"] = bench_switchover(args, qh, dev)
 

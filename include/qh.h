@@ -87,8 +87,13 @@ typedef struct qh_opts {
                              wait_ns and the call reports QH_ERR_TIMEOUT.  The kernel then
                              leaves without starting another phase; the workspace is
                              reusable for the next call. */
-    int32_t reserved;
+    int32_t small_cloud;  /* batched 3D: clouds of 4 to small_cloud points are hulled whole by
+                             one warp each during the setup (the small-cloud route), the rest
+                             by the segmented iterations; 0 = every cloud through the
+                             iterations (default); at most QH_SMALL_CLOUD_MAX */
 } qh_opts;
+
+#define QH_SMALL_CLOUD_MAX 4096
 
 /* Result record written by the device (async calls) and copied back by the
  * synchronous calls.  All counts are totals over the call. */
@@ -281,11 +286,16 @@ qh_status qh_hull3d_batched(const float *d_x, const float *d_y, const float *d_z
 /*
  * qh_autotune_3d_batched: times qh_hull3d_batched on the caller's batch for
  * every launch shape (threads per CTA 128/256/512 x points per thread
- * 2/4/8 x CTAs per SM 1/2/4, capped by occupancy): one untimed run, then
- * `reps` (1..64) runs timed with CUDA events on `stream`; the median decides.
- *  h_best    in: base options (predicate mode); out: the fastest shape
+ * 2/4/8 x CTAs per SM 1/2/4, capped by occupancy), then, at the fastest
+ * shape, for the small-cloud thresholds 0, 64, 256, 1024 and 4096
+ * (qh_opts.small_cloud: the switchover below which one warp hulls a cloud
+ * whole; no counterpart in the paper, which leaves switchover points to
+ * future work in Section 6): one untimed run, then `reps` (1..64) runs timed
+ * with CUDA events on `stream`; the median decides.
+ *  h_best    in: base options (predicate mode); out: the fastest candidate
  *  h_ms      host float[max_cand]: median ms of each candidate that ran
- *  h_shape   host int32[3*max_cand]: (block, items, CTAs per SM) of each
+ *  h_shape   host int32[4*max_cand]: (block, items, CTAs per SM,
+ *            small-cloud threshold) of each
  *  h_ncand   host: candidates reported
  * Synchronises the stream; the outputs hold the hulls of the last run.
  */

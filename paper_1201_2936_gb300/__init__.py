@@ -40,7 +40,7 @@ def version() -> str:
 
 def make_opts(pred: str = "f32", loop: str = "persistent", blocks_per_sm: int = 0,
               max_iters: int = 0, wait_ns: int = 0, block: int = 0, items: int = 0,
-              max_ctas: int = 0, test_hold: int = 0) -> QhOpts:
+              max_ctas: int = 0, test_hold: int = 0, small_cloud: int = 0) -> QhOpts:
     o = QhOpts()
     _native.lib().qh_default_opts(ctypes.byref(o))
     o.pred_mode = PRED[pred]
@@ -52,6 +52,7 @@ def make_opts(pred: str = "f32", loop: str = "persistent", blocks_per_sm: int = 
     o.items = items
     o.max_ctas = max_ctas
     o.test_hold = test_hold
+    o.small_cloud = small_cloud
     return o
 
 
@@ -455,14 +456,15 @@ class Hull3DBatch:
             raise QHError(st, "qh_hull3d_batched")
 
     def tune(self, reps: int = 3, stream=None):
-        """Autotune the launch shape on this batch (qh_autotune_3d_batched);
-        keeps the fastest in self.opts and returns [(block, items,
-        ctas_per_sm, ms), ...]."""
+        """Autotune the launch on this batch (qh_autotune_3d_batched): the
+        shape, then the small-cloud threshold at the fastest shape; keeps the
+        fastest in self.opts and returns [(block, items, ctas_per_sm,
+        small_cloud, ms), ...]."""
         import numpy as np
         best = QhOpts()
         ctypes.memmove(ctypes.byref(best), ctypes.byref(self.opts), ctypes.sizeof(QhOpts))
         ms = np.zeros(64, dtype=np.float32)
-        shape = np.zeros(3 * 64, dtype=np.int32)
+        shape = np.zeros(4 * 64, dtype=np.int32)
         nc = ctypes.c_int32(0)
         st = _native.lib().qh_autotune_3d_batched(
             *self._args(), int(reps), ctypes.byref(best), ms.ctypes.data_as(ctypes.c_void_p),
@@ -470,8 +472,8 @@ class Hull3DBatch:
         if st != 0:
             raise QHError(st, "qh_autotune_3d_batched")
         self.opts = best
-        return [(int(shape[3 * i]), int(shape[3 * i + 1]), int(shape[3 * i + 2]), float(ms[i]))
-                for i in range(nc.value)]
+        return [(int(shape[4 * i]), int(shape[4 * i + 1]), int(shape[4 * i + 2]),
+                 int(shape[4 * i + 3]), float(ms[i])) for i in range(nc.value)]
 
     def capture(self) -> None:
         """Capture one enqueue() in a CUDA graph (after a warm-up run)."""

@@ -533,6 +533,303 @@ __device__ int block_next_vertex(const Params3 &A, SmemAll3 &sm, int lo, int hi,
     return r == INT_MAX ? -1 : r;
 }
 
+// ---------------------------------------------------------------- small-cloud route
+// Below a size chosen by the autotuner (qh_opts.small_cloud) a cloud is
+// cheaper to hull whole with one warp than to run through the segmented
+// iterations (the switchover point the paper leaves to future work, Section
+// 6).  Clouds of 4..small_cloud points get that route during the setup.
+__device__ __forceinline__ bool is_small_cloud(const Params3 &A, int c)
+{
+    const int nc = cloud_start(A, c + 1) - cloud_start(A, c);
+    return A.small_cloud > 0 && nc >= 4 && nc <= A.small_cloud;
+}
+
+// Exact: p strictly above facet g.
+__device__ __forceinline__ bool above3(const Params3 &A, int g, const float *p, unsigned &fb)
+{
+    float d, e;
+    facet_value<QH_PRED_F32>(A, g, p, d, e);
+    if (d > e) return true;
+    if (-d > e) return false;
+    const Fac3 &G = A.fac[g];
+    return orient3d_sign<QH_PRED_F32>(d, e, G.p, G.p + 3, G.p + 6, p, fb) > 0;
+}
+
+// One warp, one cloud: Quickhull inserting one apex at a time (Barber et
+// al.): a tetrahedron of the cloud's extreme points (slots 4c..4c+3, exact
+// tests), every point to the first facet strictly below it, then until no
+// point is outside: the lowest outside point's facet, its farthest point
+// (exact comparisons, lowest index on ties), every alive facet of the cloud
+// strictly below it (the visible region of a convex polytope is connected,
+// so no search is needed), its horizon, the cone (one facet per horizon
+// edge, linked around the apex), and the visible facets' points to the first
+// cone facet strictly below them.  The facets land in the global table like
+// every other cloud's; the cloud's pseudo facet gets an empty cone, so the
+// segmented passes drop its points.  Scratch borrowed while the pools are
+// idle: the cloud's facet list in its candidate-list slice (kVCap per
+// point), horizon edges in its neighbour slice (kNCap per point), each
+// point's facet in code[].x.
+__device__ void small_hull_warp(const Params3 &A, int c, unsigned &fb)
+{
+    Hdr3 *H = A.hdr;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const int lo = cloud_start(A, c), hi = cloud_start(A, c + 1), nc = hi - lo;
+    const int base4 = 4 * c, pseudo = A.fcap + c;
+    int *fl = A.vpool + (size_t)lo * kVCap;
+    int *hz = A.npool + (size_t)lo * kNCap;
+    const long long fl_cap = (long long)kVCap * nc, hz_cap = (long long)kNCap * nc;
+    auto fail = [&](int st) {
+        if (lane == 0) {
+            dead_tetra_at(A, base4, pseudo);
+            A.cloud_status[c] = st;
+        }
+        __syncwarp();
+    };
+    // ---- extrema (lexicographic, lowest index) and finiteness
+    float4 mn = make_float4(INFINITY, INFINITY, INFINITY, __int_as_float(INT_MAX));
+    float4 mx = make_float4(-INFINITY, -INFINITY, -INFINITY, __int_as_float(INT_MAX));
+    bool bad = false;
+    for (int i = lo + lane; i < hi; i += 32) {
+        float4 p = load_input(A, i);
+        p.x = canon0(p.x);
+        p.y = canon0(p.y);
+        p.z = canon0(p.z);
+        bad |= !(isfinite(p.x) && isfinite(p.y) && isfinite(p.z));
+        if (lex_less(p, mn)) mn = p;
+        if (lex_greater_lowidx(p, mx)) mx = p;
+    }
+    if (__any_sync(0xffffffffu, bad)) return fail(QH_ERR_NONFINITE);
+    for (int o = 16; o > 0; o >>= 1) {
+        float4 a, b;
+        a.x = __shfl_xor_sync(0xffffffffu, mn.x, o);
+        a.y = __shfl_xor_sync(0xffffffffu, mn.y, o);
+        a.z = __shfl_xor_sync(0xffffffffu, mn.z, o);
+        a.w = __shfl_xor_sync(0xffffffffu, mn.w, o);
+        b.x = __shfl_xor_sync(0xffffffffu, mx.x, o);
+        b.y = __shfl_xor_sync(0xffffffffu, mx.y, o);
+        b.z = __shfl_xor_sync(0xffffffffu, mx.z, o);
+        b.w = __shfl_xor_sync(0xffffffffu, mx.w, o);
+        if (lex_less(a, mn)) mn = a;
+        if (lex_greater_lowidx(b, mx)) mx = b;
+    }
+    if (mn.x == mx.x && mn.y == mx.y && mn.z == mx.z) return fail(QH_ERR_DEGENERATE);
+    float4 t[4] = {mn, mx, mn, mn};
+    // ---- c: lowest index off the line ab; d: lowest index off the plane abc
+    for (int step = 0; step < 2; step++) {
+        const float a[3] = {t[0].x, t[0].y, t[0].z}, b[3] = {t[1].x, t[1].y, t[1].z};
+        const float cc[3] = {t[2].x, t[2].y, t[2].z};
+        int first = INT_MAX;
+        for (int i = lo + lane; i < hi && first == INT_MAX; i += 32) {
+            const float4 p4 = load_input(A, i);
+            const float q[3] = {p4.x, p4.y, p4.z};
+            const bool off =
+                step == 0 ? !collinear3_exact(a, b, q) : orient3d_exact_sign(a, b, cc, q) != 0;
+            if (off) first = i;
+        }
+        first = (int)__reduce_min_sync(0xffffffffu, (unsigned)first);
+        if (first == INT_MAX) return fail(QH_ERR_DEGENERATE);
+        t[2 + step] = load_input(A, first);
+    }
+    if (lane == 0) {
+        build_tetra_at(A, base4, t, pseudo);
+        A.cone[pseudo] = make_int4(0, 0, -1, 0);  // the segmented passes drop its points
+        atomicAdd(&H->hull_vertices, 4);
+    }
+    if (lane < 4) fl[lane] = base4 + lane;
+    int nf = 4;
+    __syncwarp();
+    for (int i = lo + lane; i < hi; i += 32) {
+        const float4 p4 = load_input(A, i);
+        const int idx = __float_as_int(p4.w);
+        int g = -1;
+        bool vtx = false;
+        for (int k = 0; k < 4; k++) vtx |= idx == __float_as_int(t[k].w);
+        const float p[3] = {p4.x, p4.y, p4.z};
+        for (int k = 0; k < 4 && g < 0 && !vtx; k++)
+            if (above3(A, base4 + k, p, fb)) g = base4 + k;
+        A.code[i].x = g;
+    }
+    __syncwarp();
+    // ---- insertions (each consumes its apex: at most nc)
+    for (int it = 1; it <= nc; it++) {
+        int cand = INT_MAX;
+        for (int i = lo + lane; i < hi; i += 32)
+            if (A.code[i].x >= 0) {
+                cand = i;
+                break;
+            }
+        cand = (int)__reduce_min_sync(0xffffffffu, (unsigned)cand);
+        if (cand == INT_MAX) break;
+        const int f = A.code[cand].x;
+        const Fac3 F = A.fac[f];
+        // farthest point of f's outside set
+        int best = -1;
+        float bx = 0.f, by = 0.f, bz = 0.f;
+        for (int i = lo + lane; i < hi; i += 32) {
+            if (A.code[i].x != f) continue;
+            const float4 p4 = load_input(A, i);
+            if (best >= 0) {
+                const float p[3] = {p4.x, p4.y, p4.z}, q[3] = {bx, by, bz};
+                const int sgn = cmp_dist3_exact_sign(F.p, F.p + 3, F.p + 6, p, q);
+                if (!(sgn > 0 || (sgn == 0 && i < best))) continue;
+            }
+            best = i;
+            bx = p4.x;
+            by = p4.y;
+            bz = p4.z;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const float ox = __shfl_xor_sync(0xffffffffu, bx, o);
+            const float oy = __shfl_xor_sync(0xffffffffu, by, o);
+            const float oz = __shfl_xor_sync(0xffffffffu, bz, o);
+            if (ob < 0) continue;
+            bool take = best < 0;
+            if (!take) {
+                const float p[3] = {ox, oy, oz}, q[3] = {bx, by, bz};
+                const int sgn = cmp_dist3_exact_sign(F.p, F.p + 3, F.p + 6, p, q);
+                take = sgn > 0 || (sgn == 0 && ob < best);
+            }
+            if (take) {
+                best = ob;
+                bx = ox;
+                by = oy;
+                bz = oz;
+            }
+        }
+        const float4 q4 = load_input(A, best);
+        const float q[3] = {q4.x, q4.y, q4.z};
+        const int qi = best;
+        const unsigned long long key = ((unsigned long long)(unsigned)(c + 1) << 32) | (unsigned)it;
+        // visible: every alive facet of the cloud strictly below q
+        for (int j = lane; j < nf; j += 32) {
+            const int g = fl[j];
+            if (A.fac[g].alive && above3(A, g, q, fb)) A.claim[1][g] = key;
+        }
+        __syncwarp();
+        // horizon edges: edges of visible facets whose neighbour is not visible
+        int nh = 0;
+        for (int j0 = 0; j0 < nf; j0 += 32) {
+            const int j = j0 + lane;
+            unsigned hm = 0;
+            int g = -1;
+            if (j < nf) {
+                g = fl[j];
+                if (A.claim[1][g] == key)
+                    for (int k = 0; k < 3; k++)
+                        if (A.claim[1][A.fac[g].nb[k]] != key) hm |= 1u << k;
+            }
+            const int cnt = __popc(hm);
+            int inc = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += v;
+            }
+            const int pos = nh + inc - cnt;
+            int w = 0;
+            for (int k = 0; k < 3; k++)
+                if (hm & (1u << k)) {
+                    if (pos + w < hz_cap) hz[pos + w] = g * 3 + k;
+                    w++;
+                }
+            nh += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&H->fcount, nh);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (nh > hz_cap || base + nh > A.fcap || nf + nh > fl_cap) {
+            if (lane == 0) set_status(H, QH_ERR_CAPACITY);
+            return fail(QH_ERR_CAPACITY);
+        }
+        __syncwarp();
+        // cone facets, one per horizon edge (u, v, q), the outside
+        // neighbour relinked
+        for (int j = lane; j < nh; j += 32) {
+            const int hf = hz[j] / 3, k = hz[j] - 3 * (hz[j] / 3), k1 = (k + 1) % 3;
+            const Fac3 &G0 = A.fac[hf];
+            Fac3 C;
+            C.p[0] = G0.p[3 * k + 0]; C.p[1] = G0.p[3 * k + 1]; C.p[2] = G0.p[3 * k + 2];
+            C.p[3] = G0.p[3 * k1 + 0]; C.p[4] = G0.p[3 * k1 + 1]; C.p[5] = G0.p[3 * k1 + 2];
+            C.p[6] = q4.x; C.p[7] = q4.y; C.p[8] = q4.z;
+            C.v[0] = G0.v[k];
+            C.v[1] = G0.v[k1];
+            C.v[2] = qi;
+            const int g = G0.nb[k];
+            C.nb[0] = g;
+            C.nb[1] = -1;
+            C.nb[2] = -1;
+            C.alive = 1;
+            A.fac[base + j] = C;
+            A.plane[base + j] = make_plane3(C.p, C.p + 3, C.p + 6);
+            Acc3 z = {};
+            A.acc[base + j] = z;
+            A.claim[0][base + j] = 0ull;
+            A.claim[1][base + j] = 0ull;
+            A.taken[base + j] = 0;
+            A.big_mark[base + j] = -1;
+            Fac3 &G = A.fac[g];
+            for (int tt = 0; tt < 3; tt++)
+                if (G.nb[tt] == hf) G.nb[tt] = base + j;
+        }
+        __syncwarp();
+        // around q: edge (v, q) meets the cone facet whose horizon edge
+        // starts at v, edge (q, u) the one whose horizon edge ends at u
+        for (int j = lane; j < nh; j += 32) {
+            const int u = A.fac[base + j].v[0], v = A.fac[base + j].v[1];
+            int n1 = -1, n2 = -1;
+            for (int i = 0; i < nh; i++) {
+                const int du = A.fac[base + i].v[0], dv = A.fac[base + i].v[1];
+                if (du == v) n1 = base + i;
+                if (dv == u) n2 = base + i;
+            }
+            A.fac[base + j].nb[1] = n1;
+            A.fac[base + j].nb[2] = n2;
+        }
+        for (int j = lane; j < nf; j += 32) {
+            const int g = fl[j];
+            if (A.claim[1][g] == key) A.fac[g].alive = 0;
+        }
+        for (int j = lane; j < nh; j += 32) fl[nf + j] = base + j;
+        nf += nh;
+        if (lane == 0) atomicAdd(&H->hull_vertices, 1);
+        __syncwarp();
+        // the visible facets' points: to the first cone facet strictly below
+        for (int i = lo + lane; i < hi; i += 32) {
+            const int g = A.code[i].x;
+            if (g < 0 || A.claim[1][g] != key) continue;
+            int tg = -1;
+            if (i != qi) {
+                const float4 p4 = load_input(A, i);
+                const float p[3] = {p4.x, p4.y, p4.z};
+                for (int jj = 0; jj < nh && tg < 0; jj++)
+                    if (above3(A, base + jj, p, fb)) tg = base + jj;
+            }
+            A.code[i].x = tg;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) A.cloud_status[c] = QH_OK;
+    __syncwarp();
+}
+
+// Every warp takes small clouds from a queue (the others are init_clouds').
+__device__ void small_clouds(const Params3 &A)
+{
+    Hdr3 *H = A.hdr;
+    const int lane = threadIdx.x & 31;
+    unsigned fb = 0;
+    for (;;) {
+        int c = 0;
+        if (lane == 0) c = atomicAdd(&H->next_small, 1);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= A.ncloud) break;
+        if (is_small_cloud(A, c)) small_hull_warp(A, c, fb);
+    }
+    const unsigned f = __reduce_add_sync(0xffffffffu, fb);
+    if (lane == 0 && f) atomicAdd(&H->fallbacks, (unsigned long long)f);
+}
+
 // One block per cloud: its initial simplex as facets 4c..4c+3 (dead facets
 // and a per-cloud status when the cloud does not span 3D or holds a
 // non-finite coordinate).
@@ -549,6 +846,7 @@ __device__ void init_clouds(const Params3 &A, SmemAll3 &sm, int bid, int nb)
         __syncthreads();
         const int c = sm.red.flag;
         if (c >= A.ncloud) break;
+        if (is_small_cloud(A, c)) continue;  // hulled whole by one warp (small_clouds)
         const int lo = cloud_start(A, c), hi = cloud_start(A, c + 1);
         const int base = 4 * c, pseudo = A.fcap + c;
         int st = QH_OK;
@@ -583,7 +881,6 @@ __device__ void init_clouds(const Params3 &A, SmemAll3 &sm, int bid, int nb)
         }
         __syncthreads();
     }
-    if (bid == 0 && threadIdx.x == 0) H->fcount = 4 * A.ncloud;
 }
 
 // ---------------------------------------------------------------- S: select
@@ -1653,7 +1950,10 @@ __global__ void __launch_bounds__(kMaxBlock) qh3d_persistent(Params3 A)
     // ---- initial simplex: grid-wide for one cloud, one block per cloud for
     // a batch
     if (A.cloud_off) {
-        if (go) init_clouds(A, sm, bid, nb);  // offsets checked before the launch
+        if (go) {
+            if (A.small_cloud > 0) small_clouds(A);  // one warp per small cloud
+            init_clouds(A, sm, bid, nb);               // offsets checked before the launch
+        }
         go = sync() && go;
     } else {
         if (go) {

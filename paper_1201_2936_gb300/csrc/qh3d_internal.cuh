@@ -68,6 +68,7 @@ struct Hdr3 {
     int tile_sz[2];         // points per assign / scatter tile of each table
     int n_uncert;
     int next_cloud;         // queue of the per-cloud setup
+    int next_small;         // queue of the small-cloud route (one warp per cloud)
     long long seg_total, surv_total;
     unsigned long long fallbacks, exact_argmax;
     // output stage
@@ -127,6 +128,7 @@ struct Params3 {
     int *blk_i;
     long long max_iters, wait_ns;
     int test_hold;                // CTA 0 skips its first grid-barrier arrival (tests)
+    int small_cloud;              // batched: clouds of 4..small_cloud points, one warp each
 };
 
 // The pseudo facet of cloud c in the first assignment (every point of the

@@ -151,6 +151,7 @@ Params3 make_params3(const float *x, const float *y, const float *z, int64_t n, 
     A.max_iters = o.max_iters > 0 ? o.max_iters : 4 * n + 16;
     A.wait_ns = o.wait_ns > 0 ? o.wait_ns : 2000000000ll;
     A.test_hold = o.test_hold;
+    A.small_cloud = o.small_cloud;
     const int block = o.block > 0 ? o.block : (o.pred_mode == QH_PRED_F64 ? kDefBlockF64 : kDefBlockF32);
     const int items = o.items > 0 ? o.items : kDefItems;
     A.tile = block * items;
@@ -645,6 +646,9 @@ __global__ void __launch_bounds__(256) k_finish(Params3 A, const int32_t *verts,
 // Batched input check: offsets start at 0, never decrease, end at n.
 __global__ void k_check_clouds(Params3 A)
 {
+    // facet ids 4c..4c+3 are the clouds' simplices; the small-cloud route
+    // allocates from here on during the setup
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.hdr->fcount = 4 * A.ncloud;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < A.ncloud; c += gridDim.x * blockDim.x) {
         const long long a = A.cloud_off[c], b = A.cloud_off[c + 1];
         if ((c == 0 && a != 0) || b < a || (c == A.ncloud - 1 && b != A.n))
@@ -789,7 +793,8 @@ extern "C" qh_status qh_debug_phases_3d(const void *d_ws, int64_t *h_ns, cudaStr
 
 static bool opts_ok(const qh_opts &o)
 {
-    return o.pred_mode == QH_PRED_F32 || o.pred_mode == QH_PRED_F64;
+    return (o.pred_mode == QH_PRED_F32 || o.pred_mode == QH_PRED_F64) && o.small_cloud >= 0 &&
+           o.small_cloud <= QH_SMALL_CLOUD_MAX;
 }
 
 extern "C" qh_status qh_hull3d(const float *d_x, const float *d_y, const float *d_z, int64_t n,

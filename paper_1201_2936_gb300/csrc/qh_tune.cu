@@ -1,10 +1,13 @@
-// Autotuner of the batched 3D launch shape: threads per CTA, points per
-// thread of the assign pass and CTAs per SM of the persistent grid.  Each
-// candidate runs the caller's batch on the caller's stream (one untimed run,
-// then `reps` runs timed with CUDA events); the fastest candidate whose runs
-// all end with QH_OK is returned.  The hull does not depend on the launch
-// shape (every decision is an exact predicate or an index tie-break), so
-// the outputs of the last run are valid for any candidate.
+// Autotuner of the batched 3D launch: threads per CTA, points per thread of
+// the assign pass and CTAs per SM of the persistent grid, then, at the
+// fastest shape, the small-cloud threshold (clouds of at most that many
+// points hulled whole by one warp: the switchover point below which that
+// beats the segmented iterations).  Each candidate runs the caller's batch
+// on the caller's stream (one untimed run, then `reps` runs timed with CUDA
+// events); the fastest candidate whose runs all end with QH_OK is returned.
+// The hull does not depend on these choices (every decision is an exact
+// predicate or an index tie-break), so the outputs of the last run are
+// valid for any candidate.
 #include <algorithm>
 #include <vector>
 
@@ -14,7 +17,7 @@
 namespace {
 
 struct Cand {
-    int block, items, bps;
+    int block, items, bps, small;
 };
 
 // Events are created once per call and destroyed on every exit path.
@@ -55,17 +58,27 @@ extern "C" qh_status qh_autotune_3d_batched(
     std::vector<Cand> cands;
     for (int block : {128, 256, 512})
         for (int items : {2, 4, 8})
-            for (int bps : {1, 2, 4}) cands.push_back({block, items, bps});
+            for (int bps : {1, 2, 4}) cands.push_back({block, items, bps, base.small_cloud});
+    const size_t nshape = cands.size();
     Events E(reps + 1);
     if (!E.ok()) return QH_ERR_CUDA;
     float best_ms = -1.0f;
     qh_opts best = base;
     int nc = 0;
-    for (const Cand &c : cands) {
+    for (size_t ci = 0;; ci++) {
+        if (ci == nshape && best_ms >= 0.0f) {
+            // second stage: the small-cloud threshold at the fastest shape
+            for (int sc : {0, 64, 256, 1024, 4096})
+                if (sc != best.small_cloud)
+                    cands.push_back({best.block, best.items, best.blocks_per_sm, sc});
+        }
+        if (ci >= cands.size()) break;
+        const Cand c = cands[ci];
         qh_opts o = base;
         o.block = c.block;
         o.items = c.items;
         o.blocks_per_sm = c.bps;
+        o.small_cloud = c.small;
         bool good = true;
         std::vector<float> ms;
         for (int r = 0; r <= reps && good; r++) {
@@ -99,9 +112,10 @@ extern "C" qh_status qh_autotune_3d_batched(
         const float med = ms[ms.size() / 2];
         if (nc < max_cand) {
             h_ms[nc] = med;
-            h_shape[3 * nc + 0] = c.block;
-            h_shape[3 * nc + 1] = c.items;
-            h_shape[3 * nc + 2] = c.bps;
+            h_shape[4 * nc + 0] = c.block;
+            h_shape[4 * nc + 1] = c.items;
+            h_shape[4 * nc + 2] = c.bps;
+            h_shape[4 * nc + 3] = c.small;
         }
         nc++;
         if (best_ms < 0.0f || med < best_ms) {

@@ -136,3 +136,42 @@ def test_full_batch_4096_clouds(qh):
     assert len(got) == 4096
     for c in range(4096):
         assert got[c] == want[c], c
+
+
+@pytest.mark.parametrize("small", [16, 64, 512, 4096])
+def test_small_cloud_route_matches_oracle(qh, small):
+    # clouds of 4..small points hulled whole by one warp in the setup: the
+    # mixed batch's degenerate, coplanar, non-finite, lattice, duplicated
+    # and spherical clouds included
+    x, y, z, off = _mixed_batch(43)
+    want = _want(x, y, z, off)
+    P, O = _dev(x, y, z, off)
+    for pred in ("f32", "f64"):
+        o = qh.make_opts(pred, small_cloud=small)
+        got = _split(qh.hull3d_batched(P, cloud_off=O, opts=o))
+        assert got == want, (pred, small)
+
+
+def test_full_batch_small_cloud_route(qh):
+    # the full batch with most clouds (4..4096 points) on the warp route
+    x, y, z, off = w.batched_clouds_3d(4096, w.SEED_BASE + 3)
+    want = _want(x, y, z, off)
+    P, O = _dev(x, y, z, off)
+    got = _split(qh.hull3d_batched(P, cloud_off=O, opts=qh.make_opts("f32", small_cloud=4096)))
+    assert len(got) == 4096
+    for c in range(4096):
+        assert got[c] == want[c], c
+
+
+def test_many_small_clouds_tuned(qh):
+    # a batch of many small clouds (where the warp route wins): autotuned
+    # threshold, outputs equal to the oracle's, and the same with the route off
+    x, y, z, off = w.batched_clouds_3d(2048, 98, nmin=16, nmax=256)
+    want = _want(x, y, z, off)
+    P, O = _dev(x, y, z, off)
+    b = qh.Hull3DBatch(P, cloud_off=O)
+    table = b.tune(reps=1)
+    assert {sc for *_, sc, ms in table} >= {0, 64, 256, 1024, 4096}
+    assert _split(b.outputs()) == want
+    got0 = _split(qh.hull3d_batched(P, cloud_off=O, opts=qh.make_opts("f32", small_cloud=0)))
+    assert got0 == want

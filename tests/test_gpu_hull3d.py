@@ -152,3 +152,14 @@ def test_non_finite_input(qh):
         with pytest.raises(qh.QHError) as ei:
             _gpu(qh, x, y, zz)
         assert ei.value.status == 2
+
+
+def test_near_sphere_full_size(qh):
+    # the benchmark's near-sphere workload at full size (8M points, radius
+    # 1 + 1e-4 N(0, 1)): vertex list and faces equal the oracle's
+    x, y, z = w.near_sphere(w.N_BALL_3D, w.SEED_BASE + 22, 1e-4)
+    gv, gf, res = _gpu(qh, x, y, z)
+    ov, of = _oracle(x, y, z)
+    assert res["status"] == 0
+    assert gv == ov
+    assert gf == of
