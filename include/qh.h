@@ -470,6 +470,14 @@ qh_status qh_debug_timeline_2d(const void *d_ws, int64_t n, int64_t *h_rows, int
 qh_status qh_debug_timeline_3d(const void *d_ws, int64_t n, int64_t *h_rows, int32_t max_rows,
                                int32_t *h_nrows, cudaStream_t stream);
 
+/* Per-iteration record of the last qh_hull4d call made by the calling host
+ * thread: row r (h_rows: int64[9 * max_rows]) holds {iteration, segments,
+ * live points, apexes inserted in the previous iteration, apexes that
+ * needed the exact farthest-point step, host ns of the iteration, then the
+ * candidates that claimed in selection rounds 0, 1 and 2 of the previous
+ * iteration}; at most 4096 rows.  Diagnostics only. */
+qh_status qh_debug_timeline_4d(int64_t *h_rows, int32_t max_rows, int32_t *h_nrows);
+
 /*
  * The paper's segmented primitives and a second workload built on them.
  * Arrays are int32 on the device; a segmented array of n elements carries

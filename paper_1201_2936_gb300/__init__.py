@@ -331,6 +331,21 @@ def hull4d(x: torch.Tensor, y: Optional[torch.Tensor] = None, z: Optional[torch.
     return (out, res.as_dict()) if return_result else out
 
 
+def debug_timeline_4d():
+    """Per-iteration rows of the last hull4d call on this thread: iteration,
+    segments, live points, apexes of the previous iteration, uncertified
+    apexes, host ns, candidates claiming in rounds 0-2 of the previous
+    iteration."""
+    import numpy as np
+    rows = np.zeros((4096, 9), dtype=np.int64)
+    nr = ctypes.c_int32(0)
+    st = _native.lib().qh_debug_timeline_4d(rows.ctypes.data_as(ctypes.c_void_p), 4096,
+                                            ctypes.byref(nr))
+    if st != 0:
+        raise QHError(st, "qh_debug_timeline_4d")
+    return rows[: nr.value]
+
+
 NOALLOC_MAX_POINTS = 131072
 
 

@@ -55,6 +55,7 @@ SIGNATURES = [
                                        _sz, _POpts, _vp]),
     ("qh_workspace_bytes_3d", _sz, [_i64, _POpts]),
     ("qh_workspace_bytes_4d", _sz, [_i64, _POpts]),
+    ("qh_debug_timeline_4d", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     ("qh_hull4d", ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _i64, _vp, ctypes.POINTER(_i64), _vp,
                                  _i64, _vp, _i64, ctypes.POINTER(_i64), _PRes, _vp, _sz, _POpts,
                                  _vp]),

@@ -22,6 +22,7 @@
 // vertex of the simplices around it lies on every hyperplane through it).
 
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cstdio>
 #include <cstring>
@@ -35,10 +36,20 @@
 namespace qh {
 namespace d4 {
 
-constexpr int kV = 48;         // visible facets a candidate may list
-constexpr int kN = 100;        // horizon neighbours (>= 2 kV + 2: a 3-ball of kV
-                               // tetrahedra has at most 2 kV + 2 boundary triangles)
-constexpr int kRounds4 = 3;    // selection rounds per iteration
+// Visible facets a candidate may list, and horizon neighbours (>= 2 kV + 2:
+// a 3-ball of kV tetrahedra has at most 2 kV + 2 boundary triangles).  A
+// late point at height h above a finely triangulated 3-sphere sees a cap of
+// radius ~sqrt(2h), whose facet count grows with the cube of that radius
+// (the square in 3D): the lists are longer than the 3D ones.
+#ifndef QH4D_VCAP
+#define QH4D_VCAP 128
+#endif
+constexpr int kV = QH4D_VCAP;
+constexpr int kN = 2 * kV + 2;
+#ifndef QH4D_ROUNDS
+#define QH4D_ROUNDS 3
+#endif
+constexpr int kRounds4 = QH4D_ROUNDS;  // selection rounds per iteration
 constexpr int kBlock = 256;
 constexpr int kItems = 4;      // points per thread of the assign tiles
 constexpr int kTile = kBlock * kItems;
@@ -1367,6 +1378,11 @@ extern "C" size_t qh_workspace_bytes_4d(int64_t n, const qh_opts *opts)
 
 namespace {
 
+// Per-iteration record of the last call made by this host thread:
+// iteration, segments, live points, apexes inserted, uncertified apexes,
+// host nanoseconds of the iteration (diagnostics).
+thread_local std::vector<int64_t> g_tl4;
+
 int grid_of4(long long items)
 {
     const long long g = (items + kBlock - 1) / kBlock;
@@ -1491,10 +1507,20 @@ extern "C" qh_status qh_hull4d(const float *d_x, const float *d_y, const float *
     if (h.n_uncert > 0) k4_exact<<<std::min(h.n_uncert, 8 * sm_count()), kBlock, 0, st>>>(A, 0);
     // ---- iterations: table `cur` describes the live points in buffer `cur`
     int cur = 1, iter = 0;
+    g_tl4.clear();
+    auto t_prev = std::chrono::steady_clock::now();
     for (;;) {
         if (read_hdr(A, h, st) != cudaSuccess) return QH_ERR_CUDA;
         if (h.status) return finish((qh_status)h.status, h);
         const int ne = (int)(h.tab[cur] >> 32), Lc = (int)(h.tab[cur] & 0xffffffffull);
+        if (iter > 0 && g_tl4.size() < 9 * 4096) {
+            const auto t = std::chrono::steady_clock::now();
+            g_tl4.insert(g_tl4.end(), {iter, ne, Lc, h.nwin, h.n_uncert,
+                                       (int64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                           t - t_prev).count(),
+                                       h.nact[0], h.nact[1], h.nact[2]});
+            t_prev = t;
+        }
         if (ne == 0) break;
         if (++iter > A.max_iters) return finish(QH_ERR_NO_CONVERGENCE, h);
         k4_iter_begin<<<1, 32, 0, st>>>(A, cur, iter);
@@ -1596,4 +1622,13 @@ extern "C" qh_status qh_hull4d(const float *d_x, const float *d_y, const float *
     if (read_hdr(A, h, st) != cudaSuccess) return QH_ERR_CUDA;
     h.nfidx = tot[2];
     return finish((qh_status)h.status, h);
+}
+
+extern "C" qh_status qh_debug_timeline_4d(int64_t *h_rows, int32_t max_rows, int32_t *h_nrows)
+{
+    if (!h_rows || !h_nrows || max_rows < 0) return QH_ERR_INVALID_ARG;
+    const int rows = std::min((int)(g_tl4.size() / 9), (int)max_rows);
+    std::memcpy(h_rows, g_tl4.data(), sizeof(int64_t) * 9 * (size_t)rows);
+    *h_nrows = rows;
+    return QH_OK;
 }
