@@ -23,8 +23,11 @@ constexpr int kDefBlockF64 = 256;
 constexpr int kDefItems = 4;
 constexpr int kMaxTile = 4096;           // points per assign tile (block x items), upper bound
 constexpr int kMinTile = 256;            // lower bound (sizes the tile maps)
-constexpr int kVCap = 32;                // visible facets a candidate may list
-constexpr int kNCap = 64;                // horizon neighbours a candidate may list (>= kVCap + 2)
+#ifndef QH3D_VCAP
+#define QH3D_VCAP 32
+#endif
+constexpr int kVCap = QH3D_VCAP;         // visible facets a candidate may list
+constexpr int kNCap = 2 * kVCap;         // horizon neighbours a candidate may list (>= kVCap + 2)
 constexpr int kMaxGrid = 4096;
 
 // A facet of the current triangulated hull.
