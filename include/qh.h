@@ -520,6 +520,43 @@ qh_status qh_select(const float *d_v, const int64_t *d_seg_off, int32_t nseg, in
  * Diagnostics only. */
 qh_status qh_debug_phases_3d(const void *d_ws, int64_t *h_ns, cudaStream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Device-side checks (no counterpart in the paper: a debugging aid).
+ *
+ * A library built with -DQH_DEBUG=1 checks, on the device and before the
+ * access: every bulk copy (16-byte aligned source and destination, a size
+ * that is a positive multiple of 16, QH_DBG_BULK_ALIGN), every mbarrier's
+ * 8-byte alignment (QH_DBG_MBAR_ALIGN), the range of the 2D bulk copies'
+ * sources (QH_DBG_BULK_RANGE), the destination of every 2D and 3D point
+ * scatter (QH_DBG_POINT_DST), the 2D tile map's segment indices
+ * (QH_DBG_SEG_INDEX), the 2D hull slots written by the updates
+ * (QH_DBG_HULL_SLOT) and the alignment of the 2D extrema's vector loads
+ * (QH_DBG_VEC_ALIGN).  A failed check skips the access (the call's result is
+ * then unspecified, and a skipped bulk copy ends in the bounded copy wait's
+ * QH_ERR_TIMEOUT) and is counted; nothing traps.  The default build compiles
+ * the checks out.
+ *
+ * qh_debug_checks() copies the record (failed checks since the last reset,
+ * summed over the library's translation units, and the site and two values
+ * of the first failure found) to *h_out and, when reset != 0, clears it.  It
+ * synchronises the device.  Returns QH_ERR_NOT_SUPPORTED (with
+ * h_out->enabled = 0) in a default build, QH_ERR_INVALID_ARG for a null
+ * h_out, QH_ERR_CUDA if a copy fails. */
+#define QH_DBG_BULK_ALIGN 1
+#define QH_DBG_MBAR_ALIGN 2
+#define QH_DBG_BULK_RANGE 3
+#define QH_DBG_POINT_DST 4
+#define QH_DBG_SEG_INDEX 5
+#define QH_DBG_HULL_SLOT 6
+#define QH_DBG_VEC_ALIGN 7
+typedef struct qh_debug_record {
+    int64_t failures;  /* failed checks since the last reset */
+    int32_t site;      /* QH_DBG_* of the first failure (0: none) */
+    int32_t enabled;   /* 1 in a -DQH_DEBUG=1 build */
+    uint64_t a, b;     /* the first failure's values: address or index, and bound or size */
+} qh_debug_record;
+qh_status qh_debug_checks(qh_debug_record *h_out, int32_t reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -346,6 +346,23 @@ def debug_timeline_4d():
     return rows[: nr.value]
 
 
+DEBUG_SITES = {1: "bulk copy alignment", 2: "mbarrier alignment", 3: "bulk copy source range",
+               4: "point scatter destination", 5: "segment index", 6: "hull slot",
+               7: "vector load alignment"}
+
+
+def debug_checks(reset: bool = False) -> dict:
+    """qh_debug_checks: the device-side check record of a library built with
+    QH_DEBUG_BUILD=1 (failed checks, first site and its values).  Raises
+    QHError(QH_ERR_NOT_SUPPORTED) on the default build."""
+    rec = _native.QhDebugRecord()
+    st = _native.lib().qh_debug_checks(ctypes.byref(rec), 1 if reset else 0)
+    if st != 0:
+        raise QHError(st, "qh_debug_checks")
+    return {"failures": rec.failures, "site": DEBUG_SITES.get(rec.site, rec.site),
+            "a": rec.a, "b": rec.b, "enabled": bool(rec.enabled)}
+
+
 NOALLOC_MAX_POINTS = 131072
 
 

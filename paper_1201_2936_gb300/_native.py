@@ -21,6 +21,11 @@ class QhOpts(ctypes.Structure):
                 ("test_hold", ctypes.c_int32), ("small_cloud", ctypes.c_int32)]
 
 
+class QhDebugRecord(ctypes.Structure):
+    _fields_ = [("failures", ctypes.c_int64), ("site", ctypes.c_int32),
+                ("enabled", ctypes.c_int32), ("a", ctypes.c_uint64), ("b", ctypes.c_uint64)]
+
+
 class QhResult(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int64), ("status", ctypes.c_int32),
                 ("reserved0", ctypes.c_int32), ("iterations", ctypes.c_int64),
@@ -56,6 +61,7 @@ SIGNATURES = [
     ("qh_workspace_bytes_3d", _sz, [_i64, _POpts]),
     ("qh_workspace_bytes_4d", _sz, [_i64, _POpts]),
     ("qh_debug_timeline_4d", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    ("qh_debug_checks", ctypes.c_int, [ctypes.POINTER(QhDebugRecord), ctypes.c_int32]),
     ("qh_hull4d", ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _i64, _vp, ctypes.POINTER(_i64), _vp,
                                  _i64, _vp, _i64, ctypes.POINTER(_i64), _PRes, _vp, _sz, _POpts,
                                  _vp]),

@@ -15,7 +15,10 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-BUILD = os.path.join(HERE, "_build")
+# QH_DEBUG_BUILD=1 selects the checked build (-DQH_DEBUG=1: device-side
+# alignment and bounds checks, read with qh_debug_checks) in its own folder
+DEBUG = os.environ.get("QH_DEBUG_BUILD", "") == "1"
+BUILD = os.path.join(HERE, "_build_debug" if DEBUG else "_build")
 LIB = os.path.join(BUILD, "libqh.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -48,6 +51,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     flags = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
                     "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+    if DEBUG:
+        flags += ["-DQH_DEBUG=1"]
     # tuning knobs (e.g. -DQH2D_SITEMS=4 -DQH2D_MINBLOCKS=3); a change needs force=True
     flags += os.environ.get("QH_NVCC_EXTRA", "").split()
     if verbose:

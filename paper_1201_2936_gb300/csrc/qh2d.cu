@@ -139,6 +139,8 @@ struct Params2 {
     int test_hold;  // CTA 0 skips its first grid-barrier arrival (tests of the bounded wait)
     int cap_seg;
     int first_tma;  // first pass bulk copies: 0 none, 1 separate x, y arrays, 2 interleaved xy
+    int cap_pts;    // entries of each point buffer (bounds of the debug build's checks)
+    int cap_hull;   // hull slots
 };
 
 // ---------------------------------------------------------------- smem
@@ -247,7 +249,9 @@ __device__ Ext2 extrema2d(const Params2 &A, SmemAll &sm)
     const long long nthr = (long long)gridDim.x * blockDim.x;
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     constexpr int U = 4;  // vector loads in flight per array and thread
-    if (A.first_tma == 1) {
+    if (A.first_tma == 1 &&
+        dbg_ok((((uintptr_t)A.x | (uintptr_t)A.y) & 15u) == 0u, kDbgVecAlign,
+               (unsigned long long)(uintptr_t)A.x, (unsigned long long)(uintptr_t)A.y)) {
         // separate 16-byte aligned x and y arrays: four points per load
         const float4 *x4 = reinterpret_cast<const float4 *>(A.x);
         const float4 *y4 = reinterpret_cast<const float4 *>(A.y);
@@ -601,8 +605,10 @@ __device__ __forceinline__ void pass_tile(const Params2 &A, SmemPass &sm, const 
                 if (c == 0) dst = ps + sm.gb0[ls] + (pre0 - sm.sb0[ls]);
                 else dst = ps + ln - 1 - (sm.gb1[ls] + (pre1 - sm.sb1[ls]));
             }
-            oxy[dst] = pxy[k];
-            oi[dst] = pidx[k];
+            if (dbg_ok(dst >= 0 && dst < A.cap_pts, kDbgPointDst, dst, A.cap_pts)) {
+                oxy[dst] = pxy[k];
+                oi[dst] = pidx[k];
+            }
         }
     }
 }
@@ -755,6 +761,7 @@ constexpr int kPhFull = 0, kPhBases = 4, kPhCounted = 8, kPhEmpty = 12;
 
 __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
 {
+    if (!mbar_aligned(bar)) return;
     asm volatile("mbarrier.arrive.shared.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async_global()
@@ -787,7 +794,7 @@ template <class P>
 __device__ __forceinline__ void multi_tile(SmemStream &sm, const Seg2 *seg, Acc2 *acc, int sf,
                                            int m, int v0, int v1, int p, const float2 *ixy,
                                            const int *ii, float2 *oxy, int *oi,
-                                           unsigned &fallbacks, const int *tvs)
+                                           unsigned &fallbacks, const int *tvs, int cap_pts)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
@@ -867,8 +874,10 @@ __device__ __forceinline__ void multi_tile(SmemStream &sm, const Seg2 *seg, Acc2
                 const Seg2 &G = seg[sf + (pk[k] >> 2)];
                 const int rank = base + __popc(grp & lt);
                 const int dst = c == 0 ? G.pstart + rank : G.pstart + G.len - 1 - rank;
-                oxy[dst] = pxy[k];
-                oi[dst] = pidx[k];
+                if (dbg_ok(dst >= 0 && dst < cap_pts, kDbgPointDst, dst, cap_pts)) {
+                    oxy[dst] = pxy[k];
+                    oi[dst] = pidx[k];
+                }
             }
         }
     }
@@ -956,6 +965,10 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
         const int v = (t_begin + j) * kSTile, vl = min(v + kSTile, L) - 1;
         sf = seg_of(v, staged);
         m = seg_of(vl, staged) - sf + 1;
+        if (!dbg_ok(sf >= 0 && m >= 1 && sf + m <= S, kDbgSegIndex, sf + m, S)) {
+            sf = 0;
+            m = 1;
+        }
     };
     if (WEIGHTED && !FIRST && ntiles > 0) {
         if (vs_smem)
@@ -1075,6 +1088,10 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                     mbar_arrive(&bars.full[s]);
                     return;
                 }
+                if (!dbg_ok(v0 >= 0 && v0 + c <= A.n, kDbgBulkRange, v0 + c, A.n)) {
+                    mbar_arrive(&bars.full[s]);
+                    return;
+                }
                 fence_proxy_async();
                 mbar_expect_tx(&bars.full[s], (unsigned)c * 8u);
                 if (A.first_tma == 1) {
@@ -1106,6 +1123,12 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
             const int pos0 = ps + (v0 - vs);
             const int a0 = pos0 & ~3, a1 = (pos0 + cnt + 3) & ~3, nel = a1 - a0;
             sm.shift[s] = pos0 - a0;
+            // inside the buffers and their 64-byte slack; a valid segment
+            if (!dbg_ok(a0 >= 0 && a1 <= A.cap_pts + 8, kDbgBulkRange, a1, A.cap_pts) ||
+                !dbg_ok(sf >= 0 && sf < A.cap_seg, kDbgSegIndex, sf, A.cap_seg)) {
+                mbar_arrive(&bars.full[s]);
+                return;
+            }
             fence_proxy_async();
             mbar_expect_tx(&bars.full[s], (unsigned)nel * 12u + (unsigned)sizeof(Seg2));
             bulk_g2s(sm.sxy[s], ixy + a0, (unsigned)nel * 8u, &bars.full[s]);
@@ -1294,7 +1317,7 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                     off1 = __shfl_sync(0xffffffffu, off1, 0);
                 } else if (!dead) {
                     multi_tile<P>(sm, seg, acc, sf, m, v0, v1, p, ixy, ii, oxy, oi, fallbacks,
-                                  sm.sidx[s]);
+                                  sm.sidx[s], A.cap_pts);
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bars.counted[p]);
@@ -1341,7 +1364,8 @@ __device__ void pass2d_stream(const Params2 &A, int par, SmemStream &sm, PipeBar
                     }
 #pragma unroll
                     for (int k = 0; k < kSItems; k++) {
-                        if (dst[k] >= 0) {
+                        if (dst[k] >= 0 &&
+                            dbg_ok(dst[k] < A.cap_pts, kDbgPointDst, dst[k], A.cap_pts)) {
                             oxy[dst[k]] = spt[k];
                             oi[dst[k]] = sidx[k];
                         }
@@ -1465,11 +1489,14 @@ __device__ void update2d(const Params2 &A, int par, bool first, SmemU &sm,
                 int u = atomicAdd(&H->n_uncert, 1);
                 A.uncert[u] = k;
             }
-            A.hull_idx[slot] = qi;
-            A.hull_x[slot] = g.qx;
-            A.hull_y[slot] = g.qy;
-            A.next[g.e0_slot] = slot;
-            A.next[slot] = g.e1_slot;
+            if (dbg_ok(slot < A.cap_hull && g.e0_slot >= 0 && g.e0_slot < A.cap_hull,
+                       kDbgHullSlot, slot, A.cap_hull)) {
+                A.hull_idx[slot] = qi;
+                A.hull_x[slot] = g.qx;
+                A.hull_y[slot] = g.qy;
+                A.next[g.e0_slot] = slot;
+                A.next[slot] = g.e1_slot;
+            }
             Acc2 z = {};
             an[2 * k] = z;
             an[2 * k + 1] = z;
@@ -1738,6 +1765,7 @@ __device__ __forceinline__ Params2 cloud_params(const Params2M &M, int c)
     a.acc[0] = M.A.acc[0] + 2 * c;
     a.bxy[0] = M.A.bxy[0] + C.off;
     a.bi[0] = M.A.bi[0] + C.off;
+    a.cap_pts = M.A.cap_pts - C.off;
     return a;
 }
 
@@ -1853,12 +1881,15 @@ __device__ void update2d_m(const Params2M &M, int par, bool first, SmemU &sm, in
                 const int u = atomicAdd(&H->n_uncert, 1);
                 A.uncert[u] = k;
             }
-            A.hull_idx[slot] = qi;
-            A.hull_x[slot] = g.qx;
-            A.hull_y[slot] = g.qy;
-            M.hull_cloud[slot] = cl;
-            A.next[g.e0_slot] = slot;
-            A.next[slot] = g.e1_slot;
+            if (dbg_ok(slot < A.cap_hull && g.e0_slot >= 0 && g.e0_slot < A.cap_hull,
+                       kDbgHullSlot, slot, A.cap_hull)) {
+                A.hull_idx[slot] = qi;
+                A.hull_x[slot] = g.qx;
+                A.hull_y[slot] = g.qy;
+                M.hull_cloud[slot] = cl;
+                A.next[g.e0_slot] = slot;
+                A.next[slot] = g.e1_slot;
+            }
             const Acc2 z = {};
             an[2 * k] = z;
             an[2 * k + 1] = z;
@@ -2088,13 +2119,17 @@ __device__ void pass2d_warpseg(const Params2 &A, int par, int bid, int nb)
             const unsigned b1 = __ballot_sync(0xffffffffu, c == 1);
             if (c == 0) {
                 const int dst = ps + n0 + __popc(b0 & lt);
-                oxy[dst] = cp;
-                oi[dst] = ci;
+                if (dbg_ok(dst >= 0 && dst < A.cap_pts, kDbgPointDst, dst, A.cap_pts)) {
+                    oxy[dst] = cp;
+                    oi[dst] = ci;
+                }
                 far2_add(fa, ord_f32(d), ci, __float_as_uint(e));
             } else if (c == 1) {
                 const int dst = ps + len - 1 - (n1 + __popc(b1 & lt));
-                oxy[dst] = cp;
-                oi[dst] = ci;
+                if (dbg_ok(dst >= 0 && dst < A.cap_pts, kDbgPointDst, dst, A.cap_pts)) {
+                    oxy[dst] = cp;
+                    oi[dst] = ci;
+                }
                 far2_add(fb, ord_f32(d), ci, __float_as_uint(e));
             }
             n0 += __popc(b0);
@@ -2478,6 +2513,7 @@ struct Layout2 {
     size_t hdr, bxy[2], bi[2], seg[2], acc[2], tile_seg, tile_m, uncert, hull_idx, hull_x, hull_y,
         next, res, total;
     int cap_seg;
+    int64_t np;  // entries of each point buffer
 };
 
 static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -2492,6 +2528,7 @@ static Layout2 layout2d(int64_t n)
         return r;
     };
     size_t np = (size_t)(n > 0 ? n : 1);
+    L.np = (int64_t)np;
     // live segments never exceed 2(n-2)/3: a new segment needs a live point,
     // live points and earlier apexes are disjoint, and each old segment has at
     // most two children (S_new <= min(n - 2 - A, 2A) for A earlier apexes)
@@ -2544,6 +2581,8 @@ static Params2 make_params(const float *x, const float *y, int64_t n, int64_t st
     A.next = (int *)(ws + L.next);
     A.max_iters = o.max_iters > 0 ? o.max_iters : n + 8;
     A.cap_seg = L.cap_seg;
+    A.cap_pts = (int)L.np;
+    A.cap_hull = (int)L.np + 2;
     // the first pass may bulk-copy the caller's points when they are 16-byte
     // aligned separate arrays or one interleaved xy array
     if (stride == 1 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)y & 15) == 0) A.first_tma = 1;

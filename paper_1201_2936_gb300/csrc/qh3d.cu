@@ -1720,7 +1720,7 @@ __device__ void scatter3d(const Params3 &A, int par, SmemAll3 &sm, const SmemSlo
                     if (dst[k] >= 0) p[k] = load_input(A, vb + k * blockDim.x);
 #pragma unroll
                 for (int k = 0; k < kSc; k++)
-                    if (dst[k] >= 0) Q[dst[k]] = p[k];
+                    if (dst[k] >= 0 && dbg_ok(dst[k] < A.n, kDbgPointDst, dst[k], A.n)) Q[dst[k]] = p[k];
             }
         }
     } else {
@@ -1765,7 +1765,7 @@ __device__ void scatter3d(const Params3 &A, int par, SmemAll3 &sm, const SmemSlo
                 }
 #pragma unroll
                 for (int k = 0; k < kSc; k++)
-                    if (dst[k] >= 0) Q[dst[k]] = p[k];
+                    if (dst[k] >= 0 && dbg_ok(dst[k] < A.n, kDbgPointDst, dst[k], A.n)) Q[dst[k]] = p[k];
             }
         }
     }

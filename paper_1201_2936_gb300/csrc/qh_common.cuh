@@ -16,6 +16,74 @@ constexpr int kStCapacity = QH_ERR_CAPACITY;
 constexpr int kStTimeout = QH_ERR_TIMEOUT;
 constexpr int kStNoConv = QH_ERR_NO_CONVERGENCE;
 
+// ---------------------------------------------------------------- checks
+// Device-side checks of the debug build (-DQH_DEBUG=1): alignment of every
+// bulk copy and mbarrier, bounds of scatter destinations, segment indices and
+// hull slots.  A failed check skips the access and is recorded (count, first
+// site, its two values) in a per-translation-unit record that
+// qh_debug_checks() reads; nothing traps.  In the default build the checks
+// compile to nothing.
+#ifndef QH_DEBUG
+#define QH_DEBUG 0
+#endif
+
+struct DbgDev {
+    unsigned long long n;
+    int site, pad;
+    unsigned long long a, b;
+};
+// host side: each translation unit registers a reader of its record
+typedef int (*DbgReader)(DbgDev *out, int reset);
+void dbg_register(DbgReader r);
+
+#if QH_DEBUG
+static __device__ DbgDev g_qh_dbg;
+static __device__ __noinline__ void dbg_fail(int site, unsigned long long a, unsigned long long b)
+{
+    if (atomicAdd(&g_qh_dbg.n, 1ull) == 0ull) {
+        g_qh_dbg.site = site;
+        g_qh_dbg.a = a;
+        g_qh_dbg.b = b;
+    }
+}
+namespace {
+int dbg_read_tu(DbgDev *out, int reset)
+{
+    if (cudaMemcpyFromSymbol(out, g_qh_dbg, sizeof(DbgDev)) != cudaSuccess) return 1;
+    if (reset) {
+        DbgDev z = {};
+        if (cudaMemcpyToSymbol(g_qh_dbg, &z, sizeof(DbgDev)) != cudaSuccess) return 1;
+    }
+    return 0;
+}
+struct DbgRegistrar {
+    DbgRegistrar() { dbg_register(&dbg_read_tu); }
+};
+DbgRegistrar g_dbg_registrar;
+}  // namespace
+#endif
+
+// true when the condition holds; in the debug build a failure is recorded
+__device__ __forceinline__ bool dbg_ok(bool c, int site, unsigned long long a,
+                                       unsigned long long b)
+{
+#if QH_DEBUG
+    if (!c) dbg_fail(site, a, b);
+    return c;
+#else
+    (void)site; (void)a; (void)b;
+    (void)c;
+    return true;
+#endif
+}
+constexpr int kDbgBulkAlign = QH_DBG_BULK_ALIGN;
+constexpr int kDbgMbarAlign = QH_DBG_MBAR_ALIGN;
+constexpr int kDbgBulkRange = QH_DBG_BULK_RANGE;
+constexpr int kDbgPointDst = QH_DBG_POINT_DST;
+constexpr int kDbgSegIndex = QH_DBG_SEG_INDEX;
+constexpr int kDbgHullSlot = QH_DBG_HULL_SLOT;
+constexpr int kDbgVecAlign = QH_DBG_VEC_ALIGN;
+
 // Total order on float bits that matches the numeric order (-0 < +0 apart).
 __device__ __forceinline__ uint32_t ord_f32(float f)
 {
@@ -122,8 +190,13 @@ __device__ __forceinline__ unsigned smem_u32(const void *p)
 // Bulk copy engine (TMA, non-tensor form): `bytes` (a multiple of 16) from a
 // 16-byte aligned global address to a 16-byte aligned shared address,
 // completion counted on an mbarrier.
+__device__ __forceinline__ bool mbar_aligned(const unsigned long long *bar)
+{
+    return dbg_ok((smem_u32(bar) & 7u) == 0u, kDbgMbarAlign, smem_u32(bar), 8);
+}
 __device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
 {
+    if (!mbar_aligned(bar)) return;
     asm volatile("mbarrier.init.shared.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 __device__ __forceinline__ void fence_mbar_init()
@@ -136,6 +209,7 @@ __device__ __forceinline__ void fence_proxy_async()
 }
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
 {
+    if (!mbar_aligned(bar)) return;
     asm volatile("mbarrier.arrive.expect_tx.shared.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                  "r"(bytes)
                  : "memory");
@@ -143,6 +217,14 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
                                          unsigned long long *bar)
 {
+    // 16-byte aligned source and destination, a size that is a positive
+    // multiple of 16 (a skipped copy leaves its barrier short: the bounded
+    // wait gives up)
+    if (!dbg_ok(((smem_u32(dst) | (unsigned)(uintptr_t)src | bytes) & 15u) == 0u && bytes > 0u,
+                kDbgBulkAlign, (unsigned long long)(uintptr_t)src,
+                ((unsigned long long)smem_u32(dst) << 32) | bytes) ||
+        !mbar_aligned(bar))
+        return;
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
             "r"(smem_u32(dst)),
@@ -154,6 +236,7 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity,
                                           long long max_ns)
 {
+    if (!mbar_aligned(bar)) return false;
     const unsigned a = smem_u32(bar);
     unsigned done = 0;
     unsigned long long t0 = 0;

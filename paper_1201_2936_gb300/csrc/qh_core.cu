@@ -4,9 +4,29 @@
 #include <map>
 #include <tuple>
 
+#include <vector>
+
+#include "qh_common.cuh"
 #include "qh_internal.h"
 
 namespace qh {
+
+// readers of the translation units' device-check records (debug build)
+static std::mutex &dbg_mu()
+{
+    static std::mutex mu;
+    return mu;
+}
+static std::vector<DbgReader> &dbg_readers()
+{
+    static std::vector<DbgReader> v;
+    return v;
+}
+void dbg_register(DbgReader r)
+{
+    std::lock_guard<std::mutex> g(dbg_mu());
+    dbg_readers().push_back(r);
+}
 
 int persistent_grid(const void *func, int block, int blocks_per_sm)
 {
@@ -79,6 +99,27 @@ extern "C" const char *qh_status_str(qh_status s)
     case QH_ERR_NOT_SUPPORTED: return "QH_ERR_NOT_SUPPORTED: option combination not available";
     }
     return "unknown qh_status";
+}
+
+extern "C" qh_status qh_debug_checks(qh_debug_record *h_out, int32_t reset)
+{
+    if (!h_out) return QH_ERR_INVALID_ARG;
+    std::memset(h_out, 0, sizeof(*h_out));
+    if (!QH_DEBUG) return QH_ERR_NOT_SUPPORTED;
+    h_out->enabled = 1;
+    if (cudaDeviceSynchronize() != cudaSuccess) return QH_ERR_CUDA;
+    std::lock_guard<std::mutex> g(qh::dbg_mu());
+    for (qh::DbgReader r : qh::dbg_readers()) {
+        qh::DbgDev d = {};
+        if (r(&d, reset) != 0) return QH_ERR_CUDA;
+        if (d.n > 0 && h_out->failures == 0) {
+            h_out->site = d.site;
+            h_out->a = d.a;
+            h_out->b = d.b;
+        }
+        h_out->failures += (int64_t)d.n;
+    }
+    return QH_OK;
 }
 
 extern "C" const char *qh_version(void) { return "qh 0.1 sm_103a"; }
