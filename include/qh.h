@@ -501,6 +501,16 @@ qh_status qh_debug_timeline_4d(int64_t *h_rows, int32_t max_rows, int32_t *h_nro
  *   (0 <= k < length).  d_out_idx[c] = index of the element of rank d_k[c]
  *   in the order (value, index), values ordered by their bit patterns like
  *   numbers (-0 before +0; NaNs at the ends).  *h_iters = rounds used.
+ *   One persistent cooperative launch runs every round: segments longer
+ *   than 4096 elements go through grid-wide rounds (counts around each
+ *   segment's middle pivot, decisions, ordered scatter of the kept parts,
+ *   separated by bounded grid barriers); a segment of at most 4096 elements
+ *   is finished by one CTA in shared memory with the same rounds.  Nothing is
+ *   read back between rounds.  QH_ERR_TIMEOUT if a grid barrier wait gives
+ *   up, QH_ERR_NO_CONVERGENCE past 4n + 16 global rounds.
+ * qh_select_host_loop: the same selection with one host iteration per round
+ *   (the primitives' kernels, then the kept count read back), the
+ *   round-by-round form; same arguments, results and round counts.
  */
 size_t qh_segmented_workspace_bytes(int64_t n, int32_t nseg);
 qh_status qh_flag_permute(const int32_t *d_f, const int32_t *d_s, int64_t n, int32_t k,
@@ -512,6 +522,10 @@ qh_status qh_compact(const int32_t *d_b, const int32_t *d_s, int64_t n, int32_t 
 qh_status qh_select(const float *d_v, const int64_t *d_seg_off, int32_t nseg, int64_t n,
                     const int64_t *d_k, int32_t *d_out_idx, int64_t *h_iters, void *d_ws,
                     size_t ws_bytes, cudaStream_t stream);
+qh_status qh_select_host_loop(const float *d_v, const int64_t *d_seg_off, int32_t nseg,
+                              int64_t n, const int64_t *d_k, int32_t *d_out_idx,
+                              int64_t *h_iters, void *d_ws, size_t ws_bytes,
+                              cudaStream_t stream);
 
 /* Device time of the last 3D call made on d_ws (qh_hull3d or
  * qh_hull3d_batched): h_ns[0..3] = initial simplex, first assignment, its

@@ -798,9 +798,14 @@ def compact(b: torch.Tensor, s: torch.Tensor):
     return p[:n], s_new[: nn.value], nn.value
 
 
-def select(v: torch.Tensor, seg_off: torch.Tensor, k: torch.Tensor, return_iters: bool = False):
+def select(v: torch.Tensor, seg_off: torch.Tensor, k: torch.Tensor, return_iters: bool = False,
+           loop: str = "device"):
     """Index of the element of rank k[c] in every segment c of v (qh_select):
-    v float32 CUDA [n], seg_off int64 CUDA [nseg + 1], k int64 CUDA [nseg]."""
+    v float32 CUDA [n], seg_off int64 CUDA [nseg + 1], k int64 CUDA [nseg].
+    loop="device": one persistent launch for all rounds; "host": one host
+    iteration per round (qh_select_host_loop)."""
+    if loop not in ("device", "host"):
+        raise ValueError("loop must be 'device' or 'host'")
     if v.dtype != torch.float32 or not v.is_cuda or v.dim() != 1 or \
             (v.numel() > 1 and v.stride(0) != 1):
         raise ValueError("v must be a contiguous 1-D CUDA float32 tensor")
@@ -812,9 +817,9 @@ def select(v: torch.Tensor, seg_off: torch.Tensor, k: torch.Tensor, return_iters
     out = torch.empty(nseg, dtype=torch.int32, device=v.device)
     it = ctypes.c_int64(0)
     ws = _seg_ws(v.numel(), nseg, v.device)
-    st = _native.lib().qh_select(v.data_ptr(), seg_off.data_ptr(), nseg, v.numel(), k.data_ptr(),
-                                 out.data_ptr(), ctypes.byref(it), ws.data_ptr(), ws.numel(),
-                                 _stream_handle(None))
+    fn = _native.lib().qh_select if loop == "device" else _native.lib().qh_select_host_loop
+    st = fn(v.data_ptr(), seg_off.data_ptr(), nseg, v.numel(), k.data_ptr(), out.data_ptr(),
+            ctypes.byref(it), ws.data_ptr(), ws.numel(), _stream_handle(None))
     if st != 0:
         raise QHError(st, "qh_select")
     return (out, it.value) if return_iters else out

@@ -81,6 +81,8 @@ SIGNATURES = [
     ("qh_compact", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, ctypes.POINTER(_i64), _vp, _sz, _vp]),
     ("qh_select", ctypes.c_int, [_vp, _vp, ctypes.c_int32, _i64, _vp, _vp, ctypes.POINTER(_i64),
                                  _vp, _sz, _vp]),
+    ("qh_select_host_loop", ctypes.c_int, [_vp, _vp, ctypes.c_int32, _i64, _vp, _vp,
+                                           ctypes.POINTER(_i64), _vp, _sz, _vp]),
     ("qh_workspace_bytes_2d_batched", _sz, [_i64, ctypes.c_int32, _POpts]),
     ("qh_hull2d_batched", ctypes.c_int, [_vp, _vp, _i64, _vp, ctypes.c_int32, _i64, _vp, _vp, _vp,
                                          _vp, _vp, _sz, _POpts, _vp]),

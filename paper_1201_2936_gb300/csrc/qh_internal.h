@@ -16,5 +16,7 @@ int persistent_grid_smem(const void *func, int block, int blocks_per_sm, size_t 
 // Streaming multiprocessors of the current device (cached per device; 1 on
 // a CUDA error, so that grid sizes stay valid).
 int sm_count();
+// Workspace of the persistent k-th element selection (qh_select).
+size_t select_workspace_bytes(long long n, int nseg);
 
 }  // namespace qh

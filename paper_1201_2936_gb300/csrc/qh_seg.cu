@@ -484,7 +484,7 @@ using namespace qh::seg;
 extern "C" size_t qh_segmented_workspace_bytes(int64_t n, int32_t nseg)
 {
     if (n < 0 || n > QH_MAX_POINTS / 2 || nseg < 0) return 0;
-    return layout_sel(n, nseg).total;
+    return std::max(layout_sel(n, nseg).total, qh::select_workspace_bytes(n, nseg));
 }
 
 extern "C" qh_status qh_flag_permute(const int32_t *d_f, const int32_t *d_s, int64_t n, int32_t k,
@@ -546,7 +546,9 @@ extern "C" qh_status qh_compact(const int32_t *d_b, const int32_t *d_s, int64_t 
     return QH_OK;
 }
 
-extern "C" qh_status qh_select(const float *d_v, const int64_t *d_seg_off, int32_t nseg, int64_t n,
+// The round-by-round form: one host iteration per round, the kept count and
+// segment count read back after each (Section 5's host-driven loop).
+extern "C" qh_status qh_select_host_loop(const float *d_v, const int64_t *d_seg_off, int32_t nseg, int64_t n,
                                const int64_t *d_k, int32_t *d_out_idx, int64_t *h_iters,
                                void *d_ws, size_t ws_bytes, cudaStream_t st)
 {

@@ -130,3 +130,37 @@ def test_select_rejects_bad_ranks(qh):
     off = torch.tensor([0, 4, 10], dtype=torch.int64, device="cuda")
     with pytest.raises(qh.QHError):
         qh.select(v, off, torch.tensor([4, 0], dtype=torch.int64, device="cuda"))
+
+
+@pytest.mark.parametrize("sizes", [[300_000, 9000, 4097, 1, 4096, 250_001],
+                                   [1_000_000], [5000] * 40 + [3] * 17])
+def test_select_long_segments_device_rounds(qh, sizes):
+    # segments above 4096 elements go through the grid-wide rounds (the kept
+    # parts move to shared-memory tasks once they are short): equal to the
+    # definition, and to the host loop result for result and round for round
+    rng = np.random.default_rng(sum(sizes) % 1000)
+    n = sum(sizes)
+    v = rng.standard_normal(n).astype(np.float32)
+    v[rng.integers(0, n, n // 10)] = np.float32(0.5)  # ties, ordered by index
+    off = np.zeros(len(sizes) + 1, np.int64)
+    off[1:] = np.cumsum(sizes)
+    k = np.array([rng.integers(0, s) for s in sizes], np.int64)
+    want = oracle.select(v, off, k)
+    V, O, K = (torch.from_numpy(a).cuda() for a in (v, off, k))
+    got, it_d = qh.select(V, O, K, return_iters=True)
+    host, it_h = qh.select(V, O, K, return_iters=True, loop="host")
+    assert got.cpu().numpy().tolist() == want.tolist()
+    assert host.cpu().numpy().tolist() == want.tolist()
+    assert it_d == it_h
+
+
+def test_select_device_and_host_rounds_agree_on_medians(qh):
+    rng = np.random.default_rng(19)
+    v = rng.standard_normal(512 * 4096).astype(np.float32)
+    off = np.arange(513, dtype=np.int64) * 4096
+    k = np.full(512, 2047, np.int64)
+    V, O, K = (torch.from_numpy(a).cuda() for a in (v, off, k))
+    got, it_d = qh.select(V, O, K, return_iters=True)
+    host, it_h = qh.select(V, O, K, return_iters=True, loop="host")
+    assert got.cpu().tolist() == host.cpu().tolist() == oracle.select(v, off, k).tolist()
+    assert it_d == it_h
