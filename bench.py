@@ -580,6 +580,11 @@ def main():
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-4d", action="store_true")
+    ap.add_argument("--independent", action="store_true",
+                    help="N > 1: every rank hulls its own 3 x 16M set (weak scaling) instead of "
+                         "one set sharded over the ranks")
+    ap.add_argument("--sharded", action="store_true",
+                    help="the sharded path also at N = 1 (one rank; the exchange is a copy)")
     ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--no-select", action="store_true")
     ap.add_argument("--no-switchover", action="store_true")
@@ -616,12 +621,18 @@ def main():
     import paper_1201_2936_gb300 as qh
     from paper_1201_2936_gb300 import build as qbuild
 
+    if (ws > 1 and not args.independent) or args.sharded:
+        return run_sharded(args, ws, rank)
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if ws > 1:
         dist.init_process_group("nccl")
-    qbuild.build()
+        if local == 0:
+            qbuild.build()
+        dist.barrier()
+    else:
+        qbuild.build()
 
     ncl = args.n
     data = clouds(rank, ncl)
@@ -890,6 +901,133 @@ def main():
                                 "sample": f"first {sample} points of each of the 3 clouds"}
     if ws > 1:
         dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_sharded(args, ws, rank):
+    """N > 1: one hull per cloud of the 3 x 16M set, each cloud split into
+    contiguous shards over the ranks (shard.ShardedHull2D: shard hulls in one
+    launch, one NCCL all-gather of fixed-size rank blocks, the candidates'
+    hulls in one launch).  A rank holds only its shards; the same seeded
+    clouds on every rank.  value = all points of the set / max over ranks."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1201_2936_gb300 as qh
+    from paper_1201_2936_gb300 import build as qbuild
+    from paper_1201_2936_gb300 import shard
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    multi = ws > 1
+
+    def barrier():
+        if multi:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        t = torch.tensor([v], device=dev)
+        if multi:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    if multi:
+        dist.init_process_group("nccl")
+    if local == 0:
+        qbuild.build()
+    barrier()
+    ncl = args.n
+    data = clouds(0, ncl)
+    lo, hi = shard.shard_range(ncl, rank, ws)
+    host = [torch.from_numpy(np.stack([x[lo:hi], y[lo:hi]])).pin_memory() for _, (x, y) in data]
+    dev_sh = [h.to(dev) for h in host]
+    # candidate slots per rank and cloud: above these clouds' shard hulls
+    # (at most ~900 vertices); a larger shard hull fails with QH_ERR_CAPACITY
+    sh = shard.ShardedHull2D([(t[0], t[1]) for t in dev_sh], [lo] * len(dev_sh), ws, rank,
+                             cap=4096)
+    for _ in range(args.warmup):
+        sh.step()
+    hulls, st = sh.results()
+    if any(st):
+        raise SystemExit(f"sharded hull failed: {st}")
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sh.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    total_ms = max_over_ranks(e0.elapsed_time(e1))
+    pts = len(data) * ncl
+    value = pts * args.steps / (total_ms / 1e3) / 1e6
+    # roofline of this rank's shard launch (the dominant kernel), timed alone
+    lres = [qh.result_from_tensor(sh.local_res[c * qh.RESULT_BYTES:(c + 1) * qh.RESULT_BYTES])
+            for c in range(len(dev_sh))]
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        sh.local_block()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    lms = e0.elapsed_time(e1) / args.steps
+    algo = 16 * (hi - lo) * len(dev_sh) + 24 * lres[0].survivor_total
+    peak, peak_kind = measured_peak()
+    # end to end: each step copies this rank's shards from pinned host memory
+    # and reads the hull records and indices back
+    host_res = torch.empty(len(dev_sh) * qh.RESULT_BYTES, dtype=torch.uint8).pin_memory()
+    esteps = max(5, args.steps // 5)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(esteps):
+        for h, d in zip(host, dev_sh):
+            d.copy_(h, non_blocking=True)
+        sh.step()
+        host_res.copy_(sh.final_res, non_blocking=True)
+        torch.cuda.synchronize()
+        cnts = [qh.QhResult.from_buffer_copy(bytes(
+            host_res[c * qh.RESULT_BYTES:(c + 1) * qh.RESULT_BYTES].numpy())).count
+            for c in range(len(dev_sh))]
+        idx = [sh.final_out[c][: cnts[c]].cpu() for c in range(len(dev_sh))]
+        d2h = host_res.numel() + 4 * sum(cnts)
+    torch.cuda.synchronize()
+    et = max_over_ranks(time.perf_counter() - t0) / esteps
+    line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD + f", each cloud sharded over {ws} ranks",
+                       "points_per_step_total": pts, "points_per_step_per_gpu": (hi - lo) * 3,
+                       "l2": "inputs larger than L2",
+                       "exchange": "one NCCL all-gather of fixed-size rank blocks per step",
+                       "pred": "f32-filter+exact", "loop": "persistent"},
+            "per_cloud": [{"cloud": name, "hull": int(h.numel()), "status": s}
+                          for (name, _), h, s in zip(data, hulls, st)],
+            "roofline": {"bound": "hbm", "kernel": "qh2d_multi<PredF32> (this rank's shards)",
+                         "achieved": round(algo / (lms / 1e3) / 1e9, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(algo / (lms / 1e3) / 1e9 / peak, 4),
+                         "peak_kind": peak_kind, "traffic": None,
+                         "algo_bytes_per_launch": algo, "ms": round(lms, 4)},
+            "clocks": clocks, "gpu_launches": 5 * args.steps,
+            "e2e": {"value": round(pts / et / 1e6, 2), "unit": UNIT,
+                    "h2d_bytes_per_step": sum(h.numel() * 4 for h in host),
+                    "d2h_bytes_per_step": d2h,
+                    "how": "each rank: pinned host -> device copy of its shards, the sharded "
+                           "step, result records and hull indices read back"}}
+    barrier()
+    if multi:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -535,6 +535,53 @@ qh_status qh_select_host_loop(const float *d_v, const int64_t *d_seg_off, int32_
 qh_status qh_debug_phases_3d(const void *d_ws, int64_t *h_ns, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
+ * One hull over several ranks (no counterpart in the paper, which runs one
+ * GPU): the hull of a union is the hull of the union of the parts' hulls, so
+ * every rank hulls a contiguous shard of each cloud, the shard hulls are
+ * all-gathered (by the caller, e.g. NCCL), and one final hull of the
+ * gathered candidates gives the answer.  These three calls are the device
+ * steps around the exchange; none synchronises.
+ *
+ * qh_shard_block_words(dim, cap): int32 words of one cloud's rank block:
+ *   1 + (1 + dim) * cap (0 for bad arguments).
+ * qh_shard_local: the rank block for the all-gather.  h_dout[c] (device
+ *   int32) holds the shard hull of cloud c with shard-local indices, its
+ *   count and status in d_results[c] (device qh_result[k], as
+ *   qh_hull2d_multi_async writes them); h_lo[c] is the shard's first global
+ *   index; h_dcoord[c * dim + d] (device) the shard's coordinate d, point i
+ *   at [i * stride].  Cloud c's block at d_block + c * words: word 0 =
+ *   count, words 1 + j = h_lo[c] + local index j, words 1 + (1 + d) * cap + j
+ *   = coordinate d of that point (float bits), for j < min(count, cap); a
+ *   failed shard's count word is minus its status.
+ * qh_shard_pack: d_gathered = the world rank blocks in rank order
+ *   ([world][k][words]).  For every cloud c, the candidate cloud of
+ *   m = world * cap slots: slot r * cap + j = rank r's j-th candidate, or the
+ *   cloud's first candidate where rank r has fewer (a repeated point).
+ *   d_cidx[c * m + s] = global index of slot s (-1 if no rank has any),
+ *   d_ccoord[(d * k + c) * m + s] = its coordinate d.  dim 2 or 3.
+ *   d_bad[c] (device int32[k], cleared by the caller) receives the status of
+ *   a rank whose shard of cloud c failed, or QH_ERR_CAPACITY if a rank's
+ *   count exceeds cap.
+ * qh_shard_remap: after the final hull of the candidate clouds, h_dout[c]
+ *   (device int32, its count in d_results[c]) holds candidate-local indices;
+ *   each becomes d_cidx[c * m + local], the global index.
+ * Candidate order makes the result equal the one-rank hull: ranks in rank
+ * order hold increasing global indices, each shard hull already keeps the
+ * lowest index of coincident points, and the final hull keeps the lowest
+ * candidate slot, so coincident points keep their lowest global index.
+ * 1 <= k <= 64; QH_ERR_INVALID_ARG for null pointers or bad sizes. */
+int64_t qh_shard_block_words(int32_t dim, int32_t cap);
+qh_status qh_shard_local(int32_t k, int32_t dim, const int32_t *const *h_dout,
+                         const void *d_results, const int64_t *h_lo,
+                         const float *const *h_dcoord, int64_t stride, int32_t cap,
+                         int32_t *d_block, cudaStream_t stream);
+qh_status qh_shard_pack(int32_t k, int32_t dim, const int32_t *d_gathered, int32_t world,
+                        int32_t cap, float *d_ccoord, int32_t *d_cidx, int32_t *d_bad,
+                        cudaStream_t stream);
+qh_status qh_shard_remap(int32_t k, int32_t *const *h_dout, const void *d_results,
+                         const int32_t *d_cidx, int64_t m, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
  * Device-side checks (no counterpart in the paper: a debugging aid).
  *
  * A library built with -DQH_DEBUG=1 checks, on the device and before the

@@ -62,6 +62,12 @@ SIGNATURES = [
     ("qh_workspace_bytes_4d", _sz, [_i64, _POpts]),
     ("qh_debug_timeline_4d", ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     ("qh_debug_checks", ctypes.c_int, [ctypes.POINTER(QhDebugRecord), ctypes.c_int32]),
+    ("qh_shard_block_words", _i64, [ctypes.c_int32, ctypes.c_int32]),
+    ("qh_shard_local", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, _i64,
+                                      ctypes.c_int32, _vp, _vp]),
+    ("qh_shard_pack", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int32,
+                                     ctypes.c_int32, _vp, _vp, _vp, _vp]),
+    ("qh_shard_remap", ctypes.c_int, [ctypes.c_int32, _vp, _vp, _vp, _i64, _vp]),
     ("qh_hull4d", ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _i64, _vp, ctypes.POINTER(_i64), _vp,
                                  _i64, _vp, _i64, ctypes.POINTER(_i64), _PRes, _vp, _sz, _POpts,
                                  _vp]),

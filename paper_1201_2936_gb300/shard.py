@@ -13,6 +13,7 @@ default it is the library's GPU hull.  The collective is torch.distributed
 """
 from __future__ import annotations
 
+import ctypes
 from typing import Callable, Optional, Sequence, Tuple
 
 import numpy as np
@@ -37,20 +38,15 @@ def _gpu_hull(coords: Sequence[torch.Tensor]):
     return v.long()
 
 
-def sharded_hull(coords: Sequence[torch.Tensor], group=None,
-                 hull_fn: Optional[Callable] = None):
-    """Hull of the whole cloud, whose coordinates every rank holds (1-D
-    tensors of the same length n).  Each rank hulls its shard; returns the
-    global indices of the final hull as hull_fn orders them (2D: CCW from the
-    lexicographic min; 3D: increasing vertex indices) and the gathered
-    candidate indices.  In 3D the faces of the final hull are those of
-    hull_fn on the gathered points, re-indexed by the caller if needed."""
-    hull_fn = hull_fn or _gpu_hull
+def _candidates(coords: Sequence[torch.Tensor], group, local_fn):
+    """This rank's shard hull, all-gathered: the candidates' global indices
+    in increasing order (duplicate locations keep their lowest index, as in
+    the one-rank hull)."""
     world = dist.get_world_size(group) if dist.is_initialized() else 1
     rank = dist.get_rank(group) if dist.is_initialized() else 0
     n = int(coords[0].numel())
     lo, hi = shard_range(n, rank, world)
-    local = hull_fn([c[lo:hi] for c in coords]) if hi > lo else \
+    local = local_fn([c[lo:hi] for c in coords]) if hi > lo else \
         torch.zeros(0, dtype=torch.long, device=coords[0].device)
     gidx = local.to(torch.long) + lo
     # exchange: sizes first, then the padded index lists
@@ -67,11 +63,63 @@ def sharded_hull(coords: Sequence[torch.Tensor], group=None,
         cand = torch.cat([p[: int(s.item())] for p, s in zip(parts, sizes)])
     else:
         cand = gidx
-    # candidates in increasing global index, so that duplicate locations keep
-    # their lowest index as in the one-rank hull
     cand, _ = torch.sort(cand)
+    return cand
+
+
+def sharded_hull(coords: Sequence[torch.Tensor], group=None,
+                 hull_fn: Optional[Callable] = None):
+    """Hull of the whole cloud, whose coordinates every rank holds (1-D
+    tensors of the same length n).  Each rank hulls its shard; returns the
+    global indices of the final hull as hull_fn orders them (2D: CCW from the
+    lexicographic min; 3D: increasing vertex indices) and the gathered
+    candidate indices.  sharded_hull3d also returns the 3D faces."""
+    hull_fn = hull_fn or _gpu_hull
+    cand = _candidates(coords, group, hull_fn)
     sub = hull_fn([c[cand] for c in coords])
     return cand[sub.to(torch.long)], cand
+
+
+def _gpu_hull3d_faces(coords):
+    from . import hull3d
+    v, off, idx = hull3d(coords[0], coords[1], coords[2])
+    return v.long(), off.long(), idx.long()
+
+
+def sharded_hull3d(coords: Sequence[torch.Tensor], group=None,
+                   hull_fn: Optional[Callable] = None):
+    """3D hull of the whole cloud over the ranks, with its faces: returns
+    (vertices, face_offsets, face_indices) in global indices, equal to the
+    one-rank hull's canonical output.  hull_fn(coords) -> (vertices,
+    face_offsets, face_indices) of a cloud (default: the library's GPU hull).
+    The candidates are in increasing global index, so mapping the final
+    hull's candidate-local indices to global ones keeps the canonical order
+    (sorted vertices, faces from their smallest index, faces in
+    lexicographic order)."""
+    hull_fn = hull_fn or _gpu_hull3d_faces
+    cand = _candidates(coords, group, lambda c: hull_fn(c)[0])
+    v, off, idx = hull_fn([c[cand] for c in coords])
+    return cand[v.to(torch.long)], off.to(torch.long), cand[idx.to(torch.long)]
+
+
+def sharded_hull3d_numpy(coords: Sequence[np.ndarray], hull_fn: Callable, group=None):
+    """sharded_hull3d with numpy coordinates; hull_fn(coords) -> (vertices,
+    list of faces) as numpy arrays (tests on CPU ranks).  Returns (vertices,
+    list of faces) in global indices."""
+    tc = [torch.from_numpy(np.ascontiguousarray(c)) for c in coords]
+
+    def fn(parts):
+        v, faces = hull_fn([p.numpy() for p in parts])
+        off = np.zeros(len(faces) + 1, np.int64)
+        off[1:] = np.cumsum([len(f) for f in faces])
+        idx = np.concatenate([np.asarray(f, np.int64) for f in faces]) if faces else \
+            np.zeros(0, np.int64)
+        return (torch.from_numpy(np.asarray(v, np.int64)), torch.from_numpy(off),
+                torch.from_numpy(idx))
+
+    v, off, idx = sharded_hull3d(tc, group=group, hull_fn=fn)
+    v, off, idx = v.numpy(), off.numpy(), idx.numpy()
+    return v, [idx[off[i]:off[i + 1]] for i in range(len(off) - 1)]
 
 
 def sharded_hull_numpy(coords: Sequence[np.ndarray], hull_fn: Callable, group=None):
@@ -84,3 +132,116 @@ def sharded_hull_numpy(coords: Sequence[np.ndarray], hull_fn: Callable, group=No
 
     final, cand = sharded_hull(tc, group=group, hull_fn=fn)
     return final.numpy(), cand.numpy()
+
+
+class ShardedHull2D:
+    """2D hulls of k clouds (k <= 8), each split into contiguous shards over
+    the ranks of `group`, with every device step in the library's kernels:
+
+      1. this rank's shards of all clouds in one persistent launch
+         (qh_hull2d_multi_async);
+      2. its rank block: shard-hull indices made global, with their
+         coordinates (qh_shard_local);
+      3. one all-gather of the fixed-size rank blocks (NCCL between GPUs);
+      4. the candidate clouds, rank blocks in rank order (qh_shard_pack);
+      5. their hulls in one persistent launch, then candidate-local indices
+         mapped to global ones (qh_shard_remap).
+
+    A rank holds only its shards.  No step synchronises with the host; the
+    counts and statuses are read by results().  `shards[c]` is this rank's
+    [2, hi - lo] float32 CUDA tensor (or (x, y) pair) of cloud c and
+    `lo[c]` its first global index.  `cap` bounds a shard hull's size (a
+    larger one is reported by results() as QH_ERR_CAPACITY).  For a
+    one-process run of several ranks' blocks (tests), call local_block() for
+    each and merge() on the stacked blocks."""
+
+    def __init__(self, shards, lo, world: int, rank: int, cap: int = 16384, group=None):
+        from . import Workspace, RESULT_BYTES, make_opts, _native
+        self._n = _native
+        self.k, self.world, self.rank, self.cap, self.group = len(shards), world, rank, cap, group
+        if not 1 <= self.k <= 8:
+            raise ValueError("1..8 clouds")
+        self.shards = [(s[0], s[1]) if isinstance(s, torch.Tensor) else tuple(s) for s in shards]
+        dev = self.shards[0][0].device
+        self.lo = [int(v) for v in lo]
+        self.opts = make_opts("f32", "persistent")
+        self.words = int(_native.lib().qh_shard_block_words(2, cap))
+        self.m = world * cap
+        i32 = torch.int32
+        self.local_out = [torch.empty(max(int(x.numel()), 1), dtype=i32, device=dev)
+                          for x, _ in self.shards]
+        self.local_res = torch.zeros(self.k * RESULT_BYTES, dtype=torch.uint8, device=dev)
+        self.local_ws = Workspace(dev)
+        self.block = torch.zeros(self.k * self.words, dtype=i32, device=dev)
+        self.gathered = torch.zeros(world * self.k * self.words, dtype=i32, device=dev)
+        self.ccoord = torch.zeros(2 * self.k * self.m, dtype=torch.float32, device=dev)
+        self.cidx = torch.zeros(self.k * self.m, dtype=i32, device=dev)
+        self.bad = torch.zeros(self.k, dtype=i32, device=dev)
+        self.final_out = [torch.empty(self.m, dtype=i32, device=dev) for _ in range(self.k)]
+        self.final_res = torch.zeros(self.k * RESULT_BYTES, dtype=torch.uint8, device=dev)
+        self.final_ws = Workspace(dev)
+        cc = self.ccoord.view(2, self.k, self.m)
+        self.cands = [(cc[0, c], cc[1, c]) for c in range(self.k)]
+
+    def _ptrs(self, ts):
+        return (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+    def local_block(self, shards=None, lo=None, block=None, stream=None):
+        """Steps 1-2 for the given shards (default: this rank's) into `block`."""
+        from . import hull2d_multi_async, QHError, _stream_handle
+        shards = self.shards if shards is None else shards
+        lo = self.lo if lo is None else lo
+        block = self.block if block is None else block
+        hull2d_multi_async(list(shards), self.local_out, self.local_res, self.local_ws, self.opts,
+                           stream)
+        coords = []
+        for x, y in shards:
+            coords += [x, y]
+        los = (ctypes.c_int64 * self.k)(*lo)
+        st = self._n.lib().qh_shard_local(self.k, 2, self._ptrs(self.local_out),
+                                          self.local_res.data_ptr(), los, self._ptrs(coords), 1,
+                                          self.cap, block.data_ptr(), _stream_handle(stream))
+        if st != 0:
+            raise QHError(st, "qh_shard_local")
+        return block
+
+    def exchange(self):
+        """Step 3: all-gather of the rank blocks."""
+        if self.world > 1:
+            dist.all_gather_into_tensor(self.gathered, self.block, group=self.group)
+        else:
+            self.gathered.copy_(self.block)
+
+    def merge(self, gathered=None, stream=None):
+        """Steps 4-5 on the gathered blocks ([world][k][words] int32)."""
+        from . import hull2d_multi_async, QHError, _stream_handle
+        g = self.gathered if gathered is None else gathered
+        self.bad.zero_()
+        st = self._n.lib().qh_shard_pack(self.k, 2, g.data_ptr(), self.world, self.cap,
+                                         self.ccoord.data_ptr(), self.cidx.data_ptr(),
+                                         self.bad.data_ptr(), _stream_handle(stream))
+        if st != 0:
+            raise QHError(st, "qh_shard_pack")
+        hull2d_multi_async(self.cands, self.final_out, self.final_res, self.final_ws, self.opts,
+                           stream)
+        st = self._n.lib().qh_shard_remap(self.k, self._ptrs(self.final_out),
+                                          self.final_res.data_ptr(), self.cidx.data_ptr(),
+                                          self.m, _stream_handle(stream))
+        if st != 0:
+            raise QHError(st, "qh_shard_remap")
+
+    def step(self, stream=None):
+        self.local_block(stream=stream)
+        self.exchange()
+        self.merge(stream=stream)
+
+    def results(self):
+        """(global hull indices per cloud, as int32 CUDA tensors; statuses).
+        Synchronises."""
+        from . import result_from_tensor, RESULT_BYTES
+        torch.cuda.synchronize()
+        res = [result_from_tensor(self.final_res[c * RESULT_BYTES:(c + 1) * RESULT_BYTES])
+               for c in range(self.k)]
+        bad = self.bad.cpu().tolist()
+        st = [b or r.status for r, b in zip(res, bad)]
+        return [self.final_out[c][: res[c].count] for c in range(self.k)], st

@@ -1,7 +1,8 @@
 """The multi-rank hull (paper_1201_2936_gb300.shard) on CPU ranks with gloo,
 world sizes 2 and 3: the hull of the gathered shard hulls equals the oracle's
-hull of the whole cloud (2D order and 3D vertex set), including duplicates
-across shards and a shard with no points."""
+hull of the whole cloud (2D: the vertex list in order; 3D: the vertices and
+the canonical face list), including duplicates across shards and a shard
+with no points."""
 import os
 import socket
 
@@ -47,15 +48,24 @@ def _worker(rank, world, port, dim, q):
             want = oracle.hull2d(x, y)
         else:
             x, y, z = w.uniform_ball(6000, 78)
-            final, _ = shard.sharded_hull_numpy([x, y, z],
-                                                lambda c: oracle.hull3d(c[0], c[1], c[2])[0])
-            want = oracle.hull3d(x, y, z)[0]
+            # a duplicated hull vertex in a later shard, and a cube corner set
+            # with coplanar (quadrilateral) faces
+            x = np.concatenate([x, x[:30], np.float32([2, 2, 2, 2])]).astype(np.float32)
+            y = np.concatenate([y, y[:30], np.float32([2, 2, -2, -2])]).astype(np.float32)
+            z = np.concatenate([z, z[:30], np.float32([2, -2, 2, -2])]).astype(np.float32)
+            fv, ff = shard.sharded_hull3d_numpy(
+                [x, y, z], lambda c: oracle.hull3d(c[0], c[1], c[2]))
+            wv, wf = oracle.hull3d(x, y, z)
+            final = (fv.tolist(), [f.tolist() for f in ff])
+            want = (wv.tolist(), [f.tolist() for f in wf])
+            q.put((rank, final, want))
+            return
         q.put((rank, final.tolist(), want.tolist()))
     finally:
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world,dim", [(2, 2), (3, 2), (2, 3)])
+@pytest.mark.parametrize("world,dim", [(2, 2), (3, 2), (2, 3), (3, 3)])
 def test_sharded_hull_equals_whole_hull(world, dim):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
