@@ -412,7 +412,50 @@ def bench_diff(args, qh, dev, rank):
             step()
         torch.cuda.synchronize()
         ag_ms = (time.perf_counter() - t0) / 3 * 1e3
+        # the plain per-cloud path: one FP64-predicate batch of one cloud per
+        # call (hull, measures, backward), synchronised per cloud, on the
+        # first clouds; its gradients against the fast path's
+        npl = min(nc, 256 if dim == 2 else 64)
+        grad_fast = grad.clone()
+        b.enqueue()
+        b.measures(meas)
+        b.backward(gm, grad_fast)
+        one = torch.tensor([0, 0], dtype=torch.int64, device=dev)
+        plain = []
+        for c in range(npl):
+            a, e = int(o[c]), int(o[c + 1])
+            O1 = one.clone()
+            O1[1] = e - a
+            pb = (qh.Hull2DBatch(P[:, a:e], None, O1, pred="f64") if dim == 2 else
+                  qh.Hull3DBatch(P[:, a:e], None, None, O1, pred="f64"))
+            plain.append((pb, torch.empty(1, 2, dtype=torch.float64, device=dev),
+                          torch.empty(dim, e - a, dtype=torch.float32, device=dev), a, e))
+        gm1 = torch.ones(1, 2, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for pb, m1, g1, _, _ in plain:
+            pb.enqueue()
+            pb.measures(m1)
+            pb.backward(gm1, g1)
+            torch.cuda.synchronize()
+        plain_ms = (time.perf_counter() - t0) * 1e3
+        npts = int(o[npl])
+        gerr, merr = 0.0, 0.0
+        for c, (pb, m1, g1, a, e) in enumerate(plain):
+            gf = grad_fast[:, a:e].double()
+            den = max(float(gf.abs().max()), 1e-30)
+            gerr = max(gerr, float((g1.double() - gf).abs().max()) / den)
+            merr = max(merr, float(((m1[0] - meas[c]).abs() / meas[c].abs().clamp_min(1e-300)).max()))
+        fast_per_pt = fwd_ms + bwd_ms
         n = pts.shape[1]
+        plain_rec = {"clouds": npl, "points": npts, "ms": round(plain_ms, 3),
+                     "Mpoints_s": round(npts / plain_ms / 1e3, 2),
+                     "how": "per cloud: one FP64-predicate hull, measures and backward, "
+                            "synchronised (host timer)",
+                     "fast_Mpoints_s_fwd_bwd": round(n / fast_per_pt / 1e3, 1),
+                     "speedup_of_fast_path": round((plain_ms / npts) / (fast_per_pt / n), 1),
+                     "max_rel_grad_diff": gerr, "max_rel_measure_diff": merr}
+        del plain
         out.append({"workload": (f"2D: {nc} clouds x {n // nc} points in the disk, "
                                  "loss = sum of perimeters + areas") if dim == 2 else
                                 (f"3D: {nc} clouds x {n // nc} points in the ball, "
@@ -420,7 +463,7 @@ def bench_diff(args, qh, dev, rank):
                     "fwd_ms": round(fwd_ms, 3), "bwd_ms": round(bwd_ms, 3),
                     "bwd_over_fwd": round(bwd_ms / fwd_ms, 4),
                     "fwd_Mpoints_s": round(n / fwd_ms / 1e3, 1),
-                    "autograd_step_ms": round(ag_ms, 3)})
+                    "autograd_step_ms": round(ag_ms, 3), "plain_gpu": plain_rec})
         del b, P, O
         torch.cuda.empty_cache()
     return out
