@@ -1229,13 +1229,67 @@ __device__ void cone_warp(const Params3 &A, int e, int f0, int len, const int *V
 // would touch); else it wins when it owns every facet of V in this round's
 // claims (claim[r & 1]) and no facet of N carries a higher claim.  A
 // candidate that lost claims its visible facets for round r + 1 in the
-// other claim array, which this round's checks and cones never read.  The
-// CTA's winners are collected in shared memory and their cones built one
-// warp per winner.  Winners of one round touch disjoint, non-adjacent facet
+// other claim array, which this round's checks and cones never read.  One
+// warp checks a candidate (its lanes read the lists and the claims side by
+// side) and, when it wins, builds its cone.  Winners of one round touch
+// disjoint, non-adjacent facet
 // sets (a facet of V_u in N_w would carry u's claim above w's, and one of
 // V_w in N_u w's above u's), so their cones commute; a later round's winner
 // re-checks against every earlier round's deletions.
-__device__ void round3d(const Params3 &A, int par, int iter, int r, bool last, SmemAll3 &sm,
+__device__ void round3d_warp(const Params3 &A, int par, int iter, int r, bool last, SmemAll3 &sm,
+                        int bid, int nb)
+{
+    (void)sm;
+    Hdr3 *H = A.hdr;
+    const int ne = (int)(*(volatile unsigned long long *)&H->tab[par] >> 32);
+    const Ent3 *ent = A.ent[par];
+    const unsigned long long *cl = A.claim[r & 1];
+    unsigned long long *cn = A.claim[(r + 1) & 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    int nact = 0;
+    // a contiguous chunk of candidates per CTA, one warp per candidate: the
+    // lanes read the candidate's lists and their claims side by side, and a
+    // winner's warp builds its cone at once
+    const int per = (ne + nb - 1) / nb;
+    const int e_lo = min(ne, bid * per), e_hi = min(ne, e_lo + per);
+    for (int e = e_lo + warp; e < e_hi; e += nwarp) {
+        if (A.cstate[e] != 0) continue;
+        const int2 c = A.vn[e];
+        const int *V = A.vpool + (size_t)e * kVCap;
+        int *N = A.npool + (size_t)e * kNCap;
+        const Ent3 en = ent[e];
+        const unsigned long long mine = claim_key(iter, r, en.f, en.len);
+        bool touched = false, lose = false;
+        for (int j = lane; j < c.x; j += 32) {
+            const int v = V[j];
+            touched |= r > 0 && A.taken[v] == iter;
+            lose |= cl[v] != mine;
+        }
+        for (int j = lane; j < c.y; j += 32) {
+            const int v = N[j];
+            touched |= r > 0 && A.taken[v] == iter;
+            lose |= cl[v] >= mine;
+        }
+        touched = __any_sync(0xffffffffu, touched);
+        lose = __any_sync(0xffffffffu, lose);
+        if (touched) {
+            if (lane == 0) A.cstate[e] = 2;
+        } else if (!lose) {
+            // the horizon list reuses the candidate's neighbour slice (>= |V| + 2)
+            cone_warp(A, e, en.f, en.len, V, c.x, N, iter, r, cl);
+        } else if (!last) {
+            const unsigned long long next = claim_key(iter, r + 1, en.f, en.len);
+            for (int j = lane; j < c.x; j += 32) atomicMax(&cn[V[j]], next);
+            nact++;
+        }
+    }
+    if (!last && lane == 0 && nact) atomicAdd(&H->nact[r + 1], nact);
+}
+
+// Many candidates per warp of the grid: one thread per candidate (the
+// CTA's winners collected in shared memory, their cones built one warp per
+// winner); the same decisions as round3d_warp.
+__device__ void round3d_thread(const Params3 &A, int par, int iter, int r, bool last, SmemAll3 &sm,
                         int bid, int nb)
 {
     Hdr3 *H = A.hdr;
@@ -1258,18 +1312,29 @@ __device__ void round3d(const Params3 &A, int par, int iter, int r, bool last, S
             const int *V = A.vpool + (size_t)e * kVCap;
             const int *N = A.npool + (size_t)e * kNCap;
             const Ent3 en = ent[e];
-            bool touched = false;
-            if (r > 0) {
-                for (int j = 0; j < c.x && !touched; j++) touched = A.taken[V[j]] == iter;
-                for (int j = 0; j < c.y && !touched; j++) touched = A.taken[N[j]] == iter;
+            const unsigned long long mine = claim_key(iter, r, en.f, en.len);
+            // the lists' entries in groups of eight, each group's loads in
+            // flight together (after round 0 a touched region decides
+            // before a lost claim, so the scan goes on past a loss)
+            bool touched = false, win = true;
+            for (int j0 = 0; j0 < c.x + c.y && !touched && (win || r > 0); j0 += 8) {
+                int g[8];
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    const int j = j0 + k;
+                    g[k] = j < c.x ? V[j] : (j < c.x + c.y ? N[j - c.x] : -1);
+                }
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    if (g[k] < 0) continue;
+                    touched |= r > 0 && A.taken[g[k]] == iter;
+                    const unsigned long long ck = cl[g[k]];
+                    win &= j0 + k < c.x ? ck == mine : ck < mine;
+                }
             }
             if (touched) {
                 A.cstate[e] = 2;
             } else {
-                const unsigned long long mine = claim_key(iter, r, en.f, en.len);
-                bool win = true;
-                for (int j = 0; j < c.x && win; j++) win = cl[V[j]] == mine;
-                for (int j = 0; j < c.y && win; j++) win = cl[N[j]] < mine;
                 if (win) {
                     sm.w.list[atomicAdd(&sm.w.n, 1)] = e;
                 } else if (!last) {
@@ -1293,6 +1358,16 @@ __device__ void round3d(const Params3 &A, int par, int iter, int r, bool last, S
         const int na = __reduce_add_sync(0xffffffffu, nact);
         if ((threadIdx.x & 31) == 0 && na) atomicAdd(&H->nact[r + 1], na);
     }
+}
+
+__device__ void round3d(const Params3 &A, int par, int iter, int r, bool last, SmemAll3 &sm,
+                        int bid, int nb)
+{
+    const int ne = (int)(*(volatile unsigned long long *)&A.hdr->tab[par] >> 32);
+    if (ne <= kSelWarpMul * nb * (int)(blockDim.x >> 5))
+        round3d_warp(A, par, iter, r, last, sm, bid, nb);
+    else
+        round3d_thread(A, par, iter, r, last, sm, bid, nb);
 }
 
 // No winner at all means the highest-priority candidate overflowed its
@@ -2050,7 +2125,7 @@ __global__ void __launch_bounds__(kMaxBlock) qh3d_persistent(Params3 A)
         }
         mark(0, 0);
         if (scatter_due) scatter3d<false>(A, cur ^ 1, sm, ss, bid, nb);
-        if (tab_ne(cur) <= nb * (int)(blockDim.x >> 5)) {
+        if (tab_ne(cur) <= kSelWarpMul * nb * (int)(blockDim.x >> 5)) {
             __syncthreads();  // the scatter's staging and the warps' lists share memory
             select3d_warp<MODE>(A, cur, iter, sm, bid, nb);
         } else {

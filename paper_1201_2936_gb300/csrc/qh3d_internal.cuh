@@ -29,6 +29,13 @@ constexpr int kMinTile = 256;            // lower bound (sizes the tile maps)
 constexpr int kVCap = QH3D_VCAP;         // visible facets a candidate may list
 constexpr int kNCap = 2 * kVCap;         // horizon neighbours a candidate may list (>= kVCap + 2)
 constexpr int kMaxGrid = 4096;
+// the selection and its claim rounds take one warp per candidate while
+// there are at most this many candidates per warp of the grid, else one
+// thread per candidate
+#ifndef QH3D_SELW
+#define QH3D_SELW 2
+#endif
+constexpr int kSelWarpMul = QH3D_SELW;
 
 // A facet of the current triangulated hull.
 struct Fac3 {
