@@ -408,6 +408,255 @@ __device__ void build_tetra(const Params3 &A)
     H->hull_vertices = 4;
 }
 
+// ---------------------------------------------------------------- first polytope
+// Direction k (0 <= k < kDirs) of the first polytope: the k-th non-zero
+// vector of {-1, 0, 1}^3.
+__device__ __forceinline__ void dir_of(int k, int &dx, int &dy, int &dz)
+{
+    const int i = k < 13 ? k : k + 1;
+    dx = i / 9 - 1;
+    dy = (i / 3) % 3 - 1;
+    dz = i % 3 - 1;
+}
+
+// All CTAs: the extreme point of every direction (largest FP32 dot product,
+// lowest index on ties; -0 counted as +0 so that copies of one location
+// tie), kept in H->dirkey by one atomic per CTA and direction.  Which point
+// each direction finds only shapes the first polytope: every point of it is
+// an input point, so the hull does not depend on it.
+// The directions the first polytope uses: all 26, or the 6 axes and the 8
+// diagonals (direction k of dir_of for k < kNumDirs).
+constexpr int kNumDirs = kInitDirs == 1 ? kDirs : 14;
+__device__ __forceinline__ void used_dir(int k, int &dx, int &dy, int &dz)
+{
+    if (kInitDirs == 1) {
+        dir_of(k, dx, dy, dz);
+        return;
+    }
+    if (k < 6) {  // the axes
+        dx = k / 2 == 0 ? (k & 1 ? -1 : 1) : 0;
+        dy = k / 2 == 1 ? (k & 1 ? -1 : 1) : 0;
+        dz = k / 2 == 2 ? (k & 1 ? -1 : 1) : 0;
+    } else {      // the diagonals
+        const int b = k - 6;
+        dx = b & 1 ? -1 : 1;
+        dy = b & 2 ? -1 : 1;
+        dz = b & 4 ? -1 : 1;
+    }
+}
+
+__device__ void dir_extrema3d(const Params3 &A, SmemAll3 &sm, int bid, int nb)
+{
+    Hdr3 *H = A.hdr;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    constexpr int kG = (kNumDirs + kDirGroup - 1) / kDirGroup;  // keys per pass: kDirGroup
+#pragma unroll
+    for (int g = 0; g < kG; g++) {
+        const int k0 = kDirGroup * g, nk = kNumDirs - k0 < kDirGroup ? kNumDirs - k0 : kDirGroup;
+        unsigned long long best[kDirGroup];
+#pragma unroll
+        for (int k = 0; k < kDirGroup; k++) best[k] = 0ull;
+        for (long long i = (long long)bid * blockDim.x + threadIdx.x; i < A.n;
+             i += (long long)nb * blockDim.x) {
+            const float4 p = load_input(A, i);
+            const unsigned lo = 0xffffffffu - (unsigned)i;
+#pragma unroll
+            for (int k = 0; k < kDirGroup; k++) {
+                if (k >= nk) break;
+                int dx, dy, dz;
+                used_dir(k0 + k, dx, dy, dz);
+                float sdot = 0.0f;
+                if (dx) sdot += dx > 0 ? p.x : -p.x;
+                if (dy) sdot += dy > 0 ? p.y : -p.y;
+                if (dz) sdot += dz > 0 ? p.z : -p.z;
+                sdot += 0.0f;
+                const unsigned long long key = ((unsigned long long)ord_f32(sdot) << 32) | lo;
+                best[k] = key > best[k] ? key : best[k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kDirGroup; k++) {
+            if (k >= nk) break;
+            unsigned long long b = best[k];
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long t = __shfl_xor_sync(0xffffffffu, b, o);
+                b = t > b ? t : b;
+            }
+            if (lane == 0) sm.init.key[warp][k] = b;
+        }
+        __syncthreads();
+        if (threadIdx.x < nk) {
+            unsigned long long b = 0ull;
+            for (int w = 0; w < nwarp; w++) {
+                const unsigned long long t = sm.init.key[w][threadIdx.x];
+                b = t > b ? t : b;
+            }
+            if (b) atomicMax(&H->dirkey[k0 + threadIdx.x], b);
+        }
+        __syncthreads();
+    }
+}
+
+// Warp 0 of CTA 0, after the tetrahedron: insert the directions' extreme
+// points one at a time (Barber et al.'s step with exact signs: the facets
+// the point is strictly above, their horizon edges, one new facet per edge
+// through the point), then write the polytope's facets to slots 0 .. F-1
+// with their neighbours, and give the cloud's pseudo facet the cone of all
+// of them, so the first assignment sends every point to the first facet it
+// is strictly above.  A point on or inside the current polytope is skipped.
+__device__ void expand_initial(const Params3 &A, SmemAll3 &sm)
+{
+    Hdr3 *H = A.hdr;
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    const unsigned lt = (1u << lane) - 1u;
+    SmemInit &S = sm.init;
+    // vertices get slots 0 .. nv-1 (point index in S.vid); a directed edge
+    // (slot a -> slot b) of a facet that stays is bit b of S.emask[a]
+    if (lane < 4) {
+        const Fac3 F = A.fac[lane];
+        for (int j = 0; j < 9; j++) S.p[lane][j] = F.p[j];
+        for (int j = 0; j < 3; j++) S.v[lane][j] = F.v[j];
+        S.vid[lane] = F.v[0];
+    }
+    __syncwarp();
+    if (lane == 0) {
+        // the four vertices: facet 0's three and the one facet 1 adds
+        S.vid[0] = S.v[0][0];
+        S.vid[1] = S.v[0][1];
+        S.vid[2] = S.v[0][2];
+        int o = S.v[1][0];
+        for (int t = 0; t < 3; t++) {
+            const int c = S.v[1][t];
+            if (c != S.vid[0] && c != S.vid[1] && c != S.vid[2]) o = c;
+        }
+        S.vid[3] = o;
+        // from here on a facet's vertices are slots
+        for (int j = 0; j < 4; j++)
+            for (int e = 0; e < 3; e++) {
+                int r = 0;
+                for (int t = 0; t < 4; t++)
+                    if (S.vid[t] == S.v[j][e]) r = t;
+                S.v[j][e] = r;
+            }
+        S.nf = 4;
+        S.nv = 4;
+    }
+    __syncwarp();
+    for (int k = 0; k < kNumDirs; k++) {
+        const unsigned long long key = *(volatile unsigned long long *)&H->dirkey[k];
+        const int qi = (int)(0xffffffffu - (unsigned)(key & 0xffffffffull));
+        if (key == 0ull || qi < 0 || qi >= A.n || S.nv >= 32) continue;
+        const float4 q4 = load_input(A, qi);
+        const float q[3] = {q4.x, q4.y, q4.z};
+        const int nf = S.nf;
+        int nvis = 0;
+        if (lane < 32) S.emask[lane] = 0u;
+        __syncwarp();
+        for (int j = lane; j < nf; j += 32) {
+            const int vis = orient3d_exact_sign(S.p[j], S.p[j] + 3, S.p[j] + 6, q) > 0;
+            S.vis[j] = vis;
+            nvis += vis;
+        }
+        nvis = __reduce_add_sync(0xffffffffu, nvis);
+        if (nvis == 0) continue;
+        // the directed edges of the facets that stay
+        for (int j = lane; j < nf; j += 32)
+            if (!S.vis[j])
+                for (int e = 0; e < 3; e++)
+                    atomicOr(&S.emask[S.v[j][e]], 1u << S.v[j][e == 2 ? 0 : e + 1]);
+        __syncwarp();
+        // horizon edges: an edge of a visible facet whose reverse edge stays
+        if (lane == 0) S.ne = 0;
+        __syncwarp();
+        for (int j = lane; j < nf; j += 32) {
+            if (!S.vis[j]) continue;
+            for (int e = 0; e < 3; e++) {
+                const int e1 = e == 2 ? 0 : e + 1;
+                if (!((S.emask[S.v[j][e1]] >> S.v[j][e]) & 1u)) continue;
+                const int at = atomicAdd(&S.ne, 1);
+                if (at >= kInitF) continue;
+                S.eu[at] = S.v[j][e];
+                S.ev[at] = S.v[j][e1];
+                for (int t = 0; t < 3; t++) {
+                    S.ep[at][t] = S.p[j][3 * e + t];
+                    S.ep[at][3 + t] = S.p[j][3 * e1 + t];
+                }
+            }
+        }
+        __syncwarp();
+        const int ne = S.ne;
+        if (ne > kInitF || nf - nvis + ne > kInitF) continue;  // cannot happen (V <= 32)
+        // the facets that stay, compacted in order (a chunk is read before it
+        // is written; destinations never pass their sources), then the cone
+        int w = 0;
+        for (int j0 = 0; j0 < nf; j0 += 32) {
+            const int j = j0 + lane;
+            const bool keep = j < nf && !S.vis[j];
+            float pp[9];
+            int vv[3];
+            if (keep) {
+                for (int t = 0; t < 9; t++) pp[t] = S.p[j][t];
+                for (int t = 0; t < 3; t++) vv[t] = S.v[j][t];
+            }
+            const unsigned b = __ballot_sync(0xffffffffu, keep);
+            __syncwarp();
+            if (keep) {
+                const int d = w + __popc(b & lt);
+                for (int t = 0; t < 9; t++) S.p[d][t] = pp[t];
+                for (int t = 0; t < 3; t++) S.v[d][t] = vv[t];
+            }
+            w += __popc(b);
+            __syncwarp();
+        }
+        for (int e = lane; e < ne; e += 32) {
+            const int d = w + e;
+            for (int t = 0; t < 6; t++) S.p[d][t] = S.ep[e][t];
+            S.p[d][6] = q[0];
+            S.p[d][7] = q[1];
+            S.p[d][8] = q[2];
+            S.v[d][0] = S.eu[e];
+            S.v[d][1] = S.ev[e];
+            S.v[d][2] = S.nv;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            S.nf = w + ne;
+            S.vid[S.nv] = qi;
+            S.nv = S.nv + 1;
+        }
+        __syncwarp();
+    }
+    // buried vertices keep their slots (no facet uses them); the neighbours
+    // from the edge slots
+    const int nf = S.nf;
+    for (int j = lane; j < nf; j += 32)
+        for (int e = 0; e < 3; e++) S.eid[S.v[j][e]][S.v[j][e == 2 ? 0 : e + 1]] = j;
+    __syncwarp();
+    for (int j = lane; j < nf; j += 32) {
+        Fac3 f;
+        for (int t = 0; t < 9; t++) f.p[t] = S.p[j][t];
+        for (int e = 0; e < 3; e++) {
+            f.v[e] = S.vid[S.v[j][e]];
+            f.nb[e] = S.eid[S.v[j][e == 2 ? 0 : e + 1]][S.v[j][e]];  // the facet with the reverse edge
+        }
+        f.alive = 1;
+        A.fac[j] = f;
+        A.plane[j] = make_plane3(f.p, f.p + 3, f.p + 6);
+        Acc3 z = {};
+        A.acc[j] = z;
+        A.claim[0][j] = 0ull;
+        A.claim[1][j] = 0ull;
+        A.taken[j] = 0;
+        A.big_mark[j] = -1;
+    }
+    if (lane == 0) {
+        A.cone[A.fcap] = make_int4(0, nf, -1, 0);
+        H->fcount = nf;
+        H->hull_vertices = S.nv;
+    }
+}
+
 // ---------------------------------------------------------------- clouds
 __device__ __forceinline__ int cloud_start(const Params3 &A, int c)
 {
@@ -1442,7 +1691,7 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, SmemSlots &ss,
     // tiles, so the few hot accumulators see one reservation per CTA instead
     // of one per tile.  Many targets: a table per tile, reserved at the
     // tile's end (contention is low, and the table would not hold them).
-    const int ntarget = FIRST ? 4 * A.ncloud
+    const int ntarget = FIRST ? (A.cloud_off ? 4 * A.ncloud : *(volatile int *)&H->fcount)
                               : *(volatile int *)&H->fcount - *(volatile int *)&H->fc_iter[par];
     const bool per_tile = ntarget > (3 * kSlots) / 4;
     auto reset_slots = [&]() {
@@ -2058,6 +2307,15 @@ __global__ void __launch_bounds__(kMaxBlock) qh3d_persistent(Params3 A)
         if (go) {
             if (bid == 0) build_tetra(A);
             go = sync();
+        }
+        // the first polytope: the tetrahedron and the directions' extreme points
+        if (go && A.init_dirs) {
+            dir_extrema3d(A, sm, bid, nb);
+            go = sync();
+            if (go) {
+                if (bid == 0) expand_initial(A, sm);
+                go = sync();
+            }
         }
     }
     setup_mark(0);

@@ -29,6 +29,13 @@ constexpr int kMinTile = 256;            // lower bound (sizes the tile maps)
 constexpr int kVCap = QH3D_VCAP;         // visible facets a candidate may list
 constexpr int kNCap = 2 * kVCap;         // horizon neighbours a candidate may list (>= kVCap + 2)
 constexpr int kMaxGrid = 4096;
+constexpr int kDirs = 26;  // directions of the first polytope: the non-zero vectors of {-1, 0, 1}^3
+#ifndef QH3D_INITDIRS
+#define QH3D_INITDIRS 2
+#endif
+// single cloud: start from that polytope (0: the tetrahedron; 1: all 26
+// directions; 2: the 14 of the axes and the diagonals)
+constexpr int kInitDirs = QH3D_INITDIRS;
 // the selection and its claim rounds take one warp per candidate while
 // there are at most this many candidates per warp of the grid, else one
 // thread per candidate
@@ -93,6 +100,9 @@ struct Hdr3 {
     // device time of the setup (initial simplex, first assignment, its table,
     // its scatter + certify + exact) and of the whole persistent kernel (ns)
     long long setup_ns[4], kernel_ns;
+    // extreme point of each direction of the first polytope (single cloud):
+    // (ordered dot product << 32) | ~index, the largest kept
+    unsigned long long dirkey[kDirs];
 };
 constexpr int kTimeline3 = 64;
 
@@ -139,6 +149,7 @@ struct Params3 {
     long long max_iters, wait_ns;
     int test_hold;                // CTA 0 skips its first grid-barrier arrival (tests)
     int small_cloud;              // batched: clouds of 4..small_cloud points, one warp each
+    int init_dirs;                // single cloud: first polytope from the directions' extreme points
 };
 
 // The pseudo facet of cloud c in the first assignment (every point of the
@@ -207,7 +218,24 @@ struct SmemX3 {
     int idx[kMaxBlock];
     float4 p[kMaxBlock];
 };
+// The first polytope of a single cloud (built by one warp of CTA 0): the
+// tetrahedron with the extreme points of kDirs directions inserted.
+constexpr int kInitF = 128;         // facets while it is built (2 V - 4 <= 56 at the end)
+constexpr int kDirGroup = 14;       // directions reduced per pass over the points
+struct SmemInit {
+    float p[kInitF][9];             // the three vertices' coordinates
+    int v[kInitF][3];               // their point indices (outward: counter-clockwise)
+    int vis[kInitF];
+    int eu[kInitF], ev[kInitF];     // horizon edges of the point being inserted
+    float ep[kInitF][6];
+    int nf, ne, nv;
+    int vid[32];                    // point index of each vertex slot
+    unsigned emask[32];             // directed edges of the facets that stay, by slot
+    int eid[32][32];                // the facet of each directed edge (neighbours at the end)
+    unsigned long long key[32][14]; // per warp: the best key of each direction of a group
+};
 union SmemAll3 {
+    SmemInit init;
     SmemRed red;
     SmemAssign a;
     SmemTable t;
