@@ -1361,21 +1361,21 @@ __device__ bool build_cone(const Params3 &A, int f0, int len, const int *V, int 
     return true;
 }
 
-// ---------------------------------------------------------------- C: winners
-// One warp builds one winner's cone: horizon edges found by the lanes
-// (ballot-compacted; g is in V exactly when it carries the winner's claim
-// of this round in cl), one cone facet per horizon edge, the horizon
-// neighbours relinked, and the cone facets linked around the apex by
-// matching edge ends across lanes (shuffles).
-__device__ void cone_warp(const Params3 &A, int e, int f0, int len, const int *V, int nv,
-                          int *hz, int iter, int round, const unsigned long long *cl)
+// The cone of winner e (its visible set V of nv facets, all claimed by it
+// in this round in cl), in two steps.  cone_horizon: its horizon edges
+// (edges of V whose neighbour is not V) into hz, returns their count (a
+// visible region that is not a disk cannot happen: QH_ERR_CAPACITY).
+// cone_build: with the facet slots base .. base + nh - 1 reserved, one cone
+// facet per horizon edge, the horizon neighbours relinked, the cone facets
+// linked around the apex by matching edge ends across lanes (shuffles),
+// and V deleted.  cone_warp reserves its own slots; the rounds with many
+// winners per CTA reserve all of a CTA's slots with one atomic.
+__device__ int cone_horizon(const Params3 &A, int f0, int len, const int *V, int nv, int *hz,
+                            int iter, int round, const unsigned long long *cl)
 {
-    Hdr3 *H = A.hdr;
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     const unsigned long long mine = claim_key(iter, round, f0, len);
-    const float4 q4 = A.apex[f0];
-    const int qi = __float_as_int(q4.w);
     int nh = 0;
     for (int p0 = 0; p0 < 3 * nv; p0 += 32) {
         const int p = p0 + lane;
@@ -1391,18 +1391,17 @@ __device__ void cone_warp(const Params3 &A, int e, int f0, int len, const int *V
         }
         nh += __popc(b);
     }
-    if (nh > kNCap) {  // a visible region that is not a disk: cannot happen
-        if (lane == 0) set_status(H, QH_ERR_CAPACITY);
-        return;
-    }
+    if (nh > kNCap && lane == 0) set_status(A.hdr, QH_ERR_CAPACITY);
     __syncwarp();
-    int base = 0;
-    if (lane == 0) base = atomicAdd(&H->fcount, nh);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base + nh > A.fcap) {
-        if (lane == 0) set_status(H, QH_ERR_CAPACITY);
-        return;
-    }
+    return nh;
+}
+
+__device__ void cone_build(const Params3 &A, int e, int f0, const int *V, int nv, const int *hz,
+                           int nh, int base, int iter)
+{
+    const int lane = threadIdx.x & 31;
+    const float4 q4 = A.apex[f0];
+    const int qi = __float_as_int(q4.w);
     int u[2] = {-1, -1}, w[2] = {-1, -1};
 #pragma unroll
     for (int r = 0; r < 2; r++) {
@@ -1466,10 +1465,27 @@ __device__ void cone_warp(const Params3 &A, int e, int f0, int len, const int *V
         A.taken[V[i]] = iter;
         A.cone[V[i]] = make_int4(base, nh, qi, iter);
     }
+    if (lane == 0) A.cstate[e] = 1;
+}
+
+__device__ void cone_warp(const Params3 &A, int e, int f0, int len, const int *V, int nv,
+                          int *hz, int iter, int round, const unsigned long long *cl)
+{
+    Hdr3 *H = A.hdr;
+    const int lane = threadIdx.x & 31;
+    const int nh = cone_horizon(A, f0, len, V, nv, hz, iter, round, cl);
+    if (nh > kNCap) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&H->fcount, nh);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base + nh > A.fcap) {
+        if (lane == 0) set_status(H, QH_ERR_CAPACITY);
+        return;
+    }
+    cone_build(A, e, f0, V, nv, hz, nh, base, iter);
     if (lane == 0) {
         atomicAdd(&H->hull_vertices, 1);
         atomicAdd(&H->nwin, 1);
-        A.cstate[e] = 1;
     }
 }
 
@@ -1595,11 +1611,43 @@ __device__ void round3d_thread(const Params3 &A, int par, int iter, int r, bool 
         }
         __syncthreads();
         const int nw = sm.w.n;
-        for (int i = warp; i < nw; i += nwarp) {
-            const int ew = sm.w.list[i];
-            // the horizon list reuses the candidate's neighbour slice (>= |V| + 2)
-            cone_warp(A, ew, ent[ew].f, ent[ew].len, A.vpool + (size_t)ew * kVCap, A.vn[ew].x,
-                      A.npool + (size_t)ew * kNCap, iter, r, cl);
+        if (nw > 0) {
+            // the winners' horizons (one warp per winner; the horizon list
+            // reuses the candidate's neighbour slice, >= |V| + 2), then one
+            // reservation of facet slots for all of them, then the cones
+            const int lane = threadIdx.x & 31;
+            for (int i = warp; i < nw; i += nwarp) {
+                const int ew = sm.w.list[i];
+                const int nh = cone_horizon(A, ent[ew].f, ent[ew].len, A.vpool + (size_t)ew * kVCap,
+                                            A.vn[ew].x, A.npool + (size_t)ew * kNCap, iter, r, cl);
+                if (lane == 0) sm.w.nh[i] = nh <= kNCap ? nh : -1;
+            }
+            __syncthreads();
+            const int t = threadIdx.x;
+            const int my = t < nw && sm.w.nh[t] > 0 ? sm.w.nh[t] : 0;
+            long long tot;
+            const long long ex = block_excl_scan64(my, sm.w.wsum, &tot);
+            if (t < nw) sm.w.base[t] = (int)ex;
+            if (t == 0) {
+                const int b0 = atomicAdd(&H->fcount, (int)tot);
+                if (b0 + tot > A.fcap) {
+                    set_status(H, QH_ERR_CAPACITY);
+                    sm.w.base0 = -1;
+                } else {
+                    sm.w.base0 = b0;
+                    atomicAdd(&H->hull_vertices, nw);
+                    atomicAdd(&H->nwin, nw);
+                }
+            }
+            __syncthreads();
+            const int b0 = sm.w.base0;
+            for (int i = warp; i < nw && b0 >= 0; i += nwarp) {
+                const int nh = sm.w.nh[i];
+                if (nh < 0) continue;
+                const int ew = sm.w.list[i];
+                cone_build(A, ew, ent[ew].f, A.vpool + (size_t)ew * kVCap, A.vn[ew].x,
+                           A.npool + (size_t)ew * kNCap, nh, b0 + sm.w.base[i], iter);
+            }
         }
         __syncthreads();  // the list is reused by the next chunk
     }

@@ -206,8 +206,11 @@ struct SmemTable {
     unsigned long long base;
 };
 struct SmemWin {
-    int n;
+    int n, base0;
     int list[kMaxBlock];
+    int nh[kMaxBlock];    // a winner's horizon edges (-1: too many)
+    int base[kMaxBlock];  // its first facet slot, from base0
+    long long wsum[33];
 };
 // Visible-set search with one warp per candidate: the warp's lists.
 struct SmemBfs {
