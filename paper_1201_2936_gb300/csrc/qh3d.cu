@@ -1193,10 +1193,22 @@ __device__ void select3d(const Params3 &A, int par, int iter, int bid, int nb)
         A.vn[e] = over ? make_int2(-1, -1) : make_int2(nv, nn);
         A.cstate[e] = over ? 2 : 0;
     }
+    // one atomic per CTA on each header count (many candidates: every warp
+    // of the grid has some)
+    __shared__ unsigned long long s_cnt[2];
+    if (threadIdx.x == 0) s_cnt[0] = s_cnt[1] = 0ull;
+    __syncthreads();
     unsigned f = __reduce_add_sync(0xffffffffu, fallbacks);
-    if ((threadIdx.x & 31) == 0 && f) atomicAdd(&H->fallbacks, (unsigned long long)f);
     const int na = __reduce_add_sync(0xffffffffu, nact);
-    if ((threadIdx.x & 31) == 0 && na) atomicAdd(&H->nact[0], na);
+    if ((threadIdx.x & 31) == 0) {
+        if (f) atomicAdd(&s_cnt[0], (unsigned long long)f);
+        if (na) atomicAdd(&s_cnt[1], (unsigned long long)na);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_cnt[0]) atomicAdd(&H->fallbacks, s_cnt[0]);
+        if (s_cnt[1]) atomicAdd(&H->nact[0], (int)s_cnt[1]);
+    }
 }
 
 // The same search with one warp per candidate, level by level: the lanes
@@ -1652,8 +1664,13 @@ __device__ void round3d_thread(const Params3 &A, int par, int iter, int r, bool 
         __syncthreads();  // the list is reused by the next chunk
     }
     if (!last) {
-        const int na = __reduce_add_sync(0xffffffffu, nact);
-        if ((threadIdx.x & 31) == 0 && na) atomicAdd(&H->nact[r + 1], na);
+        // one atomic per CTA
+        const int na = __syncthreads_count(nact != 0) ? __reduce_add_sync(0xffffffffu, nact) : 0;
+        if (threadIdx.x == 0) sm.w.n = 0;
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0 && na) atomicAdd(&sm.w.n, na);
+        __syncthreads();
+        if (threadIdx.x == 0 && sm.w.n) atomicAdd(&H->nact[r + 1], sm.w.n);
     }
 }
 
