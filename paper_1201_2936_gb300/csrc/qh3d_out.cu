@@ -152,7 +152,9 @@ Params3 make_params3(const float *x, const float *y, const float *z, int64_t n, 
     A.wait_ns = o.wait_ns > 0 ? o.wait_ns : 2000000000ll;
     A.test_hold = o.test_hold;
     A.small_cloud = o.small_cloud;
-    A.init_dirs = kInitDirs;
+    // the first polytope pays off with the FP32 filter; with FP64 plane
+    // tests its larger first assignment costs more than the iterations save
+    A.init_dirs = o.pred_mode == QH_PRED_F32 ? kInitDirs : 0;
     const int block = o.block > 0 ? o.block : (o.pred_mode == QH_PRED_F64 ? kDefBlockF64 : kDefBlockF32);
     const int items = o.items > 0 ? o.items : kDefItems;
     A.tile = block * items;
