@@ -773,6 +773,7 @@ def main():
     traffic = round(ratio * algo) if ratio else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                "frac_of_nominal_8TBps": round(achieved / 8000.0, 4),
                 "traffic": traffic, "kernel": "qh2d_multi<PredF32>",
                 "algo_bytes_per_launch": algo, "iterations": r0.iterations,
                 "fallback_frac": r0.filter_fallbacks / max(1, r0.live_total),
