@@ -809,6 +809,105 @@ __global__ void __launch_bounds__(kBlock) k4_select(Params4 A, int par, int iter
     if ((threadIdx.x & 31) == 0 && na) atomicAdd(&H->nact[0], na);
 }
 
+// lanes of this warp below the calling lane
+__device__ __forceinline__ unsigned lanemask_lt4()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// The selection with one warp per candidate: the breadth-first frontier
+// spread over the lanes (each frontier facet's four neighbours, duplicates
+// merged by __match_any_sync), the lists in shared memory, new entries
+// appended by ballots.  The same visible and horizon sets as k4_select.
+__global__ void __launch_bounds__(kBlock) k4_select_warp(Params4 A, int par, int iter)
+{
+    __shared__ int sV[kBlock / 32][kV];
+    __shared__ int sN[kBlock / 32][kN];
+    Hdr4 *H = A.hdr;
+    if (*(volatile int *)&H->status) return;
+    const int ne = (int)(*(volatile unsigned long long *)&H->tab[par] >> 32);
+    const Ent4 *ent = A.ent[par];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt4();
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    int *V = sV[warp];
+    int *N = sN[warp];
+    unsigned fallbacks = 0;
+    int nact = 0;
+    for (int e = gw; e < ne; e += nw) {
+        const Ent4 en = ent[e];
+        const float4 q = load4(A, A.apex[en.f]);
+        if (lane == 0) V[0] = en.f;
+        int nv = 1, nn = 0, done = 0;
+        bool over = false;
+        __syncwarp();
+        while (done < nv && !over) {
+            const int lo = done, cnt = 4 * (nv - done);
+            done = nv;
+            for (int b0 = 0; b0 < cnt && !over; b0 += 32) {
+                const int it = b0 + lane;
+                int g = -1;
+                bool bad = false;
+                if (it < cnt) {
+                    g = A.fac[V[lo + (it >> 2)]].nb[it & 3];
+                    if (g < 0 || g >= A.fcap) {  // an unlinked ridge: internal error
+                        bad = true;
+                        g = -1;
+                    }
+                }
+                if (__any_sync(0xffffffffu, bad)) {
+                    if (lane == 0) set_status4(H, QH_ERR_CAPACITY);
+                    over = true;
+                    break;
+                }
+                const unsigned same = __match_any_sync(0xffffffffu, g);
+                bool keep = g >= 0 && lane == __ffs(same) - 1;
+                for (int j = 0; j < nv && keep; j++) keep = V[j] != g;
+                for (int j = 0; j < nn && keep; j++) keep = N[j] != g;
+                bool vis = false;
+                if (keep) {
+                    float d, err;
+                    vis = facet_sign4(A, g, q, d, err, fallbacks) > 0;
+                }
+                const unsigned bv = __ballot_sync(0xffffffffu, keep && vis);
+                const unsigned bn = __ballot_sync(0xffffffffu, keep && !vis);
+                if (nv + __popc(bv) > kV || nn + __popc(bn) > kN) {
+                    over = true;
+                } else {
+                    if (keep && vis) V[nv + __popc(bv & lt)] = g;
+                    if (keep && !vis) N[nn + __popc(bn & lt)] = g;
+                    nv += __popc(bv);
+                    nn += __popc(bn);
+                }
+                __syncwarp();
+            }
+        }
+        if (!over) {
+            int *Vg = A.vpool + (size_t)e * kV;
+            int *Ng = A.npool + (size_t)e * kN;
+            const unsigned long long mine = claim_key4(iter, 0, en.f, en.len);
+            for (int j = lane; j < nv; j += 32) {
+                Vg[j] = V[j];
+                atomicMax(&A.claim[0][V[j]], mine);
+            }
+            for (int j = lane; j < nn; j += 32) Ng[j] = N[j];
+            nact += lane == 0;
+        }
+        if (lane == 0) {
+            A.vn[e] = over ? make_int2(-1, -1) : make_int2(nv, nn);
+            A.cstate[e] = over ? 2 : 0;
+        }
+        __syncwarp();
+    }
+    const unsigned f = __reduce_add_sync(0xffffffffu, fallbacks);
+    if (lane == 0 && f) atomicAdd(&H->fallbacks, (unsigned long long)f);
+    const int na = __reduce_add_sync(0xffffffffu, nact);
+    if (lane == 0 && na) atomicAdd(&H->nact[0], na);
+}
+
 // Cone of one winner (one thread): one new facet per horizon ridge (the
 // visible facet with the ridge's opposite vertex replaced by the apex keeps
 // the outward orientation), the horizon neighbour relinked, the new facets
@@ -888,6 +987,171 @@ __device__ bool build_cone4(const Params4 &A, int f0, int len, const int *V, int
     atomicAdd(&H->hull_vertices, 1);
     atomicAdd(&H->nwin, 1);
     return true;
+}
+
+// The same cone built by one warp (horizons of at most 64 ridges; returns 0
+// for a larger one, which the caller builds with build_cone4).  The horizon
+// ridges by ballots; each lane creates up to two cone facets and relinks
+// their horizon neighbours; the ridges through the apex are matched by
+// shuffling every lane's facets across the warp: the facet across facet
+// j's ridge opposite v[i] is the other cone facet holding the two
+// vertices of j other than v[i] and the apex.  Returns 1 when built, -1 on
+// a capacity failure (status raised).
+__device__ int cone4_warp(const Params4 &A, int f0, int len, const int *V, int nv, int *hz,
+                          int hcap, int iter, int round, const unsigned long long *cl)
+{
+    Hdr4 *H = A.hdr;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt4();
+    const unsigned long long mine = claim_key4(iter, round, f0, len);
+    const int qi = A.apex[f0];
+    int nh = 0;
+    bool bad = false;
+    for (int p0 = 0; p0 < 4 * nv; p0 += 32) {
+        const int p = p0 + lane;
+        bool is_h = false;
+        if (p < 4 * nv) {
+            const int g = A.fac[V[p >> 2]].nb[p & 3];
+            if (g < 0 || g >= A.fcap) bad = true;  // an unlinked ridge: internal error
+            else is_h = cl[g] != mine;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, is_h);
+        if (is_h) {
+            const int pos = nh + __popc(b & lt);
+            if (pos < hcap) hz[pos] = V[p >> 2] * 4 + (p & 3);
+        }
+        nh += __popc(b);
+    }
+    if (__any_sync(0xffffffffu, bad) || nh > hcap) {
+        if (lane == 0) set_status4(H, QH_ERR_CAPACITY);
+        return -1;
+    }
+    if (nh > 64) return 0;
+    __syncwarp();
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&H->fcount, nh);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base + nh > A.fcap) {
+        if (lane == 0) set_status4(H, QH_ERR_CAPACITY);
+        return -1;
+    }
+    int fv[2][4], fk[2];
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        const int j = lane + 32 * r;
+        fk[r] = -1;
+        for (int t = 0; t < 4; t++) fv[r][t] = -1;
+        if (j >= nh) continue;
+        const int hf = hz[j] >> 2, k = hz[j] & 3;
+        const Fac4 F = A.fac[hf];
+        int v[4] = {F.v[0], F.v[1], F.v[2], F.v[3]};
+        v[k] = qi;
+        init_facet4(A, base + j, v);
+        const int g = F.nb[k];
+        A.fac[base + j].nb[k] = g;
+        Fac4 &G = A.fac[g];
+        for (int t = 0; t < 4; t++)
+            if (G.nb[t] == hf) G.nb[t] = base + j;
+        for (int t = 0; t < 4; t++) fv[r][t] = v[t];
+        fk[r] = k;
+    }
+    // nbr[r][i]: the facet across ridge i of this lane's facet r
+    int nbr[2][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}};
+    for (int src = 0; src < 32; src++) {
+#pragma unroll
+        for (int rs = 0; rs < 2; rs++) {
+            int sv[4];
+            for (int t = 0; t < 4; t++) sv[t] = __shfl_sync(0xffffffffu, fv[rs][t], src);
+            const int sj = src + 32 * rs;
+            if (sj >= nh) continue;
+#pragma unroll
+            for (int r = 0; r < 2; r++) {
+                if (fk[r] < 0 || (src == lane && rs == r)) continue;
+                for (int i = 0; i < 4; i++) {
+                    if (i == fk[r] || nbr[r][i] >= 0) continue;
+                    int e[2], m = 0;
+                    for (int t = 0; t < 4; t++)
+                        if (t != i && t != fk[r]) e[m++] = fv[r][t];
+                    int has = 0;
+                    for (int t = 0; t < 4; t++) has += sv[t] == e[0] || sv[t] == e[1];
+                    if (has == 2) nbr[r][i] = base + sj;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        const int j = lane + 32 * r;
+        if (j >= nh) continue;
+        for (int i = 0; i < 4; i++)
+            if (i != fk[r]) A.fac[base + j].nb[i] = nbr[r][i];
+    }
+    for (int i = lane; i < nv; i += 32) {
+        A.fac[V[i]].alive = 0;
+        A.taken[V[i]] = iter;
+        A.cone[V[i]] = make_int4(base, nh, qi, iter);
+    }
+    if (lane == 0) {
+        atomicAdd(&H->hull_vertices, 1);
+        atomicAdd(&H->nwin, 1);
+    }
+    return 1;
+}
+
+// Round r with one warp per candidate (the lanes read the lists and the
+// claims side by side; a winner's warp builds its cone): the same decisions
+// as k4_round.
+__global__ void __launch_bounds__(kBlock) k4_round_warp(Params4 A, int par, int iter, int r,
+                                                        int last)
+{
+    Hdr4 *H = A.hdr;
+    if (*(volatile int *)&H->status || *(volatile int *)&H->nact[r] == 0) return;
+    const int ne = (int)(*(volatile unsigned long long *)&H->tab[par] >> 32);
+    const Ent4 *ent = A.ent[par];
+    const unsigned long long *cl = A.claim[r & 1];
+    unsigned long long *cn = A.claim[(r + 1) & 1];
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    int nact = 0;
+    for (int e = gw; e < ne; e += nw) {
+        if (A.cstate[e] != 0) continue;
+        const int2 c = A.vn[e];
+        int *V = A.vpool + (size_t)e * kV;
+        int *N = A.npool + (size_t)e * kN;
+        const Ent4 en = ent[e];
+        const unsigned long long mine = claim_key4(iter, r, en.f, en.len);
+        bool touched = false, lose = false;
+        for (int j = lane; j < c.x; j += 32) {
+            const int v = V[j];
+            touched |= r > 0 && A.taken[v] == iter;
+            lose |= cl[v] != mine;
+        }
+        for (int j = lane; j < c.y; j += 32) {
+            const int v = N[j];
+            touched |= r > 0 && A.taken[v] == iter;
+            lose |= cl[v] >= mine;
+        }
+        touched = __any_sync(0xffffffffu, touched);
+        lose = __any_sync(0xffffffffu, lose);
+        if (touched) {
+            if (lane == 0) A.cstate[e] = 2;
+        } else if (!lose) {
+            // the horizon list reuses the candidate's neighbour slice (kN >= 2 kV + 2)
+            const int b = cone4_warp(A, en.f, en.len, V, c.x, N, kN, iter, r, cl);
+            if (b > 0) {
+                if (lane == 0) A.cstate[e] = 1;
+            } else if (b == 0 && lane == 0) {
+                if (build_cone4(A, en.f, en.len, V, c.x, N, kN, iter, r, cl)) A.cstate[e] = 1;
+            }
+            __syncwarp();
+        } else if (!last) {
+            const unsigned long long next = claim_key4(iter, r + 1, en.f, en.len);
+            for (int j = lane; j < c.x; j += 32) atomicMax(&cn[V[j]], next);
+            nact++;
+        }
+    }
+    if (!last && lane == 0 && nact) atomicAdd(&H->nact[r + 1], nact);
 }
 
 // Round r, one thread per candidate: out if an earlier round's winner deleted
@@ -1524,9 +1788,10 @@ extern "C" qh_status qh_hull4d(const float *d_x, const float *d_y, const float *
         if (ne == 0) break;
         if (++iter > A.max_iters) return finish(QH_ERR_NO_CONVERGENCE, h);
         k4_iter_begin<<<1, 32, 0, st>>>(A, cur, iter);
-        k4_select<<<grid_of4(ne), kBlock, 0, st>>>(A, cur, iter);
+        k4_select_warp<<<grid_of4(32ll * ne), kBlock, 0, st>>>(A, cur, iter);
         for (int rr = 0; rr < kRounds4; rr++)
-            k4_round<<<grid_of4(ne), kBlock, 0, st>>>(A, cur, iter, rr, rr == kRounds4 - 1);
+            k4_round_warp<<<grid_of4(32ll * ne), kBlock, 0, st>>>(A, cur, iter, rr,
+                                                                rr == kRounds4 - 1);
         k4_fallback<<<1, 32, 0, st>>>(A, cur, iter);
         k4_assign<false><<<grid_of4((Lc + kItems - 1) / kItems), kBlock, 0, st>>>(A, cur);
         k4_table<<<grid_of4(ne + 64), kBlock, 0, st>>>(A, cur, 0);
