@@ -754,61 +754,6 @@ __global__ void __launch_bounds__(kBlock) k4_exact(Params4 A, int par)
 }
 
 // ---------------------------------------------------------------- S: select
-// One thread per segment: visible-set search from its facet (exact tests),
-// V the visible facets, N their non-visible neighbours; claims of round 0.
-__global__ void __launch_bounds__(kBlock) k4_select(Params4 A, int par, int iter)
-{
-    Hdr4 *H = A.hdr;
-    if (*(volatile int *)&H->status) return;
-    const int ne = (int)(*(volatile unsigned long long *)&H->tab[par] >> 32);
-    const Ent4 *ent = A.ent[par];
-    unsigned fallbacks = 0;
-    int nact = 0;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
-        const Ent4 en = ent[e];
-        const float4 q = load4(A, A.apex[en.f]);
-        int *V = A.vpool + (size_t)e * kV;
-        int *N = A.npool + (size_t)e * kN;
-        int nv = 1, nn = 0;
-        bool over = false;
-        V[0] = en.f;
-        for (int i = 0; i < nv && !over; i++) {
-            const Fac4 &F = A.fac[V[i]];
-            for (int k = 0; k < 4 && !over; k++) {
-                const int g = F.nb[k];
-                if (g < 0 || g >= A.fcap) {  // an unlinked ridge: internal error
-                    set_status4(H, QH_ERR_CAPACITY);
-                    over = true;
-                    break;
-                }
-                bool seen = false;
-                for (int j = 0; j < nv && !seen; j++) seen = V[j] == g;
-                for (int j = 0; j < nn && !seen; j++) seen = N[j] == g;
-                if (seen) continue;
-                float d, err;
-                if (facet_sign4(A, g, q, d, err, fallbacks) > 0) {
-                    if (nv == kV) over = true;
-                    else V[nv++] = g;
-                } else {
-                    if (nn == kN) over = true;
-                    else N[nn++] = g;
-                }
-            }
-        }
-        if (!over) {
-            const unsigned long long mine = claim_key4(iter, 0, en.f, en.len);
-            for (int j = 0; j < nv; j++) atomicMax(&A.claim[0][V[j]], mine);
-            nact++;
-        }
-        A.vn[e] = over ? make_int2(-1, -1) : make_int2(nv, nn);
-        A.cstate[e] = over ? 2 : 0;
-    }
-    const unsigned f = __reduce_add_sync(0xffffffffu, fallbacks);
-    if ((threadIdx.x & 31) == 0 && f) atomicAdd(&H->fallbacks, (unsigned long long)f);
-    const int na = __reduce_add_sync(0xffffffffu, nact);
-    if ((threadIdx.x & 31) == 0 && na) atomicAdd(&H->nact[0], na);
-}
-
 // lanes of this warp below the calling lane
 __device__ __forceinline__ unsigned lanemask_lt4()
 {
@@ -820,7 +765,9 @@ __device__ __forceinline__ unsigned lanemask_lt4()
 // The selection with one warp per candidate: the breadth-first frontier
 // spread over the lanes (each frontier facet's four neighbours, duplicates
 // merged by __match_any_sync), the lists in shared memory, new entries
-// appended by ballots.  The same visible and horizon sets as k4_select.
+// appended by ballots.  Per candidate: V = the facets its apex is strictly
+// above, reached across ridges from its own facet; N = the facets next to V
+// that are not in V; over the lists' capacity the candidate sits out.
 __global__ void __launch_bounds__(kBlock) k4_select_warp(Params4 A, int par, int iter)
 {
     __shared__ int sV[kBlock / 32][kV];
@@ -1098,9 +1045,11 @@ __device__ int cone4_warp(const Params4 &A, int f0, int len, const int *V, int n
     return 1;
 }
 
-// Round r with one warp per candidate (the lanes read the lists and the
-// claims side by side; a winner's warp builds its cone): the same decisions
-// as k4_round.
+// Round r, one warp per candidate (the lanes read the lists and the claims
+// side by side): out if an earlier round's winner deleted a facet of V or N;
+// a winner owns every facet of V in this round's claims and no facet of N
+// carries a higher one, and its warp builds its cone; a loser claims its
+// visible facets for round r + 1 in the other claim array.
 __global__ void __launch_bounds__(kBlock) k4_round_warp(Params4 A, int par, int iter, int r,
                                                         int last)
 {
@@ -1152,53 +1101,6 @@ __global__ void __launch_bounds__(kBlock) k4_round_warp(Params4 A, int par, int 
         }
     }
     if (!last && lane == 0 && nact) atomicAdd(&H->nact[r + 1], nact);
-}
-
-// Round r, one thread per candidate: out if an earlier round's winner deleted
-// a facet of V or N; a winner owns every facet of V in this round's claims
-// and no facet of N carries a higher one, and builds its cone; a loser
-// claims its visible facets for round r + 1 in the other claim array.
-__global__ void __launch_bounds__(kBlock) k4_round(Params4 A, int par, int iter, int r, int last)
-{
-    Hdr4 *H = A.hdr;
-    if (*(volatile int *)&H->status || *(volatile int *)&H->nact[r] == 0) return;
-    const int ne = (int)(*(volatile unsigned long long *)&H->tab[par] >> 32);
-    const Ent4 *ent = A.ent[par];
-    const unsigned long long *cl = A.claim[r & 1];
-    unsigned long long *cn = A.claim[(r + 1) & 1];
-    int nact = 0;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
-        if (A.cstate[e] != 0) continue;
-        const int2 c = A.vn[e];
-        int *V = A.vpool + (size_t)e * kV;
-        int *N = A.npool + (size_t)e * kN;
-        const Ent4 en = ent[e];
-        bool touched = false;
-        if (r > 0) {
-            for (int j = 0; j < c.x && !touched; j++) touched = A.taken[V[j]] == iter;
-            for (int j = 0; j < c.y && !touched; j++) touched = A.taken[N[j]] == iter;
-        }
-        if (touched) {
-            A.cstate[e] = 2;
-            continue;
-        }
-        const unsigned long long mine = claim_key4(iter, r, en.f, en.len);
-        bool win = true;
-        for (int j = 0; j < c.x && win; j++) win = cl[V[j]] == mine;
-        for (int j = 0; j < c.y && win; j++) win = cl[N[j]] < mine;
-        if (win) {
-            // the horizon list reuses the candidate's neighbour slice (kN >= 2 kV + 2)
-            if (build_cone4(A, en.f, en.len, V, c.x, N, kN, iter, r, cl)) A.cstate[e] = 1;
-        } else if (!last) {
-            const unsigned long long next = claim_key4(iter, r + 1, en.f, en.len);
-            for (int j = 0; j < c.x; j++) atomicMax(&cn[V[j]], next);
-            nact++;
-        }
-    }
-    if (!last) {
-        const int na = __reduce_add_sync(0xffffffffu, nact);
-        if ((threadIdx.x & 31) == 0 && na) atomicAdd(&H->nact[r + 1], na);
-    }
 }
 
 // No winner at all: the largest candidate (lowest facet on ties) inserted
