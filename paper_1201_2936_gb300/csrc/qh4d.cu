@@ -936,16 +936,16 @@ __device__ bool build_cone4(const Params4 &A, int f0, int len, const int *V, int
     return true;
 }
 
-// The same cone built by one warp (horizons of at most 64 ridges; returns 0
-// for a larger one, which the caller builds with build_cone4).  The horizon
-// ridges by ballots; each lane creates up to two cone facets and relinks
-// their horizon neighbours; the ridges through the apex are matched by
-// shuffling every lane's facets across the warp: the facet across facet
-// j's ridge opposite v[i] is the other cone facet holding the two
-// vertices of j other than v[i] and the apex.  Returns 1 when built, -1 on
-// a capacity failure (status raised).
+// The same cone built by one warp.  The horizon ridges by ballots; the
+// lanes create the cone facets, relink their horizon neighbours and keep
+// the cone's vertex lists in the warp's shared scratch sf (kN x 4); the
+// facet across facet j's ridge opposite v[i] (v[i] not the apex) is the
+// other cone facet holding the two vertices of j other than v[i] and the
+// apex, found by a scan of sf.  Returns 1 when built, -1 on a capacity
+// failure (status raised).
 __device__ int cone4_warp(const Params4 &A, int f0, int len, const int *V, int nv, int *hz,
-                          int hcap, int iter, int round, const unsigned long long *cl)
+                          int hcap, int iter, int round, const unsigned long long *cl,
+                          int (*sf)[4])
 {
     Hdr4 *H = A.hdr;
     const int lane = threadIdx.x & 31;
@@ -969,11 +969,10 @@ __device__ int cone4_warp(const Params4 &A, int f0, int len, const int *V, int n
         }
         nh += __popc(b);
     }
-    if (__any_sync(0xffffffffu, bad) || nh > hcap) {
+    if (__any_sync(0xffffffffu, bad) || nh > hcap || nh > kN) {
         if (lane == 0) set_status4(H, QH_ERR_CAPACITY);
         return -1;
     }
-    if (nh > 64) return 0;
     __syncwarp();
     int base = 0;
     if (lane == 0) base = atomicAdd(&H->fcount, nh);
@@ -982,13 +981,9 @@ __device__ int cone4_warp(const Params4 &A, int f0, int len, const int *V, int n
         if (lane == 0) set_status4(H, QH_ERR_CAPACITY);
         return -1;
     }
-    int fv[2][4], fk[2];
-#pragma unroll
-    for (int r = 0; r < 2; r++) {
-        const int j = lane + 32 * r;
-        fk[r] = -1;
-        for (int t = 0; t < 4; t++) fv[r][t] = -1;
-        if (j >= nh) continue;
+    // the cone facets: the horizon facet's vertices with the ridge's
+    // opposite vertex replaced by the apex; their vertex lists in sf
+    for (int j = lane; j < nh; j += 32) {
         const int hf = hz[j] >> 2, k = hz[j] & 3;
         const Fac4 F = A.fac[hf];
         int v[4] = {F.v[0], F.v[1], F.v[2], F.v[3]};
@@ -999,39 +994,26 @@ __device__ int cone4_warp(const Params4 &A, int f0, int len, const int *V, int n
         Fac4 &G = A.fac[g];
         for (int t = 0; t < 4; t++)
             if (G.nb[t] == hf) G.nb[t] = base + j;
-        for (int t = 0; t < 4; t++) fv[r][t] = v[t];
-        fk[r] = k;
+        for (int t = 0; t < 4; t++) sf[j][t] = v[t];
     }
-    // nbr[r][i]: the facet across ridge i of this lane's facet r
-    int nbr[2][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}};
-    for (int src = 0; src < 32; src++) {
-#pragma unroll
-        for (int rs = 0; rs < 2; rs++) {
-            int sv[4];
-            for (int t = 0; t < 4; t++) sv[t] = __shfl_sync(0xffffffffu, fv[rs][t], src);
-            const int sj = src + 32 * rs;
-            if (sj >= nh) continue;
-#pragma unroll
-            for (int r = 0; r < 2; r++) {
-                if (fk[r] < 0 || (src == lane && rs == r)) continue;
-                for (int i = 0; i < 4; i++) {
-                    if (i == fk[r] || nbr[r][i] >= 0) continue;
-                    int e[2], m = 0;
-                    for (int t = 0; t < 4; t++)
-                        if (t != i && t != fk[r]) e[m++] = fv[r][t];
-                    int has = 0;
-                    for (int t = 0; t < 4; t++) has += sv[t] == e[0] || sv[t] == e[1];
-                    if (has == 2) nbr[r][i] = base + sj;
-                }
+    __syncwarp();
+    for (int j = lane; j < nh; j += 32) {
+        int v[4];
+        for (int t = 0; t < 4; t++) v[t] = sf[j][t];
+        for (int i = 0; i < 4; i++) {
+            if (v[i] == qi) continue;
+            int e[2], m = 0;
+            for (int t = 0; t < 4; t++)
+                if (t != i && v[t] != qi) e[m++] = v[t];
+            int nbr = -1;
+            for (int g = 0; g < nh && nbr < 0; g++) {
+                if (g == j) continue;
+                int has = 0;
+                for (int t = 0; t < 4; t++) has += sf[g][t] == e[0] || sf[g][t] == e[1];
+                if (has == 2) nbr = base + g;
             }
+            A.fac[base + j].nb[i] = nbr;
         }
-    }
-#pragma unroll
-    for (int r = 0; r < 2; r++) {
-        const int j = lane + 32 * r;
-        if (j >= nh) continue;
-        for (int i = 0; i < 4; i++)
-            if (i != fk[r]) A.fac[base + j].nb[i] = nbr[r][i];
     }
     for (int i = lane; i < nv; i += 32) {
         A.fac[V[i]].alive = 0;
@@ -1042,6 +1024,7 @@ __device__ int cone4_warp(const Params4 &A, int f0, int len, const int *V, int n
         atomicAdd(&H->hull_vertices, 1);
         atomicAdd(&H->nwin, 1);
     }
+    __syncwarp();
     return 1;
 }
 
@@ -1059,6 +1042,7 @@ __global__ void __launch_bounds__(kBlock) k4_round_warp(Params4 A, int par, int 
     const Ent4 *ent = A.ent[par];
     const unsigned long long *cl = A.claim[r & 1];
     unsigned long long *cn = A.claim[(r + 1) & 1];
+    __shared__ int sF[kBlock / 32][kN][4];  // each warp's cone vertex lists
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -1087,13 +1071,9 @@ __global__ void __launch_bounds__(kBlock) k4_round_warp(Params4 A, int par, int 
             if (lane == 0) A.cstate[e] = 2;
         } else if (!lose) {
             // the horizon list reuses the candidate's neighbour slice (kN >= 2 kV + 2)
-            const int b = cone4_warp(A, en.f, en.len, V, c.x, N, kN, iter, r, cl);
-            if (b > 0) {
-                if (lane == 0) A.cstate[e] = 1;
-            } else if (b == 0 && lane == 0) {
-                if (build_cone4(A, en.f, en.len, V, c.x, N, kN, iter, r, cl)) A.cstate[e] = 1;
-            }
-            __syncwarp();
+            const int b = cone4_warp(A, en.f, en.len, V, c.x, N, kN, iter, r, cl,
+                                     sF[threadIdx.x >> 5]);
+            if (b > 0 && lane == 0) A.cstate[e] = 1;
         } else if (!last) {
             const unsigned long long next = claim_key4(iter, r + 1, en.f, en.len);
             for (int j = lane; j < c.x; j += 32) atomicMax(&cn[V[j]], next);
