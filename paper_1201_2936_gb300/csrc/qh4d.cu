@@ -432,15 +432,18 @@ __global__ void k4_build(Params4 A)
 // "in" the pseudo facet whose cone is the simplex) goes to the first facet
 // of its winner's cone that it is strictly above, else it is discarded;
 // code[v] = (target, rank in the target's segment) or (-1, 0); points of
-// surviving facets get (-2, 0).  Counts, ranks and farthest-point keys are
-// aggregated per warp (match) and per tile (shared hash), one global
-// reservation per (tile, target).
+// surviving facets get (-2, their segment's table entry).  Each tile's
+// segments are staged in shared memory first.  Counts, ranks and
+// farthest-point keys are aggregated per warp (match) and per tile (shared
+// hash), one global reservation per (tile, target).
 template <bool FIRST>
 __global__ void __launch_bounds__(kBlock) k4_assign(Params4 A, int par)
 {
     __shared__ int skey[kSlots4], scnt[kSlots4], sbase[kSlots4];
     __shared__ unsigned long long sk1[kSlots4];
     __shared__ unsigned so2[kSlots4], sem[kSlots4];
+    __shared__ int sst[kTile], sfa[kTile];  // the tile's segments: start, facet
+    __shared__ int s_m;
     Hdr4 *H = A.hdr;
     if (*(volatile int *)&H->status) return;
     const unsigned long long tb = *(volatile unsigned long long *)&H->tab[par];
@@ -463,6 +466,41 @@ __global__ void __launch_bounds__(kBlock) k4_assign(Params4 A, int par)
             sem[i] = 0u;
         }
         __syncthreads();
+        // the tile's segments, staged: the last one starting at or before
+        // the tile (probes over the table, each round narrowing the interval
+        // to one probe gap), then every one starting inside it
+        int e0 = 0;
+        if (!FIRST) {
+            const int v0 = tile * kTile, v1 = min(v0 + kTile, L);
+            int lo = 0, hi = ne - 1;  // the answer is in [lo, hi]
+            for (int round = 0; round < 6 && hi > lo; round++) {
+                const long long span = (long long)(hi - lo + 1);
+                const int pi = lo + (int)((long long)threadIdx.x * span / blockDim.x);
+                const int c = __syncthreads_count(ent[pi].start <= v0);  // >= 1: start[lo] <= v0
+                const int nlo = lo + (int)((long long)(c - 1) * span / blockDim.x);
+                const int nhi = c < (int)blockDim.x ? lo + (int)((long long)c * span / blockDim.x) - 1 : hi;
+                lo = nlo;
+                hi = nhi < nlo ? nlo : nhi;
+            }
+            e0 = lo;
+            if (threadIdx.x == 0) s_m = 0;
+            __syncthreads();
+            int mine = 0;
+            for (int i = threadIdx.x; i < kTile; i += blockDim.x) {
+                const int e = e0 + i;
+                if (e < ne) {
+                    const Ent4 en = ent[e];
+                    if (i == 0 || en.start < v1) {
+                        sst[i] = en.start;
+                        sfa[i] = en.f;
+                        mine++;
+                    }
+                }
+            }
+            if (mine) atomicAdd(&s_m, mine);
+            __syncthreads();
+        }
+        const int m = FIRST ? 0 : s_m;  // the staged entries are a prefix (starts increase)
         int tgt[kItems], rk[kItems], slot[kItems];
 #pragma unroll
         for (int k = 0; k < kItems; k++) {
@@ -474,13 +512,14 @@ __global__ void __launch_bounds__(kBlock) k4_assign(Params4 A, int par)
             int idx = 0;
             if (valid) {
                 if (!FIRST) {
-                    int lo = 0, hi = ne - 1;
+                    int lo = 0, hi = m - 1;
                     while (lo < hi) {
                         const int mid = (lo + hi + 1) >> 1;
-                        if (ent[mid].start <= v) lo = mid;
+                        if (sst[mid] <= v) lo = mid;
                         else hi = mid - 1;
                     }
-                    f = ent[lo].f;
+                    f = sfa[lo];
+                    rank = e0 + lo;  // a surviving facet's points keep their segment
                 }
                 dead = FIRST || !A.fac[f].alive;
                 if (dead) {
@@ -546,7 +585,7 @@ __global__ void __launch_bounds__(kBlock) k4_assign(Params4 A, int par)
                 rank = base + __popc(grp & lt);
             }
             tgt[k] = !valid ? -3 : (!dead ? -2 : target);
-            rk[k] = rank;
+            rk[k] = rank;  // the rank in the target's segment, or the surviving segment
             slot[k] = cone_t ? s : -1;
         }
         __syncthreads();
@@ -567,7 +606,7 @@ __global__ void __launch_bounds__(kBlock) k4_assign(Params4 A, int par)
         for (int k = 0; k < kItems; k++) {
             const int v = tile * kTile + k * blockDim.x + threadIdx.x;
             if (tgt[k] == -3) continue;
-            int r = 0;
+            int r = tgt[k] == -2 ? rk[k] : 0;
             if (tgt[k] >= 0) r = slot[k] >= 0 ? sbase[slot[k]] + rk[k] : rk[k];
             A.code[v] = make_int2(tgt[k] == -3 ? -1 : tgt[k], r);
         }
@@ -650,7 +689,6 @@ __global__ void __launch_bounds__(kBlock) k4_scatter(Params4 A, int par)
     if (*(volatile int *)&H->status) return;
     const unsigned long long tb = *(volatile unsigned long long *)&H->tab[par];
     const int L = FIRST ? A.n : (int)(tb & 0xffffffffull);
-    const int ne = (int)(tb >> 32);
     const Ent4 *ent = A.ent[par];
     float4 *Q = A.pts[par ^ 1];
     int *QI = A.pidx[par ^ 1];
@@ -659,14 +697,8 @@ __global__ void __launch_bounds__(kBlock) k4_scatter(Params4 A, int par)
         const int v = (int)vv;
         int dst = -1;
         const int2 cr = A.code[v];
-        if (cr.x == -2) {  // a surviving facet: the segment moves whole
-            int lo = 0, hi = ne - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (ent[mid].start <= v) lo = mid;
-                else hi = mid - 1;
-            }
-            const Ent4 en = ent[lo];
+        if (cr.x == -2) {  // a surviving facet: the segment (cr.y) moves whole
+            const Ent4 en = ent[cr.y];
             dst = A.nstart[en.f] + (v - en.start);
         } else if (cr.x >= 0) {
             dst = A.nstart[cr.x] + cr.y;
