@@ -243,14 +243,17 @@ __global__ void __launch_bounds__(kBlock) k4_extrema(Params4 A)
 __global__ void k4_extrema_final(Params4 A, int nblk)
 {
     Hdr4 *H = A.hdr;
-    if (threadIdx.x != 0) return;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x >= 32) return;
     if (H->nonfinite) {
-        set_status4(H, QH_ERR_NONFINITE);
+        if (lane == 0) set_status4(H, QH_ERR_NONFINITE);
         return;
     }
+    // each lane over a stride of the blocks' results, then the lanes'
+    // results by shuffles (same order and lowest-index rules)
     float4 mn = A.blk_a[0], mx = A.blk_b[0];
     int mni = A.blk_ai[0], mxi = A.blk_bi[0];
-    for (int b = 1; b < nblk; b++) {
+    for (int b = lane; b < nblk; b += 32) {
         if (lex_less4(A.blk_a[b], A.blk_ai[b], mn, mni)) {
             mn = A.blk_a[b];
             mni = A.blk_ai[b];
@@ -260,6 +263,27 @@ __global__ void k4_extrema_final(Params4 A, int nblk)
             mxi = A.blk_bi[b];
         }
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        const float4 pa = make_float4(__shfl_xor_sync(0xffffffffu, mn.x, o),
+                                      __shfl_xor_sync(0xffffffffu, mn.y, o),
+                                      __shfl_xor_sync(0xffffffffu, mn.z, o),
+                                      __shfl_xor_sync(0xffffffffu, mn.w, o));
+        const int pai = __shfl_xor_sync(0xffffffffu, mni, o);
+        const float4 pb = make_float4(__shfl_xor_sync(0xffffffffu, mx.x, o),
+                                      __shfl_xor_sync(0xffffffffu, mx.y, o),
+                                      __shfl_xor_sync(0xffffffffu, mx.z, o),
+                                      __shfl_xor_sync(0xffffffffu, mx.w, o));
+        const int pbi = __shfl_xor_sync(0xffffffffu, mxi, o);
+        if (lex_less4(pa, pai, mn, mni)) {
+            mn = pa;
+            mni = pai;
+        }
+        if (lex_greater4(pb, pbi, mx, mxi)) {
+            mx = pb;
+            mxi = pbi;
+        }
+    }
+    if (lane != 0) return;
     H->simplex[0] = mni;
     H->simplex[1] = mxi;
     if (mn.x == mx.x && mn.y == mx.y && mn.z == mx.z && mn.w == mx.w)
@@ -333,14 +357,24 @@ __device__ bool off_span4(const Params4 &A, int step, int i)
 __global__ void k4_far_final(Params4 A, int nblk, int step)
 {
     Hdr4 *H = A.hdr;
-    if (threadIdx.x != 0 || H->status) return;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x >= 32 || H->status) return;
     float bv = -2.0f;
     int bi = INT_MAX;
-    for (int b = 0; b < nblk; b++)
+    for (int b = lane; b < nblk; b += 32)
         if (A.blk_v[b] > bv || (A.blk_v[b] == bv && A.blk_i[b] < bi)) {
             bv = A.blk_v[b];
             bi = A.blk_i[b];
         }
+    for (int o = 16; o > 0; o >>= 1) {
+        const float v = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int i = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (v > bv || (v == bv && i < bi)) {
+            bv = v;
+            bi = i;
+        }
+    }
+    if (lane != 0) return;
     H->search_idx = INT_MAX;
     H->cand_ok = bi >= 0 && bi < A.n && off_span4(A, step, bi);
     if (H->cand_ok) H->simplex[step] = bi;
