@@ -75,6 +75,12 @@ struct Ent4 {
     int f, start, len, pad;
 };
 
+struct Basis4 {
+    float o[4];
+    float b[3][4];
+    int nb;
+};
+
 struct Hdr4 {
     int status, nonfinite;
     int fcount, nwin, n_uncert, iter;
@@ -89,6 +95,7 @@ struct Hdr4 {
     // output stage
     int nalive, npair, nuniq, ngroup, nvert, sort_m, uf_fail;
     long long nfidx;
+    Basis4 basis;               // span of the first simplex so far (its construction)
 };
 
 struct Params4 {
@@ -290,17 +297,48 @@ __global__ void k4_extrema_final(Params4 A, int nblk)
         set_status4(H, QH_ERR_DEGENERATE);
 }
 
-// Squared distance from the affine span of the simplex so far (origin s0,
-// orthonormal directions B[0..nb) from the host), FP32; the farthest point
-// (lowest index on ties) per block.
-struct Basis4 {
-    float o[4];
-    float b[3][4];
-    int nb;
-};
-
-__global__ void __launch_bounds__(kBlock) k4_far(Params4 A, Basis4 B)
+// Basis of the affine span of simplex[0..step) (Gram-Schmidt in FP64 on
+// the device, one thread); it only chooses the next candidate, which an
+// exact test confirms.
+__global__ void k4_basis(Params4 A, int step)
 {
+    Hdr4 *H = A.hdr;
+    if (threadIdx.x != 0 || H->status) return;
+    double P[4][4];
+    for (int k = 0; k < step; k++) {
+        const float4 c = load4(A, H->simplex[k]);
+        P[k][0] = c.x;
+        P[k][1] = c.y;
+        P[k][2] = c.z;
+        P[k][3] = c.w;
+    }
+    double Bd[3][4];
+    for (int k = 0; k < step - 1; k++) {
+        for (int d = 0; d < 4; d++) Bd[k][d] = P[k + 1][d] - P[0][d];
+        for (int r = 0; r < k; r++) {
+            double dp = 0;
+            for (int d = 0; d < 4; d++) dp += Bd[k][d] * Bd[r][d];
+            for (int d = 0; d < 4; d++) Bd[k][d] -= dp * Bd[r][d];
+        }
+        double nr = 0;
+        for (int d = 0; d < 4; d++) nr += Bd[k][d] * Bd[k][d];
+        nr = sqrt(nr);
+        for (int d = 0; d < 4; d++) Bd[k][d] = nr > 0 ? Bd[k][d] / nr : 0.0;
+    }
+    Basis4 &B = H->basis;
+    for (int d = 0; d < 4; d++) B.o[d] = (float)P[0][d];
+    for (int k = 0; k < 3; k++)
+        for (int d = 0; d < 4; d++) B.b[k][d] = k < step - 1 ? (float)Bd[k][d] : 0.0f;
+    B.nb = step - 1;
+}
+
+// Squared distance from the affine span of the simplex so far (origin s0,
+// orthonormal directions from k4_basis), FP32; the farthest point (lowest
+// index on ties) per block.
+__global__ void __launch_bounds__(kBlock) k4_far(Params4 A)
+{
+    if (*(volatile int *)&A.hdr->status) return;
+    const Basis4 B = A.hdr->basis;
     __shared__ float sv[kBlock];
     __shared__ int si[kBlock];
     float best = -1.0f;
@@ -1608,42 +1646,6 @@ cudaError_t read_hdr(const Params4 &A, Hdr4 &h, cudaStream_t st)
     return cudaStreamSynchronize(st);
 }
 
-// Host-side basis of the affine span of simplex[0..step) (Gram-Schmidt in
-// FP64 on the points read back); only chooses the next candidate, which an
-// exact test confirms.
-bool basis_of(const Params4 &A, const Hdr4 &h, int step, Basis4 &B, cudaStream_t st)
-{
-    double P[4][4];
-    for (int k = 0; k < step; k++) {
-        float c[4];
-        const float *src[4] = {A.x, A.y, A.z, A.w};
-        for (int d = 0; d < 4; d++)
-            if (cudaMemcpyAsync(&c[d], src[d] + (long long)h.simplex[k] * A.stride, sizeof(float),
-                                cudaMemcpyDeviceToHost, st) != cudaSuccess)
-                return false;
-        if (cudaStreamSynchronize(st) != cudaSuccess) return false;
-        for (int d = 0; d < 4; d++) P[k][d] = c[d];
-    }
-    double Bd[3][4];
-    for (int k = 0; k < step - 1; k++) {
-        for (int d = 0; d < 4; d++) Bd[k][d] = P[k + 1][d] - P[0][d];
-        for (int r = 0; r < k; r++) {
-            double dp = 0;
-            for (int d = 0; d < 4; d++) dp += Bd[k][d] * Bd[r][d];
-            for (int d = 0; d < 4; d++) Bd[k][d] -= dp * Bd[r][d];
-        }
-        double nr = 0;
-        for (int d = 0; d < 4; d++) nr += Bd[k][d] * Bd[k][d];
-        nr = std::sqrt(nr);
-        for (int d = 0; d < 4; d++) Bd[k][d] = nr > 0 ? Bd[k][d] / nr : 0.0;
-    }
-    for (int d = 0; d < 4; d++) B.o[d] = (float)P[0][d];
-    for (int k = 0; k < 3; k++)
-        for (int d = 0; d < 4; d++) B.b[k][d] = k < step - 1 ? (float)Bd[k][d] : 0.0f;
-    B.nb = step - 1;
-    return true;
-}
-
 }  // namespace
 
 extern "C" qh_status qh_hull4d(const float *d_x, const float *d_y, const float *d_z,
@@ -1700,9 +1702,8 @@ extern "C" qh_status qh_hull4d(const float *d_x, const float *d_y, const float *
     if (h.status) return finish((qh_status)h.status, h);
     if (n < 5) return finish(QH_ERR_DEGENERATE, h);
     for (int step = 2; step <= 4; step++) {
-        Basis4 B;
-        if (!basis_of(A, h, step, B, st)) return QH_ERR_CUDA;
-        k4_far<<<g, kBlock, 0, st>>>(A, B);
+        k4_basis<<<1, 32, 0, st>>>(A, step);
+        k4_far<<<g, kBlock, 0, st>>>(A);
         k4_far_final<<<1, 32, 0, st>>>(A, g, step);
         k4_search<<<g, kBlock, 0, st>>>(A, step);
         k4_take<<<1, 32, 0, st>>>(A, step);
