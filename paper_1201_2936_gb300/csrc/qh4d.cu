@@ -1745,10 +1745,9 @@ extern "C" qh_status qh_hull4d(const float *d_x, const float *d_y, const float *
         k4_assign<false><<<grid_of4((Lc + kItems - 1) / kItems), kBlock, 0, st>>>(A, cur);
         k4_table<<<grid_of4(ne + 64), kBlock, 0, st>>>(A, cur, 0);
         k4_scatter<false><<<grid_of4(Lc), kBlock, 0, st>>>(A, cur);
-        if (read_hdr(A, h, st) != cudaSuccess) return QH_ERR_CUDA;
-        if (h.status) return finish((qh_status)h.status, h);
-        if (h.n_uncert > 0)
-            k4_exact<<<std::min(h.n_uncert, 8 * sm_count()), kBlock, 0, st>>>(A, cur);
+        // the exact step reads its count on the device (no readback here;
+        // the next iteration's read checks the status)
+        k4_exact<<<2 * sm_count(), kBlock, 0, st>>>(A, cur);
         cur ^= 1;
     }
     // ---- output stage
