@@ -424,9 +424,9 @@ __device__ __forceinline__ void dir_of(int k, int &dx, int &dy, int &dz)
 // tie), kept in H->dirkey by one atomic per CTA and direction.  Which point
 // each direction finds only shapes the first polytope: every point of it is
 // an input point, so the hull does not depend on it.
-// The directions the first polytope uses: all 26, or the 6 axes and the 8
-// diagonals (direction k of dir_of for k < kNumDirs).
-constexpr int kNumDirs = kInitDirs == 1 ? kDirs : 14;
+// The directions the first polytope uses: all 26 (option 1), the 6 axes and
+// the 8 diagonals (option 2), or the 6 axes (option 3).
+constexpr int kNumDirs = kInitDirs == 1 ? kDirs : (kInitDirs == 3 ? 6 : 14);
 __device__ __forceinline__ void used_dir(int k, int &dx, int &dy, int &dz)
 {
     if (kInitDirs == 1) {

@@ -34,7 +34,7 @@ constexpr int kDirs = 26;  // directions of the first polytope: the non-zero vec
 #define QH3D_INITDIRS 2
 #endif
 // single cloud: start from that polytope (0: the tetrahedron; 1: all 26
-// directions; 2: the 14 of the axes and the diagonals)
+// directions; 2: the 14 of the axes and the diagonals; 3: the 6 axes)
 constexpr int kInitDirs = QH3D_INITDIRS;
 // the selection and its claim rounds take one warp per candidate while
 // there are at most this many candidates per warp of the grid, else one
