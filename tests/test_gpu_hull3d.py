@@ -163,3 +163,25 @@ def test_near_sphere_full_size(qh):
     assert res["status"] == 0
     assert gv == ov
     assert gf == of
+
+
+def test_first_polytope_extreme_copies_and_signed_zeros(qh):
+    # the single-cloud first polytope starts from each direction's extreme
+    # point (axes and diagonals): put copies of those points at lower and
+    # higher indices, with -0.0 in place of 0.0 in some copies, so that each
+    # direction's maximum ties across copies (the lowest index must win, as
+    # in the oracle)
+    rng = np.random.default_rng(64)
+    inner = (0.8 * np.stack(w.uniform_ball(30_000, 65), axis=1)).astype(np.float32)
+    ext = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1],
+                    [.6, .6, .5], [-.6, .6, .5], [.6, -.6, .5], [-.6, -.6, .5],
+                    [.6, .6, -.5], [-.6, .6, -.5], [.6, -.6, -.5], [-.6, -.6, -.5]], np.float32)
+    negz = ext.copy()
+    negz[negz == 0] = np.float32(-0.0)
+    P = np.concatenate([negz[rng.permutation(14)], inner, ext, negz])
+    for perm in (np.arange(len(P)), rng.permutation(len(P))):
+        Q = P[perm]
+        want = _oracle(Q[:, 0], Q[:, 1], Q[:, 2])
+        for pred in ("f32", "f64"):
+            v, f, _ = _gpu(qh, Q[:, 0], Q[:, 1], Q[:, 2], pred=pred)
+            assert (v, f) == (want[0], want[1]), pred
