@@ -386,7 +386,7 @@ size_t qh_workspace_bytes_4d(int64_t n, const qh_opts *opts);
  * dimensions; read as Barber et al.'s Quickhull in R^4, several
  * non-conflicting apexes inserted per iteration, horizon ridges are
  * triangles).  The iterations are driven from the host (one launch per
- * phase, the table sizes read back once per iteration).
+ * phase; the header is read back once per batch of up to 4 iterations).
  *
  *  d_x .. d_w     device, coordinate i at d_c[i*stride] (read only)
  *  d_verts        device int32[max(n,1)]: the extreme points, increasing index
@@ -470,12 +470,14 @@ qh_status qh_debug_timeline_2d(const void *d_ws, int64_t n, int64_t *h_rows, int
 qh_status qh_debug_timeline_3d(const void *d_ws, int64_t n, int64_t *h_rows, int32_t max_rows,
                                int32_t *h_nrows, cudaStream_t stream);
 
-/* Per-iteration record of the last qh_hull4d call made by the calling host
- * thread: row r (h_rows: int64[9 * max_rows]) holds {iteration, segments,
- * live points, apexes inserted in the previous iteration, apexes that
- * needed the exact farthest-point step, host ns of the iteration, then the
- * candidates that claimed in selection rounds 0, 1 and 2 of the previous
- * iteration}; at most 4096 rows.  Diagnostics only. */
+/* Record of the last qh_hull4d call made by the calling host thread, one
+ * row per read of its header (the host loop reads it once per batch of up
+ * to 4 iterations): row r (h_rows: int64[9 * max_rows]) holds {iterations
+ * enqueued so far, segments, live points, apexes inserted in the last
+ * iteration, apexes that needed the exact farthest-point step, host ns
+ * since the previous row, then the candidates that claimed in selection
+ * rounds 0, 1 and 2 of the last iteration}; at most 4096 rows.
+ * Diagnostics only. */
 qh_status qh_debug_timeline_4d(int64_t *h_rows, int32_t max_rows, int32_t *h_nrows);
 
 /*

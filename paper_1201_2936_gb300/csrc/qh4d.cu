@@ -1235,7 +1235,9 @@ __global__ void k4_iter_begin(Params4 A, int par, int iter)
 {
     Hdr4 *H = A.hdr;
     if (threadIdx.x != 0) return;
-    H->iter = iter;
+    // (an iteration enqueued after the last segment was done changes
+    // nothing, and is not counted)
+    if (H->tab[par] != 0ull) H->iter = iter;
     H->nwin = 0;
     for (int r = 0; r < 8; r++) H->nact[r] = 0;
     H->tab[par ^ 1] = 0ull;
@@ -1722,6 +1724,11 @@ extern "C" qh_status qh_hull4d(const float *d_x, const float *d_y, const float *
     int cur = 1, iter = 0;
     g_tl4.clear();
     auto t_prev = std::chrono::steady_clock::now();
+    // up to kBatch iterations are enqueued between two reads of the header:
+    // every kernel takes its sizes from the header on the device, so an
+    // iteration enqueued after the hull is done does nothing; the grids of
+    // the batch's later iterations allow for growth (any grid is correct)
+    constexpr int kBatch = 4;
     for (;;) {
         if (read_hdr(A, h, st) != cudaSuccess) return QH_ERR_CUDA;
         if (h.status) return finish((qh_status)h.status, h);
@@ -1735,20 +1742,25 @@ extern "C" qh_status qh_hull4d(const float *d_x, const float *d_y, const float *
             t_prev = t;
         }
         if (ne == 0) break;
-        if (++iter > A.max_iters) return finish(QH_ERR_NO_CONVERGENCE, h);
-        k4_iter_begin<<<1, 32, 0, st>>>(A, cur, iter);
-        k4_select_warp<<<grid_of4(32ll * ne), kBlock, 0, st>>>(A, cur, iter);
-        for (int rr = 0; rr < kRounds4; rr++)
-            k4_round_warp<<<grid_of4(32ll * ne), kBlock, 0, st>>>(A, cur, iter, rr,
-                                                                rr == kRounds4 - 1);
-        k4_fallback<<<1, 32, 0, st>>>(A, cur, iter);
-        k4_assign<false><<<grid_of4((Lc + kItems - 1) / kItems), kBlock, 0, st>>>(A, cur);
-        k4_table<<<grid_of4(ne + 64), kBlock, 0, st>>>(A, cur, 0);
-        k4_scatter<false><<<grid_of4(Lc), kBlock, 0, st>>>(A, cur);
-        // the exact step reads its count on the device (no readback here;
-        // the next iteration's read checks the status)
-        k4_exact<<<2 * sm_count(), kBlock, 0, st>>>(A, cur);
-        cur ^= 1;
+        if (iter >= A.max_iters) return finish(QH_ERR_NO_CONVERGENCE, h);
+        const int nb = (int)std::min<long long>(kBatch, A.max_iters - iter);
+        for (int b = 0; b < nb; b++) {
+            ++iter;
+            const long long grow = 1ll << (2 * b);
+            const long long ne_b = (long long)ne * grow, L_b = std::min<long long>((long long)Lc, n);
+            k4_iter_begin<<<1, 32, 0, st>>>(A, cur, iter);
+            k4_select_warp<<<grid_of4(32ll * ne_b), kBlock, 0, st>>>(A, cur, iter);
+            for (int rr = 0; rr < kRounds4; rr++)
+                k4_round_warp<<<grid_of4(32ll * ne_b), kBlock, 0, st>>>(A, cur, iter, rr,
+                                                                    rr == kRounds4 - 1);
+            k4_fallback<<<1, 32, 0, st>>>(A, cur, iter);
+            k4_assign<false><<<grid_of4((L_b + kItems - 1) / kItems), kBlock, 0, st>>>(A, cur);
+            k4_table<<<grid_of4(ne_b + 64), kBlock, 0, st>>>(A, cur, 0);
+            k4_scatter<false><<<grid_of4(L_b), kBlock, 0, st>>>(A, cur);
+            // the exact step reads its count on the device
+            k4_exact<<<2 * sm_count(), kBlock, 0, st>>>(A, cur);
+            cur ^= 1;
+        }
     }
     // ---- output stage
     using d3::radix_sort;
