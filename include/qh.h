@@ -551,7 +551,9 @@ qh_status qh_debug_phases_3d(const void *d_ws, int64_t *h_ns, cudaStream_t strea
  *   count and status in d_results[c] (device qh_result[k], as
  *   qh_hull2d_multi_async writes them); h_lo[c] is the shard's first global
  *   index; h_dcoord[c * dim + d] (device) the shard's coordinate d, point i
- *   at [i * stride].  Cloud c's block at d_block + c * words: word 0 =
+ *   at [i * stride] (may be null for an empty shard; a shard with points
+ *   and a null coordinate array is reported as QH_ERR_INVALID_ARG through
+ *   its count word).  Cloud c's block at d_block + c * words: word 0 =
  *   count, words 1 + j = h_lo[c] + local index j, words 1 + (1 + d) * cap + j
  *   = coordinate d of that point (float bits), for j < min(count, cap); a
  *   failed shard's count word is minus its status.

@@ -43,7 +43,11 @@ struct LocalArgs {
 __global__ void k_local(LocalArgs A, const qh_result *res, int32_t *block)
 {
     const int c = blockIdx.y;
-    const int st = res[c].status;
+    int st = res[c].status;
+    // an empty shard may come without coordinates; a shard with points may not
+    bool have = true;
+    for (int d = 0; d < A.dim; d++) have = have && A.coord[c][d] != nullptr;
+    if (st == 0 && res[c].count > 0 && !have) st = QH_ERR_INVALID_ARG;
     const long long cnt = st == 0 ? res[c].count : 0;
     int32_t *b = block + (long long)c * block_words(A.dim, A.cap);
     if (blockIdx.x == 0 && threadIdx.x == 0) b[0] = st == 0 ? (int32_t)cnt : -st;
@@ -151,10 +155,7 @@ extern "C" qh_status qh_shard_local(int32_t k, int32_t dim, const int32_t *const
         if (!h_dout[c] || h_lo[c] < 0) return QH_ERR_INVALID_ARG;
         A.out[c] = h_dout[c];
         A.lo[c] = h_lo[c];
-        for (int d = 0; d < dim; d++) {
-            if (!h_dcoord[c * dim + d]) return QH_ERR_INVALID_ARG;
-            A.coord[c][d] = h_dcoord[c * dim + d];
-        }
+        for (int d = 0; d < dim; d++) A.coord[c][d] = h_dcoord[c * dim + d];  // null: empty shard
     }
     k_local<<<dim3(grid_x(cap), k), kBlock, 0, st>>>(A, (const qh_result *)d_results, d_block);
     return cudaGetLastError() == cudaSuccess ? QH_OK : QH_ERR_CUDA;

@@ -164,3 +164,33 @@ def test_select_device_and_host_rounds_agree_on_medians(qh):
     host, it_h = qh.select(V, O, K, return_iters=True, loop="host")
     assert got.cpu().tolist() == host.cpu().tolist() == oracle.select(v, off, k).tolist()
     assert it_d == it_h
+
+
+def test_select_edge_cases_device_loop(qh):
+    # NaNs (ordered at the ends by their bits), every segment of one element,
+    # and one long segment (global rounds) at its first and last rank
+    rng = np.random.default_rng(23)
+    v = rng.standard_normal(20_000).astype(np.float32)
+    v[rng.integers(0, 20_000, 50)] = np.float32(np.nan)
+    v[rng.integers(0, 20_000, 50)] = -np.float32(np.nan)
+    off = np.array([0, 9_000, 9_001, 20_000], np.int64)
+    for k in ([0, 0, 0], [8_999, 0, 10_998], [4_500, 0, 5_000]):
+        k = np.array(k, np.int64)
+        want = oracle.select(v, off, k)
+        got = qh.select(torch.from_numpy(v).cuda(), torch.from_numpy(off).cuda(),
+                        torch.from_numpy(k).cuda())
+        assert got.cpu().numpy().tolist() == want.tolist(), k
+    n = 3000
+    v1 = rng.standard_normal(n).astype(np.float32)
+    off1 = np.arange(n + 1, dtype=np.int64)
+    k1 = np.zeros(n, np.int64)
+    got = qh.select(torch.from_numpy(v1).cuda(), torch.from_numpy(off1).cuda(),
+                    torch.from_numpy(k1).cuda())
+    assert got.cpu().numpy().tolist() == list(range(n))
+    big = rng.standard_normal(150_000).astype(np.float32)
+    offb = np.array([0, 150_000], np.int64)
+    for kk in (0, 149_999, 77_777):
+        kb = np.array([kk], np.int64)
+        got = qh.select(torch.from_numpy(big).cuda(), torch.from_numpy(offb).cuda(),
+                        torch.from_numpy(kb).cuda())
+        assert got.cpu().numpy().tolist() == oracle.select(big, offb, kb).tolist(), kk

@@ -79,3 +79,18 @@ def test_single_rank_sharded_hull3d_faces_match():
     assert v.cpu().numpy().tolist() == wv.tolist()
     assert [idx[off[i]:off[i + 1]].tolist() for i in range(len(off) - 1)] == \
         [f.tolist() for f in wf]
+
+
+def test_sharded_2d_more_ranks_than_points():
+    # 8 ranks over 5 and 9 points: some shards are empty, the result is still
+    # the whole cloud's hull
+    from paper_1201_2936_gb300 import build
+    build.build()
+    oracle.build()
+    rng = np.random.default_rng(99)
+    clouds = [tuple(rng.random((2, 5)).astype(np.float32)),
+              tuple(rng.random((2, 9)).astype(np.float32))]
+    hulls, st = _simulated(clouds, 8, cap=64)
+    assert st == [0, 0]
+    for h, (x, y) in zip(hulls, clouds):
+        assert h.cpu().numpy().tolist() == oracle.hull2d(x, y).tolist()
