@@ -219,3 +219,14 @@ def test_many_vertices_on_circle(qh):
     got, res = _gpu(qh, x, y, pred="f32", loop="persistent")
     assert res["status"] == 0
     assert got.tolist() == want.tolist()
+
+
+@pytest.mark.parametrize("scale", [1e-20, 1e-30, 1e20])
+def test_filter_scales_2d(qh, scale):
+    x, y = w.uniform_disk(200_000, 67)
+    s = np.float32(scale)
+    X, Y = (x * s).astype(np.float32), (y * s).astype(np.float32)
+    want = oracle.hull2d(X, Y).tolist()
+    for loop in ("persistent", "host"):
+        got = qh.hull2d(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), loop=loop)
+        assert got.cpu().numpy().tolist() == want, loop

@@ -185,3 +185,16 @@ def test_first_polytope_extreme_copies_and_signed_zeros(qh):
         for pred in ("f32", "f64"):
             v, f, _ = _gpu(qh, Q[:, 0], Q[:, 1], Q[:, 2], pred=pred)
             assert (v, f) == (want[0], want[1]), pred
+
+
+@pytest.mark.parametrize("scale", [1e-20, 1e-30])
+def test_filter_underflow_scales(qh, scale):
+    # products of coordinate differences below FP32's normal range: the
+    # filters must not decide on underflowed values
+    x, y, z = w.uniform_ball(60_000, 66)
+    s = np.float32(scale)
+    X, Y, Z = ((c * s).astype(np.float32) for c in (x, y, z))
+    want = _oracle(X, Y, Z)
+    for pred in ("f32", "f64"):
+        v, f, _ = _gpu(qh, X, Y, Z, pred=pred)
+        assert (v, f) == (want[0], want[1]), pred

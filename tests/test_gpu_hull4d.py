@@ -117,3 +117,15 @@ def test_degenerate_and_nonfinite(qh):
     assert ei.value.status == 2
     gv, gf, res = _gpu(qh, *(np.zeros(0, np.float32) for _ in range(4)))
     assert gv == [] and gf == [] and res["status"] == 0
+
+
+@pytest.mark.parametrize("scale", [1e13, 1e-20])
+def test_filter_overflow_and_underflow_scales(qh, scale):
+    # coordinates whose FP32 filter products overflow (1e13) or underflow
+    # (1e-20): the exact path decides, the hull is the oracle's
+    x, y, z, ww = w.uniform_ball_4d(20_000, 76)
+    s = np.float32(scale)
+    P = [(c * s).astype(np.float32) for c in (x, y, z, ww)]
+    gv, gf, res = _gpu(qh, *P)
+    assert res["status"] == 0
+    assert (gv, gf) == _oracle(*P)
