@@ -198,3 +198,16 @@ def test_filter_underflow_scales(qh, scale):
     for pred in ("f32", "f64"):
         v, f, _ = _gpu(qh, X, Y, Z, pred=pred)
         assert (v, f) == (want[0], want[1]), pred
+
+
+def test_every_point_twice_and_signed_zeros(qh):
+    rng = np.random.default_rng(68)
+    pts = np.stack(w.uniform_ball(50_000, 69), axis=1).astype(np.float32)
+    pts[rng.integers(0, 50_000, 2_000), rng.integers(0, 3, 2_000)] = np.float32(0.0)
+    twin = pts.copy()
+    twin[twin == 0] = np.float32(-0.0)
+    P = np.concatenate([pts, twin, pts[rng.permutation(50_000)]])
+    want = _oracle(P[:, 0], P[:, 1], P[:, 2])
+    for pred in ("f32", "f64"):
+        v, f, _ = _gpu(qh, P[:, 0], P[:, 1], P[:, 2], pred=pred)
+        assert (v, f) == (want[0], want[1]), pred

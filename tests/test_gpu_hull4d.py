@@ -129,3 +129,18 @@ def test_filter_overflow_and_underflow_scales(qh, scale):
     gv, gf, res = _gpu(qh, *P)
     assert res["status"] == 0
     assert (gv, gf) == _oracle(*P)
+
+
+def test_every_point_twice_and_signed_zeros(qh):
+    # each point also at a higher index, some of the copies with -0.0 for
+    # 0.0: every vertex is reported by its lowest index, as in the oracle
+    rng = np.random.default_rng(77)
+    pts = np.stack(w.uniform_ball_4d(4_000, 78), axis=1).astype(np.float32)
+    pts[rng.integers(0, 4_000, 200), rng.integers(0, 4, 200)] = np.float32(0.0)
+    twin = pts.copy()
+    twin[twin == 0] = np.float32(-0.0)
+    P = np.concatenate([pts, twin])
+    P = np.concatenate([P, pts[rng.permutation(4_000)]])
+    gv, gf, res = _gpu(qh, *P.T)
+    assert res["status"] == 0
+    assert (gv, gf) == _oracle(*P.T)
