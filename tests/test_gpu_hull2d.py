@@ -230,3 +230,22 @@ def test_filter_scales_2d(qh, scale):
     for loop in ("persistent", "host"):
         got = qh.hull2d(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), loop=loop)
         assert got.cpu().numpy().tolist() == want, loop
+
+
+def test_unaligned_inputs_take_the_plain_load_path(qh):
+    # bases that are not 16-byte aligned (a view one float in, an interleaved
+    # view one point in): the first pass reads them without bulk copies
+    x, y = w.uniform_disk(300_001, 68)
+    X = torch.from_numpy(np.concatenate([[0.0], x]).astype(np.float32)).cuda()[1:]
+    Y = torch.from_numpy(np.concatenate([[0.0], y]).astype(np.float32)).cuda()[1:]
+    assert X.data_ptr() % 16 != 0
+    want = oracle.hull2d(x, y).tolist()
+    assert qh.hull2d(X, Y).cpu().numpy().tolist() == want
+    P = torch.from_numpy(np.stack([np.concatenate([[0.0], x]), np.concatenate([[0.0], y])],
+                                  axis=1).astype(np.float32)).cuda()[1:]
+    assert P.data_ptr() % 16 != 0
+    assert qh.hull2d(P).cpu().numpy().tolist() == want
+    got = qh.hull2d_multi([(X, Y), P, (X[:1000], Y[:1000])])
+    assert got[0].cpu().numpy().tolist() == want
+    assert got[1].cpu().numpy().tolist() == want
+    assert got[2].cpu().numpy().tolist() == oracle.hull2d(x[:1000], y[:1000]).tolist()
