@@ -1892,6 +1892,12 @@ __device__ void assign3d(const Params3 &A, int par, SmemAll3 &sm, SmemSlots &ss,
                                 bool pos = dd[j] > ee[j];
                                 if (!pos) {
                                     const Fac3 &C = A.fac[cn.x + c0 + j];
+                                    // FIRST: the first polytope's vertices are
+                                    // input points, each on its facets' planes
+                                    // (sign 0 with no exact expansion: its
+                                    // FP64 stage has no error bound to pass)
+                                    if (FIRST && (idx == C.v[0] || idx == C.v[1] || idx == C.v[2]))
+                                        continue;
                                     pos = orient3d_sign<MODE>(dd[j], ee[j], C.p, C.p + 3, C.p + 6, p,
                                                               fallbacks) > 0;
                                 }

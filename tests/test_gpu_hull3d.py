@@ -211,3 +211,56 @@ def test_every_point_twice_and_signed_zeros(qh):
     for pred in ("f32", "f64"):
         v, f, _ = _gpu(qh, P[:, 0], P[:, 1], P[:, 2], pred=pred)
         assert (v, f) == (want[0], want[1]), pred
+
+
+@pytest.mark.parametrize("offset", [0.0, 1000.0])
+def test_first_polytope_facet_boundary(qh, offset):
+    # The single-cloud first assignment sends each point to the first facet
+    # of the first polytope (the extreme points of the axes and diagonals)
+    # that it is strictly above.  One hull vertex just outside each facet
+    # (1e-5 of its distance from the facet vertices' mean beyond the facet),
+    # interior points filling the ball of the nearest facet's distance up to
+    # its edge, and the polytope's own vertices among them: every point's
+    # first facet, or none, must be found exactly.
+    rng = np.random.default_rng(70)
+    dirs = [[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]]
+    dirs += [[sx, sy, sz] for sz in (1, -1) for sy in (1, -1) for sx in (1, -1)]
+    E = np.array(dirs, np.float64)
+    E /= np.linalg.norm(E, axis=1, keepdims=True)
+    E += rng.normal(scale=2e-3, size=E.shape)  # general position: triangular facets
+    E /= np.linalg.norm(E, axis=1, keepdims=True)
+    E = (E + offset).astype(np.float32)
+    _, faces = oracle.hull3d(E[:, 0], E[:, 1], E[:, 2])
+    assert all(len(f) == 3 for f in faces) and len(faces) == 24
+    E64 = E.astype(np.float64)
+    c = np.float32(np.mean([E64[list(f)] for f in faces], axis=(0, 1))).astype(np.float64)
+    dist, nrm = [], []
+    for f in faces:
+        a, b, d = E64[list(f)]
+        n = np.cross(b - a, d - a)
+        n /= np.linalg.norm(n)
+        if np.dot(c - a, n) > 0:
+            n = -n
+        dist.append(np.dot(a - c, n))
+        nrm.append(n)
+    r = min(dist)
+    assert r > 0.5
+    ulp = float(np.spacing(np.float32(abs(offset) + 1.0)))
+    Q = np.array([c + n * (dd + max(1e-5 * dd, 4 * ulp)) for n, dd in zip(nrm, dist)],
+                 np.float32)
+    # interior: a uniform ball to 0.98 r, and a shell around the test's
+    # radius (inside the polytope: every point strictly below every facet)
+    u = np.stack(w.uniform_ball(150_000, 71), axis=1).astype(np.float64)
+    inner = c + 0.98 * r * u
+    s = rng.normal(size=(30_000, 3))
+    s /= np.linalg.norm(s, axis=1, keepdims=True)
+    shell = c + s * r * (1.0 - rng.uniform(0.0, 2e-5, (30_000, 1)))
+    filler = np.concatenate([inner, shell]).astype(np.float32)
+    P = np.concatenate([filler[:70_000], E, filler[70_000:100_000], Q, filler[100_000:]])
+    want = _oracle(P[:, 0], P[:, 1], P[:, 2])
+    q0 = 70_000 + len(E) + 30_000
+    assert set(range(q0, q0 + len(Q))) <= set(want[0])
+    for pred in ("f32", "f64"):
+        v, f, res = _gpu(qh, P[:, 0], P[:, 1], P[:, 2], pred=pred)
+        assert res["status"] == 0
+        assert (v, f) == (want[0], want[1]), pred
