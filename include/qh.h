@@ -55,7 +55,8 @@ typedef enum qh_status {
     QH_ERR_NONFINITE = 2,     /* an input coordinate is NaN or +-Inf */
     QH_ERR_DEGENERATE = 3,    /* 3D input that does not span 3D */
     QH_ERR_NOMEM = 4,         /* workspace smaller than qh_workspace_bytes_*() */
-    QH_ERR_CAPACITY = 5,      /* an internal table overflowed (should not happen) */
+    QH_ERR_CAPACITY = 5,      /* a table overflowed: 3D facets beyond qh_opts.max_facets, or an
+                                 internal bound (which should not happen) */
     QH_ERR_TIMEOUT = 6,       /* a bounded device wait gave up (grid barrier) */
     QH_ERR_NO_CONVERGENCE = 7,/* iteration cap reached */
     QH_ERR_CUDA = 8,          /* a CUDA runtime call failed */
@@ -91,6 +92,16 @@ typedef struct qh_opts {
                              one warp each during the setup (the small-cloud route), the rest
                              by the segmented iterations; 0 = every cloud through the
                              iterations (default); at most QH_SMALL_CLOUD_MAX */
+    int64_t max_facets;   /* 3D: facets the workspace holds, counting every facet created in
+                             the run (deleted ones too); 0 = the worst-case bound
+                             6 n + 4 ncloud + 64.  A smaller capacity shrinks the workspace
+                             (about 350 B a facet, and for one cloud its segment entries,
+                             about 430 B each, are capped by the facets as well); a run that
+                             needs more facets stops with QH_ERR_CAPACITY and the workspace
+                             stays reusable.  Values below 4 ncloud + 256 (the first
+                             polytope, the clouds' tetrahedra) are raised to it, values
+                             above the bound lowered to it.  qh_workspace_bytes_3d* and the
+                             hull call must see the same value. */
 } qh_opts;
 
 #define QH_SMALL_CLOUD_MAX 4096
@@ -206,7 +217,7 @@ qh_status qh_hull2d_multi(int32_t k, const float *const *h_dx, const float *cons
 /* ---------------------------------------------------------------------- */
 
 /* Bytes of device workspace qh_hull3d needs for n points
- * (n <= QH_MAX_POINTS_3D). */
+ * (n <= QH_MAX_POINTS_3D) and opts->max_facets (null opts: the worst case). */
 #define QH_MAX_POINTS_3D ((int64_t)44000000)
 size_t qh_workspace_bytes_3d(int64_t n, const qh_opts *opts);
 

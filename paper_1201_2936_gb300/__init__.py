@@ -40,7 +40,8 @@ def version() -> str:
 
 def make_opts(pred: str = "f32", loop: str = "persistent", blocks_per_sm: int = 0,
               max_iters: int = 0, wait_ns: int = 0, block: int = 0, items: int = 0,
-              max_ctas: int = 0, test_hold: int = 0, small_cloud: int = 0) -> QhOpts:
+              max_ctas: int = 0, test_hold: int = 0, small_cloud: int = 0,
+              max_facets: int = 0) -> QhOpts:
     o = QhOpts()
     _native.lib().qh_default_opts(ctypes.byref(o))
     o.pred_mode = PRED[pred]
@@ -53,6 +54,7 @@ def make_opts(pred: str = "f32", loop: str = "persistent", blocks_per_sm: int = 
     o.max_ctas = max_ctas
     o.test_hold = test_hold
     o.small_cloud = small_cloud
+    o.max_facets = max_facets
     return o
 
 

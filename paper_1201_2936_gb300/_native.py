@@ -18,7 +18,8 @@ class QhOpts(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("max_iters", ctypes.c_int64), ("wait_ns", ctypes.c_int64),
                 ("items", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
-                ("test_hold", ctypes.c_int32), ("small_cloud", ctypes.c_int32)]
+                ("test_hold", ctypes.c_int32), ("small_cloud", ctypes.c_int32),
+                ("max_facets", ctypes.c_int64)]
 
 
 class QhDebugRecord(ctypes.Structure):

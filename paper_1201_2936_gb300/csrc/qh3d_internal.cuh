@@ -258,7 +258,7 @@ struct Layout3 {
     int fcap, ecap, hist_blocks, ncloud;
 };
 
-Layout3 layout3d(int64_t n, int ncloud = 1);
+Layout3 layout3d(int64_t n, int ncloud, bool single, int64_t max_facets);
 
 // Device-sized scan and radix sort (qh3d_out.cu), shared with the 4D output
 // stage.  Counts are read on the device (*m_ptr, or m_fix when m_ptr is

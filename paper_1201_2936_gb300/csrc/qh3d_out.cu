@@ -34,7 +34,13 @@ static size_t au(size_t v) { return (v + 255) & ~(size_t)255; }
 // CTAs of the grid-stride output kernels: four per SM of the current device
 static long long out_grid() { return 4ll * sm_count(); }
 
-Layout3 layout3d(int64_t n, int ncloud)
+// Facet capacity: the worst case 6 n + 4 ncloud + 64 (facets are never
+// reused within a run), or the caller's max_facets clamped to
+// [4 ncloud + 256, worst case].  Segment entries: one cloud needs at most
+// one per facet that can hold points, plus the pseudo facet; several clouds
+// keep one per point (the small-cloud route uses the visible and horizon
+// pools as per-point scratch).
+Layout3 layout3d(int64_t n, int ncloud, bool single, int64_t max_facets)
 {
     Layout3 L = {};
     size_t o = 0;
@@ -46,8 +52,11 @@ Layout3 layout3d(int64_t n, int ncloud)
     const size_t np = (size_t)(n > 0 ? n : 1);
     const size_t nc = (size_t)(ncloud > 0 ? ncloud : 1);
     L.ncloud = (int)nc;
-    L.fcap = (int)(6 * np + 4 * nc + 64);
-    L.ecap = (int)(np + nc + 64);
+    const size_t worst = 6 * np + 4 * nc + 64;
+    size_t fcap = worst;
+    if (max_facets > 0) fcap = std::min(worst, std::max((size_t)max_facets, 4 * nc + 256));
+    L.fcap = (int)fcap;
+    L.ecap = (int)((single ? std::min(np, fcap) : np) + nc + 64);
     const size_t fc = (size_t)L.fcap + 1;
     L.hdr = take(sizeof(Hdr3));
     L.res = take(sizeof(qh_result));
@@ -747,18 +756,18 @@ using namespace qh::d3;
 // facet ids must fit the 28-bit claim permutation: 6n + 4 ncloud + 64 < 2^28
 constexpr int64_t kMax3d = 44000000;
 
+static int64_t facet_hint(const qh_opts *opts) { return opts ? opts->max_facets : 0; }
+
 extern "C" size_t qh_workspace_bytes_3d(int64_t n, const qh_opts *opts)
 {
-    (void)opts;
-    if (n < 0 || n > kMax3d) return 0;
-    return layout3d(n, 1).total;
+    if (n < 0 || n > kMax3d || facet_hint(opts) < 0) return 0;
+    return layout3d(n, 1, true, facet_hint(opts)).total;
 }
 
 extern "C" size_t qh_workspace_bytes_3d_batched(int64_t n, int32_t ncloud, const qh_opts *opts)
 {
-    (void)opts;
-    if (n < 0 || ncloud < 1 || n + ncloud > kMax3d) return 0;
-    return layout3d(n, ncloud).total;
+    if (n < 0 || ncloud < 1 || n + ncloud > kMax3d || facet_hint(opts) < 0) return 0;
+    return layout3d(n, ncloud, false, facet_hint(opts)).total;
 }
 
 extern "C" qh_status qh_debug_timeline_3d(const void *d_ws, int64_t n, int64_t *h_rows,
@@ -766,7 +775,7 @@ extern "C" qh_status qh_debug_timeline_3d(const void *d_ws, int64_t n, int64_t *
 {
     if (!d_ws || !h_rows || !h_nrows || max_rows < 0 || n < 0 || n > kMax3d)
         return QH_ERR_INVALID_ARG;
-    const Layout3 L = layout3d(n, 1);
+    const Layout3 L = layout3d(n, 1, true, 0);  // the header's offset does not depend on it
     Hdr3 hh;
     if (cudaMemcpyAsync(&hh, (const char *)d_ws + L.hdr, sizeof(Hdr3), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
@@ -797,7 +806,7 @@ extern "C" qh_status qh_debug_phases_3d(const void *d_ws, int64_t *h_ns, cudaStr
 static bool opts_ok(const qh_opts &o)
 {
     return (o.pred_mode == QH_PRED_F32 || o.pred_mode == QH_PRED_F64) && o.small_cloud >= 0 &&
-           o.small_cloud <= QH_SMALL_CLOUD_MAX;
+           o.small_cloud <= QH_SMALL_CLOUD_MAX && o.max_facets >= 0;
 }
 
 extern "C" qh_status qh_hull3d(const float *d_x, const float *d_y, const float *d_z, int64_t n,
@@ -816,7 +825,7 @@ extern "C" qh_status qh_hull3d(const float *d_x, const float *d_y, const float *
         return QH_ERR_INVALID_ARG;
     if (!opts_ok(o)) return QH_ERR_INVALID_ARG;
     if (o.loop_mode != QH_LOOP_PERSISTENT) return QH_ERR_NOT_SUPPORTED;
-    const Layout3 L = layout3d(n, 1);
+    const Layout3 L = layout3d(n, 1, true, o.max_facets);
     if (ws_bytes < L.total || ((uintptr_t)d_ws & 255)) return QH_ERR_NOMEM;
     qh_result r = {};
     if (n == 0) {
@@ -856,7 +865,7 @@ extern "C" qh_status qh_hull3d_batched(const float *d_x, const float *d_y, const
         return QH_ERR_INVALID_ARG;
     if (!opts_ok(o)) return QH_ERR_INVALID_ARG;
     if (o.loop_mode != QH_LOOP_PERSISTENT) return QH_ERR_NOT_SUPPORTED;
-    const Layout3 L = layout3d(n, ncloud);
+    const Layout3 L = layout3d(n, ncloud, false, o.max_facets);
     if (ws_bytes < L.total || ((uintptr_t)d_ws & 255)) return QH_ERR_NOMEM;
     char *ws = (char *)d_ws;
     Params3 A = make_params3(d_x, d_y, d_z, n, stride, ws, L, o);

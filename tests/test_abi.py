@@ -50,6 +50,36 @@ def test_status_strings_and_sizes(lib):
     assert ctypes.sizeof(_native.QhResult) == 96
 
 
+def test_3d_facet_capacity_sizes_the_workspace(lib):
+    # qh_opts.max_facets: 0 or anything at or above 6 n + 4 ncloud + 64 is the
+    # worst case; below it the workspace shrinks with the facets (and, for one
+    # cloud, the segment entries), never below 4 ncloud + 256 facets; negative
+    # is refused.  Several clouds keep one entry per point.
+    from paper_1201_2936_gb300 import _native
+    L = _native.lib()
+    assert ctypes.sizeof(_native.QhOpts) == 56
+    assert _native.QhOpts.max_facets.offset == 48
+
+    def opts(f):
+        o = _native.QhOpts()
+        L.qh_default_opts(ctypes.byref(o))
+        o.max_facets = f
+        return ctypes.byref(o)
+
+    n = 200_000
+    full = L.qh_workspace_bytes_3d(n, None)
+    assert full > 0
+    for f in (0, 6 * n + 68, 10 ** 12):
+        assert L.qh_workspace_bytes_3d(n, opts(f)) == full
+    sizes = [L.qh_workspace_bytes_3d(n, opts(f)) for f in (1, 260, 261, 50_000, 150_000)]
+    assert sizes[0] == sizes[1] < sizes[2] < sizes[3] < sizes[4] < full // 3
+    assert L.qh_workspace_bytes_3d(n, opts(-1)) == 0
+    one = L.qh_workspace_bytes_3d_batched(n, 1, opts(150_000))
+    assert sizes[4] < one < L.qh_workspace_bytes_3d_batched(n, 1, None)
+    assert L.qh_workspace_bytes_3d_batched(n, 64, opts(1)) == \
+        L.qh_workspace_bytes_3d_batched(n, 64, opts(4 * 64 + 256))
+
+
 def test_host_side_argument_errors(lib):
     from paper_1201_2936_gb300 import _native
     L = _native.lib()

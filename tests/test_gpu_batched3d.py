@@ -175,3 +175,18 @@ def test_many_small_clouds_tuned(qh):
     assert _split(b.outputs()) == want
     got0 = _split(qh.hull3d_batched(P, cloud_off=O, opts=qh.make_opts("f32", small_cloud=0)))
     assert got0 == want
+
+
+@pytest.mark.parametrize("small", [0, 256])
+def test_facet_capacity_below_worst_case(qh, small):
+    # qh_opts.max_facets below the worst case (6 n + 4 ncloud + 64): the
+    # facet arrays shrink, the clouds' segment entries and the small-cloud
+    # route's per-point scratch stay; every cloud still equals the oracle
+    x, y, z, off = w.batched_clouds_3d(256, 44, nmin=16, nmax=8192)
+    n, nc = len(x), len(off) - 1
+    want = _want(x, y, z, off)
+    P, O = _dev(x, y, z, off)
+    o = qh.make_opts("f32", small_cloud=small, max_facets=3 * n + 4 * nc + 256)
+    assert qh.workspace_bytes_3d_batched(n, nc, o) < qh.workspace_bytes_3d_batched(n, nc, None)
+    got = _split(qh.hull3d_batched(P, cloud_off=O, opts=o))
+    assert got == want

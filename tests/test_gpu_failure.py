@@ -1,7 +1,8 @@
-"""Failure detection on the GPU, without a fault: the iteration cap and the
-bounded grid-barrier wait are made to run out on purpose, the call reports
-QH_ERR_NO_CONVERGENCE or QH_ERR_TIMEOUT through the C ABI, the context stays
-usable, and the same workspace then gives the oracle's hull.
+"""Failure detection on the GPU, without a fault: the iteration cap, the
+bounded grid-barrier wait and the 3D facet capacity are made to run out on
+purpose, the call reports QH_ERR_NO_CONVERGENCE, QH_ERR_TIMEOUT or
+QH_ERR_CAPACITY through the C ABI, the context stays usable, and the same
+workspace then gives the oracle's hull.
 
 The wait is made to run out by the test hook qh_opts.test_hold: CTA 0 of the
 persistent kernel does not arrive at its first grid barrier, so that round
@@ -18,6 +19,7 @@ from paper_1201_2936_gb300 import workloads as w
 
 pytestmark = pytest.mark.gpu
 
+QH_ERR_CAPACITY = 5
 QH_ERR_TIMEOUT = 6
 QH_ERR_NO_CONVERGENCE = 7
 WAIT_NS = 20_000_000  # 20 ms: every CTA's wait on the held barrier ends after this
@@ -91,6 +93,30 @@ def test_3d_iteration_cap(qh):
     assert st == 0
     want_v, want_f = oracle.hull3d(x, y, z)
     assert v == want_v.tolist() and f == [t.tolist() for t in want_f]
+
+
+@pytest.mark.parametrize("pred", ["f32", "f64"])
+def test_3d_facet_capacity(qh, pred):
+    # qh_opts.max_facets: a capacity that holds every facet the run creates
+    # gives the oracle's hull in a quarter of the worst-case workspace; one
+    # that does not (raised to its floor of 260 facets) stops the run with
+    # QH_ERR_CAPACITY, and the same workspace then serves a full run
+    x, y, z = w.uniform_ball(200_000, 4105)
+    X, Y, Z = _cuda(x, y, z)
+    n = len(x)
+    fit = qh.make_opts(pred, max_facets=150_000)
+    assert qh.workspace_bytes_3d(n, fit) < qh.workspace_bytes_3d(n, qh.make_opts(pred)) // 3
+    want_v, want_f = oracle.hull3d(x, y, z)
+    want = (want_v.tolist(), [t.tolist() for t in want_f])
+    ws = qh.Workspace()
+    st, res, v, f = _hull3d(qh, X, Y, Z, ws, fit)
+    assert st == 0 and (v, f) == want
+    for _ in range(2):
+        st, res, _, _ = _hull3d(qh, X, Y, Z, ws, qh.make_opts(pred, max_facets=1))
+        assert st == QH_ERR_CAPACITY and res.status == QH_ERR_CAPACITY
+    torch.cuda.synchronize()
+    st, res, v, f = _hull3d(qh, X, Y, Z, ws, fit)
+    assert st == 0 and (v, f) == want
 
 
 def test_2d_grid_barrier_wait_runs_out(qh):
