@@ -1,7 +1,10 @@
-"""The ctypes mirrors of the C ABI's structs (qh_opts, qh_result,
-qh_debug_record) have the header's fields, in its order, at the offsets and
-total size a C compiler gives them: a field added to one side only would
-shift every later field of every call that passes the struct."""
+"""The Python binding against the C ABI's header, without a GPU: the ctypes
+mirrors of its structs (qh_opts, qh_result, qh_debug_record) have the
+header's fields, in its order, at the offsets and total size a C compiler
+gives them (a field added to one side only would shift every later field of
+every call that passes the struct), and every function's ctypes signature
+has the prototype's arity and, per argument and result, its ABI class
+(pointer, 32-bit, 64-bit integer, size_t)."""
 import ctypes
 import os
 import re
@@ -76,3 +79,51 @@ def test_offsets_and_sizes_match_the_c_compiler():
         assert got[(name, "size")] == ctypes.sizeof(mirror), name
         for f, _ in mirror._fields_:
             assert got[(name, f)] == getattr(mirror, f).offset, (name, f)
+
+
+def _prototypes():
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    src = "\n".join(ln for ln in src.splitlines() if not ln.lstrip().startswith("#"))
+    protos = {}
+    for ret, name, params in re.findall(r"([A-Za-z_][\w\s\*]*?)\b(qh_\w+)\s*\(([^()]*)\)\s*;",
+                                        src):
+        ps = [p.strip() for p in params.split(",")] if params.strip() not in ("", "void") else []
+        protos[name] = (" ".join(ret.split()), ps)
+    return protos
+
+
+def _kind(decl):
+    """ABI class of a C parameter or return type: pointer, int32, int64,
+    size, or void."""
+    d = " ".join(decl.replace("*", " * ").split())
+    if "*" in d or d.split()[0] == "cudaStream_t":
+        return "ptr"
+    base = [t for t in d.split() if t not in ("const",)][0]
+    return {"int32_t": "i32", "int": "i32", "qh_status": "i32", "int64_t": "i64",
+            "size_t": "size", "void": "void"}[base]
+
+
+def _ctype_kind(t):
+    if t is None:
+        return "void"
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(t, ctypes._Pointer):
+        return "ptr"
+    if t in (ctypes.c_int32, ctypes.c_int):
+        return "i32"
+    if t is ctypes.c_size_t:
+        return "size"
+    if t is ctypes.c_int64:
+        return "i64"
+    raise AssertionError(t)
+
+
+def test_binding_signatures_match_the_prototypes():
+    from paper_1201_2936_gb300 import _native
+    protos = _prototypes()
+    assert set(protos) == set(_native.exported_names())
+    for name, res, args in _native.SIGNATURES:
+        ret, params = protos[name]
+        assert _ctype_kind(res) == _kind(ret), name
+        assert len(args) == len(params), (name, len(args), params)
+        for i, (a, p) in enumerate(zip(args, params)):
+            assert _ctype_kind(a) == _kind(p), (name, i, p)
