@@ -8,8 +8,12 @@ on every rank).  Only the shard hulls travel: h_g points per rank, small
 next to n / G except for points on a circle or sphere.
 
 `hull_fn` computes a hull on one rank's data and returns local indices; by
-default it is the library's GPU hull.  The collective is torch.distributed
-(NCCL between GPUs; the tests run it with gloo on CPU ranks).
+default it is the library's GPU hull.  In 3D a shard may not span space
+(fewer than four points, or all of them coplanar) although the whole cloud
+does: hull_fn then returns None and every point of that shard is a
+candidate, which keeps the union of the candidates' hull equal to the
+cloud's.  The collective is torch.distributed (NCCL between GPUs; the tests
+run it with gloo on CPU ranks).
 """
 from __future__ import annotations
 
@@ -30,12 +34,25 @@ def shard_range(n: int, rank: int, world: int) -> Tuple[int, int]:
     return lo, lo + base + (1 if rank < extra else 0)
 
 
+QH_ERR_DEGENERATE = 3
+
+
 def _gpu_hull(coords: Sequence[torch.Tensor]):
-    from . import hull2d, hull3d
+    from . import QHError, hull2d, hull3d
     if len(coords) == 2:
         return hull2d(coords[0], coords[1]).long()
-    v, _, _ = hull3d(coords[0], coords[1], coords[2])
+    try:
+        v, _, _ = hull3d(coords[0], coords[1], coords[2])
+    except QHError as e:
+        if e.status == QH_ERR_DEGENERATE:
+            return None
+        raise
     return v.long()
+
+
+def _degenerate():
+    from . import QHError
+    return QHError(QH_ERR_DEGENERATE, "sharded hull: the points do not span 3D")
 
 
 def _candidates(coords: Sequence[torch.Tensor], group, local_fn):
@@ -48,6 +65,8 @@ def _candidates(coords: Sequence[torch.Tensor], group, local_fn):
     lo, hi = shard_range(n, rank, world)
     local = local_fn([c[lo:hi] for c in coords]) if hi > lo else \
         torch.zeros(0, dtype=torch.long, device=coords[0].device)
+    if local is None:  # a shard that does not span 3D: all its points
+        local = torch.arange(hi - lo, dtype=torch.long, device=coords[0].device)
     gidx = local.to(torch.long) + lo
     # exchange: sizes first, then the padded index lists
     dev = coords[0].device
@@ -77,12 +96,19 @@ def sharded_hull(coords: Sequence[torch.Tensor], group=None,
     hull_fn = hull_fn or _gpu_hull
     cand = _candidates(coords, group, hull_fn)
     sub = hull_fn([c[cand] for c in coords])
+    if sub is None:
+        raise _degenerate()
     return cand[sub.to(torch.long)], cand
 
 
 def _gpu_hull3d_faces(coords):
-    from . import hull3d
-    v, off, idx = hull3d(coords[0], coords[1], coords[2])
+    from . import QHError, hull3d
+    try:
+        v, off, idx = hull3d(coords[0], coords[1], coords[2])
+    except QHError as e:
+        if e.status == QH_ERR_DEGENERATE:
+            return None
+        raise
     return v.long(), off.long(), idx.long()
 
 
@@ -91,25 +117,39 @@ def sharded_hull3d(coords: Sequence[torch.Tensor], group=None,
     """3D hull of the whole cloud over the ranks, with its faces: returns
     (vertices, face_offsets, face_indices) in global indices, equal to the
     one-rank hull's canonical output.  hull_fn(coords) -> (vertices,
-    face_offsets, face_indices) of a cloud (default: the library's GPU hull).
+    face_offsets, face_indices) of a cloud, or None when its points do not
+    span 3D (default: the library's GPU hull).  A whole cloud that does not
+    span 3D raises QHError(QH_ERR_DEGENERATE).
     The candidates are in increasing global index, so mapping the final
     hull's candidate-local indices to global ones keeps the canonical order
     (sorted vertices, faces from their smallest index, faces in
     lexicographic order)."""
     hull_fn = hull_fn or _gpu_hull3d_faces
-    cand = _candidates(coords, group, lambda c: hull_fn(c)[0])
-    v, off, idx = hull_fn([c[cand] for c in coords])
+
+    def vertices(c):
+        r = hull_fn(c)
+        return None if r is None else r[0]
+
+    cand = _candidates(coords, group, vertices)
+    r = hull_fn([c[cand] for c in coords])
+    if r is None:
+        raise _degenerate()
+    v, off, idx = r
     return cand[v.to(torch.long)], off.to(torch.long), cand[idx.to(torch.long)]
 
 
 def sharded_hull3d_numpy(coords: Sequence[np.ndarray], hull_fn: Callable, group=None):
     """sharded_hull3d with numpy coordinates; hull_fn(coords) -> (vertices,
-    list of faces) as numpy arrays (tests on CPU ranks).  Returns (vertices,
-    list of faces) in global indices."""
+    list of faces) as numpy arrays, or None when the points do not span 3D
+    (tests on CPU ranks).  Returns (vertices, list of faces) in global
+    indices."""
     tc = [torch.from_numpy(np.ascontiguousarray(c)) for c in coords]
 
     def fn(parts):
-        v, faces = hull_fn([p.numpy() for p in parts])
+        r = hull_fn([p.numpy() for p in parts])
+        if r is None:
+            return None
+        v, faces = r
         off = np.zeros(len(faces) + 1, np.int64)
         off[1:] = np.cumsum([len(f) for f in faces])
         idx = np.concatenate([np.asarray(f, np.int64) for f in faces]) if faces else \
@@ -128,7 +168,8 @@ def sharded_hull_numpy(coords: Sequence[np.ndarray], hull_fn: Callable, group=No
     tc = [torch.from_numpy(np.ascontiguousarray(c)) for c in coords]
 
     def fn(parts):
-        return torch.from_numpy(np.asarray(hull_fn([p.numpy() for p in parts]), np.int64))
+        r = hull_fn([p.numpy() for p in parts])
+        return None if r is None else torch.from_numpy(np.asarray(r, np.int64))
 
     final, cand = sharded_hull(tc, group=group, hull_fn=fn)
     return final.numpy(), cand.numpy()

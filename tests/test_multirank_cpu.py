@@ -1,13 +1,15 @@
 """The multi-rank hull (paper_1201_2936_gb300.shard) on CPU ranks with gloo,
-world sizes 2 and 3: the hull of the gathered shard hulls equals the oracle's
+world sizes 2 to 4: the hull of the gathered shard hulls equals the oracle's
 hull of the whole cloud (2D: the vertex list in order; 3D: the vertices and
-the canonical face list), including duplicates across shards and a shard
-with no points."""
+the canonical face list), including duplicates across shards, shards with
+no points and 3D shards that do not span space (fewer than four points, or
+coplanar), whose points are all candidates."""
 import os
 import socket
 
 import numpy as np
 import pytest
+import torch
 import torch.multiprocessing as mp
 
 import oracle
@@ -32,7 +34,35 @@ def _free_port():
     return p
 
 
-def _worker(rank, world, port, dim, q):
+def _oracle3d_or_none(c):
+    # the shard-hull protocol: None for points that do not span 3D
+    try:
+        return oracle.hull3d(c[0], c[1], c[2])
+    except oracle.OracleError as e:
+        if e.code == 3:
+            return None
+        raise
+
+
+def _cloud3d(case):
+    if case == "tiny":  # shards of 2 or 3 points: none spans 3D
+        r = np.random.default_rng(79)
+        return tuple(r.uniform(-1, 1, (3, 9)).astype(np.float32))
+    if case == "coplanar":  # the middle shard on one plane inside the ball
+        x, y, z = (c[:3000] for c in w.uniform_ball(3000, 80))
+        z = z.copy()
+        z[1000:2000] = np.float32(0.125)
+        return x, y, z
+    x, y, z = w.uniform_ball(6000, 78)
+    # a duplicated hull vertex in a later shard, and a cube corner set with
+    # coplanar (quadrilateral) faces
+    x = np.concatenate([x, x[:30], np.float32([2, 2, 2, 2])]).astype(np.float32)
+    y = np.concatenate([y, y[:30], np.float32([2, 2, -2, -2])]).astype(np.float32)
+    z = np.concatenate([z, z[:30], np.float32([2, -2, 2, -2])]).astype(np.float32)
+    return x, y, z
+
+
+def _worker(rank, world, port, dim, q, case="ball"):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -47,14 +77,8 @@ def _worker(rank, world, port, dim, q):
             final, _ = shard.sharded_hull_numpy([x, y], lambda c: oracle.hull2d(c[0], c[1]))
             want = oracle.hull2d(x, y)
         else:
-            x, y, z = w.uniform_ball(6000, 78)
-            # a duplicated hull vertex in a later shard, and a cube corner set
-            # with coplanar (quadrilateral) faces
-            x = np.concatenate([x, x[:30], np.float32([2, 2, 2, 2])]).astype(np.float32)
-            y = np.concatenate([y, y[:30], np.float32([2, 2, -2, -2])]).astype(np.float32)
-            z = np.concatenate([z, z[:30], np.float32([2, -2, 2, -2])]).astype(np.float32)
-            fv, ff = shard.sharded_hull3d_numpy(
-                [x, y, z], lambda c: oracle.hull3d(c[0], c[1], c[2]))
+            x, y, z = _cloud3d(case)
+            fv, ff = shard.sharded_hull3d_numpy([x, y, z], _oracle3d_or_none)
             wv, wf = oracle.hull3d(x, y, z)
             final = (fv.tolist(), [f.tolist() for f in ff])
             want = (wv.tolist(), [f.tolist() for f in wf])
@@ -65,12 +89,15 @@ def _worker(rank, world, port, dim, q):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world,dim", [(2, 2), (3, 2), (2, 3), (3, 3)])
-def test_sharded_hull_equals_whole_hull(world, dim):
+@pytest.mark.parametrize("world,dim,case", [(2, 2, "ball"), (3, 2, "ball"), (2, 3, "ball"),
+                                            (3, 3, "ball"), (3, 3, "tiny"), (4, 3, "tiny"),
+                                            (3, 3, "coplanar")])
+def test_sharded_hull_equals_whole_hull(world, dim, case):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, world, port, dim, q)) for r in range(world)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, dim, q, case))
+             for r in range(world)]
     for p in procs:
         p.start()
     res = [q.get(timeout=300) for _ in range(world)]
@@ -79,3 +106,30 @@ def test_sharded_hull_equals_whole_hull(world, dim):
         assert p.exitcode == 0
     for rank, final, want in res:
         assert final == want, rank
+
+
+def test_one_rank_degenerate_cloud_raises_and_gpu_hull_maps_the_status(monkeypatch):
+    from paper_1201_2936_gb300 import build
+    build.build()
+    oracle.build()
+    import paper_1201_2936_gb300 as qh
+    # the whole cloud on one plane: the final hull is degenerate too
+    x, y, z = (c[:500] for c in w.uniform_ball(500, 81))
+    z = np.zeros_like(z)
+    with pytest.raises(qh.QHError) as e:
+        shard.sharded_hull3d_numpy([x, y, z], _oracle3d_or_none)
+    assert e.value.status == shard.QH_ERR_DEGENERATE
+    # the library's hull functions: QH_ERR_DEGENERATE -> None, others raise
+    pts = [torch.zeros(4), torch.zeros(4), torch.zeros(4)]
+
+    def raising(status):
+        def f(*a, **k):
+            raise qh.QHError(status, "qh_hull3d")
+        return f
+
+    monkeypatch.setattr(qh, "hull3d", raising(3))
+    assert shard._gpu_hull(pts) is None and shard._gpu_hull3d_faces(pts) is None
+    monkeypatch.setattr(qh, "hull3d", raising(8))
+    for fn in (shard._gpu_hull, shard._gpu_hull3d_faces):
+        with pytest.raises(qh.QHError):
+            fn(pts)
